@@ -1,0 +1,491 @@
+"""Pins of the block-forest oracle (oracle.forest, oracle.solver):
+
+* with no refinement the forest equals the dense uniform-grid solver;
+* mesh invariants after seeded random refine/coarsen sequences, checked by
+  brute force (tiling, 2:1 balance, ID/gap partition, sibling contiguity,
+  ID-set membership, cell classes by rasterisation);
+* a worked example of the gap-stack allocation order;
+* linear interpolation exact on multilinear data, equilibrium preserved,
+  averaging of constants, average(interpolate(affine)) = affine;
+* a static two-level Couette flow stays linear (pins the rescaling factor);
+* Taylor-Green decay on a static two-level periodic forest;
+* the vorticity criterion on a linear shear (closed form);
+* the MLUPS update count against a brute-force leaf count.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.forest import (BLOCK_EDGE, GHOST, INACTIVE, INTERFACE, INTERIOR, NONE,
+                           REFINED, REFINED_ANY, UNREFINED, Forest, local_coords)
+from oracle.lattice import CS2, equilibrium, moments
+from oracle.solver import ForestLBM
+from oracle.uniform import UniformLBM
+
+
+# ------------------------------------------------------------------ helpers
+def global_index(lbm, b):
+    """Global cell indices (tuple of arrays) of the cells of root block b."""
+    pos = (lbm.mesh.X[b][None, :] + lbm.lc).astype(np.int64)
+    return tuple(pos[:, a] for a in range(lbm.dim))
+
+
+def load_uniform(lbm, field):
+    for b in range(lbm.mesh.n_root):
+        lbm.f[b] = field[global_index(lbm, b)]
+
+
+def to_uniform(lbm, shape, q):
+    out = np.zeros(tuple(shape) + (q,))
+    for b in range(lbm.mesh.n_root):
+        out[global_index(lbm, b)] = lbm.f[b]
+    return out
+
+
+def random_state(vs, shape, seed):
+    n = int(np.prod(shape))
+    rho, u = W.random_macro(seed, n, vs.dim)
+    f = equilibrium(vs, rho, u) + W.random_noise(seed + 1, (n, vs.q), 1e-3)
+    return f.reshape(tuple(shape) + (vs.q,))
+
+
+# ------------------------------------------------- forest == uniform grid
+CASES = [
+    ("cavity2d", lambda: W.cavity(dim=2, q=9, n=16, ny=12, max_levels=1)),
+    ("cavity3d_q19", lambda: W.cavity(dim=3, q=19, n=8, ny=12, nz=8, max_levels=1)),
+    ("periodic3d_q27", lambda: W.periodic_box(dim=3, q=27, n=8, ny=4, nz=12)),
+    ("cylinder_small", lambda: W.channel_cylinder(q=19, nx=24, ny=16, nz=4, side=4,
+                                                   cx=8, cy=8, max_levels=1)),
+]
+
+
+@pytest.mark.parametrize("name,mk", CASES, ids=[c[0] for c in CASES])
+def test_forest_equals_uniform_single_level(name, mk):
+    cfg = mk()
+    lbm = ForestLBM(cfg)
+    shape = [cfg["nx"], cfg["ny"], cfg["nz"]][:cfg["dim"]]
+    uni = UniformLBM(cfg["dim"], cfg["q"], shape, lbm.tau[0], cfg["faces"])
+    if cfg["solid"] is not None:
+        uni.solid = to_uniform(lbm, shape, cfg["q"])[..., 0] * 0 != 0
+        for b in range(lbm.mesh.n_root):
+            uni.solid[global_index(lbm, b)] = lbm.solid[b]
+    f0 = random_state(uni.vs, shape, 11)
+    if cfg["solid"] is not None:
+        f0[uni.solid] = lbm.rest
+    uni.f = f0.copy()
+    load_uniform(lbm, f0)
+    for _ in range(6):
+        uni.step()
+        lbm.step()
+    got = to_uniform(lbm, shape, cfg["q"])
+    assert np.max(np.abs(got - uni.f)) <= 1e-15
+
+
+# ------------------------------------------------------ mesh invariants
+def brute_force_check(mesh: Forest):
+    d, nc = mesh.dim, mesh.nc
+    act = mesh.active_ids()
+    aset = set(act)
+    # ID sets hold exactly the active blocks of each level, no duplicates
+    assert len(act) == len(aset)
+    for L, ids in enumerate(mesh.id_sets):
+        assert all(mesh.level[b] == L for b in ids)
+    # gap set and active IDs partition the capacity
+    gaps = set(mesh.gap)
+    assert len(gaps) == len(mesh.gap)
+    assert gaps.isdisjoint(aset)
+    assert gaps | aset == set(range(mesh.cap))
+    assert all(mesh.status[b] == INACTIVE for b in gaps)
+    # children are contiguous and point back to their parent
+    for b in act:
+        if mesh.status[b] in REFINED_ANY:
+            c0 = mesh.child0[b]
+            for c in range(nc):
+                ch = c0 + c
+                assert ch in aset and mesh.parent[ch] == b
+                off = np.array([(c >> a) & 1 for a in range(d)])
+                w = mesh.width(mesh.level[ch])
+                assert np.array_equal(mesh.X[ch], mesh.X[b] + off * w)
+        else:
+            assert mesh.status[b] == UNREFINED and mesh.child0[b] == NONE
+    # leaves tile the domain exactly once (rasterised on the finest grid)
+    fine = 2 ** (mesh.lmax - 1)
+    cover = np.zeros(tuple(int(e) * fine for e in mesh.extent), np.int64)
+    level_of = np.full(cover.shape, -1)
+    for b in act:
+        if mesh.status[b] != UNREFINED:
+            continue
+        lo = (mesh.X[b] * fine).astype(np.int64)
+        n = int(mesh.width(mesh.level[b]) * fine)
+        sl = tuple(slice(lo[a], lo[a] + n) for a in range(d))
+        cover[sl] += 1
+        level_of[sl] = mesh.level[b]
+    assert np.all(cover == 1)
+    # 2:1 balance over the full neighbourhood (incl. periodic wrap)
+    for a in range(d):
+        for shift in (-1, 1):
+            other = np.roll(level_of, shift, axis=a)
+            diff = np.abs(level_of - other)
+            if mesh.faces[2 * a][0] != "periodic":
+                idx = [slice(None)] * d
+                idx[a] = 0 if shift == 1 else -1
+                diff[tuple(idx)] = 0
+            assert diff.max() <= 1
+    # diagonal balance: every leaf's 3^d neighbourhood of finest cells
+    for sh in itertools.product((-1, 0, 1), repeat=d):
+        other = level_of
+        valid = np.ones(cover.shape, bool)
+        for a, s in enumerate(sh):
+            if s == 0:
+                continue
+            other = np.roll(other, s, axis=a)
+            if mesh.faces[2 * a][0] != "periodic":
+                idx = [slice(None)] * d
+                idx[a] = 0 if s == 1 else -1
+                valid[tuple(idx)] = False
+        assert np.abs(level_of - other)[valid].max() <= 1
+
+
+def brute_force_classes(mesh: Forest, b):
+    """Cell classes of block b from a rasterisation of same-level coverage."""
+    d = mesh.dim
+    L = mesh.level[b]
+    n_l = np.array([int(e) * 2 ** L for e in mesh.extent])
+    covered = np.zeros(n_l, bool)
+    for o in mesh.id_sets[L]:
+        lo = (mesh.X[o] * 2 ** L).astype(np.int64)
+        covered[tuple(slice(lo[a], lo[a] + 4) for a in range(d))] = True
+    pos = (mesh.X[b] * 2 ** L).astype(np.int64)[None, :] + local_coords(d)
+    best = np.full(len(pos), 99)
+    for off in itertools.product(range(-4, 5), repeat=d):
+        y = pos + np.array(off)
+        ok = np.ones(len(pos), bool)
+        for a in range(d):
+            out = (y[:, a] < 0) | (y[:, a] >= n_l[a])
+            if mesh.faces[2 * a][0] == "periodic":
+                y[:, a] %= n_l[a]
+            else:
+                ok &= ~out
+                y[:, a] = np.clip(y[:, a], 0, n_l[a] - 1)
+        unc = ok & ~covered[tuple(y[:, a] for a in range(d))]
+        best = np.where(unc, np.minimum(best, max(abs(o) for o in off)), best)
+    return np.where(best <= 2, GHOST, np.where(best <= 4, INTERFACE, INTERIOR))
+
+
+def geometric_nbr(mesh: Forest, b):
+    """Neighbour IDs of block b by scanning every active block's box."""
+    d = mesh.dim
+    w = mesh.width(mesh.level[b])
+    out = []
+    for k in range(mesh.nk):
+        pos = mesh.X[b] + mesh.dirs[k] * w
+        wall = False
+        for a in range(d):
+            if pos[a] < 0 or pos[a] >= mesh.extent[a]:
+                if mesh.faces[2 * a][0] == "periodic":
+                    pos[a] %= mesh.extent[a]
+                else:
+                    wall = True
+        if wall:
+            out.append("wall")
+            continue
+        hit = [o for o in mesh.active_ids() if mesh.level[o] == mesh.level[b]
+               and np.array_equal(mesh.X[o], pos)]
+        assert len(hit) <= 1
+        out.append(hit[0] if hit else NONE)
+    return out
+
+
+MESHES = [
+    ("2d_cavity_3x3", lambda: W.cavity(dim=2, n=12, max_levels=4, max_blocks=9 * 40)),
+    ("2d_periodic_2x3", lambda: W.periodic_box(dim=2, n=8, ny=12, max_levels=3, max_blocks=200)),
+    ("3d_cavity_2x2x2", lambda: W.cavity(dim=3, n=8, max_levels=3, max_blocks=8 * 30)),
+]
+
+
+@pytest.mark.parametrize("name,mk", MESHES, ids=[m[0] for m in MESHES])
+def test_random_adaptation_invariants(name, mk):
+    cfg = mk()
+    mesh = Forest(cfg)
+    for it in range(12):
+        marks = W.random_marks(100 + it, mesh.cap, 0.35, 0.35)
+        res = mesh.adapt(marks)
+        brute_force_check(mesh)
+        for b in mesh.active_ids()[:: max(1, len(mesh.active_ids()) // 12)]:
+            geo = geometric_nbr(mesh, b)
+            for k, g in enumerate(geo):
+                if g == "wall":
+                    assert mesh.nbr[b, k] <= -2
+                else:
+                    assert mesh.nbr[b, k] == g
+            assert np.array_equal(mesh.cell_classes(b), brute_force_classes(mesh, b))
+
+
+def test_capacity_cancels_refinement():
+    cfg = W.cavity(dim=2, n=8, max_levels=3, max_blocks=4 + 4)   # room for one group
+    mesh = Forest(cfg)
+    marks = np.zeros(mesh.cap, np.int8)
+    marks[[0, 1]] = 1
+    res = mesh.adapt(marks)
+    assert res["capacity_error"] and res["n_refined"] == 0
+    assert mesh.counts() == [4, 0, 0]
+    marks[1] = 0
+    res = mesh.adapt(marks)
+    assert not res["capacity_error"] and mesh.child0[0] == 4
+
+
+def test_allocation_order_worked_example():
+    # 2x2 root blocks (IDs 0..3), capacity 4 + 4 groups of 4.
+    cfg = W.cavity(dim=2, n=8, max_levels=3, max_blocks=20)
+    mesh = Forest(cfg)
+    assert mesh.gap[-1] == 4 and mesh.gap[0] == 19      # reverse enumeration
+    m = np.zeros(mesh.cap, np.int8)
+    m[[2, 1]] = 1                      # ascending ID order decides: 1 then 2
+    mesh.adapt(m)
+    assert mesh.child0[1] == 4 and mesh.child0[2] == 8
+    assert mesh.id_sets[1] == [4, 5, 6, 7, 8, 9, 10, 11]
+    m[:] = 0
+    m[1] = -1                          # coarsen block 1: frees 4..7
+    mesh.adapt(m)
+    assert mesh.id_sets[1] == [8, 9, 10, 11]
+    assert mesh.gap[-4:] == [7, 6, 5, 4]
+    m[:] = 0
+    m[[0, 3]] = 1                      # block 0 takes the freed group 4..7
+    mesh.adapt(m)
+    assert mesh.child0[0] == 4 and mesh.child0[3] == 12
+    assert mesh.id_sets[1] == [8, 9, 10, 11, 4, 5, 6, 7, 12, 13, 14, 15]
+    assert mesh.status[[0, 1, 2, 3]].tolist() == [REFINED, UNREFINED, REFINED, REFINED]
+
+
+def test_coarsen_reverted_next_to_finer_blocks():
+    cfg = W.cavity(dim=2, n=8, max_levels=4, max_blocks=4 + 4 * 8)
+    mesh = Forest(cfg)
+    m = np.zeros(mesh.cap, np.int8)
+    m[[0, 1, 2, 3]] = 1
+    mesh.adapt(m)                           # all four roots refined
+    child_of_1 = mesh.child0[1]
+    # refine the child of block 0 that touches block 1 (child c = 1: +x side)
+    m[:] = 0
+    m[mesh.child0[0] + 1] = 1
+    mesh.adapt(m)
+    # coarsening block 1 would put level 0 next to level 2: reverted
+    m[:] = 0
+    m[1] = -1
+    res = mesh.adapt(m)
+    assert res["n_coarsened"] == 0 and mesh.child0[1] == child_of_1
+    # blocks 2 and 3 do not touch the level-2 region [2,4]x[0,2]: allowed
+    m[:] = 0
+    m[[2, 3]] = -1
+    assert mesh.adapt(m)["n_coarsened"] == 2
+    brute_force_check(mesh)
+    # block 0 cannot be coarsened: it has a refined child
+    m[:] = 0
+    m[0] = -1
+    assert mesh.adapt(m)["n_coarsened"] == 0
+
+
+# ------------------------------------------ interpolation and averaging
+def test_interpolation_exact_on_multilinear():
+    for dim, q in ((2, 9), (3, 19)):
+        lbm = ForestLBM(W.periodic_box(dim=dim, q=q, n=8, max_levels=2))
+        Wt = lbm._interp_weights()
+        x = -0.25 + 0.5 * lbm.lc
+        corners = np.array([[(a >> ax) & 1 for ax in range(dim)] for a in range(2 ** dim)], float)
+        for mono in itertools.product((0, 1), repeat=dim):
+            Fc = np.prod(corners ** np.array(mono), axis=1)
+            expect = np.prod(x ** np.array(mono), axis=1)
+            assert np.allclose(Wt @ Fc, expect, atol=1e-15), mono
+
+
+def two_level_lbm(cfg, refine_ids):
+    lbm = ForestLBM(cfg)
+    m = np.zeros(lbm.mesh.cap, np.int8)
+    m[refine_ids] = 1
+    res = lbm.mesh.adapt(m)
+    lbm.interpolate(res["new_children"], "all")
+    return lbm
+
+
+def test_interpolation_preserves_equilibrium():
+    cfg = W.periodic_box(dim=3, q=19, n=8, max_levels=2, nu0=0.02)
+    lbm = ForestLBM(cfg)
+    rho, u = 1.01, np.array([0.03, -0.01, 0.02])
+    feq = equilibrium(lbm.vs, np.array([rho]), u[None])[0]
+    lbm.f[:] = feq
+    m = np.zeros(lbm.mesh.cap, np.int8)
+    m[0] = 1
+    res = lbm.mesh.adapt(m)
+    lbm.interpolate(res["new_children"], "all")
+    for c in res["new_children"]:
+        assert np.max(np.abs(lbm.f[c] - feq)) < 1e-15
+
+
+def test_averaging_constant_and_inverse_of_interpolation():
+    cfg = W.periodic_box(dim=2, q=9, n=8, max_levels=2, nu0=0.02)
+    lbm = ForestLBM(cfg)
+    g = np.random.default_rng(5)
+    rho = 1 + 0.01 * g.random(16)
+    u = 0.02 * (g.random((16, 2)) - 0.5)
+    # parent block 0: affine rescaled field => after interpolation every
+    # child cell holds the affine value; averaging recovers the parent cell
+    x = lbm.lc.astype(float)
+    rho = 1.0 + 0.01 * x[:, 0] - 0.02 * x[:, 1]
+    u = np.stack([0.01 * x[:, 1], 0.003 * x[:, 0]], -1)
+    feq = equilibrium(lbm.vs, rho, u)
+    # non-equilibrium part affine too (rescaling is then affine as well)
+    lbm.f[0] = feq
+    m = np.zeros(lbm.mesh.cap, np.int8)
+    m[0] = 1
+    res = lbm.mesh.adapt(m)
+    lbm.interpolate(res["new_children"], "all")
+    before = lbm.f[0].copy()
+    lbm.f[0] = 0.0
+    lbm.average(res["new_children"], "sync")
+    # sync averaging writes the parent cells over non-ghost children only
+    written = np.any(lbm.f[0] != 0.0, axis=1)
+    assert written.sum() == 4
+    # equilibrium is quadratic in u: recovered to second order only
+    assert np.max(np.abs(lbm.f[0][written] - before[written])) < 2e-5
+    # constants are reproduced exactly
+    lbm.f[res["new_children"]] = lbm.rest
+    lbm.average(res["new_children"], "sync")
+    assert np.max(np.abs(lbm.f[0][written] - lbm.rest)) < 1e-16
+
+
+def test_averaging_children_are_geometric():
+    cfg = W.periodic_box(dim=3, q=19, n=8, max_levels=2)
+    lbm = ForestLBM(cfg)
+    m = np.zeros(lbm.mesh.cap, np.int8)
+    m[3] = 1
+    res = lbm.mesh.adapt(m)
+    par = 3
+    pc = lbm.cell_centres(par)
+    for ch in res["new_children"]:
+        cc = lbm.cell_centres(ch)
+        corners = lbm.quadrant_cells(ch - lbm.mesh.child0[par])
+        for a in range(8):
+            kids = []
+            for s in range(8):
+                o = [2 * ((a >> ax) & 1) + ((s >> ax) & 1) for ax in range(3)]
+                kids.append(o[0] + 4 * o[1] + 16 * o[2])
+            # the 8 children lie inside the parent cell and average to its centre
+            h = 0.5
+            assert np.all(np.abs(cc[kids] - pc[corners[a]]) <= h / 2 + 1e-12)
+            assert np.allclose(cc[kids].mean(0), pc[corners[a]])
+
+
+# ------------------------------------------------------- level stepping
+def couette_two_level(ratio_scale=None, steps=2600):
+    cfg = W.cavity(dim=2, q=9, n=16, max_levels=2, max_blocks=16 + 8 * 4)
+    cfg["faces"] = [("periodic", (0, 0, 0)), ("periodic", (0, 0, 0)),
+                    ("noslip", (0, 0, 0)), ("moving", (0.05, 0.0, 0.0))]
+    cfg["nu0"] = 0.25
+    lbm = ForestLBM(cfg)
+    # refine the middle band y in [4, 12): root blocks with by = 1, 2
+    ids = [b for b in range(16) if (b // 4) in (1, 2)]
+    m = np.zeros(lbm.mesh.cap, np.int8)
+    m[ids] = 1
+    res = lbm.mesh.adapt(m)
+    assert lbm.mesh.counts() == [16, 32]
+    lbm.interpolate(res["new_children"], "all")
+    if ratio_scale is not None:
+        lbm._rescaled_orig = lbm._rescaled
+        lbm._rescaled = lambda f, ratio: lbm._rescaled_orig(f, ratio_scale)
+    lbm.step(steps)
+    lbm.sync()
+    rho, u = lbm.macroscopic()
+    err = 0.0
+    for b in lbm.mesh.active_ids():
+        if lbm.mesh.status[b] != UNREFINED:
+            continue
+        y = lbm.cell_centres(b)[:, 1]
+        err = max(err, np.max(np.abs(u[b, :, 0] - 0.05 * y / 16.0)))
+    return err
+
+
+def test_two_level_couette_linear():
+    # correct Dupuis-Chopard factors: the linear profile survives two levels
+    assert couette_two_level(None) < 1e-10
+    # without rescaling (factor 1) the interface visibly breaks it
+    assert couette_two_level(1.0, steps=1000) > 1e-5
+
+
+def test_taylor_green_two_level():
+    N, tau_root = 32, 0.8
+    nu0 = CS2 * (tau_root - 0.5)
+    cfg = W.periodic_box(dim=2, q=9, n=N, nu0=nu0, max_levels=2, max_blocks=64 + 4 * 64)
+    lbm = ForestLBM(cfg)
+    k = 2 * np.pi / N
+    U = 0.01
+
+    def field(x):
+        ux = -U * np.cos(k * x[:, 0]) * np.sin(k * x[:, 1])
+        uy = U * np.sin(k * x[:, 0]) * np.cos(k * x[:, 1])
+        p = -0.25 * U * U * (np.cos(2 * k * x[:, 0]) + np.cos(2 * k * x[:, 1]))
+        return 1 + p / CS2, np.stack([ux, uy], -1)
+
+    m = np.zeros(lbm.mesh.cap, np.int8)
+    m[[b for b in range(64) if 2 <= b % 8 <= 4 and 2 <= b // 8 <= 5]] = 1
+    lbm.mesh.adapt(m)
+    assert lbm.mesh.counts() == [64, 48]
+    for b in lbm.mesh.active_ids():
+        r, uu = field(lbm.cell_centres(b))
+        lbm.f[b] = equilibrium(lbm.vs, r, uu)
+    t = int(round(1.0 / (2 * nu0 * k * k)))
+    lbm.step(t)
+    lbm.sync()
+    num = den = 0.0
+    for b in lbm.mesh.active_ids():
+        if lbm.mesh.status[b] != UNREFINED:
+            continue
+        wgt = (lbm.mesh.width(lbm.mesh.level[b]) / 4) ** 2
+        _, u0 = field(lbm.cell_centres(b))
+        _, u = moments(lbm.vs, lbm.f[b])
+        num += wgt * np.sum(u * u0)
+        den += wgt * np.sum(u0 * u0)
+    amp = num / den
+    assert abs(amp / np.exp(-2 * nu0 * k * k * t) - 1) < 2e-2
+
+
+def test_refined_patch_static_flow_stays_static():
+    # uniform flow through a periodic two-level forest is an exact solution
+    cfg = W.periodic_box(dim=3, q=19, n=8, max_levels=2, nu0=0.01)
+    lbm = ForestLBM(cfg)
+    feq = equilibrium(lbm.vs, np.ones(1), np.array([[0.02, 0.01, -0.015]]))[0]
+    lbm.f[:] = feq
+    m = np.zeros(lbm.mesh.cap, np.int8)
+    m[0] = 1
+    res = lbm.mesh.adapt(m)
+    lbm.interpolate(res["new_children"], "all")
+    lbm.step(5)
+    lbm.sync()
+    for b in lbm.mesh.active_ids():
+        assert np.max(np.abs(lbm.f[b] - feq)) < 1e-14
+
+
+# ------------------------------------------------------------- criterion
+def test_criterion_linear_shear():
+    cfg = W.cavity(dim=2, q=9, n=16, max_levels=4)   # N_start -2, N_inc 1
+    lbm = ForestLBM(cfg)
+    dx = 1.0 / 16
+    for s, expect in ((0.2, 3), (0.1, 2), (0.05, 1), (0.01, 0)):
+        # u_x = s * y (physical), lattice u = s * dx * j per cell
+        j = lbm.lc[:, 1].astype(float)
+        u = np.stack([s * dx * j, np.zeros(16)], -1)
+        lbm.f[0] = equilibrium(lbm.vs, np.ones(16), u)
+        w2 = lbm.block_vorticity_sq(0)
+        assert abs(w2 - s * s) < 1e-12
+        # thresholds 2^-3, 2^-4, 2^-5 for p = 1, 2, 3
+        assert lbm.desired_level(w2) == expect
+
+
+def test_mlups_count_brute_force():
+    cfg = W.cavity(dim=3, q=19, n=8, max_levels=3, max_blocks=8 * 20)
+    lbm = ForestLBM(cfg)
+    for it in range(4):
+        lbm.mesh.adapt(W.random_marks(7 + it, lbm.mesh.cap, 0.5, 0.2))
+    leaves = [b for b in lbm.mesh.active_ids() if lbm.mesh.status[b] == UNREFINED]
+    brute = sum(2 ** lbm.mesh.level[b] * 64 for b in leaves)
+    assert lbm.updates_per_coarse_step() == brute

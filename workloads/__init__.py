@@ -1,0 +1,149 @@
+"""Seeded synthetic workloads shared by the oracle tests, the GPU tests and the
+benchmark.
+
+This module holds workload *descriptions* (domain sizes, boundary faces,
+viscosity from the Reynolds number, refinement parameters) and seeded random
+number draws.  It contains none of the lattice Boltzmann or mesh-adaptation
+arithmetic: the oracle and the CUDA library each implement that on their own.
+
+Config dictionary keys
+----------------------
+dim, q            velocity set (2, 9) | (3, 19) | (3, 27)
+nx, ny, nz        root grid in cells, multiples of 4 (nz == 4 and ignored in 2D)
+max_levels        L_max >= 1
+nu0               kinematic viscosity in root-lattice units
+faces             2*dim entries in the order x-, x+, y-, y+, (z-, z+); each is
+                  (kind, (ux, uy, uz)) with kind one of 'noslip', 'moving',
+                  'outlet', 'periodic'
+crit_start        N_start of the vorticity criterion
+crit_inc          N_inc of the vorticity criterion
+max_blocks        block capacity (IDs 0 .. max_blocks-1)
+solid             None or (x0, x1, y0, y1): a square prism spanning z, in
+                  root-cell units; a cell is solid when its centre lies inside
+length_x          physical domain length along x (dx_0 = length_x / nx)
+"""
+import numpy as np
+
+FACE_KINDS = ("noslip", "moving", "outlet", "periodic")
+
+
+def _round_capacity(max_blocks, n_root, nc):
+    # keep (capacity - root blocks) a multiple of the child-group size
+    cap = max(int(max_blocks), n_root + nc)
+    cap += (-(cap - n_root)) % nc
+    return cap
+
+
+def root_blocks(cfg):
+    n = (cfg["nx"] // 4) * (cfg["ny"] // 4)
+    if cfg["dim"] == 3:
+        n *= cfg["nz"] // 4
+    return n
+
+
+def finalize(cfg):
+    nc = 4 if cfg["dim"] == 2 else 8
+    cfg["max_blocks"] = _round_capacity(cfg["max_blocks"], root_blocks(cfg), nc)
+    return cfg
+
+
+def cavity(dim=2, q=None, n=64, re=100.0, u_lid=0.05, max_levels=3,
+           crit_start=-2, crit_inc=1, max_blocks=None, ny=None, nz=None):
+    """Lid-driven cavity (Section 5.2): all walls no-slip, the top wall (y+ in
+    2D, z+ in 3D) moves along +x with speed u_lid.  nu0 = u_lid * n / Re in
+    root-lattice units (characteristic length = cavity side)."""
+    q = q or (9 if dim == 2 else 19)
+    ny = ny or n
+    nz = (nz or n) if dim == 3 else 4
+    faces = [("noslip", (0.0, 0.0, 0.0)) for _ in range(2 * dim)]
+    faces[2 * dim - 1] = ("moving", (u_lid, 0.0, 0.0))
+    nroot = (n // 4) * (ny // 4) * ((nz // 4) if dim == 3 else 1)
+    cfg = dict(dim=dim, q=q, nx=n, ny=ny, nz=nz, max_levels=max_levels,
+               nu0=u_lid * n / re, faces=faces, crit_start=crit_start,
+               crit_inc=crit_inc,
+               max_blocks=max_blocks or nroot * 6 + 64,
+               solid=None, length_x=1.0)
+    return finalize(cfg)
+
+
+def periodic_box(dim=2, q=None, n=32, nu0=0.05, max_levels=1, max_blocks=None,
+                 ny=None, nz=None):
+    """Fully periodic box (Taylor-Green and random-field parity cases)."""
+    q = q or (9 if dim == 2 else 19)
+    ny = ny or n
+    nz = (nz or n) if dim == 3 else 4
+    faces = [("periodic", (0.0, 0.0, 0.0)) for _ in range(2 * dim)]
+    nroot = (n // 4) * (ny // 4) * ((nz // 4) if dim == 3 else 1)
+    cfg = dict(dim=dim, q=q, nx=n, ny=ny, nz=nz, max_levels=max_levels,
+               nu0=nu0, faces=faces, crit_start=-2, crit_inc=1,
+               max_blocks=max_blocks or nroot * 4 + 64, solid=None,
+               length_x=1.0)
+    return finalize(cfg)
+
+
+def channel_cylinder(q=27, nx=256, ny=64, nz=64, side=8, cx=64, cy=32,
+                     u0=0.05, re=100.0, max_levels=5, max_blocks=None,
+                     crit_start=-3, crit_inc=1):
+    """3D channel past a square prism (Section 5.3 in 3D): uniform inlet at
+    x- and far field on the y/z faces (moving-wall bounce-back with
+    u = (u0, 0, 0)), anti-bounce-back outlet at x+.  nu0 = u0 * side / Re."""
+    faces = [("moving", (u0, 0.0, 0.0)), ("outlet", (0.0, 0.0, 0.0)),
+             ("moving", (u0, 0.0, 0.0)), ("moving", (u0, 0.0, 0.0)),
+             ("moving", (u0, 0.0, 0.0)), ("moving", (u0, 0.0, 0.0))]
+    h = side / 2.0
+    nroot = (nx // 4) * (ny // 4) * (nz // 4)
+    cfg = dict(dim=3, q=q, nx=nx, ny=ny, nz=nz, max_levels=max_levels,
+               nu0=u0 * side / re, faces=faces, crit_start=crit_start,
+               crit_inc=crit_inc, max_blocks=max_blocks or nroot * 8 + 64,
+               solid=(cx - h, cx + h, cy - h, cy + h), length_x=1.0)
+    return finalize(cfg)
+
+
+# --------------------------------------------------------------- seeded draws
+
+def rng(seed):
+    return np.random.default_rng(int(seed))
+
+
+def random_macro(seed, n_cells, dim, drho=0.02, umax=0.04):
+    """Seeded density and velocity samples: rho in 1 +- drho, |u_i| <= umax."""
+    g = rng(seed)
+    rho = 1.0 + drho * (2.0 * g.random(n_cells) - 1.0)
+    u = umax * (2.0 * g.random((n_cells, dim)) - 1.0)
+    return rho, u
+
+
+def random_noise(seed, shape, scale=1e-3):
+    """Seeded uniform noise in [-scale, scale)."""
+    return scale * (2.0 * rng(seed).random(shape) - 1.0)
+
+
+def random_marks(seed, n, p_refine=0.3, p_coarsen=0.3):
+    """Seeded per-block marks: +1 refine, -1 coarsen, 0 keep (int8)."""
+    x = rng(seed).random(n)
+    m = np.zeros(n, dtype=np.int8)
+    m[x < p_refine] = 1
+    m[(x >= p_refine) & (x < p_refine + p_coarsen)] = -1
+    return m
+
+
+# ------------------------------------------------------- named configurations
+
+def config_c0():
+    """2D lid-driven cavity, D2Q9, FP64: 64x64 root cells, Re 100, lid 0.05,
+    up to 2 extra levels (L_max = 3), adapt every 100 coarse steps, 2000 steps."""
+    return cavity(dim=2, q=9, n=64, re=100.0, max_levels=3, max_blocks=256 * 24)
+
+
+def config_c1(n=64, re=1000.0, max_blocks=None):
+    """3D lid-driven cavity, D3Q19, FP32: 64^3 root cells, Re 1000, lid 0.05,
+    up to 3 extra levels (L_max = 4), adapt every 50 coarse steps."""
+    nroot = (n // 4) ** 3
+    return cavity(dim=3, q=19, n=n, re=re, max_levels=4,
+                  max_blocks=max_blocks or nroot * 80)
+
+
+def config_uniform_bar(n=256):
+    """Single-level D3Q19 periodic block forest of n^3 cells (roofline bar)."""
+    return periodic_box(dim=3, q=19, n=n, nu0=0.01, max_levels=1,
+                        max_blocks=(n // 4) ** 3)
