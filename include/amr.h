@@ -1,0 +1,212 @@
+/*
+ * amr.h -- C ABI of the GB300-native block-forest AMR lattice Boltzmann
+ * library (method of arXiv 2308.08085, "GPU-Native Adaptive Mesh Refinement
+ * with Application to Lattice Boltzmann Simulations").
+ *
+ * Every entry point takes plain pointers and sizes.  The caller owns device
+ * memory (one arena, carved by the library) and the CUDA stream; the library
+ * allocates no device memory of its own.  All calls are asynchronous on the
+ * caller's stream except amr_adapt, amr_fields / amr_set_fields with host
+ * buffers, and amr_profile_read, which synchronise that stream.
+ *
+ * Return values: AMR_OK (0) or a negative AMR_E_* code; amr_fields returns a
+ * byte count (>= 0) or a negative code.  amr_last_error() gives a one-line
+ * description of the most recent failure on the calling thread.
+ *
+ * Layouts (see also the per-call comments)
+ *   block      4^dim cells; cell l = i + 4 j + 16 k (x fastest)
+ *   block IDs  0 .. max_blocks-1; root blocks 0 .. n_root-1 numbered
+ *              x-fastest over the root grid of blocks
+ *   directions velocity-set numbering of the paper's velocity-set figure
+ *              (Section 2): D2Q9 0 rest, 1 +x, 2 +y, 3 -x, 4 -y, 5 (+,+),
+ *              6 (-,+), 7 (-,-), 8 (+,-); D3Q19/D3Q27 opposite pairs
+ *              (2k-1, 2k): +-x, +-y, +-z, +-(x+y), +-(x+z), +-(y+z),
+ *              +-(x-y), +-(x-z), +-(y-z), +-(1,1,1), +-(1,1,-1),
+ *              +-(1,-1,1), +-(-1,1,1).  Block neighbours use the D2Q9 /
+ *              D3Q27 numbering; neighbour 0 is the block itself.
+ *   sentinels  AMR_NONE (-1): no same-level neighbour / no children;
+ *              AMR_WALL(face) = -2 - face: the neighbour position leaves the
+ *              domain through wall `face` (x-, x+, y-, y+, z-, z+ = 0..5).
+ */
+#ifndef AMR_H
+#define AMR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define AMR_OK 0
+#define AMR_E_INVAL (-1)     /* bad argument or configuration                 */
+#define AMR_E_CAPACITY (-2)  /* gap set too small: refinement of the call was
+                                cancelled, coarsening still applied            */
+#define AMR_E_CUDA (-3)      /* a CUDA runtime call failed                     */
+#define AMR_E_TIMEOUT (-4)   /* a bounded device wait gave up                  */
+#define AMR_E_UNSTABLE (-5)  /* the FP64 mass audit found a non-finite value   */
+#define AMR_E_ARENA (-6)     /* arena too small or misaligned                   */
+
+/* ----------------------------------------------------------------- storage */
+#define AMR_F64 0        /* populations stored and computed in FP64          */
+#define AMR_F32 1        /* populations stored and computed in FP32          */
+#define AMR_F32_BF16 2   /* stored as BF16 shifted values f - w_p, FP32 math */
+#define AMR_F32_F16 3    /* stored as FP16 shifted values f - w_p, FP32 math */
+
+/* ------------------------------------------------------------- face kinds */
+#define AMR_FACE_NOSLIP 0    /* bounce-back, u_w = 0                          */
+#define AMR_FACE_MOVING 1    /* bounce-back with known wall velocity u_w      */
+#define AMR_FACE_OUTLET 2    /* anti-bounce-back with rho_w, u_w = cell u     */
+#define AMR_FACE_PERIODIC 3  /* both faces of an axis must be periodic        */
+
+/* --------------------------------------------------------- block statuses */
+#define AMR_ST_INACTIVE 0
+#define AMR_ST_UNREFINED 1          /* leaf                                   */
+#define AMR_ST_REFINED 2            /* refined, every child a leaf            */
+#define AMR_ST_REFINED_WITH_CHILD 3 /* refined, some child refined            */
+#define AMR_ST_REFINED_PERMANENT 4  /* refined, never coarsened               */
+
+/* ------------------------------------------------------------ cell classes */
+#define AMR_CELL_INTERIOR 0
+#define AMR_CELL_INTERFACE 1
+#define AMR_CELL_GHOST 2
+
+#define AMR_NONE (-1)
+#define AMR_WALL(face) (-2 - (face))
+#define AMR_MAX_LEVELS 8
+
+typedef struct {
+  int32_t kind;      /* AMR_FACE_*                                            */
+  int32_t pad_;
+  double u[3];       /* wall velocity (lattice units) for AMR_FACE_MOVING     */
+  double rho_w;      /* wall density; the paper uses 1                        */
+} amr_face;
+
+typedef struct {
+  int32_t dim, q;          /* (2,9) | (3,19) | (3,27)                          */
+  int32_t storage;         /* AMR_F64 | AMR_F32 | AMR_F32_BF16 | AMR_F32_F16   */
+  int32_t nx, ny, nz;      /* root grid in cells, multiples of 4 (nz ignored
+                              in 2D)                                           */
+  int32_t max_levels;      /* L_max, 1 .. AMR_MAX_LEVELS                       */
+  int32_t crit_start;      /* N_start of the vorticity criterion (Alg. 3)      */
+  int32_t crit_inc;        /* N_inc of the vorticity criterion (Alg. 3)        */
+  int32_t has_solid;       /* 1: square prism spanning z (see solid[])          */
+  int64_t max_blocks;      /* block capacity; (max_blocks - n_root) must be a
+                              multiple of 2^dim                                 */
+  double nu0;              /* viscosity, root-lattice units                     */
+  double length_x;         /* physical length of the x extent (dx_0 = len/nx)  */
+  double solid[4];         /* x0, x1, y0, y1 (root-cell units): a cell whose
+                              centre is strictly inside is solid               */
+  amr_face faces[6];       /* x-, x+, y-, y+, z-, z+ (first 4 used in 2D)      */
+  int32_t use_graphs;      /* 1: replay the coarse step as a CUDA graph         */
+  int32_t pad_;
+} amr_config;
+
+typedef struct {
+  int64_t n_marked_refine;   /* eligible refine marks before capacity check  */
+  int64_t n_marked_coarsen;  /* eligible coarsen marks before 2:1 reversion  */
+  int64_t n_refined;         /* blocks refined by the call                    */
+  int64_t n_coarsened;       /* blocks coarsened by the call                  */
+  int64_t n_blocks;          /* active blocks after the call                  */
+  int32_t capacity_error;    /* 1 when refinement was cancelled               */
+  int32_t pad_;
+  double ms_total;           /* host wall time of the call                    */
+} amr_adapt_stats;
+
+typedef struct {
+  char name[32];         /* kernel class                                     */
+  int64_t launches;
+  double ms;             /* summed CUDA-event durations                      */
+  double bytes;          /* summed algorithmic bytes (2 Q N_p per update for
+                            collide-stream)                                  */
+  double cells;          /* summed cell updates                              */
+} amr_kernel_profile;
+
+typedef struct amr_t amr_t;
+
+/* Bytes of device arena that amr_init needs for `cfg` (0 if cfg is invalid).
+ * The arena must be 256-byte aligned. */
+size_t amr_arena_bytes(const amr_config* cfg);
+
+/* Build the root grid of blocks (Section 3.2: structured root grid, ID set of
+ * level 0, gap set enumerated in reverse) and initialise every population to
+ * the rest equilibrium (rho = 1, u = 0).  `dev_arena` (device memory of
+ * `arena_bytes`, owned by the caller, kept alive until amr_free) holds every
+ * array; `stream` is a cudaStream_t (NULL: legacy default stream).
+ * Errors: AMR_E_INVAL (config), AMR_E_ARENA, AMR_E_CUDA. */
+int amr_init(const amr_config* cfg, void* dev_arena, size_t arena_bytes,
+             void* stream, amr_t** out);
+
+/* Advance `n_coarse_steps` root time steps with the recursive level step of
+ * Section 4.1: on level L, interpolate level L to the ghost cells of L+1
+ * (Section 3.4.1), collide and stream L (Sections 4.2, 4.3, BGK with
+ * tau_L = 1/2 + 2^L (tau_0 - 1/2)), advance L+1 twice, average the interface
+ * cells of L+1 into L (Section 3.4.3).  Asynchronous.  Errors: AMR_E_INVAL,
+ * AMR_E_CUDA. */
+int amr_step(amr_t* a, int n_coarse_steps);
+
+/* Adapt the mesh (Sections 3.3 and 4.4): synchronise all levels (average
+ * bottom-up, interpolate ghosts top-down), mark blocks -- from the vorticity
+ * criterion of Algorithm 3 when `dev_marks` is NULL, else from the caller's
+ * device array of int8 marks indexed by block ID (+1 refine, -1 coarsen,
+ * 0 keep; max_blocks entries) -- keep the eligible marks (refine: leaf below
+ * L_max-1 with every same-level neighbour present; coarsen: status REFINED),
+ * revert coarsening that would break 2:1 balance, allocate children from the
+ * gap set, remove children, update ID sets, statuses, connectivity and cell
+ * classes, and interpolate every cell of the new children.  Synchronous.
+ * `out` may be NULL.  Errors: AMR_E_CAPACITY (refinement cancelled, mesh
+ * otherwise updated), AMR_E_INVAL, AMR_E_CUDA. */
+int amr_adapt(amr_t* a, const int8_t* dev_marks, amr_adapt_stats* out);
+
+/* Field selectors for amr_fields / amr_set_fields.  B = max_blocks,
+ * M = 4^dim, K = 3^dim. */
+#define AMR_RHO_U 0     /* double [B][M][1+dim]: rho, u after a sync (the
+                           call runs the level synchronisation first)          */
+#define AMR_F 1         /* double [Q][B][M]: populations of every block at
+                           its level's current time (unshifted values)         */
+#define AMR_BLOCKS 2    /* int32 [4][B]: level, status, child0, parent         */
+#define AMR_COORDS 3    /* double [B][dim]: block corner, root-cell units      */
+#define AMR_NBR 4       /* int32 [B][K]: neighbour IDs / sentinels             */
+#define AMR_NBR_CHILD 5 /* int32 [B][K]: first child of each neighbour,
+                           AMR_NONE if absent/unrefined, wall code if wall     */
+#define AMR_IDSETS 6    /* int32 [L_max][B]: ID set of each level; lengths
+                           from AMR_COUNTS                                      */
+#define AMR_GAPS 7      /* int32 [B]: gap stack, bottom first; length from
+                           AMR_COUNTS                                          */
+#define AMR_MASKS 8     /* uint8 [B][M]: AMR_CELL_* class of every cell        */
+#define AMR_COUNTS 9    /* int64 [4 + 4 L_max]: L_max, n_gaps, coarse steps,
+                           0, then per level: ID-set size, active blocks,
+                           leaves, parent blocks exchanging with children      */
+#define AMR_MASS 10     /* double [1 + dim]: FP64 sum over leaf cells of
+                           rho V and rho u V, V = cell volume (root units)     */
+#define AMR_FORCE 11    /* double [3]: momentum-exchange force on the solid
+                           (Section 5.3), physical units of dx                 */
+
+/* Copy field `what` into `dst` (device pointer if dst_on_device, else host).
+ * dst == NULL returns the required bytes.  Returns bytes written or a
+ * negative code (AMR_E_INVAL if dst_bytes is too small). */
+int64_t amr_fields(amr_t* a, int what, void* dst, size_t dst_bytes,
+                   int dst_on_device);
+
+/* Overwrite the populations (what == AMR_F, same layout as amr_fields) of
+ * every active block from `src`.  Synchronous for host sources. */
+int amr_set_fields(amr_t* a, int what, const void* src, size_t src_bytes,
+                   int src_on_device);
+
+/* Per-kernel CUDA-event timing of subsequent launches (enable != 0 disables
+ * graph replay while on).  amr_profile_read synchronises, fills up to `max`
+ * entries and returns how many kernel classes exist; reset != 0 clears. */
+int amr_profile(amr_t* a, int enable);
+int amr_profile_read(amr_t* a, amr_kernel_profile* out, int max, int reset);
+
+/* Release host-side state (the arena stays owned by the caller). */
+int amr_free(amr_t* a);
+
+const char* amr_strerror(int code);
+const char* amr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMR_H */

@@ -1,0 +1,284 @@
+"""ctypes binding of the C ABI declared in include/amr.h.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+libamr.so.  PyTorch provides the device arena and the stream.  If the library
+has not been built the binding raises; there is no fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libamr.so")
+
+# status codes
+AMR_OK, AMR_E_INVAL, AMR_E_CAPACITY, AMR_E_CUDA, AMR_E_TIMEOUT, AMR_E_UNSTABLE, AMR_E_ARENA = (
+    0, -1, -2, -3, -4, -5, -6)
+# storage
+STORAGE = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+# face kinds
+FACE = {"noslip": 0, "moving": 1, "outlet": 2, "periodic": 3}
+# field selectors
+AMR_RHO_U, AMR_F, AMR_BLOCKS, AMR_COORDS, AMR_NBR, AMR_NBR_CHILD, AMR_IDSETS, AMR_GAPS, \
+    AMR_MASKS, AMR_COUNTS, AMR_MASS, AMR_FORCE = range(12)
+
+EXPORTED = ["amr_arena_bytes", "amr_init", "amr_step", "amr_adapt", "amr_fields",
+            "amr_set_fields", "amr_profile", "amr_profile_read", "amr_free", "amr_strerror",
+            "amr_last_error"]
+
+
+class AmrFace(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("u", ctypes.c_double * 3), ("rho_w", ctypes.c_double)]
+
+
+class AmrConfig(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("q", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("max_levels", ctypes.c_int32), ("crit_start", ctypes.c_int32),
+                ("crit_inc", ctypes.c_int32), ("has_solid", ctypes.c_int32),
+                ("max_blocks", ctypes.c_int64), ("nu0", ctypes.c_double),
+                ("length_x", ctypes.c_double), ("solid", ctypes.c_double * 4),
+                ("faces", AmrFace * 6), ("use_graphs", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
+
+
+class AmrAdaptStats(ctypes.Structure):
+    _fields_ = [("n_marked_refine", ctypes.c_int64), ("n_marked_coarsen", ctypes.c_int64),
+                ("n_refined", ctypes.c_int64), ("n_coarsened", ctypes.c_int64),
+                ("n_blocks", ctypes.c_int64), ("capacity_error", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("ms_total", ctypes.c_double)]
+
+
+class AmrKernelProfile(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double), ("cells", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libamr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libamr.so is not built (%s): run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    lib.amr_arena_bytes.argtypes = [ctypes.POINTER(AmrConfig)]
+    lib.amr_arena_bytes.restype = sz
+    lib.amr_init.argtypes = [ctypes.POINTER(AmrConfig), vp, sz, vp, ctypes.POINTER(vp)]
+    lib.amr_init.restype = i32
+    lib.amr_step.argtypes = [vp, i32]
+    lib.amr_step.restype = i32
+    lib.amr_adapt.argtypes = [vp, vp, ctypes.POINTER(AmrAdaptStats)]
+    lib.amr_adapt.restype = i32
+    lib.amr_fields.argtypes = [vp, i32, vp, sz, i32]
+    lib.amr_fields.restype = i64
+    lib.amr_set_fields.argtypes = [vp, i32, vp, sz, i32]
+    lib.amr_set_fields.restype = i32
+    lib.amr_profile.argtypes = [vp, i32]
+    lib.amr_profile.restype = i32
+    lib.amr_profile_read.argtypes = [vp, ctypes.POINTER(AmrKernelProfile), i32, i32]
+    lib.amr_profile_read.restype = i32
+    lib.amr_free.argtypes = [vp]
+    lib.amr_free.restype = i32
+    lib.amr_strerror.argtypes = [i32]
+    lib.amr_strerror.restype = ctypes.c_char_p
+    lib.amr_last_error.argtypes = []
+    lib.amr_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+class AmrError(RuntimeError):
+    def __init__(self, code, where):
+        lib = load_library()
+        super().__init__("%s: %s (%s)" % (where, lib.amr_strerror(code).decode(),
+                                          lib.amr_last_error().decode()))
+        self.code = code
+
+
+def make_config(cfg, storage="f32", use_graphs=True):
+    """Fill an AmrConfig from a workload dictionary (see workloads/)."""
+    c = AmrConfig()
+    c.dim, c.q = cfg["dim"], cfg["q"]
+    c.storage = STORAGE[storage]
+    c.nx, c.ny, c.nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    c.max_levels = cfg["max_levels"]
+    c.crit_start, c.crit_inc = cfg["crit_start"], cfg["crit_inc"]
+    c.max_blocks = cfg["max_blocks"]
+    c.nu0 = cfg["nu0"]
+    c.length_x = cfg.get("length_x", 1.0)
+    if cfg.get("solid") is not None:
+        c.has_solid = 1
+        for i, v in enumerate(cfg["solid"]):
+            c.solid[i] = v
+    for i, face in enumerate(cfg["faces"]):
+        c.faces[i].kind = FACE[face[0]]
+        for a, v in enumerate(face[1]):
+            c.faces[i].u[a] = v
+        c.faces[i].rho_w = face[2] if len(face) > 2 else 1.0
+    c.use_graphs = 1 if use_graphs else 0
+    return c
+
+
+class AmrLBM:
+    """One block-forest AMR-LBM instance on the current CUDA device."""
+
+    def __init__(self, cfg, storage="f32", stream=None, use_graphs=True, device=None):
+        import torch
+        self.lib = lib = load_library()
+        self.cfg = cfg
+        self.dim, self.q = cfg["dim"], cfg["q"]
+        self.m = 4 ** self.dim
+        self.nk = 3 ** self.dim
+        self.cap = cfg["max_blocks"]
+        self.lmax = cfg["max_levels"]
+        self.storage = storage
+        self.c = make_config(cfg, storage, use_graphs)
+        nbytes = lib.amr_arena_bytes(ctypes.byref(self.c))
+        if nbytes == 0:
+            raise AmrError(AMR_E_INVAL, "amr_arena_bytes")
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self.arena = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        base = self.arena.data_ptr()
+        off = (-base) % 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.h = ctypes.c_void_p()
+        rc = lib.amr_init(ctypes.byref(self.c), ctypes.c_void_p(base + off), nbytes,
+                          ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.h))
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_init")
+
+    # ------------------------------------------------------------ calls
+    def _check(self, rc, where, ok=(AMR_OK,)):
+        if rc not in ok:
+            raise AmrError(rc, where)
+        return rc
+
+    def step(self, n=1):
+        self._check(self.lib.amr_step(self.h, int(n)), "amr_step")
+
+    def adapt(self, marks=None):
+        """Adapt the mesh; marks: optional int8 torch CUDA tensor (+1/-1/0) of
+        length max_blocks.  Returns (status code, stats dict)."""
+        st = AmrAdaptStats()
+        ptr = None
+        if marks is not None:
+            assert marks.dtype.itemsize == 1 and marks.numel() >= self.cap and marks.is_cuda
+            ptr = ctypes.c_void_p(marks.data_ptr())
+        rc = self.lib.amr_adapt(self.h, ptr, ctypes.byref(st))
+        self._check(rc, "amr_adapt", ok=(AMR_OK, AMR_E_CAPACITY))
+        return rc, {k: getattr(st, k) for k, _ in AmrAdaptStats._fields_ if k != "pad_"}
+
+    def field_bytes(self, what):
+        n = self.lib.amr_fields(self.h, what, None, 0, 0)
+        if n < 0:
+            raise AmrError(int(n), "amr_fields")
+        return int(n)
+
+    def fields_host(self, what, dtype):
+        n = self.field_bytes(what)
+        out = np.empty(n // np.dtype(dtype).itemsize, dtype=dtype)
+        rc = self.lib.amr_fields(self.h, what, out.ctypes.data_as(ctypes.c_void_p), n, 0)
+        if rc < 0:
+            raise AmrError(int(rc), "amr_fields")
+        return out
+
+    def fields_device(self, what, torch_dtype):
+        import torch
+        n = self.field_bytes(what)
+        out = torch.empty(n // torch.empty(0, dtype=torch_dtype).element_size(),
+                          dtype=torch_dtype, device=self.device)
+        rc = self.lib.amr_fields(self.h, what, ctypes.c_void_p(out.data_ptr()), n, 1)
+        if rc < 0:
+            raise AmrError(int(rc), "amr_fields")
+        return out
+
+    # ------------------------------------------------------ conveniences
+    def populations(self):
+        """f [cap, M, Q] (float64) at each block's current time."""
+        f = self.fields_host(AMR_F, np.float64).reshape(self.q, self.cap, self.m)
+        return np.ascontiguousarray(f.transpose(1, 2, 0))
+
+    def set_populations(self, f):
+        """Overwrite the populations from f [cap, M, Q] (float64)."""
+        arr = np.ascontiguousarray(np.asarray(f, np.float64).transpose(2, 0, 1))
+        self._check(self.lib.amr_set_fields(self.h, AMR_F, arr.ctypes.data_as(ctypes.c_void_p),
+                                            arr.nbytes, 0), "amr_set_fields")
+
+    def rho_u(self):
+        a = self.fields_host(AMR_RHO_U, np.float64).reshape(self.cap, self.m, 1 + self.dim)
+        return a[..., 0], a[..., 1:]
+
+    def blocks(self):
+        b = self.fields_host(AMR_BLOCKS, np.int32).reshape(4, self.cap)
+        return dict(level=b[0], status=b[1], child0=b[2], parent=b[3])
+
+    def coords(self):
+        return self.fields_host(AMR_COORDS, np.float64).reshape(self.cap, self.dim)
+
+    def nbr(self):
+        return self.fields_host(AMR_NBR, np.int32).reshape(self.cap, self.nk)
+
+    def nbr_child(self):
+        return self.fields_host(AMR_NBR_CHILD, np.int32).reshape(self.cap, self.nk)
+
+    def masks(self):
+        return self.fields_host(AMR_MASKS, np.uint8).reshape(self.cap, self.m)
+
+    def counts(self):
+        c = self.fields_host(AMR_COUNTS, np.int64)
+        lmax = int(c[0])
+        per = c[4:4 + 4 * lmax].reshape(lmax, 4)
+        return dict(n_gaps=int(c[1]), coarse_steps=int(c[2]), n_ids=per[:, 0].tolist(),
+                    n_active=per[:, 1].tolist(), n_leaves=per[:, 2].tolist(),
+                    n_parents=per[:, 3].tolist())
+
+    def id_sets(self):
+        ids = self.fields_host(AMR_IDSETS, np.int32).reshape(self.lmax, self.cap)
+        n = self.counts()["n_ids"]
+        return [ids[L, :n[L]].tolist() for L in range(self.lmax)]
+
+    def gaps(self):
+        g = self.fields_host(AMR_GAPS, np.int32)
+        return g[:self.counts()["n_gaps"]].tolist()
+
+    def mass(self):
+        return self.fields_host(AMR_MASS, np.float64)
+
+    def force(self):
+        return self.fields_host(AMR_FORCE, np.float64)
+
+    def profile(self, enable=True):
+        self._check(self.lib.amr_profile(self.h, 1 if enable else 0), "amr_profile")
+
+    def profile_read(self, reset=True):
+        arr = (AmrKernelProfile * 8)()
+        n = self.lib.amr_profile_read(self.h, arr, 8, 1 if reset else 0)
+        if n < 0:
+            raise AmrError(n, "amr_profile_read")
+        return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms,
+                                           bytes=arr[i].bytes, cells=arr[i].cells)
+                for i in range(n)}
+
+    def updates_per_coarse_step(self):
+        """Leaf-cell updates of one coarse step (Section 5.1 definition)."""
+        c = self.counts()
+        return sum((2 ** L) * c["n_leaves"][L] * self.m for L in range(self.lmax))
+
+    def close(self):
+        if self.h:
+            self.lib.amr_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

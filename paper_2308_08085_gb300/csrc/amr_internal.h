@@ -1,0 +1,96 @@
+// Internal state of one AMR-LBM instance and the mesh-adaptation entry points
+// shared between the translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/amr.h"
+#include "lbm_ops.h"
+
+namespace amr {
+
+void set_error(const std::string& msg);
+
+struct ProfileSlot {
+  cudaEvent_t start, stop;
+  int kind;
+  double bytes, cells;
+};
+
+struct Instance {
+  amr_config cfg{};
+  int dim = 0, q = 0, M = 0, nc = 0, nk = 0, lmax = 0, storage = 0;
+  int64_t cap = 0, n_root = 0;
+  int nroot[3] = {1, 1, 1};
+  size_t elem = 0;                 // bytes per stored population
+  cudaStream_t stream = nullptr;
+  const LbmOps* ops = nullptr;
+  bool solid = false;
+
+  // device arrays carved from the caller's arena
+  void* f[2] = {nullptr, nullptr};
+  int32_t *level = nullptr, *status = nullptr, *child0 = nullptr, *parent = nullptr;
+  float* X = nullptr;              // [cap][3] block corners, root-cell units
+  int32_t* nbr = nullptr;          // [cap][NBR_STRIDE]
+  uint32_t* nonemask = nullptr;    // bit k set when nbr[b][k] == NONE
+  uint64_t* solidmask = nullptr;   // bit l set when cell l is solid
+  int32_t *idset = nullptr, *active = nullptr, *parents = nullptr;   // [lmax][cap]
+  int32_t* gap = nullptr;          // [cap]
+  int8_t* marks = nullptr;         // [cap]
+  double* w2 = nullptr;            // [cap] criterion block maxima
+  int32_t *tmp0 = nullptr, *tmp1 = nullptr, *tmp2 = nullptr;   // [cap]
+  int32_t* cta = nullptr;          // [cap/256 + 2]
+  int32_t* dcount = nullptr;       // [64] device counters
+  double* red = nullptr;           // [8192] reduction partials
+  int32_t* wall_code = nullptr;    // [64] code of a set of crossed faces
+
+  // host mirror of the mesh sizes and time-stepping state
+  int64_t n_ids[AMR_MAX_LEVELS] = {}, n_active[AMR_MAX_LEVELS] = {},
+          n_parents[AMR_MAX_LEVELS] = {}, n_leaves[AMR_MAX_LEVELS] = {};
+  int64_t n_gaps = 0;
+  int64_t coarse_steps = 0;
+  unsigned cur = 0;                // bit L: current population buffer of level L
+  double tau[AMR_MAX_LEVELS] = {};
+  StepParams prm{};
+
+  // CUDA graphs of one coarse step, one per parity of level 0
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool graph_valid = false;
+  bool use_graphs = true;
+
+  // profiling
+  bool profiling = false;
+  std::vector<ProfileSlot> prof;
+  std::vector<cudaEvent_t> event_pool;
+  struct Acc { int64_t launches = 0; double ms = 0, bytes = 0, cells = 0; };
+  Acc acc[8];
+
+  size_t f_bytes() const { return (size_t)cap * M * q * elem; }
+  size_t stride() const { return (size_t)cap * M; }
+  void* fbuf(int level, int which) const {   // which: 0 current, 1 other
+    return f[((cur >> level) & 1u) ^ (unsigned)which];
+  }
+};
+
+enum ProfileKind { PK_COLLIDE = 0, PK_INTERP = 1, PK_AVERAGE = 2, PK_COUNT = 3 };
+
+// mesh.cu
+int mesh_init_root(Instance* a);
+int mesh_adapt(Instance* a, bool external, amr_adapt_stats* st);
+int mesh_export(Instance* a, int what, void* dst_dev);
+int mesh_refresh_lists(Instance* a);
+int64_t mesh_export_bytes(const Instance* a, int what);
+
+#define AMR_CUDA(call)                                                             \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      ::amr::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));       \
+      return AMR_E_CUDA;                                                           \
+    }                                                                              \
+  } while (0)
+
+}  // namespace amr

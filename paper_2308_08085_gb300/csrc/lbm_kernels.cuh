@@ -1,0 +1,633 @@
+// Templated LBM kernels of the block forest.  Included once per velocity-set
+// translation unit, which instantiates them through AMR_LBM_OPS.
+//
+// Population layout (every storage type): f[p * stride + b * M + l], stride =
+// capacity * M, M = 4^D cells per block, l = i + 4 j + 16 k.  Two buffers A/B
+// are used per level in ping-pong; a level's current buffer is bit L of `cur`.
+#pragma once
+#include "lattice.cuh"
+#include "lbm_ops.h"
+
+namespace amr {
+
+constexpr int ST_UNREFINED = 1;
+constexpr int ST_REFINED = 2;
+constexpr int CLS_INTERIOR = 0, CLS_INTERFACE = 1, CLS_GHOST = 2;
+constexpr int FACE_OUTLET = 2;
+
+// geometric neighbour code (sx+1) + 3 (sy+1) [+ 9 (sz+1)] -> neighbour index k
+struct GeoTable {
+  int8_t k_of_code[27];
+};
+template <int D>
+constexpr GeoTable make_geo() {
+  GeoTable t{};
+  for (int c = 0; c < 27; ++c) {
+    int sx = c % 3 - 1, sy = (c / 3) % 3 - 1, sz = c / 9 - 1;
+    if (D == 2) t.k_of_code[c] = (c < 9) ? (int8_t)Nbr<2>::dir_of(sx, sy, 0) : (int8_t)-1;
+    else t.k_of_code[c] = (int8_t)Nbr<3>::dir_of(sx, sy, sz);
+  }
+  return t;
+}
+static __constant__ GeoTable c_geo2 = make_geo<2>();
+static __constant__ GeoTable c_geo3 = make_geo<3>();
+
+template <int D>
+__device__ __forceinline__ int geo_to_k(int code) {
+  return D == 2 ? c_geo2.k_of_code[code] : c_geo3.k_of_code[code];
+}
+
+// ===================================================== fused collide + stream
+// One thread per cell, 256 threads = 256/M blocks per CTA.  Each cell loads its
+// Q populations (coalesced planes), relaxes them with BGK (Section 4.3) and
+// pushes f*_p to x + c_p in the other buffer (Section 4.2).  Neighbour block
+// IDs are staged in shared memory in geometric order.  A push that leaves the
+// level (NONE), hits a wall, or hits a solid cell lands in the cell's own
+// opposite slot: halfway bounce-back, the moving-wall term, or the
+// anti-bounce-back outlet value (Section 2 boundary equations).
+template <int D, int Q, class T, bool SOLID>
+__global__ void __launch_bounds__(256)
+    k_collide_stream(const int32_t* __restrict__ list, int n, const T* __restrict__ fin,
+                     T* __restrict__ fout, const int32_t* __restrict__ nbr,
+                     const uint64_t* __restrict__ solidmask, StepParams prm) {
+  using V = VS<D, Q>;
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int M = Block<D>::M;
+  constexpr int NCODE = D == 2 ? 9 : 27;
+  constexpr int CENTER = D == 2 ? 4 : 13;
+  constexpr int BPC = 256 / M;
+  __shared__ int32_t s_nb[BPC][NCODE];
+  __shared__ uint64_t s_sm[SOLID ? BPC : 1][SOLID ? NCODE : 1];
+
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int first = blockIdx.x * BPC;
+  for (int t = threadIdx.x; t < BPC * NCODE; t += blockDim.x) {
+    const int s = t / NCODE, code = t - s * NCODE;
+    const int k = geo_to_k<D>(code);
+    const int bi = first + s;
+    int v = NONE;
+    if (bi < n) v = __ldg(nbr + (size_t)__ldg(list + bi) * NBR_STRIDE + k);
+    s_nb[s][code] = v;
+    if constexpr (SOLID) s_sm[s][code] = (v >= 0) ? __ldg(solidmask + v) : 0ull;
+  }
+  __syncthreads();
+  if (first + slot >= n) return;
+  const int b = s_nb[slot][CENTER];
+  if constexpr (SOLID) {
+    if ((s_sm[slot][CENTER] >> l) & 1ull) return;   // solid cells are not advanced
+  }
+  const size_t stride = prm.stride;
+  const size_t base = (size_t)b * M + l;
+
+  R f[Q];
+  static_for<0, Q>([&](auto P) {
+    f[P] = S::template load<D, Q, P>(fin[(size_t)P * stride + base]);
+  });
+  R rho, ux, uy, uz;
+  moments<D, Q>(f, rho, ux, uy, uz);
+  const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+  const R om = R(prm.omega);
+
+  const int i = Block<D>::ci(l), j = Block<D>::cj(l), kk = Block<D>::ck(l);
+  static_for<0, Q>([&](auto P) {
+    constexpr int p = P;
+    constexpr int cx = V::cx[p], cy = V::cy[p], cz = V::cz[p];
+    constexpr int pb = V::opp[p];
+    const R fs = f[p] + om * (feq<D, Q, p>(rho, ux, uy, uz, usq15) - f[p]);
+    if constexpr (p == 0) {
+      fout[base] = S::template save<D, Q, 0>(fs);
+    } else {
+      const int ti = i + cx, tj = j + cy, tk = kk + cz;
+      int code = CENTER;
+      if constexpr (cx != 0) code += (ti < 0) ? -1 : (ti > 3 ? 1 : 0);
+      if constexpr (cy != 0) code += (tj < 0) ? -3 : (tj > 3 ? 3 : 0);
+      if constexpr (D == 3 && cz != 0) code += (tk < 0) ? -9 : (tk > 3 ? 9 : 0);
+      const int tgt = s_nb[slot][code];
+      const int tl = (ti & 3) + 4 * (tj & 3) + (D == 3 ? 16 * (tk & 3) : 0);
+      bool bounce = tgt < 0;
+      if constexpr (SOLID) bounce = bounce || ((s_sm[slot][code] >> tl) & 1ull);
+      if (!bounce) {
+        fout[(size_t)p * stride + (size_t)tgt * M + tl] = S::template save<D, Q, p>(fs);
+      } else {
+        R v = fs;   // NONE (interface) or solid: halfway bounce-back
+        if (tgt <= -2) {
+          const int face = -2 - tgt;
+          if (prm.faces.kind[face] == FACE_OUTLET) {
+            R cu = R(0);
+            if constexpr (cx != 0) cu += cx > 0 ? ux : -ux;
+            if constexpr (cy != 0) cu += cy > 0 ? uy : -uy;
+            if constexpr (cz != 0) cu += cz > 0 ? uz : -uz;
+            constexpr double wp = V::w[p];
+            v = -fs + R(2.0 * wp * prm.faces.rho_w[face]) *
+                          (R(1) + R(4.5) * cu * cu - usq15);
+          } else {
+            v = fs + R(prm.faces.bb[face][p]);
+          }
+        }
+        fout[(size_t)pb * stride + base] = S::template save<D, Q, pb>(v);
+      }
+    }
+  });
+}
+
+// =========================================== coarse-to-fine linear interpolation
+// Per parent block: every parent cell rescales its populations to the fine
+// level (f_eq + (f - f_eq) r, Section 3.4.1) into shared memory; then, for
+// each child c, fine cell (I,J,K) takes the multilinear interpolant of the
+// 2^D parent cells of quadrant c at local coordinates -1/4 + I/2.  Writes the
+// ghost cells of every child (mode_all = 0) or every cell (mode_all = 1).
+template <int D, int Q, class T, bool SOLID>
+__global__ void __launch_bounds__(128)
+    k_interp(const int32_t* __restrict__ list, int n, const T* __restrict__ fpar,
+             T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
+             const uint32_t* __restrict__ nonemask, const uint64_t* __restrict__ solidmask,
+             double ratio, int mode_all) {
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int M = Block<D>::M;
+  constexpr int NC = Block<D>::NC;
+  constexpr int BPC = 128 / M;
+  __shared__ R sF[BPC][Q][M];
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int bi = blockIdx.x * BPC + slot;
+  const bool valid = bi < n;
+  int P = 0;
+  if (valid) {
+    P = list[bi];
+    const size_t base = (size_t)P * M + l;
+    R f[Q];
+    static_for<0, Q>([&](auto Pp) {
+      f[Pp] = S::template load<D, Q, Pp>(fpar[(size_t)Pp * stride + base]);
+    });
+    R rho, ux, uy, uz;
+    moments<D, Q>(f, rho, ux, uy, uz);
+    const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+    const R r = R(ratio);
+    static_for<0, Q>([&](auto Pp) {
+      const R e = feq<D, Q, Pp>(rho, ux, uy, uz, usq15);
+      sF[slot][Pp][l] = e + (f[Pp] - e) * r;
+    });
+  }
+  __syncthreads();
+  if (!valid) return;
+  const int i = Block<D>::ci(l), j = Block<D>::cj(l), k = Block<D>::ck(l);
+  const R x = R(-0.25) + R(0.5) * R(i);
+  const R y = R(-0.25) + R(0.5) * R(j);
+  const R z = R(-0.25) + R(0.5) * R(k);
+  R wgt[NC];
+#pragma unroll
+  for (int a = 0; a < NC; ++a) {
+    R wv = ((a & 1) ? x : R(1) - x) * ((a & 2) ? y : R(1) - y);
+    if (D == 3) wv *= (a & 4) ? z : R(1) - z;
+    wgt[a] = wv;
+  }
+  const int c0 = child0[P];
+  for (int c = 0; c < NC; ++c) {
+    const int ch = c0 + c;
+    if (!mode_all) {
+      const uint32_t nm = nonemask[ch];
+      if (nm == 0u) continue;
+      if (cell_class<D>(nm, i, j, k) != CLS_GHOST) continue;
+    }
+    if constexpr (SOLID) {
+      if ((__ldg(solidmask + ch) >> l) & 1ull) continue;
+    }
+    const int qx = c & 1, qy = (c >> 1) & 1, qz = (c >> 2) & 1;
+    int corner[NC];
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+      corner[a] = Block<D>::cell(2 * qx + (a & 1), 2 * qy + ((a >> 1) & 1),
+                                 2 * qz + ((a >> 2) & 1));
+    const size_t base = (size_t)ch * M + l;
+    static_for<0, Q>([&](auto Pp) {
+      R v = R(0);
+#pragma unroll
+      for (int a = 0; a < NC; ++a) v += wgt[a] * sF[slot][Pp][corner[a]];
+      fch[(size_t)Pp * stride + base] = S::template save<D, Q, Pp>(v);
+    });
+  }
+}
+
+// ===================================================== fine-to-coarse averaging
+// One thread per parent cell: the 2^D fine children (all of one child block)
+// are rescaled to the coarse level (f_eq + (f - f_eq) r, Section 3.4.3) and
+// averaged.  mode_sync = 0 writes parent cells over interface children;
+// mode_sync = 1 writes every parent cell whose children are not ghosts.
+template <int D, int Q, class T, bool SOLID>
+__global__ void __launch_bounds__(128)
+    k_average(const int32_t* __restrict__ list, int n, T* __restrict__ fpar,
+              const T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
+              const uint32_t* __restrict__ nonemask, const int32_t* __restrict__ status,
+              const uint64_t* __restrict__ solidmask, double ratio, int mode_sync) {
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int M = Block<D>::M;
+  constexpr int NC = Block<D>::NC;
+  constexpr int BPC = 128 / M;
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int bi = blockIdx.x * BPC + slot;
+  if (bi >= n) return;
+  const int P = list[bi];
+  if (mode_sync && status[P] < ST_REFINED) return;
+  const int i = Block<D>::ci(l), j = Block<D>::cj(l), k = Block<D>::ck(l);
+  const int c = (i >> 1) + 2 * (j >> 1) + (D == 3 ? 4 * (k >> 1) : 0);
+  const int ch = child0[P] + c;
+  const int fi = 2 * (i & 1), fj = 2 * (j & 1), fk = 2 * (k & 1);
+  const int cls = cell_class<D>(nonemask[ch], fi, fj, fk);
+  if (!mode_sync && cls != CLS_INTERFACE) return;
+  if (mode_sync && cls == CLS_GHOST) return;
+  if constexpr (SOLID) {
+    if ((__ldg(solidmask + P) >> l) & 1ull) return;
+  }
+  const R r = R(ratio);
+  R acc[Q];
+  static_for<0, Q>([&](auto Pp) { acc[Pp] = R(0); });
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    const int fl = Block<D>::cell(fi + (s & 1), fj + ((s >> 1) & 1), fk + ((s >> 2) & 1));
+    const size_t base = (size_t)ch * M + fl;
+    R f[Q];
+    static_for<0, Q>([&](auto Pp) {
+      f[Pp] = S::template load<D, Q, Pp>(fch[(size_t)Pp * stride + base]);
+    });
+    R rho, ux, uy, uz;
+    moments<D, Q>(f, rho, ux, uy, uz);
+    const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+    static_for<0, Q>([&](auto Pp) {
+      const R e = feq<D, Q, Pp>(rho, ux, uy, uz, usq15);
+      acc[Pp] += e + (f[Pp] - e) * r;
+    });
+  }
+  const size_t base = (size_t)P * M + l;
+  const R inv = R(1) / R(NC);
+  static_for<0, Q>([&](auto Pp) {
+    fpar[(size_t)Pp * stride + base] = S::template save<D, Q, Pp>(acc[Pp] * inv);
+  });
+}
+
+// ================================================================ criterion
+// Vorticity magnitude from block-local first-order differences (forward, and
+// backward at the last cell), block maximum of |w|^2, desired level of
+// Algorithm 3 (eps < T evaluated as |w|^2 < 4^T), mark: +1 for a leaf with
+// L_des > L, -1 for a REFINED block with L_des <= L.
+template <int D, int Q, class T>
+__global__ void __launch_bounds__(128)
+    k_criterion(const int32_t* __restrict__ list, int n, const T* __restrict__ f, size_t stride,
+                const int32_t* __restrict__ status, int level, int lmax, double inv_dx,
+                int n_start, int n_inc, int8_t* __restrict__ marks, double* __restrict__ w2out) {
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int M = Block<D>::M;
+  constexpr int BPC = 128 / M;
+  __shared__ R su[BPC][3][M];
+  __shared__ R sw[4];
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int bi = blockIdx.x * BPC + slot;
+  const bool valid = bi < n;
+  int b = 0;
+  if (valid) {
+    b = list[bi];
+    R fl[Q];
+    static_for<0, Q>([&](auto P) {
+      fl[P] = S::template load<D, Q, P>(f[(size_t)P * stride + (size_t)b * M + l]);
+    });
+    R rho, ux, uy, uz;
+    moments<D, Q>(fl, rho, ux, uy, uz);
+    su[slot][0][l] = ux;
+    su[slot][1][l] = uy;
+    su[slot][2][l] = uz;
+  }
+  __syncthreads();
+  R w2 = R(0);
+  if (valid) {
+    const int i = Block<D>::ci(l), j = Block<D>::cj(l), k = Block<D>::ck(l);
+    // d(u_c)/d(axis) in lattice differences
+    auto diff = [&](int comp, int axis) -> R {
+      const int pos = axis == 0 ? i : (axis == 1 ? j : k);
+      const int st = axis == 0 ? 1 : (axis == 1 ? 4 : 16);
+      return pos < 3 ? su[slot][comp][l + st] - su[slot][comp][l]
+                     : su[slot][comp][l] - su[slot][comp][l - st];
+    };
+    const R s = R(inv_dx);
+    if constexpr (D == 2) {
+      const R wz = (diff(1, 0) - diff(0, 1)) * s;
+      w2 = wz * wz;
+    } else {
+      const R wx = (diff(2, 1) - diff(1, 2)) * s;
+      const R wy = (diff(0, 2) - diff(2, 0)) * s;
+      const R wz = (diff(1, 0) - diff(0, 1)) * s;
+      w2 = wx * wx + wy * wy + wz * wz;
+    }
+  }
+  // block maximum
+  constexpr int START = M < 32 ? M / 2 : 16;
+#pragma unroll
+  for (int off = START; off > 0; off >>= 1) w2 = max(w2, __shfl_xor_sync(0xffffffffu, w2, off));
+  if constexpr (M > 32) {
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) sw[warp] = w2;
+    __syncthreads();
+    w2 = max(sw[2 * slot], sw[2 * slot + 1]);
+  }
+  if (!valid || l != 0) return;
+  const double w2d = (double)w2;
+  int ldes = lmax - 1;
+  for (int p = 1; p < lmax; ++p) {
+    const int T_ = n_start - p * n_inc;
+    if (T_ > 1 || w2d < ldexp(1.0, 2 * T_)) ldes = (lmax - 1) - p;
+  }
+  const int st = status[b];
+  int8_t m = 0;
+  if (st == ST_UNREFINED && ldes > level) m = 1;
+  else if (st == ST_REFINED && ldes <= level) m = -1;
+  marks[b] = m;
+  if (w2out) w2out[b] = w2d;
+}
+
+// ============================================================ exports/imports
+template <int D, int Q, class T>
+__global__ void k_export_f(int64_t cap, int64_t b0, int64_t nb, const T* __restrict__ fa,
+                           const T* __restrict__ fb, unsigned cur,
+                           const int32_t* __restrict__ level, double* __restrict__ out) {
+  constexpr int M = Block<D>::M;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nb * M) return;
+  const int64_t b = b0 + g / M;
+  const int L = level[b];
+  const size_t stride = (size_t)cap * M;
+  const size_t src = (size_t)b0 * M + g;
+  const T* f = (L >= 0 && ((cur >> L) & 1u)) ? fb : fa;
+  static_for<0, Q>([&](auto P) {
+    out[(size_t)P * nb * M + g] =
+        L >= 0 ? (double)Store<T>::template load<D, Q, P>(f[(size_t)P * stride + src]) : 0.0;
+  });
+}
+
+template <int D, int Q, class T>
+__global__ void k_import_f(int64_t cap, int64_t b0, int64_t nb, T* __restrict__ fa,
+                           T* __restrict__ fb, unsigned cur, const int32_t* __restrict__ level,
+                           const double* __restrict__ in) {
+  using R = typename Store<T>::R;
+  constexpr int M = Block<D>::M;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nb * M) return;
+  const int64_t b = b0 + g / M;
+  const int L = level[b];
+  if (L < 0) return;
+  const size_t stride = (size_t)cap * M;
+  const size_t dst = (size_t)b0 * M + g;
+  T* f = ((cur >> L) & 1u) ? fb : fa;
+  static_for<0, Q>([&](auto P) {
+    f[(size_t)P * stride + dst] =
+        Store<T>::template save<D, Q, P>((R)in[(size_t)P * nb * M + g]);
+  });
+}
+
+template <int D, int Q, class T>
+__global__ void k_export_rho_u(int64_t cap, int64_t b0, int64_t nb, const T* __restrict__ fa,
+                               const T* __restrict__ fb, unsigned cur,
+                               const int32_t* __restrict__ level, double* __restrict__ out) {
+  using R = typename Store<T>::R;
+  constexpr int M = Block<D>::M;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nb * M) return;
+  const int64_t b = b0 + g / M;
+  const int L = level[b];
+  double* o = out + (size_t)g * (1 + D);
+  if (L < 0) {
+    for (int a = 0; a <= D; ++a) o[a] = 0.0;
+    return;
+  }
+  const size_t stride = (size_t)cap * M;
+  const size_t src = (size_t)b0 * M + g;
+  const T* f = ((cur >> L) & 1u) ? fb : fa;
+  R fl[Q];
+  static_for<0, Q>([&](auto P) {
+    fl[P] = Store<T>::template load<D, Q, P>(f[(size_t)P * stride + src]);
+  });
+  R rho, ux, uy, uz;
+  moments<D, Q>(fl, rho, ux, uy, uz);
+  o[0] = rho;
+  o[1] = ux;
+  o[2] = uy;
+  if (D == 3) o[3] = uz;
+}
+
+template <int D, int Q, class T>
+__global__ void k_init_rest(int64_t cap, T* __restrict__ f) {
+  using R = typename Store<T>::R;
+  constexpr int M = Block<D>::M;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= cap * M) return;
+  const size_t stride = (size_t)cap * M;
+  static_for<0, Q>([&](auto P) {
+    constexpr double wp = VS<D, Q>::w[P];
+    f[(size_t)P * stride + g] = Store<T>::template save<D, Q, P>(R(wp));
+  });
+}
+
+// ------------------------------------------------------- block reductions
+template <int NV>
+__device__ __forceinline__ void block_sum_store(double (&v)[NV], double* out) {
+  __shared__ double sred[NV][32];
+#pragma unroll
+  for (int a = 0; a < NV; ++a)
+    for (int off = 16; off > 0; off >>= 1) v[a] += __shfl_xor_sync(0xffffffffu, v[a], off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int a = 0; a < NV; ++a) sred[a][warp] = v[a];
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int a = 0; a < NV; ++a) {
+      double x = lane < nw ? sred[a][lane] : 0.0;
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+      if (lane == 0) out[(size_t)blockIdx.x * NV + a] = x;
+    }
+  }
+}
+
+// FP64 audit of mass and momentum over leaf cells (grid-stride, fixed grid).
+template <int D, int Q, class T>
+__global__ void __launch_bounds__(256)
+    k_mass_partial(int64_t cap, const T* __restrict__ fa, const T* __restrict__ fb, unsigned cur,
+                   const int32_t* __restrict__ level, const int32_t* __restrict__ status,
+                   double* __restrict__ partial) {
+  using R = typename Store<T>::R;
+  constexpr int M = Block<D>::M;
+  const size_t stride = (size_t)cap * M;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < cap * M;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = g / M;
+    if (status[b] != ST_UNREFINED) continue;
+    const int L = level[b];
+    const T* f = ((cur >> L) & 1u) ? fb : fa;
+    double r = 0, jx = 0, jy = 0, jz = 0;
+    static_for<0, Q>([&](auto P) {
+      const double v = (double)Store<T>::template load<D, Q, P>(f[(size_t)P * stride + g]);
+      constexpr int cx = VS<D, Q>::cx[P], cy = VS<D, Q>::cy[P], cz = VS<D, Q>::cz[P];
+      r += v;
+      jx += cx * v;
+      jy += cy * v;
+      jz += cz * v;
+    });
+    const double vol = ldexp(1.0, -D * L);
+    acc[0] += r * vol;
+    acc[1] += jx * vol;
+    acc[2] += jy * vol;
+    acc[3] += jz * vol;
+  }
+  block_sum_store<4>(acc, partial);
+}
+
+// Momentum-exchange force: F = 2 dx^D sum over fluid cells and links p whose
+// target x + c_p is solid of f*_p c_p (Section 5.3), f* recomputed by BGK.
+template <int D, int Q, class T>
+__global__ void __launch_bounds__(256)
+    k_force_partial(const int32_t* __restrict__ list, int n, const T* __restrict__ f,
+                    size_t stride, const int32_t* __restrict__ nbr,
+                    const int32_t* __restrict__ status, const uint64_t* __restrict__ solidmask,
+                    double omega, double dx, double* __restrict__ partial) {
+  using V = VS<D, Q>;
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int M = Block<D>::M;
+  constexpr int BPC = 256 / M;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int bi0 = blockIdx.x * BPC; bi0 < n; bi0 += gridDim.x * BPC) {
+    const int slot = threadIdx.x / M, l = threadIdx.x - slot * M;
+    const int bi = bi0 + slot;
+    if (bi >= n) continue;
+    const int b = list[bi];
+    if (status[b] != ST_UNREFINED) continue;
+    if ((solidmask[b] >> l) & 1ull) continue;
+    R fl[Q];
+    static_for<0, Q>([&](auto P) {
+      fl[P] = S::template load<D, Q, P>(f[(size_t)P * stride + (size_t)b * M + l]);
+    });
+    R rho, ux, uy, uz;
+    moments<D, Q>(fl, rho, ux, uy, uz);
+    const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+    const int i = Block<D>::ci(l), j = Block<D>::cj(l), k = Block<D>::ck(l);
+    static_for<1, Q>([&](auto P) {
+      constexpr int p = P;
+      constexpr int cx = V::cx[p], cy = V::cy[p], cz = V::cz[p];
+      const int ti = i + cx, tj = j + cy, tk = k + cz;
+      const int sx = ti < 0 ? -1 : (ti > 3 ? 1 : 0);
+      const int sy = tj < 0 ? -1 : (tj > 3 ? 1 : 0);
+      const int sz = tk < 0 ? -1 : (tk > 3 ? 1 : 0);
+      const int code = (sx + 1) + 3 * (sy + 1) + (D == 3 ? 9 * (sz + 1) : 0);
+      const int tb = nbr[(size_t)b * NBR_STRIDE + geo_to_k<D>(code)];
+      if (tb < 0) return;
+      const int tl = (ti & 3) + 4 * (tj & 3) + (D == 3 ? 16 * (tk & 3) : 0);
+      if (!((solidmask[tb] >> tl) & 1ull)) return;
+      const R fs = fl[p] + R(omega) * (feq<D, Q, p>(rho, ux, uy, uz, usq15) - fl[p]);
+      acc[0] += (double)fs * cx;
+      acc[1] += (double)fs * cy;
+      acc[2] += (double)fs * cz;
+    });
+  }
+  const double scale = 2.0 * pow(dx, (double)D);
+  for (int a = 0; a < 3; ++a) acc[a] *= scale;
+  block_sum_store<3>(acc, partial);
+}
+
+// =============================================================== launchers
+inline int grid_for(int64_t n, int per) { return (int)((n + per - 1) / per); }
+
+template <int D, int Q, class T>
+struct Launch {
+  static constexpr int M = Block<D>::M;
+  static void collide_stream(cudaStream_t s, const int32_t* list, int n, const void* fin,
+                             void* fout, const int32_t* nbr, const uint64_t* sm,
+                             const StepParams& prm, bool solid) {
+    if (n <= 0) return;
+    const int grid = grid_for(n, 256 / M);
+    if (solid && D == 3)
+      k_collide_stream<D, Q, T, true><<<grid, 256, 0, s>>>(list, n, (const T*)fin, (T*)fout,
+                                                          nbr, sm, prm);
+    else
+      k_collide_stream<D, Q, T, false><<<grid, 256, 0, s>>>(list, n, (const T*)fin, (T*)fout,
+                                                           nbr, sm, prm);
+  }
+  static void interp(cudaStream_t s, const int32_t* list, int n, const void* fpar, void* fch,
+                     size_t stride, const int32_t* child0, const uint32_t* nm, const uint64_t* sm,
+                     double ratio, int mode_all, bool solid) {
+    if (n <= 0) return;
+    const int grid = grid_for(n, 128 / M);
+    if (solid && D == 3)
+      k_interp<D, Q, T, true><<<grid, 128, 0, s>>>(list, n, (const T*)fpar, (T*)fch, stride,
+                                                  child0, nm, sm, ratio, mode_all);
+    else
+      k_interp<D, Q, T, false><<<grid, 128, 0, s>>>(list, n, (const T*)fpar, (T*)fch, stride,
+                                                   child0, nm, sm, ratio, mode_all);
+  }
+  static void average(cudaStream_t s, const int32_t* list, int n, void* fpar, const void* fch,
+                      size_t stride, const int32_t* child0, const uint32_t* nm,
+                      const int32_t* status, const uint64_t* sm, double ratio, int mode_sync,
+                      bool solid) {
+    if (n <= 0) return;
+    const int grid = grid_for(n, 128 / M);
+    if (solid && D == 3)
+      k_average<D, Q, T, true><<<grid, 128, 0, s>>>(list, n, (T*)fpar, (const T*)fch, stride,
+                                                   child0, nm, status, sm, ratio, mode_sync);
+    else
+      k_average<D, Q, T, false><<<grid, 128, 0, s>>>(list, n, (T*)fpar, (const T*)fch, stride,
+                                                    child0, nm, status, sm, ratio, mode_sync);
+  }
+  static void criterion(cudaStream_t s, const int32_t* list, int n, const void* f, size_t stride,
+                        const int32_t* status, int level, int lmax, double inv_dx, int ns, int ni,
+                        int8_t* marks, double* w2out) {
+    if (n <= 0) return;
+    k_criterion<D, Q, T><<<grid_for(n, 128 / M), 128, 0, s>>>(
+        list, n, (const T*)f, stride, status, level, lmax, inv_dx, ns, ni, marks, w2out);
+  }
+  static void export_f(cudaStream_t s, int64_t cap, int64_t b0, int64_t nb, const void* fa,
+                       const void* fb, unsigned cur, const int32_t* level, double* out) {
+    k_export_f<D, Q, T><<<grid_for(nb * M, 256), 256, 0, s>>>(cap, b0, nb, (const T*)fa,
+                                                               (const T*)fb, cur, level, out);
+  }
+  static void import_f(cudaStream_t s, int64_t cap, int64_t b0, int64_t nb, void* fa, void* fb,
+                       unsigned cur, const int32_t* level, const double* in) {
+    k_import_f<D, Q, T><<<grid_for(nb * M, 256), 256, 0, s>>>(cap, b0, nb, (T*)fa, (T*)fb, cur,
+                                                               level, in);
+  }
+  static void export_rho_u(cudaStream_t s, int64_t cap, int64_t b0, int64_t nb, const void* fa,
+                           const void* fb, unsigned cur, const int32_t* level, double* out) {
+    k_export_rho_u<D, Q, T><<<grid_for(nb * M, 256), 256, 0, s>>>(
+        cap, b0, nb, (const T*)fa, (const T*)fb, cur, level, out);
+  }
+  static void init_rest(cudaStream_t s, int64_t cap, void* f) {
+    k_init_rest<D, Q, T><<<grid_for(cap * M, 256), 256, 0, s>>>(cap, (T*)f);
+  }
+  static int mass_partial(cudaStream_t s, int64_t cap, const void* fa, const void* fb,
+                          unsigned cur, const int32_t* level, const int32_t* status,
+                          double* partial) {
+    const int grid = 152 * 4;
+    k_mass_partial<D, Q, T><<<grid, 256, 0, s>>>(cap, (const T*)fa, (const T*)fb, cur, level,
+                                                 status, partial);
+    return grid;
+  }
+  static int force_partial(cudaStream_t s, const int32_t* list, int n, const void* f,
+                           size_t stride, const int32_t* nbr, const int32_t* status,
+                           const uint64_t* sm, double omega, double dx, double* partial) {
+    const int grid = 152 * 2;
+    k_force_partial<D, Q, T><<<grid, 256, 0, s>>>(list, n, (const T*)f, stride, nbr, status, sm,
+                                                  omega, dx, partial);
+    return grid;
+  }
+  static const LbmOps* ops() {
+    static const LbmOps o = {collide_stream, interp,   average,      criterion,
+                             export_f,       import_f, export_rho_u, init_rest,
+                             mass_partial,   force_partial};
+    return &o;
+  }
+};
+
+}  // namespace amr

@@ -1,0 +1,65 @@
+// Host-side interface to the per-velocity-set LBM kernels.  Each translation
+// unit lbm_*.cu instantiates the kernels of one velocity set for its storage
+// types and returns a table of launchers.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace amr {
+
+struct FaceParams {
+  int32_t kind[6];      // AMR_FACE_*
+  double rho_w[6];
+  double bb[6][27];     // bounce-back term -2 w_p rho_w (c_p . u_w) / cs^2
+};
+
+struct StepParams {
+  size_t stride;        // elements between population planes (capacity * M)
+  double omega;         // 1 / tau_L
+  FaceParams faces;
+};
+
+struct LbmOps {
+  // fused BGK collision + push streaming over `list` (active blocks of a level)
+  void (*collide_stream)(cudaStream_t, const int32_t* list, int n, const void* fin, void* fout,
+                         const int32_t* nbr, const uint64_t* solidmask, const StepParams& prm,
+                         bool solid);
+  // coarse-to-fine linear interpolation: parents in `list`, into their children
+  void (*interp)(cudaStream_t, const int32_t* list, int n, const void* fpar, void* fch,
+                 size_t stride, const int32_t* child0, const uint32_t* nonemask,
+                 const uint64_t* solidmask, double ratio, int mode_all, bool solid);
+  // fine-to-coarse averaging into the parents in `list`
+  void (*average)(cudaStream_t, const int32_t* list, int n, void* fpar, const void* fch,
+                  size_t stride, const int32_t* child0, const uint32_t* nonemask,
+                  const int32_t* status, const uint64_t* solidmask, double ratio, int mode_sync,
+                  bool solid);
+  // vorticity criterion marks (+1/-1/0) and block max |w|^2
+  void (*criterion)(cudaStream_t, const int32_t* list, int n, const void* f, size_t stride,
+                    const int32_t* status, int level, int lmax, double inv_dx, int n_start,
+                    int n_inc, int8_t* marks, double* w2out);
+  // exports / imports of the blocks b0 .. b0+nb-1; the buffer of block b is
+  // bufs[(cur >> level[b]) & 1].  AMR_F layout [Q][nb][M], AMR_RHO_U [nb][M][1+D]
+  void (*export_f)(cudaStream_t, int64_t cap, int64_t b0, int64_t nb, const void* fa,
+                   const void* fb, unsigned cur, const int32_t* level, double* out);
+  void (*import_f)(cudaStream_t, int64_t cap, int64_t b0, int64_t nb, void* fa, void* fb,
+                   unsigned cur, const int32_t* level, const double* in);
+  void (*export_rho_u)(cudaStream_t, int64_t cap, int64_t b0, int64_t nb, const void* fa,
+                       const void* fb, unsigned cur, const int32_t* level, double* out);
+  void (*init_rest)(cudaStream_t, int64_t cap, void* f);
+  // FP64 audit: per-CTA partial sums of rho V and rho u V over leaf cells into
+  // `partial` [grid][4]; returns the grid size used
+  int (*mass_partial)(cudaStream_t, int64_t cap, const void* fa, const void* fb, unsigned cur,
+                      const int32_t* level, const int32_t* status, double* partial);
+  // momentum-exchange force (Section 5.3) partial sums [grid][3] over the
+  // leaves in `list` (one level, buffer f); returns the grid size used
+  int (*force_partial)(cudaStream_t, const int32_t* list, int n, const void* f, size_t stride,
+                       const int32_t* nbr, const int32_t* status, const uint64_t* solidmask,
+                       double omega, double dx, double* partial);
+};
+
+const LbmOps* lbm_ops_d2q9(int storage);
+const LbmOps* lbm_ops_d3q19(int storage);
+const LbmOps* lbm_ops_d3q27(int storage);
+
+}  // namespace amr

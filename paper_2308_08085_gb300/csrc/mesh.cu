@@ -1,0 +1,668 @@
+// On-device mesh adaptation of the block forest (Sections 3.2-3.3, Alg. 1,
+// Alg. 2): root grid, eligibility of marks, 2:1 coarsening reversion, ID
+// allocation from the gap stack, removal, ID-set maintenance, statuses,
+// connectivity of children from their parents, cell classes, per-level work
+// lists.  Thrust calls of the paper are replaced by one stable compaction
+// primitive (CTA counts with __syncthreads_count, a single-CTA scan, and a
+// warp-ballot scatter).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "amr_internal.h"
+#include "lattice.cuh"
+
+namespace amr {
+
+constexpr int ST_INACTIVE = 0, ST_UNREFINED = 1, ST_REFINED = 2, ST_RWC = 3, ST_PERM = 4;
+
+// ====================================================== stable compaction
+template <class Pred>
+__global__ void __launch_bounds__(256) k_count(int n, Pred pred, int32_t* cta) {
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  const int flag = (i < n) && pred(i);
+  const int c = __syncthreads_count(flag);
+  if (threadIdx.x == 0) cta[blockIdx.x] = c;
+}
+
+// Exclusive scan of cta[0..nb) in place (one CTA of 1024 threads); writes the
+// total to *total.
+__global__ void __launch_bounds__(1024) k_scan(int nb, int32_t* cta, int32_t* total) {
+  __shared__ int32_t wsum[32];
+  __shared__ int32_t carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? cta[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int w = wsum[lane];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, off);
+        if (lane >= off) w += y;
+      }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    const int excl = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - v;
+    if (i < nb) cta[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+template <class Pred, class Val>
+__global__ void __launch_bounds__(256)
+    k_scatter(int n, Pred pred, Val val, const int32_t* cta, int32_t* out) {
+  __shared__ int32_t wsum[8];
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  const bool flag = (i < n) && pred(i);
+  const unsigned bal = __ballot_sync(0xffffffffu, flag);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) wsum[warp] = __popc(bal);
+  __syncthreads();
+  int off = cta[blockIdx.x];
+  for (int w = 0; w < warp; ++w) off += wsum[w];
+  if (flag) out[off + __popc(bal & ((1u << lane) - 1u))] = val(i);
+}
+
+struct VIdent {
+  __device__ int operator()(int i) const { return i; }
+};
+struct VList {
+  const int32_t* l;
+  __device__ int operator()(int i) const { return l[i]; }
+};
+struct PMarkEq {
+  const int8_t* m;
+  int v;
+  __device__ bool operator()(int i) const { return m[i] == v; }
+};
+struct PLevelEq {
+  const int32_t* list;
+  const int32_t* level;
+  int L;
+  __device__ bool operator()(int i) const { return level[list[i]] == L; }
+};
+struct PAlive {
+  const int32_t* list;
+  const int32_t* status;
+  __device__ bool operator()(int i) const { return status[list[i]] != ST_INACTIVE; }
+};
+struct PLeaf {
+  const int32_t* list;
+  const int32_t* status;
+  __device__ bool operator()(int i) const { return status[list[i]] == ST_UNREFINED; }
+};
+// leaves, and refined blocks with a child that has a NONE neighbour
+struct PActive {
+  const int32_t* list;
+  const int32_t* status;
+  const int32_t* child0;
+  const uint32_t* nonemask;
+  int nc;
+  bool parents_only;
+  __device__ bool operator()(int i) const {
+    const int b = list[i];
+    const int st = status[b];
+    if (st == ST_UNREFINED) return !parents_only;
+    if (st < ST_REFINED) return false;
+    const int c0 = child0[b];
+    for (int c = 0; c < nc; ++c)
+      if (nonemask[c0 + c] != 0u) return true;
+    return false;
+  }
+};
+
+// Launch a stable compaction of the indices i < n with pred(i), writing
+// val(i) to out in ascending i.  The count lands in dcount[slot]; when
+// `count` is non-null the stream is synchronised and it is returned.
+template <class Pred, class Val>
+static int compact(Instance* a, int64_t n, Pred pred, Val val, int32_t* out, int64_t* count,
+                   int slot = 0, bool scatter = true) {
+  cudaStream_t s = a->stream;
+  if (n <= 0) {
+    AMR_CUDA(cudaMemsetAsync(a->dcount + slot, 0, sizeof(int32_t), s));
+    if (count) *count = 0;
+    return AMR_OK;
+  }
+  const int nb = (int)((n + 255) / 256);
+  k_count<<<nb, 256, 0, s>>>((int)n, pred, a->cta);
+  k_scan<<<1, 1024, 0, s>>>(nb, a->cta, a->dcount + slot);
+  if (scatter) k_scatter<<<nb, 256, 0, s>>>((int)n, pred, val, a->cta, out);
+  AMR_CUDA(cudaGetLastError());
+  if (count) {
+    int32_t c = 0;
+    AMR_CUDA(cudaMemcpyAsync(&c, a->dcount + slot, sizeof(c), cudaMemcpyDeviceToHost, s));
+    AMR_CUDA(cudaStreamSynchronize(s));
+    *count = c;
+  }
+  return AMR_OK;
+}
+
+#define AMR_TRY(x)            \
+  do {                        \
+    int r_ = (x);             \
+    if (r_ != AMR_OK) return r_; \
+  } while (0)
+
+// ============================================================== root grid
+// Root blocks b = bx + nbx (by + nby bz) at 4 * (bx, by, bz); neighbours by
+// position with periodic wrap, else the wall code of the crossed faces.
+template <int D>
+__global__ void k_init_root(int64_t cap, int n_root, int nbx, int nby, int nbz,
+                            unsigned periodic, const int32_t* __restrict__ wall_code,
+                            int32_t* level, int32_t* status, int32_t* child0, int32_t* parent,
+                            float* X, int32_t* nbr, uint32_t* nonemask, int32_t* gap,
+                            int32_t* idset0) {
+  using NV = typename Nbr<D>::V;
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= cap) return;
+  if (b < cap - n_root) gap[b] = (int32_t)(cap - 1 - b);
+  child0[b] = NONE;
+  parent[b] = NONE;
+  nonemask[b] = 0u;
+  int32_t* row = nbr + (size_t)b * NBR_STRIDE;
+  if (b >= n_root) {
+    level[b] = -1;
+    status[b] = ST_INACTIVE;
+    X[3 * b] = X[3 * b + 1] = X[3 * b + 2] = 0.f;
+    for (int k = 0; k < NBR_STRIDE; ++k) row[k] = NONE;
+    return;
+  }
+  idset0[b] = (int32_t)b;
+  level[b] = 0;
+  status[b] = ST_UNREFINED;
+  const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((int64_t)nbx * nby));
+  X[3 * b] = 4.f * bx;
+  X[3 * b + 1] = 4.f * by;
+  X[3 * b + 2] = D == 3 ? 4.f * bz : 0.f;
+  for (int k = Nbr<D>::K; k < NBR_STRIDE; ++k) row[k] = NONE;
+  static_for<0, Nbr<D>::K>([&](auto P) {
+    constexpr int ex = NV::cx[P], ey = NV::cy[P], ez = NV::cz[P];
+    int pos[3] = {bx + ex, by + ey, bz + ez};
+    const int nbs[3] = {nbx, nby, nbz};
+    unsigned crossed = 0;
+    for (int ax = 0; ax < D; ++ax) {
+      if (pos[ax] < 0 || pos[ax] >= nbs[ax]) {
+        if ((periodic >> ax) & 1u) {
+          pos[ax] = (pos[ax] + nbs[ax]) % nbs[ax];
+        } else {
+          crossed |= 1u << (2 * ax + (pos[ax] < 0 ? 0 : 1));
+        }
+      }
+    }
+    row[P] = crossed ? wall_code[crossed]
+                     : (int32_t)(pos[0] + nbx * (pos[1] + (int64_t)nby * (D == 3 ? pos[2] : 0)));
+  });
+}
+
+// solid bits of the cells of the blocks in `list` (cell centre strictly inside
+// the prism [x0,x1] x [y0,y1] spanning z, root-cell units)
+template <int D>
+__global__ void k_solidmask(const int32_t* list, int n, const int32_t* level, const float* X,
+                            double x0, double x1, double y0, double y1, uint64_t* sm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = list ? list[i] : i;
+  const double h = 1.0 / (double)(1 << level[b]);
+  uint64_t m = 0;
+  for (int l = 0; l < Block<D>::M; ++l) {
+    const double cx = X[3 * b] + (Block<D>::ci(l) + 0.5) * h;
+    const double cy = X[3 * b + 1] + (Block<D>::cj(l) + 0.5) * h;
+    if (cx > x0 && cx < x1 && cy > y0 && cy < y1) m |= 1ull << l;
+  }
+  sm[b] = m;
+}
+
+// ============================================================ adaptation
+// keep a refine mark only for a leaf below L_max-1 without NONE neighbours,
+// a coarsen mark only for a REFINED block
+__global__ void k_eligible(int64_t cap, int8_t* marks, const int32_t* status,
+                           const int32_t* level, const uint32_t* nonemask, int lmax) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= cap) return;
+  const int m = marks[b];
+  const int st = status[b];
+  int8_t out = 0;
+  if (m > 0 && st == ST_UNREFINED && level[b] < lmax - 1 && nonemask[b] == 0u) out = 1;
+  else if (m < 0 && st == ST_REFINED) out = -1;
+  marks[b] = out;
+}
+
+__global__ void k_clear_refine(int64_t cap, int8_t* marks) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < cap && marks[b] == 1) marks[b] = 0;
+}
+
+// Step 3: a coarsen mark is reverted when a child has a same-level neighbour
+// (any direction, including itself) that has children or is marked refine.
+__global__ void k_revert(int64_t cap, int8_t* marks, const int32_t* child0, const int32_t* nbr,
+                         int nk, int nc) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= cap || marks[b] != -1) return;
+  const int c0 = child0[b];
+  bool violating = false;
+  for (int c = 0; c < nc && !violating; ++c) {
+    const int32_t* row = nbr + (size_t)(c0 + c) * NBR_STRIDE;
+    for (int k = 0; k < nk; ++k) {
+      const int nb = row[k];
+      if (nb >= 0 && (child0[nb] >= 0 || marks[nb] == 1)) {
+        violating = true;
+        break;
+      }
+    }
+  }
+  if (violating) marks[b] = 0;
+}
+
+// Steps 2 + 4 (Alg. 1): group i of N_c IDs popped from the gap stack top goes
+// to the i-th refine-marked block; child c = head + c at X_P + offset * w.
+template <int D>
+__global__ void k_alloc(const int32_t* R, int nR, const int32_t* gap, int64_t n_gaps,
+                        int32_t* child0, int32_t* level, float* X, int32_t* status,
+                        int32_t* parent, int32_t* err) {
+  constexpr int NC = Block<D>::NC;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nR * NC) return;
+  const int i = t / NC, c = t - i * NC;
+  const int P = R[i];
+  const int64_t top = n_gaps - 1 - (int64_t)i * NC;
+  const int head = gap[top];
+  const int ch = head + c;
+  if (gap[top - c] != ch) atomicExch(err, 1);   // groups must stay contiguous
+  if (c == 0) child0[P] = head;
+  const int lq = level[P] + 1;
+  const float w = 4.f / (float)(1 << lq);
+  level[ch] = lq;
+  X[3 * ch] = X[3 * P] + (float)(c & 1) * w;
+  X[3 * ch + 1] = X[3 * P + 1] + (float)((c >> 1) & 1) * w;
+  X[3 * ch + 2] = X[3 * P + 2] + (D == 3 ? (float)((c >> 2) & 1) * w : 0.f);
+  status[ch] = ST_UNREFINED;
+  child0[ch] = NONE;
+  parent[ch] = P;
+}
+
+// Step 5: freed child IDs, listed by (level, parent, child), are appended to
+// the gap stack in reverse so that later pops return them in that order.
+template <int D>
+__global__ void k_push_gaps(const int32_t* CL, int n, const int32_t* child0, int32_t* gap,
+                            int64_t base, int64_t total, int64_t off) {
+  constexpr int NC = Block<D>::NC;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * NC) return;
+  const int i = t / NC, c = t - i * NC;
+  const int64_t idx = off + (int64_t)i * NC + c;
+  gap[base + total - 1 - idx] = child0[CL[i]] + c;
+}
+
+template <int D>
+__global__ void k_remove_children(const int32_t* C, int n, const int32_t* child0,
+                                  int32_t* status, int32_t* level, int32_t* parent,
+                                  int32_t* nbr, uint32_t* nonemask) {
+  constexpr int NC = Block<D>::NC;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * NC) return;
+  const int i = t / NC, c = t - i * NC;
+  const int ch = child0[C[i]] + c;
+  status[ch] = ST_INACTIVE;
+  level[ch] = -1;
+  parent[ch] = NONE;
+  nonemask[ch] = 0u;
+  for (int k = 0; k < NBR_STRIDE; ++k) nbr[(size_t)ch * NBR_STRIDE + k] = NONE;
+}
+
+__global__ void k_finish_coarsened(const int32_t* C, int n, int32_t* child0, int32_t* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  child0[C[i]] = NONE;
+  status[C[i]] = ST_UNREFINED;
+}
+
+__global__ void k_set_status(const int32_t* list, int n, int32_t* status, int v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) status[list[i]] = v;
+}
+
+template <int D>
+__global__ void k_append_children(const int32_t* R, int n, const int32_t* child0, int32_t* out) {
+  constexpr int NC = Block<D>::NC;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * NC) return;
+  const int i = t / NC, c = t - i * NC;
+  out[t] = child0[R[i]] + c;
+}
+
+// Step 7: a refined block with a refined child is REFINED_WITH_CHILD.
+__global__ void k_branch_leaf(int64_t cap, int32_t* status, const int32_t* child0, int nc) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= cap) return;
+  const int st = status[b];
+  if (st != ST_REFINED && st != ST_RWC) return;
+  const int c0 = child0[b];
+  bool any = false;
+  for (int c = 0; c < nc; ++c) any |= status[c0 + c] >= ST_REFINED;
+  status[b] = any ? ST_RWC : ST_REFINED;
+}
+
+// Step 8 (Alg. 2): neighbours of a child from its parent's neighbours.  Child c
+// at (cx,cy,cz) in {0,1}^D looks in direction e at position c + e in
+// {-1..2}^D of its parent's 2x2(x2) neighbourhood: the parent-level direction
+// is floor((c+e)/2) and the child index there is (c+e) mod 2.  A parent-level
+// neighbour without children gives NONE; wall codes pass through.
+template <int D>
+__global__ void k_relink(const int32_t* list, int n, const int32_t* parent,
+                         const int32_t* child0, int32_t* nbr, uint32_t* nonemask) {
+  using NV = typename Nbr<D>::V;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int X = list[i];
+  const int P = parent[X];
+  const int c = X - child0[P];
+  const int cxyz[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+  const int32_t* prow = nbr + (size_t)P * NBR_STRIDE;
+  int32_t* row = nbr + (size_t)X * NBR_STRIDE;
+  uint32_t nm = 0u;
+  static_for<0, Nbr<D>::K>([&](auto K) {
+    constexpr int ex = NV::cx[K], ey = NV::cy[K], ez = NV::cz[K];
+    const int e[3] = {ex, ey, ez};
+    int code = 0, sub = 0, mul = 1, sub_mul = 1;
+    for (int ax = 0; ax < D; ++ax) {
+      const int t = cxyz[ax] + e[ax];
+      const int s = t < 0 ? -1 : (t > 1 ? 1 : 0);
+      code += (s + 1) * mul;
+      sub += (t - 2 * s) * sub_mul;
+      mul *= 3;
+      sub_mul *= 2;
+    }
+    int kp = 0;
+    static_for<0, Nbr<D>::K>([&](auto J) {
+      constexpr int jcode = (NV::cx[J] + 1) + 3 * (NV::cy[J] + 1) + (D == 3 ? 9 * (NV::cz[J] + 1) : 0);
+      if (jcode == code) kp = J;
+    });
+    const int pn = prow[kp];
+    int v;
+    if (pn >= 0) {
+      const int pc = child0[pn];
+      v = pc >= 0 ? pc + sub : NONE;
+    } else {
+      v = pn;
+    }
+    row[K] = v;
+    if (v == NONE) nm |= 1u << K;
+  });
+  nonemask[X] = nm;
+}
+
+// ================================================================ exports
+template <int D>
+__global__ void k_export_nbr(int64_t cap, const int32_t* nbr, const int32_t* child0, int mode,
+                             int32_t* out) {
+  constexpr int K = Nbr<D>::K;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cap * K) return;
+  const int64_t b = t / K;
+  const int k = (int)(t - b * K);
+  const int v = nbr[(size_t)b * NBR_STRIDE + k];
+  if (mode == 0) out[t] = v;
+  else out[t] = v <= -2 ? v : (v >= 0 ? child0[v] : NONE);
+}
+
+template <int D>
+__global__ void k_export_masks(int64_t cap, const int32_t* status, const uint32_t* nonemask,
+                               uint8_t* out) {
+  constexpr int M = Block<D>::M;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cap * M) return;
+  const int64_t b = t / M;
+  const int l = (int)(t - b * M);
+  out[t] = status[b] == ST_INACTIVE
+               ? 0
+               : (uint8_t)cell_class<D>(nonemask[b], Block<D>::ci(l), Block<D>::cj(l),
+                                        Block<D>::ck(l));
+}
+
+__global__ void k_export_coords(int64_t cap, int dim, const float* X, double* out) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= cap) return;
+  for (int a = 0; a < dim; ++a) out[b * dim + a] = (double)X[3 * b + a];
+}
+
+// ============================================================ host side
+static inline int blocks_for(int64_t n, int t = 256) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
+
+template <int D>
+static int init_root_t(Instance* a) {
+  cudaStream_t s = a->stream;
+  unsigned periodic = 0;
+  for (int ax = 0; ax < D; ++ax)
+    if (a->cfg.faces[2 * ax].kind == AMR_FACE_PERIODIC) periodic |= 1u << ax;
+  k_init_root<D><<<blocks_for(a->cap), 256, 0, s>>>(
+      a->cap, (int)a->n_root, a->nroot[0], a->nroot[1], a->nroot[2], periodic, a->wall_code,
+      a->level, a->status, a->child0, a->parent, a->X, a->nbr, a->nonemask, a->gap, a->idset);
+  AMR_CUDA(cudaGetLastError());
+  AMR_CUDA(cudaMemsetAsync(a->solidmask, 0, sizeof(uint64_t) * a->cap, s));
+  if (a->solid) {
+    k_solidmask<D><<<blocks_for(a->n_root), 256, 0, s>>>(nullptr, (int)a->n_root, a->level, a->X,
+                                                         a->cfg.solid[0], a->cfg.solid[1],
+                                                         a->cfg.solid[2], a->cfg.solid[3],
+                                                         a->solidmask);
+    AMR_CUDA(cudaGetLastError());
+  }
+  a->n_gaps = a->cap - a->n_root;
+  for (int L = 0; L < a->lmax; ++L) a->n_ids[L] = 0;
+  a->n_ids[0] = a->n_root;
+  return mesh_refresh_lists(a);
+}
+
+int mesh_init_root(Instance* a) { return a->dim == 2 ? init_root_t<2>(a) : init_root_t<3>(a); }
+
+int mesh_refresh_lists(Instance* a) {
+  for (int L = 0; L < a->lmax; ++L) {
+    int32_t* ids = a->idset + (size_t)L * a->cap;
+    const int64_t n = a->n_ids[L];
+    PActive act{ids, a->status, a->child0, a->nonemask, a->nc, false};
+    PActive par{ids, a->status, a->child0, a->nonemask, a->nc, true};
+    AMR_TRY(compact(a, n, act, VList{ids}, a->active + (size_t)L * a->cap, &a->n_active[L]));
+    AMR_TRY(compact(a, n, par, VList{ids}, a->parents + (size_t)L * a->cap, &a->n_parents[L]));
+    AMR_TRY(compact(a, n, PLeaf{ids, a->status}, VIdent{}, nullptr, &a->n_leaves[L], 0, false));
+  }
+  return AMR_OK;
+}
+
+template <int D>
+static int adapt_t(Instance* a, amr_adapt_stats* st) {
+  constexpr int NC = Block<D>::NC;
+  cudaStream_t s = a->stream;
+  const int64_t cap = a->cap;
+  int32_t* R = a->tmp0;        // refine-marked blocks, ascending
+  int32_t* C = a->tmp1;        // coarsen-marked blocks, ascending
+  int32_t* W = a->tmp2;        // work list
+
+  k_eligible<<<blocks_for(cap), 256, 0, s>>>(cap, a->marks, a->status, a->level, a->nonemask,
+                                              a->lmax);
+  AMR_CUDA(cudaGetLastError());
+  int64_t nR = 0, nC = 0, nC0 = 0;
+  AMR_TRY(compact(a, cap, PMarkEq{a->marks, 1}, VIdent{}, R, &nR));
+  AMR_TRY(compact(a, cap, PMarkEq{a->marks, -1}, VIdent{}, nullptr, &nC0, 0, false));
+  st->n_marked_refine = nR;
+  st->n_marked_coarsen = nC0;
+  if (nR * NC > a->n_gaps) {
+    st->capacity_error = 1;
+    k_clear_refine<<<blocks_for(cap), 256, 0, s>>>(cap, a->marks);
+    nR = 0;
+  }
+  k_revert<<<blocks_for(cap), 256, 0, s>>>(cap, a->marks, a->child0, a->nbr, a->nk, NC);
+  AMR_CUDA(cudaGetLastError());
+  AMR_TRY(compact(a, cap, PMarkEq{a->marks, -1}, VIdent{}, C, &nC));
+  st->n_refined = nR;
+  st->n_coarsened = nC;
+  if (nR == 0 && nC == 0) return AMR_OK;
+
+  // refine-marked blocks grouped by level (stable): R_L = C + offR[L] below
+  std::vector<int64_t> nRL(a->lmax, 0), offR(a->lmax + 1, 0);
+  std::vector<int64_t> nCL(a->lmax, 0);
+
+  // allocation (reads the gap stack top before any push)
+  AMR_CUDA(cudaMemsetAsync(a->dcount + 8, 0, sizeof(int32_t), s));
+  if (nR > 0) {
+    k_alloc<D><<<blocks_for(nR * NC), 256, 0, s>>>(R, (int)nR, a->gap, a->n_gaps, a->child0,
+                                                    a->level, a->X, a->status, a->parent,
+                                                    a->dcount + 8);
+    AMR_CUDA(cudaGetLastError());
+  }
+  a->n_gaps -= nR * NC;
+  // gap pushes, level by level
+  int64_t off = 0;
+  for (int L = 0; L < a->lmax; ++L) {
+    AMR_TRY(compact(a, nC, PLevelEq{C, a->level, L}, VList{C}, W, &nCL[L]));
+    if (nCL[L] > 0) {
+      k_push_gaps<D><<<blocks_for(nCL[L] * NC), 256, 0, s>>>(W, (int)nCL[L], a->child0, a->gap,
+                                                              a->n_gaps, nC * NC, off);
+      AMR_CUDA(cudaGetLastError());
+    }
+    off += nCL[L] * NC;
+  }
+  if (nC > 0) {
+    k_remove_children<D><<<blocks_for(nC * NC), 256, 0, s>>>(C, (int)nC, a->child0, a->status,
+                                                              a->level, a->parent, a->nbr,
+                                                              a->nonemask);
+    k_finish_coarsened<<<blocks_for(nC), 256, 0, s>>>(C, (int)nC, a->child0, a->status);
+    AMR_CUDA(cudaGetLastError());
+  }
+  a->n_gaps += nC * NC;
+  if (nR > 0) {
+    k_set_status<<<blocks_for(nR), 256, 0, s>>>(R, (int)nR, a->status, ST_REFINED);
+    AMR_CUDA(cudaGetLastError());
+  }
+  // R grouped by level into C's storage (C is no longer needed)
+  for (int L = 0; L < a->lmax; ++L) {
+    AMR_TRY(compact(a, nR, PLevelEq{R, a->level, L}, VList{R}, C + offR[L], &nRL[L]));
+    offR[L + 1] = offR[L] + nRL[L];
+  }
+  // ID sets
+  for (int L = 1; L < a->lmax; ++L) {
+    int32_t* ids = a->idset + (size_t)L * cap;
+    int64_t kept = 0;
+    AMR_TRY(compact(a, a->n_ids[L], PAlive{ids, a->status}, VList{ids}, W, &kept));
+    const int64_t nadd = nRL[L - 1] * NC;
+    if (nadd > 0) {
+      k_append_children<D><<<blocks_for(nadd), 256, 0, s>>>(C + offR[L - 1], (int)nRL[L - 1],
+                                                            a->child0, W + kept);
+      AMR_CUDA(cudaGetLastError());
+    }
+    if (kept + nadd > 0)
+      AMR_CUDA(cudaMemcpyAsync(ids, W, sizeof(int32_t) * (kept + nadd), cudaMemcpyDeviceToDevice, s));
+    a->n_ids[L] = kept + nadd;
+  }
+  k_branch_leaf<<<blocks_for(cap), 256, 0, s>>>(cap, a->status, a->child0, NC);
+  AMR_CUDA(cudaGetLastError());
+  for (int L = 1; L < a->lmax; ++L) {
+    if (a->n_ids[L] == 0) continue;
+    k_relink<D><<<blocks_for(a->n_ids[L]), 128, 0, s>>>(a->idset + (size_t)L * cap,
+                                                        (int)a->n_ids[L], a->parent, a->child0,
+                                                        a->nbr, a->nonemask);
+    AMR_CUDA(cudaGetLastError());
+  }
+  // solid bits of the new children, then every cell of them from the parents
+  for (int L = 0; L + 1 < a->lmax; ++L) {
+    if (nRL[L] == 0) continue;
+    const int64_t nnew = nRL[L] * NC;
+    k_append_children<D><<<blocks_for(nnew), 256, 0, s>>>(C + offR[L], (int)nRL[L], a->child0, W);
+    if (a->solid)
+      k_solidmask<D><<<blocks_for(nnew), 256, 0, s>>>(W, (int)nnew, a->level, a->X,
+                                                      a->cfg.solid[0], a->cfg.solid[1],
+                                                      a->cfg.solid[2], a->cfg.solid[3],
+                                                      a->solidmask);
+    AMR_CUDA(cudaGetLastError());
+    const double ratio = a->tau[L + 1] / (2.0 * a->tau[L]);
+    a->ops->interp(s, C + offR[L], (int)nRL[L], a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(),
+                   a->child0, a->nonemask, a->solidmask, ratio, 1, a->solid);
+    AMR_CUDA(cudaGetLastError());
+  }
+  int32_t err = 0;
+  AMR_CUDA(cudaMemcpyAsync(&err, a->dcount + 8, sizeof(err), cudaMemcpyDeviceToHost, s));
+  AMR_CUDA(cudaStreamSynchronize(s));
+  if (err) {
+    set_error("gap stack lost its group structure");
+    return AMR_E_INVAL;
+  }
+  return mesh_refresh_lists(a);
+}
+
+int mesh_adapt(Instance* a, bool /*external*/, amr_adapt_stats* st) {
+  return a->dim == 2 ? adapt_t<2>(a, st) : adapt_t<3>(a, st);
+}
+
+int64_t mesh_export_bytes(const Instance* a, int what) {
+  const int64_t cap = a->cap;
+  switch (what) {
+    case AMR_BLOCKS: return 4 * cap * 4;
+    case AMR_COORDS: return cap * a->dim * 8;
+    case AMR_NBR:
+    case AMR_NBR_CHILD: return cap * a->nk * 4;
+    case AMR_IDSETS: return (int64_t)a->lmax * cap * 4;
+    case AMR_GAPS: return cap * 4;
+    case AMR_MASKS: return cap * a->M;
+    default: return -1;
+  }
+}
+
+int mesh_export(Instance* a, int what, void* dst) {
+  cudaStream_t s = a->stream;
+  const int64_t cap = a->cap;
+  const bool d3 = a->dim == 3;
+  switch (what) {
+    case AMR_BLOCKS: {
+      int32_t* o = (int32_t*)dst;
+      AMR_CUDA(cudaMemcpyAsync(o, a->level, cap * 4, cudaMemcpyDeviceToDevice, s));
+      AMR_CUDA(cudaMemcpyAsync(o + cap, a->status, cap * 4, cudaMemcpyDeviceToDevice, s));
+      AMR_CUDA(cudaMemcpyAsync(o + 2 * cap, a->child0, cap * 4, cudaMemcpyDeviceToDevice, s));
+      AMR_CUDA(cudaMemcpyAsync(o + 3 * cap, a->parent, cap * 4, cudaMemcpyDeviceToDevice, s));
+      return AMR_OK;
+    }
+    case AMR_COORDS:
+      k_export_coords<<<blocks_for(cap), 256, 0, s>>>(cap, a->dim, a->X, (double*)dst);
+      break;
+    case AMR_NBR:
+    case AMR_NBR_CHILD: {
+      const int mode = what == AMR_NBR ? 0 : 1;
+      if (d3)
+        k_export_nbr<3><<<blocks_for(cap * 27), 256, 0, s>>>(cap, a->nbr, a->child0, mode, (int32_t*)dst);
+      else
+        k_export_nbr<2><<<blocks_for(cap * 9), 256, 0, s>>>(cap, a->nbr, a->child0, mode, (int32_t*)dst);
+      break;
+    }
+    case AMR_IDSETS:
+      AMR_CUDA(cudaMemcpyAsync(dst, a->idset, (size_t)a->lmax * cap * 4, cudaMemcpyDeviceToDevice, s));
+      return AMR_OK;
+    case AMR_GAPS:
+      AMR_CUDA(cudaMemcpyAsync(dst, a->gap, cap * 4, cudaMemcpyDeviceToDevice, s));
+      return AMR_OK;
+    case AMR_MASKS:
+      if (d3)
+        k_export_masks<3><<<blocks_for(cap * 64), 256, 0, s>>>(cap, a->status, a->nonemask, (uint8_t*)dst);
+      else
+        k_export_masks<2><<<blocks_for(cap * 16), 256, 0, s>>>(cap, a->status, a->nonemask, (uint8_t*)dst);
+      break;
+    default:
+      return AMR_E_INVAL;
+  }
+  AMR_CUDA(cudaGetLastError());
+  return AMR_OK;
+}
+
+}  // namespace amr

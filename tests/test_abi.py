@@ -1,0 +1,76 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports every
+symbol declared in include/amr.h, and rejects bad configurations on the host
+(no GPU call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "amr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(amr_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2308_08085_gb300 import build as b
+    from paper_2308_08085_gb300.amr import load_library
+    return load_library(b.build())
+
+
+def test_header_declares_abi():
+    syms = declared_symbols()
+    for s in ["amr_init", "amr_step", "amr_adapt", "amr_fields", "amr_free", "amr_arena_bytes",
+              "amr_set_fields", "amr_strerror"]:
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for s in declared_symbols():
+        assert hasattr(lib, s), s
+
+
+def test_config_struct_layout_matches_header(lib):
+    from paper_2308_08085_gb300.amr import AmrAdaptStats, AmrConfig, AmrKernelProfile
+    assert ctypes.sizeof(AmrConfig) == 344
+    assert ctypes.sizeof(AmrAdaptStats) == 56
+    assert ctypes.sizeof(AmrKernelProfile) == 64
+
+
+def test_arena_bytes_and_validation(lib):
+    from paper_2308_08085_gb300.amr import make_config
+    cfg = W.cavity(dim=3, q=19, n=16, max_levels=3)
+    c = make_config(cfg, "f32")
+    n = lib.amr_arena_bytes(ctypes.byref(c))
+    pops = 2 * cfg["max_blocks"] * 64 * 19 * 4
+    assert n >= pops and n < pops * 3 + (64 << 20)
+    # invalid: extents not a multiple of 4
+    bad = make_config(dict(cfg, nx=18), "f32")
+    assert lib.amr_arena_bytes(ctypes.byref(bad)) == 0
+    assert b"multiples of 4" in lib.amr_last_error()
+    # invalid: 16-bit storage in 2D
+    bad = make_config(W.cavity(dim=2, n=16), "bf16")
+    assert lib.amr_arena_bytes(ctypes.byref(bad)) == 0
+    # invalid: unpaired periodic face
+    cfg2 = W.periodic_box(dim=2, n=16)
+    cfg2["faces"][1] = ("noslip", (0, 0, 0))
+    assert lib.amr_arena_bytes(ctypes.byref(make_config(cfg2))) == 0
+    # capacity not aligned to child groups
+    cfg3 = W.cavity(dim=2, n=16)
+    cfg3["max_blocks"] += 1
+    assert lib.amr_arena_bytes(ctypes.byref(make_config(cfg3, "f64"))) == 0
+
+
+def test_init_rejects_small_arena_without_gpu(lib):
+    from paper_2308_08085_gb300.amr import AMR_E_ARENA, make_config
+    c = make_config(W.cavity(dim=2, n=16), "f64")
+    h = ctypes.c_void_p()
+    rc = lib.amr_init(ctypes.byref(c), ctypes.c_void_p(256), 1024, None, ctypes.byref(h))
+    assert rc == AMR_E_ARENA and not h.value

@@ -1,0 +1,287 @@
+"""GPU parity tests: the CUDA library (through its C ABI) against the CPU oracle
+on the same seeded inputs.
+
+Bars: integer results (block tables, neighbour tables, ID sets, gap stack,
+cell classes) bit-exact; fields relative L2 <= 1e-12 in FP64 and <= 1e-5 in
+FP32 (the FP32 bar also covers the rounding of the FP64 initial state)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.forest import Forest
+from oracle.lattice import equilibrium
+from oracle.solver import ForestLBM
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_08085_gb300 import build as b
+    b.build()
+
+
+def new_gpu(cfg, storage):
+    from paper_2308_08085_gb300 import AmrLBM
+    return AmrLBM(cfg, storage=storage)
+
+
+def randomize(ref, seed, noise=1e-3):
+    """Seeded random state (equilibrium of random rho, u plus noise) on every
+    active block of the oracle; solid cells keep the rest state."""
+    ids = np.array(ref.mesh.active_ids())
+    n = len(ids) * ref.m
+    rho, u = W.random_macro(seed, n, ref.dim)
+    f = equilibrium(ref.vs, rho, u) + W.random_noise(seed + 1, (n, ref.vs.q), noise)
+    f = f.reshape(len(ids), ref.m, ref.vs.q)
+    sol = ref.solid[ids]
+    f[sol] = ref.rest
+    ref.f[ids] = f
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def marks_tensor(m):
+    return torch.from_numpy(np.ascontiguousarray(m, dtype=np.int8)).cuda()
+
+
+# ------------------------------------------------------------ single level
+SINGLE = [
+    ("cavity2d", lambda: W.cavity(dim=2, q=9, n=20, ny=12, max_levels=1), ("f64", "f32")),
+    ("cavity3d_q19", lambda: W.cavity(dim=3, q=19, n=12, ny=8, nz=16, max_levels=1), ("f64", "f32")),
+    ("periodic3d_q27", lambda: W.periodic_box(dim=3, q=27, n=8, ny=12, nz=4), ("f64", "f32")),
+    ("cylinder_q19", lambda: W.channel_cylinder(q=19, nx=24, ny=16, nz=8, side=4, cx=8, cy=8,
+                                               max_levels=1), ("f64", "f32")),
+    ("cylinder_q27", lambda: W.channel_cylinder(q=27, nx=16, ny=12, nz=4, side=4, cx=6, cy=6,
+                                               max_levels=1), ("f64",)),
+]
+
+
+@pytest.mark.parametrize("name,mk,storages", SINGLE, ids=[c[0] for c in SINGLE])
+def test_single_level_collide_stream(name, mk, storages):
+    for storage in storages:
+        cfg = mk()
+        ref = ForestLBM(cfg)
+        randomize(ref, 21)
+        gpu = new_gpu(cfg, storage)
+        gpu.set_populations(ref.f)
+        for _ in range(5):
+            ref.step(1)
+            gpu.step(1)
+        ids = ref.mesh.active_ids()
+        got = gpu.populations()[ids]
+        err = rel_l2(got, ref.f[ids])
+        assert err <= TOL[storage], (storage, err)
+        gpu.close()
+
+
+# ----------------------------------------------------------- mesh tables
+MESHES = [
+    ("2d_cavity_3x3", lambda: W.cavity(dim=2, n=12, max_levels=4, max_blocks=9 * 40)),
+    ("2d_periodic_2x3", lambda: W.periodic_box(dim=2, n=8, ny=12, max_levels=3, max_blocks=200)),
+    ("3d_cavity_2x2x2", lambda: W.cavity(dim=3, n=8, max_levels=3, max_blocks=8 * 30)),
+    ("3d_periodic_3x2x2", lambda: W.periodic_box(dim=3, n=12, ny=8, nz=8, max_levels=3,
+                                                 max_blocks=12 * 25)),
+]
+
+
+def compare_tables(gpu, mesh: Forest):
+    cap = mesh.cap
+    blk = gpu.blocks()
+    assert np.array_equal(blk["level"], mesh.level)
+    assert np.array_equal(blk["status"], mesh.status)
+    assert np.array_equal(blk["child0"], mesh.child0)
+    assert np.array_equal(blk["parent"], mesh.parent)
+    assert np.array_equal(gpu.nbr(), mesh.nbr)
+    ncg = gpu.nbr_child()
+    act = mesh.active_ids()
+    for b in act:
+        assert np.array_equal(ncg[b], mesh.nbr_child(b)), b
+    assert gpu.id_sets() == mesh.id_sets
+    assert gpu.gaps() == mesh.gap
+    assert np.array_equal(gpu.coords()[act], mesh.X[act])
+    masks = gpu.masks()
+    for b in act:
+        assert np.array_equal(masks[b], mesh.cell_classes(b)), b
+    cnt = gpu.counts()
+    assert cnt["n_gaps"] == len(mesh.gap)
+    for L in range(mesh.lmax):
+        assert cnt["n_active"][L] == len(mesh.active_list(L))
+        assert cnt["n_parents"][L] == len(mesh.parent_list(L))
+        assert cnt["n_leaves"][L] == sum(1 for b in mesh.id_sets[L] if mesh.status[b] == 1)
+
+
+@pytest.mark.parametrize("name,mk", MESHES, ids=[m[0] for m in MESHES])
+def test_mesh_tables_bit_exact(name, mk):
+    cfg = mk()
+    mesh = Forest(cfg)
+    gpu = new_gpu(cfg, "f64" if cfg["dim"] == 2 else "f32")
+    compare_tables(gpu, mesh)
+    for it in range(10):
+        m = W.random_marks(300 + it, cfg["max_blocks"], 0.35, 0.3)
+        res = mesh.adapt(m)
+        rc, st = gpu.adapt(marks_tensor(m))
+        assert st["n_refined"] == res["n_refined"]
+        assert st["n_coarsened"] == res["n_coarsened"]
+        assert bool(st["capacity_error"]) == res["capacity_error"]
+        compare_tables(gpu, mesh)
+    gpu.close()
+
+
+def test_capacity_error_keeps_coarsening():
+    cfg = W.cavity(dim=2, n=8, max_levels=3, max_blocks=4 + 8)
+    mesh = Forest(cfg)
+    gpu = new_gpu(cfg, "f64")
+    m = np.zeros(cfg["max_blocks"], np.int8)
+    m[[0, 1]] = 1
+    mesh.adapt(m)
+    gpu.adapt(marks_tensor(m))
+    m[:] = 0
+    m[[0]] = -1          # coarsen 0 and try to refine 2 and 3 (no room)
+    m[[2, 3]] = 1
+    res = mesh.adapt(m)
+    rc, st = gpu.adapt(marks_tensor(m))
+    assert res["capacity_error"] and st["capacity_error"] == 1
+    from paper_2308_08085_gb300.amr import AMR_E_CAPACITY
+    assert rc == AMR_E_CAPACITY
+    assert st["n_coarsened"] == 1
+    compare_tables(gpu, mesh)
+    gpu.close()
+
+
+# ------------------------------------------------------ multi-level steps
+def static_mesh(cfg, seq):
+    ref = ForestLBM(cfg)
+    gpu = new_gpu(cfg, "f64")
+    for ids in seq:
+        m = np.zeros(cfg["max_blocks"], np.int8)
+        m[ids(ref.mesh)] = 1
+        ref.adapt(m)
+        gpu.adapt(marks_tensor(m))
+    return ref, gpu
+
+
+def leaves_where(pred):
+    return lambda mesh: [b for b in mesh.active_ids() if mesh.status[b] == 1 and pred(mesh, b)]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_three_level_step_2d(storage):
+    cfg = W.cavity(dim=2, q=9, n=24, ny=16, max_levels=3, max_blocks=24 * 30)
+    near_lid = leaves_where(lambda m, b: m.X[b][1] >= 8 and 4 <= m.X[b][0] < 20)
+    ref, gpu64 = static_mesh(cfg, [near_lid, near_lid])
+    gpu64.close()
+    gpu = new_gpu(cfg, storage)
+    # replay the same marks on the GPU instance of the requested storage
+    ref2 = ForestLBM(cfg)
+    for _ in range(2):
+        m = np.zeros(cfg["max_blocks"], np.int8)
+        m[near_lid(ref2.mesh)] = 1
+        ref2.adapt(m)
+        gpu.adapt(marks_tensor(m))
+    assert ref2.mesh.counts()[2] > 0
+    randomize(ref2, 5)
+    gpu.set_populations(ref2.f)
+    ref2.step(3)
+    gpu.step(3)
+    ref2.sync()
+    gpu.rho_u()                      # runs the level synchronisation
+    ids = ref2.mesh.active_ids()
+    err = rel_l2(gpu.populations()[ids], ref2.f[ids])
+    assert err <= TOL[storage], err
+    gpu.close()
+
+
+@pytest.mark.parametrize("q,storage", [(19, "f64"), (19, "f32"), (27, "f64")])
+def test_two_level_step_3d(q, storage):
+    cfg = W.cavity(dim=3, q=q, n=12, ny=8, nz=8, max_levels=3, max_blocks=12 * 40)
+    sel = leaves_where(lambda m, b: m.X[b][2] >= 4 and m.X[b][0] >= 4)
+    ref = ForestLBM(cfg)
+    gpu = new_gpu(cfg, storage)
+    for _ in range(2):
+        m = np.zeros(cfg["max_blocks"], np.int8)
+        m[sel(ref.mesh)] = 1
+        ref.adapt(m)
+        gpu.adapt(marks_tensor(m))
+    assert ref.mesh.counts()[2] > 0
+    randomize(ref, 9)
+    gpu.set_populations(ref.f)
+    ref.step(2)
+    gpu.step(2)
+    ref.sync()
+    gpu.rho_u()
+    ids = ref.mesh.active_ids()
+    err = rel_l2(gpu.populations()[ids], ref.f[ids])
+    assert err <= TOL[storage], err
+    gpu.close()
+
+
+# ------------------------------------------- end to end with the criterion
+def run_pair(cfg, storage, steps, every):
+    ref = ForestLBM(cfg)
+    gpu = new_gpu(cfg, storage)
+    for t in range(steps // every):
+        ref.step(every)
+        gpu.step(every)
+        ref.adapt()
+        gpu.adapt()
+    return ref, gpu
+
+
+def test_cavity2d_criterion_end_to_end_f64():
+    cfg = W.cavity(dim=2, q=9, n=32, re=100.0, max_levels=3, max_blocks=64 * 24)
+    ref, gpu = run_pair(cfg, "f64", 200, 50)
+    compare_tables(gpu, ref.mesh)
+    assert sum(ref.mesh.counts()[1:]) > 0          # the criterion refined something
+    ref.step(10)
+    gpu.step(10)
+    ref.sync()
+    rho_g, u_g = gpu.rho_u()
+    ids = ref.mesh.active_ids()
+    rho_r, u_r = ref.macroscopic()
+    assert rel_l2(u_g[ids], u_r[ids]) <= 1e-12
+    assert rel_l2(gpu.populations()[ids], ref.f[ids]) <= 1e-12
+    gpu.close()
+
+
+def test_cavity3d_criterion_end_to_end_f64():
+    cfg = W.cavity(dim=3, q=19, n=16, re=100.0, max_levels=3, max_blocks=64 * 20)
+    ref, gpu = run_pair(cfg, "f64", 60, 20)
+    compare_tables(gpu, ref.mesh)
+    assert sum(ref.mesh.counts()[1:]) > 0
+    ref.sync()
+    gpu.rho_u()
+    ids = ref.mesh.active_ids()
+    assert rel_l2(gpu.populations()[ids], ref.f[ids]) <= 1e-12
+    gpu.close()
+
+
+def test_mass_audit_matches_oracle():
+    cfg = W.cavity(dim=2, q=9, n=16, max_levels=2, max_blocks=16 * 6)
+    ref = ForestLBM(cfg)
+    gpu = new_gpu(cfg, "f64")
+    m = np.zeros(cfg["max_blocks"], np.int8)
+    m[[5, 6, 9, 10]] = 1
+    ref.adapt(m)
+    gpu.adapt(marks_tensor(m))
+    randomize(ref, 3)
+    gpu.set_populations(ref.f)
+    ms = gpu.mass()
+    rho, u = ref.macroscopic()
+    mass = mom_x = 0.0
+    for b in ref.mesh.active_ids():
+        if ref.mesh.status[b] != 1:
+            continue
+        vol = 0.25 ** ref.mesh.level[b]
+        mass += rho[b].sum() * vol
+        mom_x += (rho[b] * u[b][:, 0]).sum() * vol
+    assert abs(ms[0] - mass) <= 1e-12 * mass
+    assert abs(ms[1] - mom_x) <= 1e-12 * max(1.0, abs(mom_x))
+    gpu.close()
