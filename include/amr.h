@@ -176,8 +176,9 @@ int amr_adapt(amr_t* a, const int8_t* dev_marks, amr_adapt_stats* out);
                            AMR_COUNTS                                          */
 #define AMR_MASKS 8     /* uint8 [B][M]: AMR_CELL_* class of every cell        */
 #define AMR_COUNTS 9    /* int64 [4 + 4 L_max]: L_max, n_gaps, coarse steps,
-                           0, then per level: ID-set size, active blocks,
-                           leaves, parent blocks exchanging with children      */
+                           kernels launched so far, then per level: ID-set
+                           size, active blocks, leaves, parent blocks
+                           exchanging with children                            */
 #define AMR_MASS 10     /* double [1 + dim]: FP64 sum over leaf cells of
                            rho V and rho u V, V = cell volume (root units)     */
 #define AMR_FORCE 11    /* double [3]: momentum-exchange force on the solid
@@ -194,10 +195,14 @@ int64_t amr_fields(amr_t* a, int what, void* dst, size_t dst_bytes,
 int amr_set_fields(amr_t* a, int what, const void* src, size_t src_bytes,
                    int src_on_device);
 
-/* Per-kernel CUDA-event timing of subsequent launches (enable != 0 disables
- * graph replay while on).  amr_profile_read synchronises, fills up to `max`
- * entries and returns how many kernel classes exist; reset != 0 clears. */
-int amr_profile(amr_t* a, int enable);
+/* Per-kernel CUDA-event timing.  mode 0: off.  mode 1: events around every
+ * launch of amr_step (graph replay is off while on).  mode 2: events are
+ * captured inside the coarse-step graphs; each amr_profile_read adds one
+ * sample, the launches of the most recently replayed coarse step.
+ * amr_profile_read synchronises, fills up to `max` entries (collide_stream,
+ * interp, average) and returns how many kernel classes exist; reset != 0
+ * clears the sums.  Bytes are algorithmic: 2 Q N_p per cell update. */
+int amr_profile(amr_t* a, int mode);
 int amr_profile_read(amr_t* a, amr_kernel_profile* out, int max, int reset);
 
 /* Release host-side state (the arena stays owned by the caller). */

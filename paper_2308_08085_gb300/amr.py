@@ -236,7 +236,8 @@ class AmrLBM:
         c = self.fields_host(AMR_COUNTS, np.int64)
         lmax = int(c[0])
         per = c[4:4 + 4 * lmax].reshape(lmax, 4)
-        return dict(n_gaps=int(c[1]), coarse_steps=int(c[2]), n_ids=per[:, 0].tolist(),
+        return dict(n_gaps=int(c[1]), coarse_steps=int(c[2]), launches=int(c[3]),
+                    n_ids=per[:, 0].tolist(),
                     n_active=per[:, 1].tolist(), n_leaves=per[:, 2].tolist(),
                     n_parents=per[:, 3].tolist())
 
@@ -255,8 +256,10 @@ class AmrLBM:
     def force(self):
         return self.fields_host(AMR_FORCE, np.float64)
 
-    def profile(self, enable=True):
-        self._check(self.lib.amr_profile(self.h, 1 if enable else 0), "amr_profile")
+    def profile(self, mode=1):
+        """0 off, 1 events around every launch (no graphs), 2 events inside the
+        coarse-step graphs (one sample per profile_read)."""
+        self._check(self.lib.amr_profile(self.h, int(mode)), "amr_profile")
 
     def profile_read(self, reset=True):
         arr = (AmrKernelProfile * 8)()

@@ -52,6 +52,8 @@ struct Instance {
           n_parents[AMR_MAX_LEVELS] = {}, n_leaves[AMR_MAX_LEVELS] = {};
   int64_t n_gaps = 0;
   int64_t coarse_steps = 0;
+  int64_t launches = 0;            // kernels launched by this instance
+  int64_t graph_launches[2] = {0, 0};   // kernels per captured coarse step
   unsigned cur = 0;                // bit L: current population buffer of level L
   double tau[AMR_MAX_LEVELS] = {};
   StepParams prm{};
@@ -61,9 +63,14 @@ struct Instance {
   bool graph_valid = false;
   bool use_graphs = true;
 
-  // profiling
-  bool profiling = false;
+  // profiling: 1 = events around every launch (graphs off); 2 = events captured
+  // inside the graphs, the last replayed coarse step sampled on each read
+  int profiling = 0;
+  bool capturing = false;
+  int capture_parity = 0;
+  int last_parity = -1;
   std::vector<ProfileSlot> prof;
+  std::vector<ProfileSlot> gprof[2];
   std::vector<cudaEvent_t> event_pool;
   struct Acc { int64_t launches = 0; double ms = 0, bytes = 0, cells = 0; };
   Acc acc[8];

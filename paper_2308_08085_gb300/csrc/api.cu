@@ -151,7 +151,8 @@ struct ProfScope {
   Instance* a;
   ProfileSlot slot{};
   bool on;
-  ProfScope(Instance* a_, int kind, double bytes, double cells) : a(a_), on(a_->profiling) {
+  ProfScope(Instance* a_, int kind, double bytes, double cells)
+      : a(a_), on(a_->profiling == 1 || (a_->profiling == 2 && a_->capturing)) {
     if (!on) return;
     slot.start = take_event(a);
     slot.stop = take_event(a);
@@ -163,11 +164,29 @@ struct ProfScope {
   ~ProfScope() {
     if (!on) return;
     cudaEventRecord(slot.stop, a->stream);
-    a->prof.push_back(slot);
+    if (a->capturing) a->gprof[a->capture_parity].push_back(slot);
+    else a->prof.push_back(slot);
   }
 };
 
 static int drain_profile(Instance* a) {
+  if (a->profiling == 2 && a->last_parity >= 0) {
+    // one sample: the launches of the most recently replayed coarse step
+    AMR_CUDA(cudaStreamSynchronize(a->stream));
+    for (auto& s : a->gprof[a->last_parity]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, s.start, s.stop) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      auto& acc = a->acc[s.kind];
+      acc.launches += 1;
+      acc.ms += ms;
+      acc.bytes += s.bytes;
+      acc.cells += s.cells;
+    }
+    a->last_parity = -1;
+  }
   if (a->prof.empty()) return AMR_OK;
   AMR_CUDA(cudaStreamSynchronize(a->stream));
   for (auto& s : a->prof) {
@@ -198,6 +217,7 @@ static void collide_stream_level(Instance* a, int L) {
     ProfScope ps(a, PK_COLLIDE, (double)n * a->M * 2.0 * a->q * a->elem, (double)n * a->M);
     a->ops->collide_stream(a->stream, a->active + (size_t)L * a->cap, (int)n, a->fbuf(L, 0),
                            a->fbuf(L, 1), a->nbr, a->solidmask, prm, a->solid);
+    a->launches += 1;
   }
   a->cur ^= 1u << L;
 }
@@ -210,6 +230,7 @@ static void advance(Instance* a, int L) {
     a->ops->interp(a->stream, a->parents + (size_t)L * a->cap, (int)np, a->fbuf(L, 0),
                    a->fbuf(L + 1, 0), a->stride(), a->child0, a->nonemask, a->solidmask,
                    ratio_cf(a, L), 0, a->solid);
+    a->launches += 1;
   }
   collide_stream_level(a, L);
   if (fine) {
@@ -220,6 +241,7 @@ static void advance(Instance* a, int L) {
       a->ops->average(a->stream, a->parents + (size_t)L * a->cap, (int)np, a->fbuf(L, 0),
                       a->fbuf(L + 1, 0), a->stride(), a->child0, a->nonemask, a->status,
                       a->solidmask, ratio_fc(a, L), 0, a->solid);
+      a->launches += 1;
     }
   }
 }
@@ -229,6 +251,14 @@ static void destroy_graphs(Instance* a) {
     if (g) cudaGraphExecDestroy(g);
     g = nullptr;
   }
+  for (auto& v : a->gprof) {
+    for (auto& s : v) {
+      a->event_pool.push_back(s.start);
+      a->event_pool.push_back(s.stop);
+    }
+    v.clear();
+  }
+  a->last_parity = -1;
   a->graph_valid = false;
 }
 
@@ -242,7 +272,13 @@ static int build_graphs(Handle* h) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
+      h->capturing = true;
+      h->capture_parity = parity;
+      const int64_t before = h->launches;
       advance(h, 0);
+      h->graph_launches[parity] = h->launches - before;
+      h->launches = before;
+      h->capturing = false;
       e = cudaStreamEndCapture(h->stream, &g);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph[parity], g, 0);
@@ -270,12 +306,14 @@ static void level_sync(Instance* a) {
     a->ops->average(a->stream, a->idset + (size_t)L * a->cap, (int)a->n_ids[L], a->fbuf(L, 0),
                     a->fbuf(L + 1, 0), a->stride(), a->child0, a->nonemask, a->status,
                     a->solidmask, ratio_fc(a, L), 1, a->solid);
+    a->launches += 1;
   }
   for (int L = 0; L + 1 < a->lmax; ++L) {
     if (a->n_parents[L] == 0) continue;
     a->ops->interp(a->stream, a->parents + (size_t)L * a->cap, (int)a->n_parents[L],
                    a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0, a->nonemask,
                    a->solidmask, ratio_cf(a, L), 0, a->solid);
+    a->launches += 1;
   }
 }
 
@@ -454,14 +492,17 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
 int amr_step(amr_t* h, int n) {
   Handle* a = reinterpret_cast<Handle*>(h);
   if (!a || n < 0) return AMR_E_INVAL;
-  const bool graphs = a->use_graphs && !a->profiling;
+  const bool graphs = a->use_graphs && a->profiling != 1;
   if (graphs && !a->graph_valid) {
     int rc = build_graphs(a);
     if (rc != AMR_OK) return rc;
   }
   for (int s = 0; s < n; ++s) {
     if (graphs) {
-      AMR_CUDA(cudaGraphLaunch(a->graph[a->cur & 1u], a->stream));
+      const int parity = (int)(a->cur & 1u);
+      AMR_CUDA(cudaGraphLaunch(a->graph[parity], a->stream));
+      a->launches += a->graph_launches[parity];
+      a->last_parity = parity;
       a->cur ^= 1u;   // levels >= 1 flip an even number of times per coarse step
     } else {
       advance(a, 0);
@@ -488,6 +529,7 @@ int amr_adapt(amr_t* h, const int8_t* dev_marks, amr_adapt_stats* out) {
       a->ops->criterion(a->stream, a->idset + (size_t)L * a->cap, (int)a->n_ids[L],
                         a->fbuf(L, 0), a->stride(), a->status, L, a->lmax, inv_dx,
                         a->cfg.crit_start, a->cfg.crit_inc, a->marks, a->w2);
+      a->launches += 1;
     }
   }
   AMR_CUDA(cudaGetLastError());
@@ -532,6 +574,7 @@ int64_t amr_fields(amr_t* h, int what, void* dst, size_t dst_bytes, int dst_on_d
     c[0] = a->lmax;
     c[1] = a->n_gaps;
     c[2] = a->coarse_steps;
+    c[3] = a->launches;
     for (int L = 0; L < a->lmax; ++L) {
       c[4 + 4 * L] = a->n_ids[L];
       c[5 + 4 * L] = a->n_active[L];
@@ -685,10 +728,13 @@ int amr_set_fields(amr_t* h, int what, const void* src, size_t src_bytes, int sr
   return AMR_OK;
 }
 
-int amr_profile(amr_t* h, int enable) {
+int amr_profile(amr_t* h, int mode) {
   Handle* a = reinterpret_cast<Handle*>(h);
-  if (!a) return AMR_E_INVAL;
-  a->profiling = enable != 0;
+  if (!a || mode < 0 || mode > 2) return AMR_E_INVAL;
+  int rc = drain_profile(a);
+  if (rc != AMR_OK) return rc;
+  if (mode != a->profiling) destroy_graphs(a);
+  a->profiling = mode;
   return AMR_OK;
 }
 

@@ -143,6 +143,7 @@ static int compact(Instance* a, int64_t n, Pred pred, Val val, int32_t* out, int
   k_count<<<nb, 256, 0, s>>>((int)n, pred, a->cta);
   k_scan<<<1, 1024, 0, s>>>(nb, a->cta, a->dcount + slot);
   if (scatter) k_scatter<<<nb, 256, 0, s>>>((int)n, pred, val, a->cta, out);
+  a->launches += scatter ? 3 : 2;
   AMR_CUDA(cudaGetLastError());
   if (count) {
     int32_t c = 0;
@@ -494,6 +495,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
 
   k_eligible<<<blocks_for(cap), 256, 0, s>>>(cap, a->marks, a->status, a->level, a->nonemask,
                                               a->lmax);
+  a->launches += 1;
   AMR_CUDA(cudaGetLastError());
   int64_t nR = 0, nC = 0, nC0 = 0;
   AMR_TRY(compact(a, cap, PMarkEq{a->marks, 1}, VIdent{}, R, &nR));
@@ -503,9 +505,11 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
   if (nR * NC > a->n_gaps) {
     st->capacity_error = 1;
     k_clear_refine<<<blocks_for(cap), 256, 0, s>>>(cap, a->marks);
+    a->launches += 1;
     nR = 0;
   }
   k_revert<<<blocks_for(cap), 256, 0, s>>>(cap, a->marks, a->child0, a->nbr, a->nk, NC);
+  a->launches += 1;
   AMR_CUDA(cudaGetLastError());
   AMR_TRY(compact(a, cap, PMarkEq{a->marks, -1}, VIdent{}, C, &nC));
   st->n_refined = nR;
@@ -522,6 +526,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     k_alloc<D><<<blocks_for(nR * NC), 256, 0, s>>>(R, (int)nR, a->gap, a->n_gaps, a->child0,
                                                     a->level, a->X, a->status, a->parent,
                                                     a->dcount + 8);
+    a->launches += 1;
     AMR_CUDA(cudaGetLastError());
   }
   a->n_gaps -= nR * NC;
@@ -532,6 +537,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     if (nCL[L] > 0) {
       k_push_gaps<D><<<blocks_for(nCL[L] * NC), 256, 0, s>>>(W, (int)nCL[L], a->child0, a->gap,
                                                               a->n_gaps, nC * NC, off);
+      a->launches += 1;
       AMR_CUDA(cudaGetLastError());
     }
     off += nCL[L] * NC;
@@ -540,12 +546,15 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     k_remove_children<D><<<blocks_for(nC * NC), 256, 0, s>>>(C, (int)nC, a->child0, a->status,
                                                               a->level, a->parent, a->nbr,
                                                               a->nonemask);
+    a->launches += 1;
     k_finish_coarsened<<<blocks_for(nC), 256, 0, s>>>(C, (int)nC, a->child0, a->status);
+    a->launches += 1;
     AMR_CUDA(cudaGetLastError());
   }
   a->n_gaps += nC * NC;
   if (nR > 0) {
     k_set_status<<<blocks_for(nR), 256, 0, s>>>(R, (int)nR, a->status, ST_REFINED);
+    a->launches += 1;
     AMR_CUDA(cudaGetLastError());
   }
   // R grouped by level into C's storage (C is no longer needed)
@@ -562,6 +571,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     if (nadd > 0) {
       k_append_children<D><<<blocks_for(nadd), 256, 0, s>>>(C + offR[L - 1], (int)nRL[L - 1],
                                                             a->child0, W + kept);
+      a->launches += 1;
       AMR_CUDA(cudaGetLastError());
     }
     if (kept + nadd > 0)
@@ -569,12 +579,14 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     a->n_ids[L] = kept + nadd;
   }
   k_branch_leaf<<<blocks_for(cap), 256, 0, s>>>(cap, a->status, a->child0, NC);
+  a->launches += 1;
   AMR_CUDA(cudaGetLastError());
   for (int L = 1; L < a->lmax; ++L) {
     if (a->n_ids[L] == 0) continue;
-    k_relink<D><<<blocks_for(a->n_ids[L]), 128, 0, s>>>(a->idset + (size_t)L * cap,
+    k_relink<D><<<blocks_for(a->n_ids[L], 128), 128, 0, s>>>(a->idset + (size_t)L * cap,
                                                         (int)a->n_ids[L], a->parent, a->child0,
                                                         a->nbr, a->nonemask);
+    a->launches += 1;
     AMR_CUDA(cudaGetLastError());
   }
   // solid bits of the new children, then every cell of them from the parents
@@ -582,15 +594,18 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     if (nRL[L] == 0) continue;
     const int64_t nnew = nRL[L] * NC;
     k_append_children<D><<<blocks_for(nnew), 256, 0, s>>>(C + offR[L], (int)nRL[L], a->child0, W);
+    a->launches += 1;
     if (a->solid)
       k_solidmask<D><<<blocks_for(nnew), 256, 0, s>>>(W, (int)nnew, a->level, a->X,
                                                       a->cfg.solid[0], a->cfg.solid[1],
                                                       a->cfg.solid[2], a->cfg.solid[3],
                                                       a->solidmask);
+      a->launches += 1;
     AMR_CUDA(cudaGetLastError());
     const double ratio = a->tau[L + 1] / (2.0 * a->tau[L]);
     a->ops->interp(s, C + offR[L], (int)nRL[L], a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(),
                    a->child0, a->nonemask, a->solidmask, ratio, 1, a->solid);
+    a->launches += 1;
     AMR_CUDA(cudaGetLastError());
   }
   int32_t err = 0;

@@ -92,14 +92,21 @@ MESHES = [
 ]
 
 
+def same(name, got, want):
+    got, want = np.asarray(got), np.asarray(want)
+    if got.shape == want.shape and np.array_equal(got, want):
+        return
+    rows = np.nonzero(np.any((got != want).reshape(len(got), -1), axis=1))[0][:5]
+    msg = "; ".join("row %d: got %s want %s" % (r, got[r].tolist(), want[r].tolist())
+                    for r in rows)
+    raise AssertionError("%s differs: %s" % (name, msg))
+
+
 def compare_tables(gpu, mesh: Forest):
-    cap = mesh.cap
     blk = gpu.blocks()
-    assert np.array_equal(blk["level"], mesh.level)
-    assert np.array_equal(blk["status"], mesh.status)
-    assert np.array_equal(blk["child0"], mesh.child0)
-    assert np.array_equal(blk["parent"], mesh.parent)
-    assert np.array_equal(gpu.nbr(), mesh.nbr)
+    for k in ("level", "status", "child0", "parent"):
+        same(k, blk[k], getattr(mesh, k))
+    same("nbr", gpu.nbr(), mesh.nbr)
     ncg = gpu.nbr_child()
     act = mesh.active_ids()
     for b in act:
