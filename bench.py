@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark of the block-forest AMR lattice Boltzmann step on one GB300.
+
+Workload: 3D lid-driven cavity, D3Q19, FP32, 64^3 root cells in 4^3-cell
+blocks, lid u = 0.05, Re = 1000, up to 3 extra levels (L_max = 4) by the
+vorticity criterion, adaptation every 50 coarse steps.  One bench step = one
+adaptation period: 50 coarse steps of the recursive level step (interpolate,
+collide + stream, average on every level) followed by one adaptation (sync,
+criterion, refine/coarsen, relink, interpolation to new children).
+
+value   = MLUPS over the timed steps (lattice updates of leaf cells, the
+          Section 5.1 definition: sum_L 2^L N_leaf_cells,L per coarse step),
+          device time from CUDA events, L2 flushed before every timed step.
+e2e     = the same metric through the C ABI with every step's result (rho, u
+          of all blocks) copied to pinned host memory inside the timed region.
+roofline= fused collide-stream kernel: algorithmic bytes 2 Q N_p per update
+          over its CUDA-event time (events captured inside the coarse-step
+          graph), against the measured HBM copy bandwidth.
+
+Multi-GPU: one independent replica per rank (the instance does not shard);
+value = all ranks' updates / max-over-ranks time, scaling "weak".
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PERIOD = 50
+HBM_FALLBACK_GBS = 6800.0
+PAPER_A100_MLUPS = 1753.0     # paper, 3D LDC D3Q19 FP32 64^3 L_max 4 on A100 (context)
+
+# ncu DRAM traffic of k_collide_stream<3,19,float> per cell update, and the
+# hash of the kernel source it was measured on (profiles/ summary); None until
+# captured.  A changed source hash reports traffic as null.
+NCU_TRAFFIC_PER_UPDATE = None
+NCU_SOURCE_SHA = None
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("lbm_kernels.cuh", "lattice.cuh"):
+        with open(os.path.join(ROOT, "paper_2308_08085_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        import numpy as np
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------- the oracle leg
+class OracleSample:
+    """The CPU oracle, as it stands, on a bounded sample of the workload: the
+    same cavity (D3Q19, Re 1000, L_max 4, vorticity criterion) on a 16^3-cell
+    root grid, spun up with adaptation every 10 coarse steps (untimed); then
+    whole coarse steps are timed until a budget of seconds has passed."""
+
+    def __init__(self, n=16, spin_periods=3, spin_every=10):
+        import workloads as W
+        from oracle.solver import ForestLBM
+        self.n, self.spin = n, (spin_periods, spin_every)
+        self.sim = ForestLBM(W.config_c1(n=n, max_blocks=(n // 4) ** 3 * 80))
+        for _ in range(spin_periods):
+            self.sim.step(spin_every)
+            self.sim.adapt()
+        self.ups = self.sim.updates_per_coarse_step()
+
+    def run(self, budget_s):
+        t0 = time.perf_counter()
+        steps = 0
+        while time.perf_counter() - t0 < budget_s or steps == 0:
+            self.sim.step(1)
+            steps += 1
+        return self.ups * steps, time.perf_counter() - t0, steps
+
+    def describe(self, steps):
+        return ("oracle ForestLBM (numpy, FP64, one thread) on the same cavity at a %d^3 "
+                "root grid after %d coarse steps with adaptation every %d; %d timed coarse "
+                "steps of %d leaf updates each; blocks per level %s" %
+                (self.n, self.spin[0] * self.spin[1], self.spin[1], steps, self.ups,
+                 self.sim.mesh.counts()))
+
+
+def oracle_sample(budget_s=20.0):
+    s = OracleSample()
+    upd, dt, steps = s.run(budget_s)
+    return upd / dt / 1e6, s.describe(steps), dt, upd
+
+
+def cpu_worker(args):
+    mlups, desc, dt, upd = oracle_sample(args.cpu_budget)
+    print(json.dumps({"mlups": mlups, "desc": desc, "seconds": dt, "updates": upd}))
+
+
+def run_cpu_baseline(budget):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker",
+                        "--cpu-budget", str(budget)], capture_output=True, text=True, env=env,
+                       timeout=budget * 20 + 300)
+    line = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    if r.returncode != 0 or not line:
+        return None
+    d = json.loads(line[-1])
+    return {"value": d["mlups"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": d["desc"], "seconds": d["seconds"]}
+
+
+# ---------------------------------------------------------------- our arm
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2308_08085_gb300 import AmrLBM
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    cfg = W.config_c1(n=args.n, max_blocks=(args.n // 4) ** 3 * args.cap_factor)
+    sim = AmrLBM(cfg, storage="f32")
+    capacity_errors = 0
+    for _ in range(args.warmup):
+        sim.step(PERIOD)
+        rc, _ = sim.adapt()
+        capacity_errors += rc != 0
+    torch.cuda.synchronize()
+    start_counts = sim.counts()
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sim.profile(2)
+    sim.profile_read(reset=True)
+    updates = 0
+    launches0 = sim.counts()["launches"]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)                      # untimed: evict L2 between steps
+        updates += PERIOD * sim.updates_per_coarse_step()
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        sim.step(PERIOD)
+        e1.record(stream)
+        rc, _ = sim.adapt()
+        capacity_errors += rc != 0
+        e2.record(stream)
+        sim.profile_read(reset=False)              # one graph-captured coarse-step sample
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = sim.counts()["launches"] - launches0     # this library's kernels only
+    t_total = sum(e0.elapsed_time(e2) for e0, _, e2 in ev) / 1e3
+    t_solver = sum(e0.elapsed_time(e1) for e0, e1, _ in ev) / 1e3
+    prof = sim.profile_read(reset=True)
+    sim.profile(0)
+    end_counts = sim.counts()
+
+    t_max = t_total
+    upd_all = updates
+    if dist is not None:
+        t = torch.tensor([t_total, float(updates)], dtype=torch.float64, device=dev)
+        tm = t.clone()
+        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
+        t_max, upd_all = float(tm[0]), float(tm[1])
+
+    # end to end through the C ABI: result fields to pinned host memory
+    nbytes = sim.field_bytes(0)
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    import ctypes
+    e2e_updates = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        e2e_updates += PERIOD * sim.updates_per_coarse_step()
+        sim.step(PERIOD)
+        sim.adapt()
+        rc = sim.lib.amr_fields(sim.h, 0, ctypes.c_void_p(host.data_ptr()), nbytes, 0)
+        assert rc == nbytes
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([t_e2e, float(e2e_updates)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        t_e2e, e2e_updates = float(t[0]), float(t[1])
+
+    # roofline of the fused collide-stream kernel
+    cs = prof.get("collide_stream", {})
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if cs.get("ms", 0) > 0:
+        achieved = cs["bytes"] / (cs["ms"] / 1e3) / 1e9
+        per_launch_updates = cs["cells"] / max(1, cs["launches"])
+        traffic = None
+        if NCU_TRAFFIC_PER_UPDATE is not None and NCU_SOURCE_SHA == kernel_source_sha():
+            traffic = NCU_TRAFFIC_PER_UPDATE * per_launch_updates
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": peak_kind + " hbm_gbs (MEASURED_PEAKS.json copy test)",
+                "kernel": "k_collide_stream<3,19,float>",
+                "bytes_per_update": 2 * 19 * 4,
+                "sampled_launches": cs["launches"],
+                "avg_launch_ms": round(cs["ms"] / max(1, cs["launches"]), 5),
+                "avg_updates_per_launch": round(per_launch_updates, 1)}
+    share = {k: round(v["ms"], 4) for k, v in prof.items()}
+
+    # single-level periodic 256^3 D3Q19 FP32 forest: the stencil's roofline bar
+    bar = None
+    if not args.no_bar:
+        del flush
+        bar = run_bar(args, AmrLBM, W, torch, dev, stream)
+
+    out = None
+    if rank == 0:
+        value = upd_all / t_max / 1e6
+        out = {
+            "metric": "MLUPS", "value": round(value, 2), "unit": "MLUP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_max * 1e3 / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": round(value / PAPER_A100_MLUPS, 3),
+            "dtype": "f32", "data": "synthetic",
+            "config": {
+                "workload": "3D lid-driven cavity D3Q19 BGK FP32, 64^3 root cells in 4^3 "
+                            "blocks, lid 0.05, Re 1000, L_max 4 (vorticity criterion "
+                            "N_start -2, N_inc 1), adaptation every 50 coarse steps",
+                "step": "50 coarse steps (recursive level step) + 1 adaptation",
+                "parallelism": "replicas" if world > 1 else "single GPU",
+                "l2": "flushed between timed steps (256 MiB write, untimed)",
+                "coarse_step_at_start": start_counts["coarse_steps"],
+                "blocks_per_level_start": start_counts["n_ids"],
+                "blocks_per_level_end": end_counts["n_ids"],
+                "leaf_updates_per_coarse_step_end": sim.updates_per_coarse_step(),
+                "solver_mlups_excl_adapt": round(updates / t_solver / 1e6, 2),
+                "adapt_share": round(1 - t_solver / t_total, 4),
+                "capacity_errors": int(capacity_errors),
+                "kernel_ms_last_sampled": share,
+                "baseline": "paper A100 mean MLUPS 1753 (D3Q19 FP32 64^3, L_max 4): context",
+                "uniform_bar": bar,
+            },
+            "roofline": roof,
+            "e2e": {"value": round(e2e_updates / t_e2e / 1e6, 2), "unit": "MLUP/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes,
+                    "note": "amr_step + amr_adapt + amr_fields(AMR_RHO_U) to pinned host "
+                            "memory every step; the workload's input is its configuration "
+                            "(the initial state is the rest equilibrium built by amr_init)"},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+    sim.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def run_bar(args, AmrLBM, W, torch, dev, stream):
+    """Single-level periodic D3Q19 FP32 forest of 256^3 cells (2 x 1.27 GB of
+    populations, far above L2): fused collide-stream only."""
+    cfg = W.config_uniform_bar(256)
+    sim = AmrLBM(cfg, storage="f32")
+    sim.step(3)
+    sim.profile(1)
+    sim.profile_read(reset=True)
+    n = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = sim.profile_read(reset=True)["collide_stream"]
+    sim.close()
+    peak, _ = measured_peaks()
+    ups = 256 ** 3
+    kernel_gbs = prof["bytes"] / (prof["ms"] / 1e3) / 1e9
+    return {"cells": ups, "mlups": round(ups * n / (e0.elapsed_time(e1) / 1e3) / 1e6, 1),
+            "kernel_gbs": round(kernel_gbs, 1), "frac": round(kernel_gbs / peak, 4)}
+
+
+# ----------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return None
+    per_step = max(1.0, 120.0 / max(1, args.steps + args.warmup))
+    sample = OracleSample()
+    upd = dt = 0.0
+    steps = 0
+    for i in range(args.warmup + args.steps):
+        u, t, s = sample.run(per_step)
+        if i >= args.warmup:
+            upd, dt, steps = upd + u, dt + t, steps + s
+    value = upd / dt / 1e6
+    desc = sample.describe(steps)
+    return {"impl": "reference", "metric": "MLUPS", "value": round(value, 4),
+            "unit": "MLUP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3 / max(1, args.steps), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "3D lid-driven cavity D3Q19, Re 1000, L_max 4, "
+                                   "vorticity criterion (oracle sample on a 16^3 root grid)"},
+            "cpu_baseline": {"value": round(value, 4), "unit": "MLUP/s",
+                             "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": round(value, 4), "unit": "MLUP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--cap-factor", type=int, default=64)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-bar", action="store_true")
+    ap.add_argument("--cpu-worker", action="store_true")
+    ap.add_argument("--bar-only", action="store_true",
+                    help="only the single-level 256^3 D3Q19 FP32 forest (profiling)")
+    args = ap.parse_args()
+    if args.cpu_worker:
+        cpu_worker(args)
+        return
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.bar_only:
+        import torch
+        import workloads as W
+        from paper_2308_08085_gb300 import AmrLBM
+        torch.cuda.set_device(0)
+        print(json.dumps(run_bar(args, AmrLBM, W, torch, torch.device("cuda", 0),
+                                 torch.cuda.current_stream())))
+        return
+    if args.impl == "reference":
+        out = run_reference(args)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    world, rank, local = dist_setup()
+    out = run_ours(args)
+    if rank == 0 and out is not None:
+        if world == 1 and not args.no_cpu:
+            out["cpu_baseline"] = run_cpu_baseline(args.cpu_budget)
+        else:
+            out["cpu_baseline"] = None
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
