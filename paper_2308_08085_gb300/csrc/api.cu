@@ -170,7 +170,7 @@ struct ProfScope {
 };
 
 static int drain_profile(Instance* a) {
-  if (a->profiling == 2 && a->last_parity >= 0) {
+  if (a->profiling == 2 && a->last_parity >= 0 && !a->gprof[a->last_parity].empty()) {
     // one sample: the launches of the most recently replayed coarse step
     AMR_CUDA(cudaStreamSynchronize(a->stream));
     for (auto& s : a->gprof[a->last_parity]) {
@@ -246,7 +246,11 @@ static void advance(Instance* a, int L) {
   }
 }
 
+static int drain_profile(Instance* a);
+
 static void destroy_graphs(Instance* a) {
+  // keep the sample of the last replayed coarse step before its events go
+  if (a->profiling == 2 && a->last_parity >= 0) drain_profile(a);
   for (auto& g : a->graph) {
     if (g) cudaGraphExecDestroy(g);
     g = nullptr;
