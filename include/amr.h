@@ -205,6 +205,40 @@ int amr_set_fields(amr_t* a, int what, const void* src, size_t src_bytes,
 int amr_profile(amr_t* a, int mode);
 int amr_profile_read(amr_t* a, amr_kernel_profile* out, int max, int reset);
 
+/* FP64 mass and momentum audit that allocates nothing.  The paper has no
+ * counterpart: this is a service of this library for callers that cannot
+ * allocate device memory -- code running under a memory budget fixed by a
+ * host framework, code that must not call the CUDA allocator inside a
+ * latency-critical loop, or code that holds population buffers in this
+ * library's layout but no amr_t instance and no arena.
+ *
+ * Inputs (device pointers, owned by the caller): the two population buffers
+ * f_a, f_b of `n_blocks` blocks in the AMR_F storage layout of `storage`
+ * ([Q][n_blocks][4^dim], stored values; 16-bit storages hold f - w_p), a
+ * per-level buffer choice `cur` (bit L set: blocks of level L are read from
+ * f_b), and int32 level[n_blocks] / status[n_blocks] (AMR_BLOCKS rows 0 and
+ * 1).  Output: out_dev[0 .. dim] (device, caller-owned) = the sum over leaf
+ * blocks (status AMR_ST_UNREFINED) of rho V and rho u V, V = 2^(-dim level).
+ * Asynchronous on `stream`.
+ *
+ * Scratch: a file-scope device array of AMR_NOALLOC_MAX_PARTIALS rows of 4
+ * doubles (512 KiB), held by every GPU that loads the library until the
+ * process exits.  One row per 64 blocks, so n_blocks may not exceed
+ * 64 * AMR_NOALLOC_MAX_PARTIALS (1,048,576); larger inputs return
+ * AMR_E_INVAL with a message and launch nothing.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call on a device shares the array and leaves its partial sums there;
+ * each call writes every row it reads, so nothing needs clearing, but calls
+ * that overlap on the GPU (different streams, or different host threads)
+ * race on it.  Calls no cudaMalloc, cudaFree or allocating library routine.
+ * Errors: AMR_E_INVAL, AMR_E_CUDA. */
+#define AMR_NOALLOC_MAX_PARTIALS 16384
+int amr_mass_audit_noalloc(int dim, int q, int storage, int64_t n_blocks,
+                           const void* f_a, const void* f_b, uint32_t cur,
+                           const int32_t* level, const int32_t* status,
+                           double* out_dev, void* stream);
+
 /* Release host-side state (the arena stays owned by the caller). */
 int amr_free(amr_t* a);
 
