@@ -188,7 +188,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     cfg = W.config_c1(n=args.n, max_blocks=(args.n // 4) ** 3 * args.cap_factor)
-    sim = AmrLBM(cfg, storage="f32")
+    sim = AmrLBM(cfg, storage="f32", kernel_variant=args.variant)
     capacity_errors = 0
     for _ in range(args.warmup):
         sim.step(PERIOD)
@@ -332,7 +332,7 @@ def run_bar(args, AmrLBM, W, torch, dev, stream):
     """Single-level periodic D3Q19 FP32 forest of 256^3 cells (2 x 1.27 GB of
     populations, far above L2): fused collide-stream only."""
     cfg = W.config_uniform_bar(256)
-    sim = AmrLBM(cfg, storage="f32")
+    sim = AmrLBM(cfg, storage="f32", kernel_variant=args.variant)
     sim.step(3)
     sim.profile(1)
     sim.profile_read(reset=True)
@@ -348,7 +348,8 @@ def run_bar(args, AmrLBM, W, torch, dev, stream):
     peak, _ = measured_peaks()
     ups = 256 ** 3
     kernel_gbs = prof["bytes"] / (prof["ms"] / 1e3) / 1e9
-    return {"cells": ups, "mlups": round(ups * n / (e0.elapsed_time(e1) / 1e3) / 1e6, 1),
+    return {"cells": ups, "variant": args.variant,
+            "mlups": round(ups * n / (e0.elapsed_time(e1) / 1e3) / 1e6, 1),
             "kernel_gbs": round(kernel_gbs, 1), "frac": round(kernel_gbs / peak, 4)}
 
 
@@ -393,6 +394,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-bar", action="store_true")
     ap.add_argument("--cpu-worker", action="store_true")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="collide-stream kernel: 0 auto, 1 one-pass, 2/3 pipelined stages")
     ap.add_argument("--bar-only", action="store_true",
                     help="only the single-level 256^3 D3Q19 FP32 forest (profiling)")
     args = ap.parse_args()

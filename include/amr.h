@@ -100,7 +100,10 @@ typedef struct {
                               centre is strictly inside is solid               */
   amr_face faces[6];       /* x-, x+, y-, y+, z-, z+ (first 4 used in 2D)      */
   int32_t use_graphs;      /* 1: replay the coarse step as a CUDA graph         */
-  int32_t pad_;
+  int32_t kernel_variant;  /* collide-stream kernel: 0 auto (2-stage pipeline for
+                              launches of two or more waves, else one-pass),
+                              1 one-pass, 2 / 3: 2- / 3-stage cp.async pipeline
+                              in a persistent grid                             */
 } amr_config;
 
 typedef struct {

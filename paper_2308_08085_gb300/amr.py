@@ -41,7 +41,7 @@ class AmrConfig(ctypes.Structure):
                 ("max_blocks", ctypes.c_int64), ("nu0", ctypes.c_double),
                 ("length_x", ctypes.c_double), ("solid", ctypes.c_double * 4),
                 ("faces", AmrFace * 6), ("use_graphs", ctypes.c_int32),
-                ("pad_", ctypes.c_int32)]
+                ("kernel_variant", ctypes.c_int32)]
 
 
 class AmrAdaptStats(ctypes.Structure):
@@ -102,7 +102,7 @@ class AmrError(RuntimeError):
         self.code = code
 
 
-def make_config(cfg, storage="f32", use_graphs=True):
+def make_config(cfg, storage="f32", use_graphs=True, kernel_variant=0):
     """Fill an AmrConfig from a workload dictionary (see workloads/)."""
     c = AmrConfig()
     c.dim, c.q = cfg["dim"], cfg["q"]
@@ -123,13 +123,15 @@ def make_config(cfg, storage="f32", use_graphs=True):
             c.faces[i].u[a] = v
         c.faces[i].rho_w = face[2] if len(face) > 2 else 1.0
     c.use_graphs = 1 if use_graphs else 0
+    c.kernel_variant = int(kernel_variant)
     return c
 
 
 class AmrLBM:
     """One block-forest AMR-LBM instance on the current CUDA device."""
 
-    def __init__(self, cfg, storage="f32", stream=None, use_graphs=True, device=None):
+    def __init__(self, cfg, storage="f32", stream=None, use_graphs=True, device=None,
+                 kernel_variant=0):
         import torch
         self.lib = lib = load_library()
         self.cfg = cfg
@@ -139,7 +141,7 @@ class AmrLBM:
         self.cap = cfg["max_blocks"]
         self.lmax = cfg["max_levels"]
         self.storage = storage
-        self.c = make_config(cfg, storage, use_graphs)
+        self.c = make_config(cfg, storage, use_graphs, kernel_variant)
         nbytes = lib.amr_arena_bytes(ctypes.byref(self.c))
         if nbytes == 0:
             raise AmrError(AMR_E_INVAL, "amr_arena_bytes")

@@ -37,6 +37,7 @@ struct Instance {
   int32_t* nbr = nullptr;          // [cap][NBR_STRIDE]
   uint32_t* nonemask = nullptr;    // bit k set when nbr[b][k] == NONE
   uint64_t* solidmask = nullptr;   // bit l set when cell l is solid
+  uint64_t* cellmask = nullptr;    // [cap][2]: ghost cells, interface cells (bit l)
   int32_t *idset = nullptr, *active = nullptr, *parents = nullptr;   // [lmax][cap]
   int32_t* gap = nullptr;          // [cap]
   int8_t* marks = nullptr;         // [cap]

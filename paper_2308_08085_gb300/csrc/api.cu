@@ -117,6 +117,7 @@ static Layout layout_for(const amr_config* c) {
       8192 * 8,                                // 21 red
       64 * 4,                                  // 22 wall_code
       STAGING_BYTES,                           // 23 staging
+      (size_t)cap * 16,                        // 24 cellmask
   };
   size_t off = 0;
   int i = 0;
@@ -159,11 +160,16 @@ struct ProfScope {
     slot.kind = kind;
     slot.bytes = bytes;
     slot.cells = cells;
-    cudaEventRecord(slot.start, a->stream);
+    record(slot.start);
+  }
+  // inside a stream capture the record must become an event node of the graph
+  void record(cudaEvent_t e) {
+    if (a->capturing) cudaEventRecordWithFlags(e, a->stream, cudaEventRecordExternal);
+    else cudaEventRecord(e, a->stream);
   }
   ~ProfScope() {
     if (!on) return;
-    cudaEventRecord(slot.stop, a->stream);
+    record(slot.stop);
     if (a->capturing) a->gprof[a->capture_parity].push_back(slot);
     else a->prof.push_back(slot);
   }
@@ -228,7 +234,7 @@ static void advance(Instance* a, int L) {
   if (fine && np > 0) {
     ProfScope ps(a, PK_INTERP, 0.0, 0.0);
     a->ops->interp(a->stream, a->parents + (size_t)L * a->cap, (int)np, a->fbuf(L, 0),
-                   a->fbuf(L + 1, 0), a->stride(), a->child0, a->nonemask, a->solidmask,
+                   a->fbuf(L + 1, 0), a->stride(), a->child0, a->cellmask, a->solidmask,
                    ratio_cf(a, L), 0, a->solid);
     a->launches += 1;
   }
@@ -239,7 +245,7 @@ static void advance(Instance* a, int L) {
     if (np > 0) {
       ProfScope ps(a, PK_AVERAGE, 0.0, 0.0);
       a->ops->average(a->stream, a->parents + (size_t)L * a->cap, (int)np, a->fbuf(L, 0),
-                      a->fbuf(L + 1, 0), a->stride(), a->child0, a->nonemask, a->status,
+                      a->fbuf(L + 1, 0), a->stride(), a->child0, a->cellmask, a->status,
                       a->solidmask, ratio_fc(a, L), 0, a->solid);
       a->launches += 1;
     }
@@ -308,14 +314,14 @@ static void level_sync(Instance* a) {
   for (int L = a->lmax - 2; L >= 0; --L) {
     if (a->n_ids[L + 1] == 0) continue;
     a->ops->average(a->stream, a->idset + (size_t)L * a->cap, (int)a->n_ids[L], a->fbuf(L, 0),
-                    a->fbuf(L + 1, 0), a->stride(), a->child0, a->nonemask, a->status,
+                    a->fbuf(L + 1, 0), a->stride(), a->child0, a->cellmask, a->status,
                     a->solidmask, ratio_fc(a, L), 1, a->solid);
     a->launches += 1;
   }
   for (int L = 0; L + 1 < a->lmax; ++L) {
     if (a->n_parents[L] == 0) continue;
     a->ops->interp(a->stream, a->parents + (size_t)L * a->cap, (int)a->n_parents[L],
-                   a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0, a->nonemask,
+                   a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0, a->cellmask,
                    a->solidmask, ratio_cf(a, L), 0, a->solid);
     a->launches += 1;
   }
@@ -433,6 +439,7 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
   a->red = (double*)(base + L.off[i++]);
   a->wall_code = (int32_t*)(base + L.off[i++]);
   a->staging = base + L.off[i++];
+  a->cellmask = (uint64_t*)(base + L.off[i++]);
 
   const double tau0 = 3.0 * cfg->nu0 + 0.5;
   for (int l = 0; l < a->lmax; ++l) a->tau[l] = 0.5 + std::ldexp(tau0 - 0.5, l);
@@ -454,6 +461,12 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
   host_velocities(a->dim, a->q, c, w);
   std::memset(&a->prm, 0, sizeof(a->prm));
   a->prm.stride = a->stride();
+  a->prm.variant = cfg->kernel_variant;
+  if (a->ops->setup() != 0) {
+    set_error(std::string("kernel setup: ") + cudaGetErrorString(cudaGetLastError()));
+    delete a;
+    return AMR_E_CUDA;
+  }
   for (int f = 0; f < 6; ++f) {
     const amr_face& fc = cfg->faces[f];
     a->prm.faces.kind[f] = fc.kind;

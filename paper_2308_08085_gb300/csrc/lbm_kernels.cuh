@@ -8,6 +8,8 @@
 #include "lattice.cuh"
 #include "lbm_ops.h"
 
+#include <algorithm>
+
 namespace amr {
 
 constexpr int ST_UNREFINED = 1;
@@ -132,6 +134,162 @@ __global__ void __launch_bounds__(256)
   });
 }
 
+
+// ================================== pipelined persistent collide + stream
+// Same arithmetic as k_collide_stream.  Each CTA walks tiles of 256/M blocks
+// (stride gridDim.x) and double-buffers them in shared memory: while tile t
+// is collided and pushed from shared memory, the populations and neighbour
+// rows of its next tile stream in with 16-byte cp.async copies, so the
+// memory system always has loads in flight.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int D, int Q, class T, int STAGES>
+struct PipeShape {
+  static constexpr int M = Block<D>::M;
+  static constexpr int TILE = 256 / M;
+  static constexpr int STAGE_ELEMS = TILE * Q * M;
+  static constexpr int PLANE_CHUNKS = M * (int)sizeof(T) / 16;
+  static constexpr size_t SMEM =
+      STAGES * ((size_t)STAGE_ELEMS * sizeof(T) + (size_t)TILE * NBR_STRIDE * 4);
+};
+
+template <int D, int Q, class T, bool SOLID, int STAGES>
+__global__ void __launch_bounds__(256, (sizeof(T) == 8 && Q == 27) ? 1 : 2)
+    k_collide_stream_pipe(const int32_t* __restrict__ list, int n, const T* __restrict__ fin,
+                          T* __restrict__ fout, const int32_t* __restrict__ nbr,
+                          const uint64_t* __restrict__ solidmask, StepParams prm) {
+  using V = VS<D, Q>;
+  using S = Store<T>;
+  using R = typename S::R;
+  using PS = PipeShape<D, Q, T, STAGES>;
+  constexpr int M = PS::M, TILE = PS::TILE;
+  constexpr int NCODE = D == 2 ? 9 : 27;
+  constexpr int CENTER = D == 2 ? 4 : 13;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sf = reinterpret_cast<T*>(smem_raw);                           // [STAGES][TILE][Q][M]
+  int32_t* srow = reinterpret_cast<int32_t*>(smem_raw + STAGES * (size_t)PS::STAGE_ELEMS * sizeof(T));
+  __shared__ int32_t s_nb[TILE][NCODE];
+  __shared__ uint64_t s_sm[SOLID ? TILE : 1][SOLID ? NCODE : 1];
+  const size_t stride = prm.stride;
+  const int n_tiles = (n + TILE - 1) / TILE;
+
+  auto issue = [&](int tile, int stage) {
+    constexpr int NCH = TILE * Q * PS::PLANE_CHUNKS;
+#pragma unroll 1
+    for (int c = threadIdx.x; c < NCH; c += blockDim.x) {
+      const int s = c / (Q * PS::PLANE_CHUNKS);
+      const int rem = c - s * Q * PS::PLANE_CHUNKS;
+      const int p = rem / PS::PLANE_CHUNKS;
+      const int ch = rem - p * PS::PLANE_CHUNKS;
+      const int bi = tile * TILE + s;
+      if (bi < n) {
+        const int b = __ldg(list + bi);
+        cp_async16(reinterpret_cast<char*>(sf + (size_t)stage * PS::STAGE_ELEMS + (s * Q + p) * M) + 16 * ch,
+                   reinterpret_cast<const char*>(fin + (size_t)p * stride + (size_t)b * M) + 16 * ch);
+      }
+    }
+#pragma unroll 1
+    for (int c = threadIdx.x; c < TILE * (NBR_STRIDE / 4); c += blockDim.x) {
+      const int s = c / (NBR_STRIDE / 4), ch = c - s * (NBR_STRIDE / 4);
+      const int bi = tile * TILE + s;
+      if (bi < n)
+        cp_async16(srow + (stage * TILE + s) * NBR_STRIDE + 4 * ch,
+                   nbr + (size_t)__ldg(list + bi) * NBR_STRIDE + 4 * ch);
+    }
+  };
+
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int i = Block<D>::ci(l), j = Block<D>::cj(l), kk = Block<D>::ck(l);
+  const R om = R(prm.omega);
+  // prologue: the first STAGES-1 tiles of this CTA are requested up front
+#pragma unroll
+  for (int k = 0; k < STAGES - 1; ++k) {
+    const int t = blockIdx.x + k * gridDim.x;
+    if (t < n_tiles) issue(t, k);
+    cp_async_commit();
+  }
+  int stage = 0;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int ahead = tile + (STAGES - 1) * gridDim.x;
+    if (ahead < n_tiles) issue(ahead, (stage + STAGES - 1) % STAGES);
+    cp_async_commit();
+    cp_async_wait<STAGES - 1>();   // this tile's group has landed
+    __syncthreads();
+#pragma unroll 1
+    for (int t = threadIdx.x; t < TILE * NCODE; t += blockDim.x) {
+      const int s = t / NCODE, code = t - s * NCODE;
+      const int v = (tile * TILE + s < n) ? srow[(stage * TILE + s) * NBR_STRIDE + geo_to_k<D>(code)]
+                                          : NONE;
+      s_nb[s][code] = v;
+      if constexpr (SOLID) s_sm[s][code] = (v >= 0) ? __ldg(solidmask + v) : 0ull;
+    }
+    __syncthreads();
+    const bool active = tile * TILE + slot < n;
+    bool solid_cell = false;
+    if constexpr (SOLID) solid_cell = active && ((s_sm[slot][CENTER] >> l) & 1ull);
+    if (active && !solid_cell) {
+      const int b = s_nb[slot][CENTER];
+      const size_t base = (size_t)b * M + l;
+      const T* sblk = sf + (size_t)stage * PS::STAGE_ELEMS + slot * Q * M;
+      R f[Q];
+      static_for<0, Q>([&](auto P) { f[P] = S::template load<D, Q, P>(sblk[P * M + l]); });
+      R rho, ux, uy, uz;
+      moments<D, Q>(f, rho, ux, uy, uz);
+      const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+      static_for<0, Q>([&](auto P) {
+        constexpr int p = P;
+        constexpr int cx = V::cx[p], cy = V::cy[p], cz = V::cz[p];
+        constexpr int pb = V::opp[p];
+        const R fs = f[p] + om * (feq<D, Q, p>(rho, ux, uy, uz, usq15) - f[p]);
+        if constexpr (p == 0) {
+          fout[base] = S::template save<D, Q, 0>(fs);
+        } else {
+          const int ti = i + cx, tj = j + cy, tk = kk + cz;
+          int code = CENTER;
+          if constexpr (cx != 0) code += (ti < 0) ? -1 : (ti > 3 ? 1 : 0);
+          if constexpr (cy != 0) code += (tj < 0) ? -3 : (tj > 3 ? 3 : 0);
+          if constexpr (D == 3 && cz != 0) code += (tk < 0) ? -9 : (tk > 3 ? 9 : 0);
+          const int tgt = s_nb[slot][code];
+          const int tl = (ti & 3) + 4 * (tj & 3) + (D == 3 ? 16 * (tk & 3) : 0);
+          bool bounce = tgt < 0;
+          if constexpr (SOLID) bounce = bounce || ((s_sm[slot][code] >> tl) & 1ull);
+          if (!bounce) {
+            fout[(size_t)p * stride + (size_t)tgt * M + tl] = S::template save<D, Q, p>(fs);
+          } else {
+            R v = fs;
+            if (tgt <= -2) {
+              const int face = -2 - tgt;
+              if (prm.faces.kind[face] == FACE_OUTLET) {
+                R cu = R(0);
+                if constexpr (cx != 0) cu += cx > 0 ? ux : -ux;
+                if constexpr (cy != 0) cu += cy > 0 ? uy : -uy;
+                if constexpr (cz != 0) cu += cz > 0 ? uz : -uz;
+                constexpr double wp = V::w[p];
+                v = -fs + R(2.0 * wp * prm.faces.rho_w[face]) * (R(1) + R(4.5) * cu * cu - usq15);
+              } else {
+                v = fs + R(prm.faces.bb[face][p]);
+              }
+            }
+            fout[(size_t)pb * stride + base] = S::template save<D, Q, pb>(v);
+          }
+        }
+      });
+    }
+    __syncthreads();
+    stage = (stage + 1) % STAGES;
+  }
+  cp_async_wait<0>();
+}
+
 // =========================================== coarse-to-fine linear interpolation
 // Per parent block: every parent cell rescales its populations to the fine
 // level (f_eq + (f - f_eq) r, Section 3.4.1) into shared memory; then, for
@@ -142,7 +300,7 @@ template <int D, int Q, class T, bool SOLID>
 __global__ void __launch_bounds__(128)
     k_interp(const int32_t* __restrict__ list, int n, const T* __restrict__ fpar,
              T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
-             const uint32_t* __restrict__ nonemask, const uint64_t* __restrict__ solidmask,
+             const uint64_t* __restrict__ cellmask, const uint64_t* __restrict__ solidmask,
              double ratio, int mode_all) {
   using S = Store<T>;
   using R = typename S::R;
@@ -188,9 +346,9 @@ __global__ void __launch_bounds__(128)
   for (int c = 0; c < NC; ++c) {
     const int ch = c0 + c;
     if (!mode_all) {
-      const uint32_t nm = nonemask[ch];
-      if (nm == 0u) continue;
-      if (cell_class<D>(nm, i, j, k) != CLS_GHOST) continue;
+      const uint64_t gm = __ldg(cellmask + 2 * (size_t)ch);   // ghost cells of the child
+      if (gm == 0ull) continue;
+      if (!((gm >> l) & 1ull)) continue;
     }
     if constexpr (SOLID) {
       if ((__ldg(solidmask + ch) >> l) & 1ull) continue;
@@ -220,7 +378,7 @@ template <int D, int Q, class T, bool SOLID>
 __global__ void __launch_bounds__(128)
     k_average(const int32_t* __restrict__ list, int n, T* __restrict__ fpar,
               const T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
-              const uint32_t* __restrict__ nonemask, const int32_t* __restrict__ status,
+              const uint64_t* __restrict__ cellmask, const int32_t* __restrict__ status,
               const uint64_t* __restrict__ solidmask, double ratio, int mode_sync) {
   using S = Store<T>;
   using R = typename S::R;
@@ -237,9 +395,10 @@ __global__ void __launch_bounds__(128)
   const int c = (i >> 1) + 2 * (j >> 1) + (D == 3 ? 4 * (k >> 1) : 0);
   const int ch = child0[P] + c;
   const int fi = 2 * (i & 1), fj = 2 * (j & 1), fk = 2 * (k & 1);
-  const int cls = cell_class<D>(nonemask[ch], fi, fj, fk);
-  if (!mode_sync && cls != CLS_INTERFACE) return;
-  if (mode_sync && cls == CLS_GHOST) return;
+  // all 2^D children of a parent cell share one class; test the first
+  const int f0 = Block<D>::cell(fi, fj, fk);
+  if (!mode_sync && !((__ldg(cellmask + 2 * (size_t)ch + 1) >> f0) & 1ull)) return;
+  if (mode_sync && ((__ldg(cellmask + 2 * (size_t)ch) >> f0) & 1ull)) return;
   if constexpr (SOLID) {
     if ((__ldg(solidmask + P) >> l) & 1ull) return;
   }
@@ -544,10 +703,65 @@ inline int grid_for(int64_t n, int per) { return (int)((n + per - 1) / per); }
 template <int D, int Q, class T>
 struct Launch {
   static constexpr int M = Block<D>::M;
+  // persistent grid of the pipelined kernel: [solid][stages - 2]
+  static inline int pipe_grid[2][2] = {{0, 0}, {0, 0}};
+
+  template <bool SOLID, int STAGES>
+  static int setup_one(int sms) {
+    using PS = PipeShape<D, Q, T, STAGES>;
+    const void* fn = (const void*)k_collide_stream_pipe<D, Q, T, SOLID, STAGES>;
+    if (PS::SMEM > 227 * 1024) return 0;   // not launchable: leave grid 0
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PS::SMEM) !=
+        cudaSuccess)
+      return -1;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, PS::SMEM) != cudaSuccess)
+      return -1;
+    pipe_grid[SOLID ? 1 : 0][STAGES - 2] = per_sm > 0 ? per_sm * sms : 0;
+    return 0;
+  }
+
+  static int setup() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+    if (setup_one<false, 2>(sms) || setup_one<true, 2>(sms) || setup_one<false, 3>(sms) ||
+        setup_one<true, 3>(sms))
+      return -1;
+    return 0;
+  }
+
+  template <bool SOLID, int STAGES>
+  static void launch_pipe(cudaStream_t s, int grid, const int32_t* list, int n, const void* fin,
+                          void* fout, const int32_t* nbr, const uint64_t* sm,
+                          const StepParams& prm) {
+    k_collide_stream_pipe<D, Q, T, SOLID, STAGES>
+        <<<grid, 256, PipeShape<D, Q, T, STAGES>::SMEM, s>>>(list, n, (const T*)fin, (T*)fout,
+                                                            nbr, sm, prm);
+  }
+
   static void collide_stream(cudaStream_t s, const int32_t* list, int n, const void* fin,
                              void* fout, const int32_t* nbr, const uint64_t* sm,
                              const StepParams& prm, bool solid) {
     if (n <= 0) return;
+    const int tile = 256 / M;
+    const int n_tiles = (n + tile - 1) / tile;
+    const bool sol = solid && D == 3;
+    // variant 0 (auto): 2-stage pipeline for launches of at least two waves
+    const int stages = prm.variant == 3 ? 3 : 2;
+    const int pg = pipe_grid[sol ? 1 : 0][stages - 2];
+    const bool pipe = pg > 0 && (prm.variant >= 2 || (prm.variant == 0 && n_tiles >= 2 * pg));
+    if (pipe) {
+      const int grid = std::min(n_tiles, pg);
+      if (sol) {
+        if (stages == 3) launch_pipe<true, 3>(s, grid, list, n, fin, fout, nbr, sm, prm);
+        else launch_pipe<true, 2>(s, grid, list, n, fin, fout, nbr, sm, prm);
+      } else {
+        if (stages == 3) launch_pipe<false, 3>(s, grid, list, n, fin, fout, nbr, sm, prm);
+        else launch_pipe<false, 2>(s, grid, list, n, fin, fout, nbr, sm, prm);
+      }
+      return;
+    }
     const int grid = grid_for(n, 256 / M);
     if (solid && D == 3)
       k_collide_stream<D, Q, T, true><<<grid, 256, 0, s>>>(list, n, (const T*)fin, (T*)fout,
@@ -557,7 +771,7 @@ struct Launch {
                                                            nbr, sm, prm);
   }
   static void interp(cudaStream_t s, const int32_t* list, int n, const void* fpar, void* fch,
-                     size_t stride, const int32_t* child0, const uint32_t* nm, const uint64_t* sm,
+                     size_t stride, const int32_t* child0, const uint64_t* nm, const uint64_t* sm,
                      double ratio, int mode_all, bool solid) {
     if (n <= 0) return;
     const int grid = grid_for(n, 128 / M);
@@ -569,7 +783,7 @@ struct Launch {
                                                    child0, nm, sm, ratio, mode_all);
   }
   static void average(cudaStream_t s, const int32_t* list, int n, void* fpar, const void* fch,
-                      size_t stride, const int32_t* child0, const uint32_t* nm,
+                      size_t stride, const int32_t* child0, const uint64_t* nm,
                       const int32_t* status, const uint64_t* sm, double ratio, int mode_sync,
                       bool solid) {
     if (n <= 0) return;
@@ -623,7 +837,7 @@ struct Launch {
     return grid;
   }
   static const LbmOps* ops() {
-    static const LbmOps o = {collide_stream, interp,   average,      criterion,
+    static const LbmOps o = {setup, collide_stream, interp,   average,      criterion,
                              export_f,       import_f, export_rho_u, init_rest,
                              mass_partial,   force_partial};
     return &o;

@@ -17,21 +17,25 @@ struct FaceParams {
 struct StepParams {
   size_t stride;        // elements between population planes (capacity * M)
   double omega;         // 1 / tau_L
+  int variant;          // 0 auto, 1 one-pass, 2 / 3 pipelined (stages)
   FaceParams faces;
 };
 
 struct LbmOps {
+  // one-time kernel attributes (dynamic shared memory, occupancy); call
+  // outside any stream capture
+  int (*setup)();
   // fused BGK collision + push streaming over `list` (active blocks of a level)
   void (*collide_stream)(cudaStream_t, const int32_t* list, int n, const void* fin, void* fout,
                          const int32_t* nbr, const uint64_t* solidmask, const StepParams& prm,
                          bool solid);
   // coarse-to-fine linear interpolation: parents in `list`, into their children
   void (*interp)(cudaStream_t, const int32_t* list, int n, const void* fpar, void* fch,
-                 size_t stride, const int32_t* child0, const uint32_t* nonemask,
+                 size_t stride, const int32_t* child0, const uint64_t* cellmask,
                  const uint64_t* solidmask, double ratio, int mode_all, bool solid);
   // fine-to-coarse averaging into the parents in `list`
   void (*average)(cudaStream_t, const int32_t* list, int n, void* fpar, const void* fch,
-                  size_t stride, const int32_t* child0, const uint32_t* nonemask,
+                  size_t stride, const int32_t* child0, const uint64_t* cellmask,
                   const int32_t* status, const uint64_t* solidmask, double ratio, int mode_sync,
                   bool solid);
   // vorticity criterion marks (+1/-1/0) and block max |w|^2

@@ -167,8 +167,8 @@ template <int D>
 __global__ void k_init_root(int64_t cap, int n_root, int nbx, int nby, int nbz,
                             unsigned periodic, const int32_t* __restrict__ wall_code,
                             int32_t* level, int32_t* status, int32_t* child0, int32_t* parent,
-                            float* X, int32_t* nbr, uint32_t* nonemask, int32_t* gap,
-                            int32_t* idset0) {
+                            float* X, int32_t* nbr, uint32_t* nonemask, uint64_t* cellmask,
+                            int32_t* gap, int32_t* idset0) {
   using NV = typename Nbr<D>::V;
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= cap) return;
@@ -176,6 +176,7 @@ __global__ void k_init_root(int64_t cap, int n_root, int nbx, int nby, int nbz,
   child0[b] = NONE;
   parent[b] = NONE;
   nonemask[b] = 0u;
+  cellmask[2 * b] = cellmask[2 * b + 1] = 0ull;
   int32_t* row = nbr + (size_t)b * NBR_STRIDE;
   if (b >= n_root) {
     level[b] = -1;
@@ -313,7 +314,7 @@ __global__ void k_push_gaps(const int32_t* CL, int n, const int32_t* child0, int
 template <int D>
 __global__ void k_remove_children(const int32_t* C, int n, const int32_t* child0,
                                   int32_t* status, int32_t* level, int32_t* parent,
-                                  int32_t* nbr, uint32_t* nonemask) {
+                                  int32_t* nbr, uint32_t* nonemask, uint64_t* cellmask) {
   constexpr int NC = Block<D>::NC;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * NC) return;
@@ -323,6 +324,7 @@ __global__ void k_remove_children(const int32_t* C, int n, const int32_t* child0
   level[ch] = -1;
   parent[ch] = NONE;
   nonemask[ch] = 0u;
+  cellmask[2 * ch] = cellmask[2 * ch + 1] = 0ull;
   for (int k = 0; k < NBR_STRIDE; ++k) nbr[(size_t)ch * NBR_STRIDE + k] = NONE;
 }
 
@@ -366,7 +368,8 @@ __global__ void k_branch_leaf(int64_t cap, int32_t* status, const int32_t* child
 // neighbour without children gives NONE; wall codes pass through.
 template <int D>
 __global__ void k_relink(const int32_t* list, int n, const int32_t* parent,
-                         const int32_t* child0, int32_t* nbr, uint32_t* nonemask) {
+                         const int32_t* child0, int32_t* nbr, uint32_t* nonemask,
+                         uint64_t* cellmask) {
   using NV = typename Nbr<D>::V;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -406,6 +409,17 @@ __global__ void k_relink(const int32_t* list, int n, const int32_t* parent,
     if (v == NONE) nm |= 1u << K;
   });
   nonemask[X] = nm;
+  // ghost and interface cells of the block (Section 3.4 cell classes)
+  uint64_t gm = 0ull, im = 0ull;
+  if (nm != 0u) {
+    for (int l = 0; l < Block<D>::M; ++l) {
+      const int cls = cell_class<D>(nm, Block<D>::ci(l), Block<D>::cj(l), Block<D>::ck(l));
+      if (cls == 2) gm |= 1ull << l;
+      else if (cls == 1) im |= 1ull << l;
+    }
+  }
+  cellmask[2 * (size_t)X] = gm;
+  cellmask[2 * (size_t)X + 1] = im;
 }
 
 // ================================================================ exports
@@ -423,17 +437,16 @@ __global__ void k_export_nbr(int64_t cap, const int32_t* nbr, const int32_t* chi
 }
 
 template <int D>
-__global__ void k_export_masks(int64_t cap, const int32_t* status, const uint32_t* nonemask,
+__global__ void k_export_masks(int64_t cap, const int32_t* status, const uint64_t* cellmask,
                                uint8_t* out) {
   constexpr int M = Block<D>::M;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cap * M) return;
   const int64_t b = t / M;
   const int l = (int)(t - b * M);
-  out[t] = status[b] == ST_INACTIVE
-               ? 0
-               : (uint8_t)cell_class<D>(nonemask[b], Block<D>::ci(l), Block<D>::cj(l),
-                                        Block<D>::ck(l));
+  const bool ghost = (cellmask[2 * b] >> l) & 1ull;
+  const bool iface = (cellmask[2 * b + 1] >> l) & 1ull;
+  out[t] = status[b] == ST_INACTIVE ? 0 : (ghost ? 2 : (iface ? 1 : 0));
 }
 
 __global__ void k_export_coords(int64_t cap, int dim, const float* X, double* out) {
@@ -453,7 +466,8 @@ static int init_root_t(Instance* a) {
     if (a->cfg.faces[2 * ax].kind == AMR_FACE_PERIODIC) periodic |= 1u << ax;
   k_init_root<D><<<blocks_for(a->cap), 256, 0, s>>>(
       a->cap, (int)a->n_root, a->nroot[0], a->nroot[1], a->nroot[2], periodic, a->wall_code,
-      a->level, a->status, a->child0, a->parent, a->X, a->nbr, a->nonemask, a->gap, a->idset);
+      a->level, a->status, a->child0, a->parent, a->X, a->nbr, a->nonemask, a->cellmask, a->gap,
+      a->idset);
   AMR_CUDA(cudaGetLastError());
   AMR_CUDA(cudaMemsetAsync(a->solidmask, 0, sizeof(uint64_t) * a->cap, s));
   if (a->solid) {
@@ -545,7 +559,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
   if (nC > 0) {
     k_remove_children<D><<<blocks_for(nC * NC), 256, 0, s>>>(C, (int)nC, a->child0, a->status,
                                                               a->level, a->parent, a->nbr,
-                                                              a->nonemask);
+                                                              a->nonemask, a->cellmask);
     a->launches += 1;
     k_finish_coarsened<<<blocks_for(nC), 256, 0, s>>>(C, (int)nC, a->child0, a->status);
     a->launches += 1;
@@ -585,7 +599,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     if (a->n_ids[L] == 0) continue;
     k_relink<D><<<blocks_for(a->n_ids[L], 128), 128, 0, s>>>(a->idset + (size_t)L * cap,
                                                         (int)a->n_ids[L], a->parent, a->child0,
-                                                        a->nbr, a->nonemask);
+                                                        a->nbr, a->nonemask, a->cellmask);
     a->launches += 1;
     AMR_CUDA(cudaGetLastError());
   }
@@ -604,7 +618,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     AMR_CUDA(cudaGetLastError());
     const double ratio = a->tau[L + 1] / (2.0 * a->tau[L]);
     a->ops->interp(s, C + offR[L], (int)nRL[L], a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(),
-                   a->child0, a->nonemask, a->solidmask, ratio, 1, a->solid);
+                   a->child0, a->cellmask, a->solidmask, ratio, 1, a->solid);
     a->launches += 1;
     AMR_CUDA(cudaGetLastError());
   }
@@ -669,9 +683,9 @@ int mesh_export(Instance* a, int what, void* dst) {
       return AMR_OK;
     case AMR_MASKS:
       if (d3)
-        k_export_masks<3><<<blocks_for(cap * 64), 256, 0, s>>>(cap, a->status, a->nonemask, (uint8_t*)dst);
+        k_export_masks<3><<<blocks_for(cap * 64), 256, 0, s>>>(cap, a->status, a->cellmask, (uint8_t*)dst);
       else
-        k_export_masks<2><<<blocks_for(cap * 16), 256, 0, s>>>(cap, a->status, a->nonemask, (uint8_t*)dst);
+        k_export_masks<2><<<blocks_for(cap * 16), 256, 0, s>>>(cap, a->status, a->cellmask, (uint8_t*)dst);
       break;
     default:
       return AMR_E_INVAL;

@@ -26,9 +26,9 @@ def _lib():
     b.build()
 
 
-def new_gpu(cfg, storage):
+def new_gpu(cfg, storage, variant=0):
     from paper_2308_08085_gb300 import AmrLBM
-    return AmrLBM(cfg, storage=storage)
+    return AmrLBM(cfg, storage=storage, kernel_variant=variant)
 
 
 def randomize(ref, seed, noise=1e-3):
@@ -64,13 +64,16 @@ SINGLE = [
 ]
 
 
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("name,mk,storages", SINGLE, ids=[c[0] for c in SINGLE])
-def test_single_level_collide_stream(name, mk, storages):
+def test_single_level_collide_stream(name, mk, storages, variant):
+    """variant 1: one-pass kernel; 2 / 3: pipelined persistent kernel with 2 / 3
+    cp.async stages (forced here; the automatic choice uses it for large launches)."""
     for storage in storages:
         cfg = mk()
         ref = ForestLBM(cfg)
         randomize(ref, 21)
-        gpu = new_gpu(cfg, storage)
+        gpu = new_gpu(cfg, storage, variant)
         gpu.set_populations(ref.f)
         for _ in range(5):
             ref.step(1)
@@ -206,12 +209,13 @@ def test_three_level_step_2d(storage):
     gpu.close()
 
 
-@pytest.mark.parametrize("q,storage", [(19, "f64"), (19, "f32"), (27, "f64")])
-def test_two_level_step_3d(q, storage):
+@pytest.mark.parametrize("q,storage,variant", [(19, "f64", 1), (19, "f32", 1), (27, "f64", 1),
+                                               (19, "f32", 2), (27, "f32", 3)])
+def test_two_level_step_3d(q, storage, variant):
     cfg = W.cavity(dim=3, q=q, n=12, ny=8, nz=8, max_levels=3, max_blocks=12 * 40)
     sel = leaves_where(lambda m, b: m.X[b][2] >= 4 and m.X[b][0] >= 4)
     ref = ForestLBM(cfg)
-    gpu = new_gpu(cfg, storage)
+    gpu = new_gpu(cfg, storage, variant)
     for _ in range(2):
         m = np.zeros(cfg["max_blocks"], np.int8)
         m[sel(ref.mesh)] = 1
