@@ -39,6 +39,91 @@ __device__ __forceinline__ int geo_to_k(int code) {
   return D == 2 ? c_geo2.k_of_code[code] : c_geo3.k_of_code[code];
 }
 
+
+// Push targets of the fused collide-stream: for direction p and cell l the
+// entry packs the geometric code of the block that holds x + c_p (5 bits)
+// and the cell index inside it (6 bits): e = code | (cell << 5).
+template <int D, int Q>
+struct StreamTable {
+  uint16_t e[Q * Block<D>::M];
+};
+template <int D, int Q>
+constexpr StreamTable<D, Q> make_stream_table() {
+  StreamTable<D, Q> t{};
+  constexpr int M = Block<D>::M;
+  for (int p = 0; p < Q; ++p)
+    for (int l = 0; l < M; ++l) {
+      const int ti = Block<D>::ci(l) + VS<D, Q>::cx[p];
+      const int tj = Block<D>::cj(l) + VS<D, Q>::cy[p];
+      const int tk = Block<D>::ck(l) + VS<D, Q>::cz[p];
+      const int sx = ti < 0 ? -1 : (ti > 3 ? 1 : 0);
+      const int sy = tj < 0 ? -1 : (tj > 3 ? 1 : 0);
+      const int sz = tk < 0 ? -1 : (tk > 3 ? 1 : 0);
+      const int code = (sx + 1) + 3 * (sy + 1) + (D == 3 ? 9 * (sz + 1) : 0);
+      const int cell = (ti & 3) + 4 * (tj & 3) + (D == 3 ? 16 * (tk & 3) : 0);
+      t.e[p * M + l] = (uint16_t)(code | (cell << 5));
+    }
+  return t;
+}
+template <int D, int Q>
+__device__ const StreamTable<D, Q> g_stream_table = make_stream_table<D, Q>();
+
+// One BGK collision + push of a cell whose populations are f[]: the common
+// body of both collide-stream kernels.  `tab` is the stream table in shared
+// memory, `nb` the neighbour block IDs of the cell's block in geometric order.
+template <int D, int Q, class T, bool SOLID>
+__device__ __forceinline__ void collide_push(typename Store<T>::R (&f)[Q], int l, int b,
+                                             const uint16_t* __restrict__ tab,
+                                             const int32_t* __restrict__ nb,
+                                             const uint64_t* __restrict__ sm_nb,
+                                             T* __restrict__ fout, const StepParams& prm) {
+  using V = VS<D, Q>;
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int M = Block<D>::M;
+  const size_t stride = prm.stride;
+  R rho, ux, uy, uz;
+  moments<D, Q>(f, rho, ux, uy, uz);
+  const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+  const R om = R(prm.omega);
+  const int own = b * M + l;
+  static_for<0, Q>([&](auto P) {
+    constexpr int p = P;
+    constexpr int cx = V::cx[p], cy = V::cy[p], cz = V::cz[p];
+    constexpr int pb = V::opp[p];
+    const R fs = f[p] + om * (feq<D, Q, p>(rho, ux, uy, uz, usq15) - f[p]);
+    T* __restrict__ outp = fout + (size_t)p * stride;
+    if constexpr (p == 0) {
+      outp[own] = S::template save<D, Q, 0>(fs);
+    } else {
+      const int e = tab[p * M + l];
+      const int code = e & 31, tl = e >> 5;
+      const int tgt = nb[code];
+      bool bounce = tgt < 0;
+      if constexpr (SOLID) bounce = bounce || ((sm_nb[code] >> tl) & 1ull);
+      if (!bounce) {
+        outp[tgt * M + tl] = S::template save<D, Q, p>(fs);
+      } else {
+        R v = fs;   // NONE (interface) or solid: halfway bounce-back
+        if (tgt <= -2) {
+          const int face = -2 - tgt;
+          if (prm.faces.kind[face] == FACE_OUTLET) {
+            R cu = R(0);
+            if constexpr (cx != 0) cu += cx > 0 ? ux : -ux;
+            if constexpr (cy != 0) cu += cy > 0 ? uy : -uy;
+            if constexpr (cz != 0) cu += cz > 0 ? uz : -uz;
+            constexpr double wp = V::w[p];
+            v = -fs + R(2.0 * wp * prm.faces.rho_w[face]) * (R(1) + R(4.5) * cu * cu - usq15);
+          } else {
+            v = fs + R(prm.faces.bb[face][p]);
+          }
+        }
+        fout[(size_t)pb * stride + own] = S::template save<D, Q, pb>(v);
+      }
+    }
+  });
+}
+
 // ===================================================== fused collide + stream
 // One thread per cell, 256 threads = 256/M blocks per CTA.  Each cell loads its
 // Q populations (coalesced planes), relaxes them with BGK (Section 4.3) and
@@ -52,7 +137,6 @@ __global__ void __launch_bounds__(256)
     k_collide_stream(const int32_t* __restrict__ list, int n, const T* __restrict__ fin,
                      T* __restrict__ fout, const int32_t* __restrict__ nbr,
                      const uint64_t* __restrict__ solidmask, StepParams prm) {
-  using V = VS<D, Q>;
   using S = Store<T>;
   using R = typename S::R;
   constexpr int M = Block<D>::M;
@@ -61,10 +145,12 @@ __global__ void __launch_bounds__(256)
   constexpr int BPC = 256 / M;
   __shared__ int32_t s_nb[BPC][NCODE];
   __shared__ uint64_t s_sm[SOLID ? BPC : 1][SOLID ? NCODE : 1];
+  __shared__ uint16_t s_tab[Q * M];
 
   const int slot = threadIdx.x / M;
   const int l = threadIdx.x - slot * M;
   const int first = blockIdx.x * BPC;
+  for (int t = threadIdx.x; t < Q * M; t += blockDim.x) s_tab[t] = g_stream_table<D, Q>.e[t];
   for (int t = threadIdx.x; t < BPC * NCODE; t += blockDim.x) {
     const int s = t / NCODE, code = t - s * NCODE;
     const int k = geo_to_k<D>(code);
@@ -81,59 +167,14 @@ __global__ void __launch_bounds__(256)
     if ((s_sm[slot][CENTER] >> l) & 1ull) return;   // solid cells are not advanced
   }
   const size_t stride = prm.stride;
-  const size_t base = (size_t)b * M + l;
-
+  const int own = b * M + l;
   R f[Q];
   static_for<0, Q>([&](auto P) {
-    f[P] = S::template load<D, Q, P>(fin[(size_t)P * stride + base]);
+    f[P] = S::template load<D, Q, P>(fin[(size_t)P * stride + own]);
   });
-  R rho, ux, uy, uz;
-  moments<D, Q>(f, rho, ux, uy, uz);
-  const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
-  const R om = R(prm.omega);
-
-  const int i = Block<D>::ci(l), j = Block<D>::cj(l), kk = Block<D>::ck(l);
-  static_for<0, Q>([&](auto P) {
-    constexpr int p = P;
-    constexpr int cx = V::cx[p], cy = V::cy[p], cz = V::cz[p];
-    constexpr int pb = V::opp[p];
-    const R fs = f[p] + om * (feq<D, Q, p>(rho, ux, uy, uz, usq15) - f[p]);
-    if constexpr (p == 0) {
-      fout[base] = S::template save<D, Q, 0>(fs);
-    } else {
-      const int ti = i + cx, tj = j + cy, tk = kk + cz;
-      int code = CENTER;
-      if constexpr (cx != 0) code += (ti < 0) ? -1 : (ti > 3 ? 1 : 0);
-      if constexpr (cy != 0) code += (tj < 0) ? -3 : (tj > 3 ? 3 : 0);
-      if constexpr (D == 3 && cz != 0) code += (tk < 0) ? -9 : (tk > 3 ? 9 : 0);
-      const int tgt = s_nb[slot][code];
-      const int tl = (ti & 3) + 4 * (tj & 3) + (D == 3 ? 16 * (tk & 3) : 0);
-      bool bounce = tgt < 0;
-      if constexpr (SOLID) bounce = bounce || ((s_sm[slot][code] >> tl) & 1ull);
-      if (!bounce) {
-        fout[(size_t)p * stride + (size_t)tgt * M + tl] = S::template save<D, Q, p>(fs);
-      } else {
-        R v = fs;   // NONE (interface) or solid: halfway bounce-back
-        if (tgt <= -2) {
-          const int face = -2 - tgt;
-          if (prm.faces.kind[face] == FACE_OUTLET) {
-            R cu = R(0);
-            if constexpr (cx != 0) cu += cx > 0 ? ux : -ux;
-            if constexpr (cy != 0) cu += cy > 0 ? uy : -uy;
-            if constexpr (cz != 0) cu += cz > 0 ? uz : -uz;
-            constexpr double wp = V::w[p];
-            v = -fs + R(2.0 * wp * prm.faces.rho_w[face]) *
-                          (R(1) + R(4.5) * cu * cu - usq15);
-          } else {
-            v = fs + R(prm.faces.bb[face][p]);
-          }
-        }
-        fout[(size_t)pb * stride + base] = S::template save<D, Q, pb>(v);
-      }
-    }
-  });
+  collide_push<D, Q, T, SOLID>(f, l, b, s_tab, s_nb[slot], SOLID ? s_sm[slot] : nullptr, fout,
+                               prm);
 }
-
 
 // ================================== pipelined persistent collide + stream
 // Same arithmetic as k_collide_stream.  Each CTA walks tiles of 256/M blocks
@@ -178,8 +219,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 8 && Q == 27) ? 1 : 2)
   int32_t* srow = reinterpret_cast<int32_t*>(smem_raw + STAGES * (size_t)PS::STAGE_ELEMS * sizeof(T));
   __shared__ int32_t s_nb[TILE][NCODE];
   __shared__ uint64_t s_sm[SOLID ? TILE : 1][SOLID ? NCODE : 1];
+  __shared__ uint16_t s_tab[Q * M];
   const size_t stride = prm.stride;
   const int n_tiles = (n + TILE - 1) / TILE;
+  for (int t = threadIdx.x; t < Q * M; t += blockDim.x) s_tab[t] = g_stream_table<D, Q>.e[t];
 
   auto issue = [&](int tile, int stage) {
     constexpr int NCH = TILE * Q * PS::PLANE_CHUNKS;
@@ -208,8 +251,6 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 8 && Q == 27) ? 1 : 2)
 
   const int slot = threadIdx.x / M;
   const int l = threadIdx.x - slot * M;
-  const int i = Block<D>::ci(l), j = Block<D>::cj(l), kk = Block<D>::ck(l);
-  const R om = R(prm.omega);
   // prologue: the first STAGES-1 tiles of this CTA are requested up front
 #pragma unroll
   for (int k = 0; k < STAGES - 1; ++k) {
@@ -238,51 +279,11 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 8 && Q == 27) ? 1 : 2)
     if constexpr (SOLID) solid_cell = active && ((s_sm[slot][CENTER] >> l) & 1ull);
     if (active && !solid_cell) {
       const int b = s_nb[slot][CENTER];
-      const size_t base = (size_t)b * M + l;
       const T* sblk = sf + (size_t)stage * PS::STAGE_ELEMS + slot * Q * M;
       R f[Q];
       static_for<0, Q>([&](auto P) { f[P] = S::template load<D, Q, P>(sblk[P * M + l]); });
-      R rho, ux, uy, uz;
-      moments<D, Q>(f, rho, ux, uy, uz);
-      const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
-      static_for<0, Q>([&](auto P) {
-        constexpr int p = P;
-        constexpr int cx = V::cx[p], cy = V::cy[p], cz = V::cz[p];
-        constexpr int pb = V::opp[p];
-        const R fs = f[p] + om * (feq<D, Q, p>(rho, ux, uy, uz, usq15) - f[p]);
-        if constexpr (p == 0) {
-          fout[base] = S::template save<D, Q, 0>(fs);
-        } else {
-          const int ti = i + cx, tj = j + cy, tk = kk + cz;
-          int code = CENTER;
-          if constexpr (cx != 0) code += (ti < 0) ? -1 : (ti > 3 ? 1 : 0);
-          if constexpr (cy != 0) code += (tj < 0) ? -3 : (tj > 3 ? 3 : 0);
-          if constexpr (D == 3 && cz != 0) code += (tk < 0) ? -9 : (tk > 3 ? 9 : 0);
-          const int tgt = s_nb[slot][code];
-          const int tl = (ti & 3) + 4 * (tj & 3) + (D == 3 ? 16 * (tk & 3) : 0);
-          bool bounce = tgt < 0;
-          if constexpr (SOLID) bounce = bounce || ((s_sm[slot][code] >> tl) & 1ull);
-          if (!bounce) {
-            fout[(size_t)p * stride + (size_t)tgt * M + tl] = S::template save<D, Q, p>(fs);
-          } else {
-            R v = fs;
-            if (tgt <= -2) {
-              const int face = -2 - tgt;
-              if (prm.faces.kind[face] == FACE_OUTLET) {
-                R cu = R(0);
-                if constexpr (cx != 0) cu += cx > 0 ? ux : -ux;
-                if constexpr (cy != 0) cu += cy > 0 ? uy : -uy;
-                if constexpr (cz != 0) cu += cz > 0 ? uz : -uz;
-                constexpr double wp = V::w[p];
-                v = -fs + R(2.0 * wp * prm.faces.rho_w[face]) * (R(1) + R(4.5) * cu * cu - usq15);
-              } else {
-                v = fs + R(prm.faces.bb[face][p]);
-              }
-            }
-            fout[(size_t)pb * stride + base] = S::template save<D, Q, pb>(v);
-          }
-        }
-      });
+      collide_push<D, Q, T, SOLID>(f, l, b, s_tab, s_nb[slot], SOLID ? s_sm[slot] : nullptr,
+                                   fout, prm);
     }
     __syncthreads();
     stage = (stage + 1) % STAGES;
