@@ -96,7 +96,7 @@ __device__ __forceinline__ void collide_push(typename Store<T>::R (&f)[Q], int l
     if constexpr (p == 0) {
       outp[own] = S::template save<D, Q, 0>(fs);
     } else {
-      const int e = tab[p * M + l];
+      const int e = __ldg(tab + p * M + l);
       const int code = e & 31, tl = e >> 5;
       const int tgt = nb[code];
       bool bounce = tgt < 0;
@@ -132,8 +132,17 @@ __device__ __forceinline__ void collide_push(typename Store<T>::R (&f)[Q], int l
 // level (NONE), hits a wall, or hits a solid cell lands in the cell's own
 // opposite slot: halfway bounce-back, the moving-wall term, or the
 // anti-bounce-back outlet value (Section 2 boundary equations).
-template <int D, int Q, class T, bool SOLID>
-__global__ void __launch_bounds__(256)
+// resident warps per SM targeted by the one-pass kernel: 48 for FP32 math
+// with Q <= 19 (40 registers), fewer for the larger register footprints
+template <class T, int Q, int THREADS>
+constexpr int one_pass_min_blocks() {
+  const int threads_per_sm = sizeof(typename Store<T>::R) == 4 ? (Q <= 19 ? 1536 : 1024)
+                                                                : (Q <= 19 ? 1024 : 512);
+  return threads_per_sm / THREADS > 0 ? threads_per_sm / THREADS : 1;
+}
+
+template <int D, int Q, class T, bool SOLID, int THREADS, bool TAB_SMEM>
+__global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS>()))
     k_collide_stream(const int32_t* __restrict__ list, int n, const T* __restrict__ fin,
                      T* __restrict__ fout, const int32_t* __restrict__ nbr,
                      const uint64_t* __restrict__ solidmask, StepParams prm) {
@@ -142,16 +151,17 @@ __global__ void __launch_bounds__(256)
   constexpr int M = Block<D>::M;
   constexpr int NCODE = D == 2 ? 9 : 27;
   constexpr int CENTER = D == 2 ? 4 : 13;
-  constexpr int BPC = 256 / M;
+  constexpr int BPC = THREADS / M;
   __shared__ int32_t s_nb[BPC][NCODE];
   __shared__ uint64_t s_sm[SOLID ? BPC : 1][SOLID ? NCODE : 1];
-  __shared__ uint16_t s_tab[Q * M];
+  __shared__ uint16_t s_tab[TAB_SMEM ? Q * M : 1];
 
   const int slot = threadIdx.x / M;
   const int l = threadIdx.x - slot * M;
   const int first = blockIdx.x * BPC;
-  for (int t = threadIdx.x; t < Q * M; t += blockDim.x) s_tab[t] = g_stream_table<D, Q>.e[t];
-  for (int t = threadIdx.x; t < BPC * NCODE; t += blockDim.x) {
+  if constexpr (TAB_SMEM)
+    for (int t = threadIdx.x; t < Q * M; t += THREADS) s_tab[t] = g_stream_table<D, Q>.e[t];
+  for (int t = threadIdx.x; t < BPC * NCODE; t += THREADS) {
     const int s = t / NCODE, code = t - s * NCODE;
     const int k = geo_to_k<D>(code);
     const int bi = first + s;
@@ -172,7 +182,8 @@ __global__ void __launch_bounds__(256)
   static_for<0, Q>([&](auto P) {
     f[P] = S::template load<D, Q, P>(fin[(size_t)P * stride + own]);
   });
-  collide_push<D, Q, T, SOLID>(f, l, b, s_tab, s_nb[slot], SOLID ? s_sm[slot] : nullptr, fout,
+  const uint16_t* tab = TAB_SMEM ? s_tab : g_stream_table<D, Q>.e;
+  collide_push<D, Q, T, SOLID>(f, l, b, tab, s_nb[slot], SOLID ? s_sm[slot] : nullptr, fout,
                                prm);
 }
 
@@ -751,7 +762,8 @@ struct Launch {
     // variant 0 (auto): 2-stage pipeline for launches of at least two waves
     const int stages = prm.variant == 3 ? 3 : 2;
     const int pg = pipe_grid[sol ? 1 : 0][stages - 2];
-    const bool pipe = pg > 0 && (prm.variant >= 2 || (prm.variant == 0 && n_tiles >= 2 * pg));
+    const bool pipe = pg > 0 && (prm.variant == 2 || prm.variant == 3);
+    (void)n_tiles;
     if (pipe) {
       const int grid = std::min(n_tiles, pg);
       if (sol) {
@@ -763,13 +775,27 @@ struct Launch {
       }
       return;
     }
-    const int grid = grid_for(n, 256 / M);
-    if (solid && D == 3)
-      k_collide_stream<D, Q, T, true><<<grid, 256, 0, s>>>(list, n, (const T*)fin, (T*)fout,
-                                                          nbr, sm, prm);
-    else
-      k_collide_stream<D, Q, T, false><<<grid, 256, 0, s>>>(list, n, (const T*)fin, (T*)fout,
-                                                           nbr, sm, prm);
+    // one-pass kernel: variants 1 / 0 (auto): 512 threads, table in shared
+    // memory; 4: 256 threads, shared; 5: 256 threads, table from L1; 6: 512, L1
+    const int v = prm.variant;
+    if (sol) {
+      if (v == 4) one_pass<true, 256, true>(s, list, n, fin, fout, nbr, sm, prm);
+      else if (v == 5) one_pass<true, 256, false>(s, list, n, fin, fout, nbr, sm, prm);
+      else if (v == 6) one_pass<true, 512, false>(s, list, n, fin, fout, nbr, sm, prm);
+      else one_pass<true, 512, true>(s, list, n, fin, fout, nbr, sm, prm);
+    } else {
+      if (v == 4) one_pass<false, 256, true>(s, list, n, fin, fout, nbr, sm, prm);
+      else if (v == 5) one_pass<false, 256, false>(s, list, n, fin, fout, nbr, sm, prm);
+      else if (v == 6) one_pass<false, 512, false>(s, list, n, fin, fout, nbr, sm, prm);
+      else one_pass<false, 512, true>(s, list, n, fin, fout, nbr, sm, prm);
+    }
+  }
+
+  template <bool SOLID, int THREADS, bool TAB_SMEM>
+  static void one_pass(cudaStream_t s, const int32_t* list, int n, const void* fin, void* fout,
+                       const int32_t* nbr, const uint64_t* sm, const StepParams& prm) {
+    k_collide_stream<D, Q, T, SOLID, THREADS, TAB_SMEM><<<grid_for(n, THREADS / M), THREADS, 0, s>>>(
+        list, n, (const T*)fin, (T*)fout, nbr, sm, prm);
   }
   static void interp(cudaStream_t s, const int32_t* list, int n, const void* fpar, void* fch,
                      size_t stride, const int32_t* child0, const uint64_t* nm, const uint64_t* sm,

@@ -17,7 +17,7 @@ struct FaceParams {
 struct StepParams {
   size_t stride;        // elements between population planes (capacity * M)
   double omega;         // 1 / tau_L
-  int variant;          // 0 auto, 1 one-pass, 2 / 3 pipelined (stages)
+  int variant;          // collide-stream kernel variant (amr_config.kernel_variant)
   FaceParams faces;
 };
 

@@ -64,11 +64,12 @@ SINGLE = [
 ]
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("name,mk,storages", SINGLE, ids=[c[0] for c in SINGLE])
 def test_single_level_collide_stream(name, mk, storages, variant):
-    """variant 1: one-pass kernel; 2 / 3: pipelined persistent kernel with 2 / 3
-    cp.async stages (forced here; the automatic choice uses it for large launches)."""
+    """Every collide-stream kernel variant: one-pass with 512 / 256 threads and
+    the push table in shared memory or read through L1 (1, 4, 5, 6), and the
+    pipelined persistent kernel with 2 / 3 cp.async stages (2, 3)."""
     for storage in storages:
         cfg = mk()
         ref = ForestLBM(cfg)
