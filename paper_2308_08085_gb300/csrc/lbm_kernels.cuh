@@ -69,9 +69,10 @@ template <int D, int Q>
 __device__ const StreamTable<D, Q> g_stream_table = make_stream_table<D, Q>();
 
 // One BGK collision + push of a cell whose populations are f[]: the common
-// body of both collide-stream kernels.  `tab` is the stream table in shared
-// memory, `nb` the neighbour block IDs of the cell's block in geometric order.
-template <int D, int Q, class T, bool SOLID>
+// body of both collide-stream kernels.  `tab` is the stream table, in shared
+// memory when TAB_SMEM, else the global copy read through the read-only
+// path; `nb` the neighbour block IDs of the cell's block in geometric order.
+template <int D, int Q, class T, bool SOLID, bool TAB_SMEM>
 __device__ __forceinline__ void collide_push(typename Store<T>::R (&f)[Q], int l, int b,
                                              const uint16_t* __restrict__ tab,
                                              const int32_t* __restrict__ nb,
@@ -96,7 +97,9 @@ __device__ __forceinline__ void collide_push(typename Store<T>::R (&f)[Q], int l
     if constexpr (p == 0) {
       outp[own] = S::template save<D, Q, 0>(fs);
     } else {
-      const int e = __ldg(tab + p * M + l);
+      int e;
+      if constexpr (TAB_SMEM) e = tab[p * M + l];
+      else e = __ldg(tab + p * M + l);
       const int code = e & 31, tl = e >> 5;
       const int tgt = nb[code];
       bool bounce = tgt < 0;
@@ -182,9 +185,12 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS>()
   static_for<0, Q>([&](auto P) {
     f[P] = S::template load<D, Q, P>(fin[(size_t)P * stride + own]);
   });
-  const uint16_t* tab = TAB_SMEM ? s_tab : g_stream_table<D, Q>.e;
-  collide_push<D, Q, T, SOLID>(f, l, b, tab, s_nb[slot], SOLID ? s_sm[slot] : nullptr, fout,
-                               prm);
+  if constexpr (TAB_SMEM)
+    collide_push<D, Q, T, SOLID, true>(f, l, b, s_tab, s_nb[slot], SOLID ? s_sm[slot] : nullptr,
+                                       fout, prm);
+  else
+    collide_push<D, Q, T, SOLID, false>(f, l, b, g_stream_table<D, Q>.e, s_nb[slot],
+                                        SOLID ? s_sm[slot] : nullptr, fout, prm);
 }
 
 // ================================== pipelined persistent collide + stream
@@ -293,8 +299,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 8 && Q == 27) ? 1 : 2)
       const T* sblk = sf + (size_t)stage * PS::STAGE_ELEMS + slot * Q * M;
       R f[Q];
       static_for<0, Q>([&](auto P) { f[P] = S::template load<D, Q, P>(sblk[P * M + l]); });
-      collide_push<D, Q, T, SOLID>(f, l, b, s_tab, s_nb[slot], SOLID ? s_sm[slot] : nullptr,
-                                   fout, prm);
+      collide_push<D, Q, T, SOLID, true>(f, l, b, s_tab, s_nb[slot],
+                                         SOLID ? s_sm[slot] : nullptr, fout, prm);
     }
     __syncthreads();
     stage = (stage + 1) % STAGES;
