@@ -100,11 +100,11 @@ typedef struct {
                               centre is strictly inside is solid               */
   amr_face faces[6];       /* x-, x+, y-, y+, z-, z+ (first 4 used in 2D)      */
   int32_t use_graphs;      /* 1: replay the coarse step as a CUDA graph         */
-  int32_t kernel_variant;  /* collide-stream kernel: 0 / 1 one-pass, 512-thread
-                              CTAs, push table in shared memory; 4: 256-thread
-                              CTAs; 5: 256 threads, table read through L1;
-                              6: 512 threads, table through L1; 2 / 3: 2- / 3-
-                              stage cp.async pipeline in a persistent grid    */
+  int32_t kernel_variant;  /* collide-stream kernel: 0 (default) / 6 one-pass,
+                              512-thread CTAs, push table read through L1;
+                              1: 512 threads, table in shared memory; 4: 256
+                              threads, shared; 5: 256 threads, L1; 2 / 3: 2- /
+                              3-stage cp.async pipeline in a persistent grid  */
 } amr_config;
 
 typedef struct {

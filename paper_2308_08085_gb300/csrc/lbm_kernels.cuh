@@ -781,19 +781,20 @@ struct Launch {
       }
       return;
     }
-    // one-pass kernel: variants 1 / 0 (auto): 512 threads, table in shared
-    // memory; 4: 256 threads, shared; 5: 256 threads, table from L1; 6: 512, L1
+    // one-pass kernel: 1: 512 threads, table in shared memory; 4: 256 threads,
+    // shared; 5: 256 threads, table read through L1; 6 and 0 (auto, the fastest
+    // on the 256^3 forest): 512 threads, table through L1
     const int v = prm.variant;
     if (sol) {
-      if (v == 4) one_pass<true, 256, true>(s, list, n, fin, fout, nbr, sm, prm);
+      if (v == 1) one_pass<true, 512, true>(s, list, n, fin, fout, nbr, sm, prm);
+      else if (v == 4) one_pass<true, 256, true>(s, list, n, fin, fout, nbr, sm, prm);
       else if (v == 5) one_pass<true, 256, false>(s, list, n, fin, fout, nbr, sm, prm);
-      else if (v == 6) one_pass<true, 512, false>(s, list, n, fin, fout, nbr, sm, prm);
-      else one_pass<true, 512, true>(s, list, n, fin, fout, nbr, sm, prm);
+      else one_pass<true, 512, false>(s, list, n, fin, fout, nbr, sm, prm);
     } else {
-      if (v == 4) one_pass<false, 256, true>(s, list, n, fin, fout, nbr, sm, prm);
+      if (v == 1) one_pass<false, 512, true>(s, list, n, fin, fout, nbr, sm, prm);
+      else if (v == 4) one_pass<false, 256, true>(s, list, n, fin, fout, nbr, sm, prm);
       else if (v == 5) one_pass<false, 256, false>(s, list, n, fin, fout, nbr, sm, prm);
-      else if (v == 6) one_pass<false, 512, false>(s, list, n, fin, fout, nbr, sm, prm);
-      else one_pass<false, 512, true>(s, list, n, fin, fout, nbr, sm, prm);
+      else one_pass<false, 512, false>(s, list, n, fin, fout, nbr, sm, prm);
     }
   }
 
