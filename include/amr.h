@@ -105,6 +105,12 @@ typedef struct {
                               1: 512 threads, table in shared memory; 4: 256
                               threads, shared; 5: 256 threads, L1; 2 / 3: 2- /
                               3-stage cp.async pipeline in a persistent grid  */
+  double refine_dist;      /* distance refinement (Section 4.4): a leaf on level
+                              L within refine_dist / 2^L (physical units) of a
+                              target is marked for refinement; 0 = off        */
+  int32_t refine_dist_targets; /* bit 0: the solid prism, bit 1: outlet faces */
+  int32_t refine_dist_freeze;  /* 1: blocks refined by distance become
+                                  AMR_ST_REFINED_PERMANENT                    */
 } amr_config;
 
 typedef struct {
@@ -152,9 +158,10 @@ int amr_step(amr_t* a, int n_coarse_steps);
 
 /* Adapt the mesh (Sections 3.3 and 4.4): synchronise all levels (average
  * bottom-up, interpolate ghosts top-down), mark blocks -- from the vorticity
- * criterion of Algorithm 3 when `dev_marks` is NULL, else from the caller's
- * device array of int8 marks indexed by block ID (+1 refine, -1 coarsen,
- * 0 keep; max_blocks entries) -- keep the eligible marks (refine: leaf below
+ * criterion of Algorithm 3 and the distance rule (refine_dist) when
+ * `dev_marks` is NULL, else from the caller's device array of int8 marks
+ * indexed by block ID (+1 refine, +2 refine and freeze, -1 coarsen, 0 keep;
+ * max_blocks entries) -- keep the eligible marks (refine: leaf below
  * L_max-1 with every same-level neighbour present; coarsen: status REFINED),
  * revert coarsening that would break 2:1 balance, allocate children from the
  * gap set, remove children, update ID sets, statuses, connectivity and cell

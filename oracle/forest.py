@@ -235,11 +235,13 @@ class Forest:
         return self.status[b] == REFINED
 
     def adapt(self, marks, permanent=None):
-        """Apply per-block marks (+1 refine, -1 coarsen, 0 keep; indexed by
-        block ID).  `permanent` (optional bool array) makes refined blocks
-        REFINED_PERMANENT.  Returns a dict of counts and the list of new
-        children."""
+        """Apply per-block marks (+1 refine, +2 refine and freeze, -1 coarsen,
+        0 keep; indexed by block ID).  A frozen (or `permanent`) refined block
+        becomes REFINED_PERMANENT and is never coarsened.  Returns a dict of
+        counts and the list of new children."""
         marks = np.asarray(marks)
+        if permanent is None:
+            permanent = marks == 2
         ids = sorted(self.active_ids())
         refine = [b for b in ids if marks[b] > 0 and self.can_refine(b)]
         coarsen = [b for b in ids if marks[b] < 0 and self.can_coarsen(b)]

@@ -35,6 +35,17 @@ Readings of the paper (where it is silent or garbled)
   |w|^2 < 4^T for T = N_start - p N_inc (p = 1 .. L_max-1, last hit wins).
   Leaves with L_des > L are marked for refinement, REFINED blocks whose own
   cells give L_des <= L are marked for coarsening.
+* Distance rule (Section 4.4, used by the channel flow of Section 5.3): a leaf
+  on level L whose block lies within d_spec / 2^L (physical) of a target -- the
+  solid prism (Euclidean distance between the block square and the prism
+  square in the x-y plane) or an outlet face -- is marked for refinement
+  (+2, frozen, when refine_dist_freeze); a refined block within that distance
+  loses any coarsening mark.  Distances are compared squared, in root-cell
+  units, without fused operations.
+* Momentum exchange (Section 5.3): the printed F = 2 dx^N_d sum f* c is read
+  with the time step dt = dx of the link: F = 2 dx^(N_d - 1) sum f*_p c_p over
+  links from fluid cells into solid cells, dx the physical cell size of the
+  cell's level; C_D = 2 F_x / (rho_0 U_0^2 D H) with the span H in 3D.
 * Solid cells always hold the rest equilibrium: they are not collided,
   streamed, interpolated into or averaged into.
 """
@@ -304,7 +315,8 @@ class ForestLBM:
         return ldes
 
     def criterion_marks(self):
-        """Per-block marks from the vorticity criterion (after sync())."""
+        """Per-block marks from the vorticity criterion and the distance rule
+        (after sync())."""
         mesh = self.mesh
         marks = np.zeros(mesh.cap, np.int8)
         w2s = {}
@@ -320,7 +332,40 @@ class ForestLBM:
                 marks[b] = 1
             elif st == REFINED and ldes <= L:
                 marks[b] = -1
+        if self.cfg.get("refine_dist", 0.0) > 0.0:
+            freeze = bool(self.cfg.get("refine_dist_freeze", 0))
+            for b in mesh.active_ids():
+                if self.within_refine_distance(b):
+                    if mesh.status[b] == UNREFINED:
+                        marks[b] = 2 if freeze else 1
+                    elif marks[b] < 0:
+                        marks[b] = 0
         return marks, w2s
+
+    def within_refine_distance(self, b):
+        """Distance rule of Section 4.4 (see module doc)."""
+        cfg, mesh = self.cfg, self.mesh
+        L = int(mesh.level[b])
+        thr = (cfg["refine_dist"] * cfg["nx"] / cfg["length_x"]) / (2.0 ** L)
+        thr2 = thr * thr
+        w = mesh.width(L)
+        X = mesh.X[b]
+        targets = int(cfg.get("refine_dist_targets", 0))
+        if targets & 1 and cfg.get("solid") is not None:
+            x0, x1, y0, y1 = cfg["solid"]
+            dx = max(x0 - (X[0] + w), X[0] - x1, 0.0)
+            dy = max(y0 - (X[1] + w), X[1] - y1, 0.0)
+            if dx * dx + dy * dy < thr2:
+                return True
+        if targets & 2:
+            for fi, face in enumerate(cfg["faces"][:2 * self.dim]):
+                if face[0] != "outlet":
+                    continue
+                a = fi // 2
+                d = (mesh.extent[a] - (X[a] + w)) if fi % 2 else X[a]
+                if d * d < thr2:
+                    return True
+        return False
 
     # ------------------------------------------------------------ adapting
     def adapt(self, marks=None):
@@ -348,8 +393,8 @@ class ForestLBM:
 
     def mea_force(self, level=None):
         """Momentum-exchange force on the solid (Section 5.3):
-        F = 2 dx^dim sum over fluid cells x_b and links p with x_b + c_p solid
-        of f*_p c_p, dx in physical units of the cell's level.  Parity
+        F = 2 dx^(dim-1) sum over fluid leaf cells x_b and links p with x_b + c_p
+        solid of f*_p c_p, dx the physical cell size of the level.  Parity
         unpinned in 3D (no printed value); computed from the current state
         (post-collision values recomputed here)."""
         mesh, vs = self.mesh, self.vs
@@ -375,7 +420,7 @@ class ForestLBM:
                     tl = np.mod(t, BLOCK_EDGE)
                     li = tl[0] + 4 * tl[1] + (16 * tl[2] if self.dim == 3 else 0)
                     if self.solid[nb, li]:
-                        F += 2.0 * dx ** self.dim * fstar[l, p] * vs.cf[p]
+                        F += 2.0 * dx ** (self.dim - 1) * fstar[l, p] * vs.cf[p]
         return F
 
     def _near_solid(self, b):

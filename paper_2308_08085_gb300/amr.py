@@ -41,7 +41,8 @@ class AmrConfig(ctypes.Structure):
                 ("max_blocks", ctypes.c_int64), ("nu0", ctypes.c_double),
                 ("length_x", ctypes.c_double), ("solid", ctypes.c_double * 4),
                 ("faces", AmrFace * 6), ("use_graphs", ctypes.c_int32),
-                ("kernel_variant", ctypes.c_int32)]
+                ("kernel_variant", ctypes.c_int32), ("refine_dist", ctypes.c_double),
+                ("refine_dist_targets", ctypes.c_int32), ("refine_dist_freeze", ctypes.c_int32)]
 
 
 class AmrAdaptStats(ctypes.Structure):
@@ -124,6 +125,9 @@ def make_config(cfg, storage="f32", use_graphs=True, kernel_variant=0):
         c.faces[i].rho_w = face[2] if len(face) > 2 else 1.0
     c.use_graphs = 1 if use_graphs else 0
     c.kernel_variant = int(kernel_variant)
+    c.refine_dist = float(cfg.get("refine_dist", 0.0))
+    c.refine_dist_targets = int(cfg.get("refine_dist_targets", 0))
+    c.refine_dist_freeze = int(cfg.get("refine_dist_freeze", 0))
     return c
 
 

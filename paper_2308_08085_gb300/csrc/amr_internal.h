@@ -90,6 +90,7 @@ int mesh_init_root(Instance* a);
 int mesh_adapt(Instance* a, bool external, amr_adapt_stats* st);
 int mesh_export(Instance* a, int what, void* dst_dev);
 int mesh_refresh_lists(Instance* a);
+int mesh_distance_marks(Instance* a);
 int64_t mesh_export_bytes(const Instance* a, int what);
 
 #define AMR_CUDA(call)                                                             \

@@ -16,6 +16,10 @@
 #include "amr_internal.h"
 #include "lattice.cuh"
 
+static_assert(sizeof(amr_config) == 360, "amr_config layout is part of the ABI");
+static_assert(sizeof(amr_adapt_stats) == 56, "amr_adapt_stats layout is part of the ABI");
+static_assert(sizeof(amr_kernel_profile) == 64, "amr_kernel_profile layout is part of the ABI");
+
 namespace amr {
 
 static thread_local std::string g_last_error;
@@ -548,6 +552,8 @@ int amr_adapt(amr_t* h, const int8_t* dev_marks, amr_adapt_stats* out) {
                         a->cfg.crit_start, a->cfg.crit_inc, a->marks, a->w2);
       a->launches += 1;
     }
+    const int drc = mesh_distance_marks(a);
+    if (drc != AMR_OK) return drc;
   }
   AMR_CUDA(cudaGetLastError());
   int rc = mesh_adapt(a, dev_marks != nullptr, &st);

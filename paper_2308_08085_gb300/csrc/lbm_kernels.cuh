@@ -663,8 +663,9 @@ __global__ void __launch_bounds__(256)
   block_sum_store<4>(acc, partial);
 }
 
-// Momentum-exchange force: F = 2 dx^D sum over fluid cells and links p whose
-// target x + c_p is solid of f*_p c_p (Section 5.3), f* recomputed by BGK.
+// Momentum-exchange force: F = 2 dx^(D-1) sum over fluid cells and links p
+// whose target x + c_p is solid of f*_p c_p (Section 5.3, with dt = dx per
+// link), f* recomputed by BGK from the stored state.
 template <int D, int Q, class T>
 __global__ void __launch_bounds__(256)
     k_force_partial(const int32_t* __restrict__ list, int n, const T* __restrict__ f,
@@ -710,7 +711,7 @@ __global__ void __launch_bounds__(256)
       acc[2] += (double)fs * cz;
     });
   }
-  const double scale = 2.0 * pow(dx, (double)D);
+  const double scale = 2.0 * pow(dx, (double)(D - 1));
   for (int a = 0; a < 3; ++a) acc[a] *= scale;
   block_sum_store<3>(acc, partial);
 }

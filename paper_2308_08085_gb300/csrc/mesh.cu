@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 
 #include "amr_internal.h"
@@ -91,6 +92,10 @@ struct PMarkEq {
   int v;
   __device__ bool operator()(int i) const { return m[i] == v; }
 };
+struct PMarkPos {   // refine marks: +1, or +2 (refine and freeze)
+  const int8_t* m;
+  __device__ bool operator()(int i) const { return m[i] > 0; }
+};
 struct PLevelEq {
   const int32_t* list;
   const int32_t* level;
@@ -152,6 +157,10 @@ static int compact(Instance* a, int64_t n, Pred pred, Val val, int32_t* out, int
     *count = c;
   }
   return AMR_OK;
+}
+
+static inline int blocks_for(int64_t n, int t = 256) {
+  return (int)std::max<int64_t>(1, (n + t - 1) / t);
 }
 
 #define AMR_TRY(x)            \
@@ -240,14 +249,14 @@ __global__ void k_eligible(int64_t cap, int8_t* marks, const int32_t* status,
   const int m = marks[b];
   const int st = status[b];
   int8_t out = 0;
-  if (m > 0 && st == ST_UNREFINED && level[b] < lmax - 1 && nonemask[b] == 0u) out = 1;
+  if (m > 0 && st == ST_UNREFINED && level[b] < lmax - 1 && nonemask[b] == 0u) out = m > 1 ? 2 : 1;
   else if (m < 0 && st == ST_REFINED) out = -1;
   marks[b] = out;
 }
 
 __global__ void k_clear_refine(int64_t cap, int8_t* marks) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < cap && marks[b] == 1) marks[b] = 0;
+  if (b < cap && marks[b] > 0) marks[b] = 0;
 }
 
 // Step 3: a coarsen mark is reverted when a child has a same-level neighbour
@@ -262,7 +271,7 @@ __global__ void k_revert(int64_t cap, int8_t* marks, const int32_t* child0, cons
     const int32_t* row = nbr + (size_t)(c0 + c) * NBR_STRIDE;
     for (int k = 0; k < nk; ++k) {
       const int nb = row[k];
-      if (nb >= 0 && (child0[nb] >= 0 || marks[nb] == 1)) {
+      if (nb >= 0 && (child0[nb] >= 0 || marks[nb] > 0)) {
         violating = true;
         break;
       }
@@ -335,9 +344,10 @@ __global__ void k_finish_coarsened(const int32_t* C, int n, int32_t* child0, int
   status[C[i]] = ST_UNREFINED;
 }
 
-__global__ void k_set_status(const int32_t* list, int n, int32_t* status, int v) {
+// refined blocks: REFINED, or REFINED_PERMANENT when the mark froze them
+__global__ void k_set_refined(const int32_t* list, int n, const int8_t* marks, int32_t* status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) status[list[i]] = v;
+  if (i < n) status[list[i]] = marks[list[i]] == 2 ? ST_PERM : ST_REFINED;
 }
 
 template <int D>
@@ -422,6 +432,61 @@ __global__ void k_relink(const int32_t* list, int n, const int32_t* parent,
   cellmask[2 * (size_t)X + 1] = im;
 }
 
+// Distance rule (Section 4.4): a leaf on level L within thr (root-cell units,
+// compared squared) of the solid prism or an outlet face is marked +1 (+2 when
+// frozen); a refined block within thr loses its coarsening mark.  Products and
+// sums are rounded separately so the decision is that of plain FP64.
+__global__ void k_distance_marks(const int32_t* list, int n, int level, const int32_t* status,
+                                 const float* X, int8_t* marks, double thr2, int targets,
+                                 int has_solid, double sx0, double sx1, double sy0, double sy1,
+                                 unsigned outlet_faces, double ex, double ey, double ez,
+                                 int freeze) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = list[i];
+  const double w = 4.0 / (double)(1 << level);
+  const double x = (double)X[3 * b], y = (double)X[3 * b + 1], z = (double)X[3 * b + 2];
+  bool within = false;
+  if ((targets & 1) && has_solid) {
+    const double dx = fmax(fmax(__dsub_rn(sx0, __dadd_rn(x, w)), __dsub_rn(x, sx1)), 0.0);
+    const double dy = fmax(fmax(__dsub_rn(sy0, __dadd_rn(y, w)), __dsub_rn(y, sy1)), 0.0);
+    within = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) < thr2;
+  }
+  if (targets & 2) {
+    const double lo[3] = {x, y, z};
+    const double ext[3] = {ex, ey, ez};
+    for (int f = 0; f < 6; ++f) {
+      if (!((outlet_faces >> f) & 1u)) continue;
+      const int ax = f >> 1;
+      const double d = (f & 1) ? __dsub_rn(ext[ax], __dadd_rn(lo[ax], w)) : lo[ax];
+      if (__dmul_rn(d, d) < thr2) within = true;
+    }
+  }
+  if (!within) return;
+  const int st = status[b];
+  if (st == ST_UNREFINED) marks[b] = freeze ? 2 : 1;
+  else if (marks[b] < 0) marks[b] = 0;
+}
+
+int mesh_distance_marks(Instance* a) {
+  const amr_config& c = a->cfg;
+  if (!(c.refine_dist > 0.0) || c.refine_dist_targets == 0) return AMR_OK;
+  unsigned outlets = 0;
+  for (int f = 0; f < 2 * a->dim; ++f)
+    if (c.faces[f].kind == AMR_FACE_OUTLET) outlets |= 1u << f;
+  for (int L = 0; L < a->lmax; ++L) {
+    if (a->n_ids[L] == 0) continue;
+    const double thr = (c.refine_dist * c.nx / c.length_x) / std::ldexp(1.0, L);
+    k_distance_marks<<<blocks_for(a->n_ids[L]), 256, 0, a->stream>>>(
+        a->idset + (size_t)L * a->cap, (int)a->n_ids[L], L, a->status, a->X, a->marks, thr * thr,
+        c.refine_dist_targets, c.has_solid, c.solid[0], c.solid[1], c.solid[2], c.solid[3],
+        outlets, (double)c.nx, (double)c.ny, (double)(a->dim == 3 ? c.nz : 0), c.refine_dist_freeze);
+    a->launches += 1;
+    AMR_CUDA(cudaGetLastError());
+  }
+  return AMR_OK;
+}
+
 // ================================================================ exports
 template <int D>
 __global__ void k_export_nbr(int64_t cap, const int32_t* nbr, const int32_t* child0, int mode,
@@ -456,7 +521,6 @@ __global__ void k_export_coords(int64_t cap, int dim, const float* X, double* ou
 }
 
 // ============================================================ host side
-static inline int blocks_for(int64_t n, int t = 256) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
 
 template <int D>
 static int init_root_t(Instance* a) {
@@ -512,7 +576,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
   a->launches += 1;
   AMR_CUDA(cudaGetLastError());
   int64_t nR = 0, nC = 0, nC0 = 0;
-  AMR_TRY(compact(a, cap, PMarkEq{a->marks, 1}, VIdent{}, R, &nR));
+  AMR_TRY(compact(a, cap, PMarkPos{a->marks}, VIdent{}, R, &nR));
   AMR_TRY(compact(a, cap, PMarkEq{a->marks, -1}, VIdent{}, nullptr, &nC0, 0, false));
   st->n_marked_refine = nR;
   st->n_marked_coarsen = nC0;
@@ -567,7 +631,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
   }
   a->n_gaps += nC * NC;
   if (nR > 0) {
-    k_set_status<<<blocks_for(nR), 256, 0, s>>>(R, (int)nR, a->status, ST_REFINED);
+    k_set_refined<<<blocks_for(nR), 256, 0, s>>>(R, (int)nR, a->marks, a->status);
     a->launches += 1;
     AMR_CUDA(cudaGetLastError());
   }

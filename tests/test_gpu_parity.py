@@ -297,3 +297,62 @@ def test_mass_audit_matches_oracle():
     assert abs(ms[0] - mass) <= 1e-12 * mass
     assert abs(ms[1] - mom_x) <= 1e-12 * max(1.0, abs(mom_x))
     gpu.close()
+
+
+# ------------------------------------------------ cylinder, distance rule, force
+def test_cylinder_distance_rule_force_end_to_end():
+    cfg = W.channel_cylinder(q=19, nx=48, ny=24, nz=8, side=4, cx=16, cy=12, max_levels=3,
+                             max_blocks=72 * 30, refine_dist=0.15)
+    ref, gpu = run_pair(cfg, "f64", 60, 20)
+    compare_tables(gpu, ref.mesh)
+    assert np.any(ref.mesh.status == 4)             # frozen blocks around prism and outlet
+    ref.sync()
+    gpu.rho_u()
+    ids = ref.mesh.active_ids()
+    assert rel_l2(gpu.populations()[ids], ref.f[ids]) <= 1e-12
+    f_ref = ref.mea_force()
+    f_gpu = gpu.force()
+    assert abs(f_ref[0]) > 0
+    assert np.max(np.abs(f_gpu - f_ref)) <= 1e-11 * np.max(np.abs(f_ref))
+    gpu.close()
+
+
+# ------------------------------------------------------- 16-bit storage
+@pytest.mark.parametrize("storage,unit_roundoff", [("bf16", 2.0 ** -8), ("f16", 2.0 ** -11)])
+def test_shifted_16bit_storage_within_rounding_bound(storage, unit_roundoff):
+    """Populations stored as g = f - w_p in BF16 / FP16 (FP32 arithmetic).
+    Every store rounds g to nearest with relative error <= u (unit roundoff);
+    the error after n coarse steps of a two-level forest is bounded by the
+    number of stores a value goes through, K = 1 + n * 2^(L_max-1) * 2
+    (collide-stream plus interpolation/averaging), times u |g| / |f|."""
+    cfg = W.cavity(dim=3, q=19, n=12, ny=8, nz=8, max_levels=2, max_blocks=12 * 12)
+    sel = leaves_where(lambda m, b: m.X[b][0] >= 4)
+    ref = ForestLBM(cfg)
+    gpu = new_gpu(cfg, storage)
+    gpu32 = new_gpu(cfg, "f32")
+    m = np.zeros(cfg["max_blocks"], np.int8)
+    m[sel(ref.mesh)] = 1
+    ref.adapt(m)
+    gpu.adapt(marks_tensor(m))
+    gpu32.adapt(marks_tensor(m))
+    randomize(ref, 31)
+    ids = ref.mesh.active_ids()
+    g = ref.f[ids] - ref.vs.w
+    ratio = np.linalg.norm(g) / np.linalg.norm(ref.f[ids])
+    gpu.set_populations(ref.f)
+    gpu32.set_populations(ref.f)
+    n = 4
+    ref.step(n)
+    gpu.step(n)
+    gpu32.step(n)
+    ref.sync()
+    gpu.rho_u()
+    gpu32.rho_u()
+    err = rel_l2(gpu.populations()[ids], ref.f[ids])
+    err32 = rel_l2(gpu32.populations()[ids], ref.f[ids])
+    K = 1 + n * 2 ** (cfg["max_levels"] - 1) * 2
+    bound = K * unit_roundoff * ratio
+    assert 0 < err <= bound, (err, bound)
+    assert err32 < err / 10
+    gpu.close()
+    gpu32.close()

@@ -489,3 +489,54 @@ def test_mlups_count_brute_force():
     leaves = [b for b in lbm.mesh.active_ids() if lbm.mesh.status[b] == UNREFINED]
     brute = sum(2 ** lbm.mesh.level[b] * 64 for b in leaves)
     assert lbm.updates_per_coarse_step() == brute
+
+
+# ---------------------------------------------------------- distance rule
+def brute_distance(box_a, box_b, n=41):
+    """Minimum Euclidean distance between two axis-aligned squares by dense
+    sampling of both (exact to the sampling step)."""
+    def pts(b):
+        xs = np.linspace(b[0], b[1], n)
+        ys = np.linspace(b[2], b[3], n)
+        X, Y = np.meshgrid(xs, ys)
+        return np.stack([X.ravel(), Y.ravel()], 1)
+    pa, pb = pts(box_a), pts(box_b)
+    d = np.sqrt(((pa[:, None, :] - pb[None, :, :]) ** 2).sum(-1))
+    return d.min(), max((box_a[1] - box_a[0]), (box_b[1] - box_b[0])) / (n - 1)
+
+
+def test_distance_rule_matches_brute_force():
+    cfg = W.channel_cylinder(q=19, nx=48, ny=24, nz=4, side=4, cx=16, cy=12, max_levels=3,
+                             refine_dist=0.15)
+    lbm = ForestLBM(cfg)
+    lbm.mesh.adapt(np.ones(lbm.mesh.cap, np.int8))      # two levels to test
+    lbm.mesh.adapt(np.ones(lbm.mesh.cap, np.int8))
+    x0, x1, y0, y1 = cfg["solid"]
+    checked = 0
+    for b in lbm.mesh.active_ids():
+        L = int(lbm.mesh.level[b])
+        w = lbm.mesh.width(L)
+        X = lbm.mesh.X[b]
+        thr = 0.15 * cfg["nx"] / 2 ** L
+        d_solid, step = brute_distance((X[0], X[0] + w, X[1], X[1] + w), (x0, x1, y0, y1))
+        d_out = cfg["nx"] - (X[0] + w)
+        near = min(d_solid, d_out)
+        if abs(near - thr) <= 2 * step:
+            continue                                      # undecidable at this sampling
+        assert lbm.within_refine_distance(b) == (near < thr), b
+        checked += 1
+    assert checked > 50
+
+
+def test_frozen_blocks_are_never_coarsened():
+    cfg = W.cavity(dim=2, n=8, max_levels=3, max_blocks=4 + 4 * 8)
+    mesh = Forest(cfg)
+    m = np.zeros(mesh.cap, np.int8)
+    m[[0, 1]] = [2, 1]                                   # 0 frozen, 1 plain
+    mesh.adapt(m)
+    assert mesh.status[0] == 4 and mesh.status[1] == REFINED
+    m[:] = 0
+    m[[0, 1]] = -1
+    res = mesh.adapt(m)
+    assert res["n_coarsened"] == 1 and mesh.status[0] == 4 and mesh.status[1] == UNREFINED
+    brute_force_check(mesh)

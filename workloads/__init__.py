@@ -21,6 +21,9 @@ max_blocks        block capacity (IDs 0 .. max_blocks-1)
 solid             None or (x0, x1, y0, y1): a square prism spanning z, in
                   root-cell units; a cell is solid when its centre lies inside
 length_x          physical domain length along x (dx_0 = length_x / nx)
+refine_dist       distance refinement: physical distance d_spec (0 = off)
+refine_dist_targets  bit 0 the solid prism, bit 1 the outlet faces
+refine_dist_freeze   1: blocks refined by distance are never coarsened
 """
 import numpy as np
 
@@ -83,10 +86,12 @@ def periodic_box(dim=2, q=None, n=32, nu0=0.05, max_levels=1, max_blocks=None,
 
 def channel_cylinder(q=27, nx=256, ny=64, nz=64, side=8, cx=64, cy=32,
                      u0=0.05, re=100.0, max_levels=5, max_blocks=None,
-                     crit_start=-3, crit_inc=1):
+                     crit_start=-3, crit_inc=1, refine_dist=0.15):
     """3D channel past a square prism (Section 5.3 in 3D): uniform inlet at
     x- and far field on the y/z faces (moving-wall bounce-back with
-    u = (u0, 0, 0)), anti-bounce-back outlet at x+.  nu0 = u0 * side / Re."""
+    u = (u0, 0, 0)), anti-bounce-back outlet at x+.  nu0 = u0 * side / Re.
+    Blocks within refine_dist / 2^L of the prism or the outlet are refined and
+    frozen (the paper's 0.15 / 2^L rule, channel length 1)."""
     faces = [("moving", (u0, 0.0, 0.0)), ("outlet", (0.0, 0.0, 0.0)),
              ("moving", (u0, 0.0, 0.0)), ("moving", (u0, 0.0, 0.0)),
              ("moving", (u0, 0.0, 0.0)), ("moving", (u0, 0.0, 0.0))]
@@ -95,7 +100,8 @@ def channel_cylinder(q=27, nx=256, ny=64, nz=64, side=8, cx=64, cy=32,
     cfg = dict(dim=3, q=q, nx=nx, ny=ny, nz=nz, max_levels=max_levels,
                nu0=u0 * side / re, faces=faces, crit_start=crit_start,
                crit_inc=crit_inc, max_blocks=max_blocks or nroot * 8 + 64,
-               solid=(cx - h, cx + h, cy - h, cy + h), length_x=1.0)
+               solid=(cx - h, cx + h, cy - h, cy + h), length_x=1.0,
+               refine_dist=refine_dist, refine_dist_targets=3, refine_dist_freeze=1)
     return finalize(cfg)
 
 
