@@ -353,6 +353,81 @@ def run_bar(args, AmrLBM, W, torch, dev, stream):
             "kernel_gbs": round(kernel_gbs, 1), "frac": round(kernel_gbs / peak, 4)}
 
 
+# ------------------------------------------------------- cylinder workload
+def run_cylinder(args):
+    """Channel past a square prism, D3Q27 BGK, FP32 arithmetic with FP64 /
+    FP32 / BF16 / FP16 storage on one static mesh (distance refinement with
+    freezing, vorticity refinement off so every storage sees the same mesh).
+    Reports MLUPS per storage, relative L2 of rho and u per level against the
+    FP64 run, and the drag coefficient from the momentum-exchange force."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2308_08085_gb300 import AMR_RHO_U, AmrLBM
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    nx = args.cyl_nx
+    scale = nx / 256
+    cfg = W.channel_cylinder(q=27, nx=nx, ny=int(64 * scale), nz=int(64 * scale),
+                             side=8 * scale, cx=64 * scale, cy=32 * scale,
+                             max_levels=args.cyl_levels, crit_start=100, crit_inc=1,
+                             max_blocks=args.cyl_cap)
+    u0, side = 0.05, 8 * scale
+    area = (side / nx) * (cfg["nz"] / nx)           # D * H in physical units (length_x = 1)
+    results, ref = {}, None
+    for storage in args.cyl_storages.split(","):
+        sim = AmrLBM(cfg, storage=storage)
+        for _ in range(args.cyl_levels):            # static distance-refined mesh
+            sim.adapt()
+        counts = sim.counts()
+        ups = sim.updates_per_coarse_step()
+        sim.step(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        forces = []
+        n_done = 2
+        t_ms = 0.0
+        while n_done < args.cyl_steps:
+            chunk = min(16, args.cyl_steps - n_done)
+            e0.record(stream)
+            sim.step(chunk)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_ms += e0.elapsed_time(e1)
+            n_done += chunk
+            forces.append(sim.force()[0])
+        rho_u = sim.fields_device(AMR_RHO_U, torch.float64).reshape(sim.cap, sim.m, 4)
+        lev = torch.from_numpy(sim.blocks()["level"]).to(dev)
+        tail = forces[int(0.8 * len(forces)):] or forces[-1:]
+        cd = [2.0 * f / (u0 * u0 * area) for f in tail]
+        entry = {"mlups": round(ups * (n_done - 2) / (t_ms / 1e3) / 1e6, 1),
+                 "blocks_per_level": counts["n_ids"], "leaf_updates_per_coarse_step": ups,
+                 "coarse_steps": n_done, "C_D_last20pct_mean": float(np.mean(cd)),
+                 "bytes_per_update": 2 * 27 * {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[storage]}
+        if ref is None:
+            ref, ref_lev = rho_u, lev
+        else:
+            per_level = {}
+            for L in range(cfg["max_levels"]):
+                sel = lev == L
+                if not bool(sel.any()):
+                    continue
+                a, b = rho_u[sel], ref[sel]
+                per_level[L] = {
+                    "rho": float(torch.linalg.norm(a[..., 0] - b[..., 0]) / torch.linalg.norm(b[..., 0])),
+                    "u": float(torch.linalg.norm(a[..., 1:] - b[..., 1:]) / torch.linalg.norm(b[..., 1:]))}
+            entry["rel_l2_vs_first"] = per_level
+        results[storage] = entry
+        del rho_u
+        sim.close()
+        torch.cuda.empty_cache()
+    return {"workload": "channel past a square prism, D3Q27, %dx%dx%d root cells, side %g, "
+                        "Re 100, L_max %d, static distance refinement (0.15/2^L, frozen)" %
+                        (nx, cfg["ny"], cfg["nz"], side, cfg["max_levels"]),
+            "reference_storage": args.cyl_storages.split(",")[0], "results": results}
+
+
 # ----------------------------------------------------------- reference arm
 def run_reference(args):
     world, rank, local = dist_setup()
@@ -396,6 +471,12 @@ def main():
     ap.add_argument("--cpu-worker", action="store_true")
     ap.add_argument("--variant", type=int, default=0,
                     help="collide-stream kernel: 0 auto, 1 one-pass, 2/3 pipelined stages")
+    ap.add_argument("--workload", default="cavity", choices=["cavity", "cylinder"])
+    ap.add_argument("--cyl-nx", type=int, default=256)
+    ap.add_argument("--cyl-levels", type=int, default=5)
+    ap.add_argument("--cyl-steps", type=int, default=400)
+    ap.add_argument("--cyl-cap", type=int, default=4_000_000)
+    ap.add_argument("--cyl-storages", default="f64,f32,bf16,f16")
     ap.add_argument("--bar-only", action="store_true",
                     help="only the single-level 256^3 D3Q19 FP32 forest (profiling)")
     args = ap.parse_args()
@@ -404,6 +485,9 @@ def main():
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.workload == "cylinder":
+        print(json.dumps(run_cylinder(args)))
+        return
     if args.bar_only:
         import torch
         import workloads as W
