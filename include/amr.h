@@ -253,6 +253,37 @@ int amr_mass_audit_noalloc(int dim, int q, int storage, int64_t n_blocks,
 /* Release host-side state (the arena stays owned by the caller). */
 int amr_free(amr_t* a);
 
+/* ---------------------------------------------------------- batched instances
+ * Many independent instances (same velocity set and storage, no solid) are
+ * advanced in lock-step: each level operation of the recursive level step
+ * (Section 4.1) is one launch over an instance-major list of
+ * (instance, block) items, and the batched coarse step is replayed as a CUDA
+ * graph.  The paper runs one forest per GPU; batching is this library's
+ * extension.  Members keep their own arenas; the batch arena holds the
+ * instance descriptors and the per-level item lists.
+ *
+ * amr_batch_arena_bytes: device bytes for a batch of these instances.
+ * amr_batch_create: members must have equal buffer parities (equally many
+ *   coarse steps since amr_init, modulo 2) and capacities below 2^25 blocks;
+ *   at most 127 members.  `stream` as in amr_init.
+ * amr_batch_refresh: rebuild the item lists after any member was adapted.
+ * amr_batch_step: advance every member by n coarse steps (asynchronous);
+ *   AMR_E_INVAL if a member was stepped outside the batch since.
+ * amr_batch_autotune: time the collide-stream kernel with 8 and 4 blocks per
+ *   CTA (512 / 256 threads) on `trial_steps` coarse steps each (the members
+ *   advance), keep the faster, return it in *variant_out (6 or 4).
+ * amr_batch_launches: kernels launched by the batch so far.
+ * Errors: AMR_E_INVAL, AMR_E_ARENA, AMR_E_CUDA. */
+typedef struct amr_batch_t amr_batch_t;
+size_t amr_batch_arena_bytes(amr_t* const* instances, int n);
+int amr_batch_create(amr_t* const* instances, int n, void* dev_arena, size_t arena_bytes,
+                     void* stream, amr_batch_t** out);
+int amr_batch_refresh(amr_batch_t* b);
+int amr_batch_step(amr_batch_t* b, int n_coarse_steps);
+int amr_batch_autotune(amr_batch_t* b, int trial_steps, int* variant_out);
+int64_t amr_batch_launches(amr_batch_t* b);
+int amr_batch_free(amr_batch_t* b);
+
 const char* amr_strerror(int code);
 const char* amr_last_error(void);
 

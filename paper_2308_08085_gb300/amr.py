@@ -91,6 +91,21 @@ def load_library(path=LIB_PATH):
     lib.amr_strerror.restype = ctypes.c_char_p
     lib.amr_last_error.argtypes = []
     lib.amr_last_error.restype = ctypes.c_char_p
+    pp = ctypes.POINTER(vp)
+    lib.amr_batch_arena_bytes.argtypes = [pp, i32]
+    lib.amr_batch_arena_bytes.restype = sz
+    lib.amr_batch_create.argtypes = [pp, i32, vp, sz, vp, pp]
+    lib.amr_batch_create.restype = i32
+    lib.amr_batch_refresh.argtypes = [vp]
+    lib.amr_batch_refresh.restype = i32
+    lib.amr_batch_step.argtypes = [vp, i32]
+    lib.amr_batch_step.restype = i32
+    lib.amr_batch_autotune.argtypes = [vp, i32, ctypes.POINTER(i32)]
+    lib.amr_batch_autotune.restype = i32
+    lib.amr_batch_launches.argtypes = [vp]
+    lib.amr_batch_launches.restype = i64
+    lib.amr_batch_free.argtypes = [vp]
+    lib.amr_batch_free.restype = i32
     _lib = lib
     return lib
 
@@ -276,6 +291,9 @@ class AmrLBM:
                                            bytes=arr[i].bytes, cells=arr[i].cells)
                 for i in range(n)}
 
+    def launches(self):
+        return self.counts()["launches"]
+
     def updates_per_coarse_step(self):
         """Leaf-cell updates of one coarse step (Section 5.1 definition)."""
         c = self.counts()
@@ -284,6 +302,62 @@ class AmrLBM:
     def close(self):
         if self.h:
             self.lib.amr_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class AmrBatch:
+    """Lock-step batch of AmrLBM instances (same velocity set and storage)."""
+
+    def __init__(self, members, stream=None):
+        import torch
+        self.lib = lib = load_library()
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m.h.value for m in self.members])
+        self._arr = arr
+        n = len(self.members)
+        nbytes = lib.amr_batch_arena_bytes(arr, n)
+        if nbytes == 0:
+            raise AmrError(AMR_E_INVAL, "amr_batch_arena_bytes")
+        dev = self.members[0].device
+        self.arena = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        base = self.arena.data_ptr()
+        off = (-base) % 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.h = ctypes.c_void_p()
+        rc = lib.amr_batch_create(arr, n, ctypes.c_void_p(base + off), nbytes,
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.h))
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_batch_create")
+
+    def refresh(self):
+        rc = self.lib.amr_batch_refresh(self.h)
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_batch_refresh")
+
+    def step(self, n=1):
+        rc = self.lib.amr_batch_step(self.h, int(n))
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_batch_step")
+
+    def autotune(self, trial_steps=2):
+        v = ctypes.c_int(0)
+        rc = self.lib.amr_batch_autotune(self.h, int(trial_steps), ctypes.byref(v))
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_batch_autotune")
+        return v.value
+
+    def launches(self):
+        return int(self.lib.amr_batch_launches(self.h))
+
+    def close(self):
+        if self.h:
+            self.lib.amr_batch_free(self.h)
             self.h = ctypes.c_void_p()
 
     def __del__(self):

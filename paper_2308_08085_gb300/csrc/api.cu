@@ -220,7 +220,12 @@ static double ratio_fc(const Instance* a, int L) { return 2.0 * a->tau[L] / a->t
 
 static void collide_stream_level(Instance* a, int L) {
   const int64_t n = a->n_active[L];
-  if (n == 0) return;
+  // the parity flips even without active blocks: graph replay and batches
+  // rely on level 0 flipping once and deeper levels an even number of times
+  if (n == 0) {
+    a->cur ^= 1u << L;
+    return;
+  }
   StepParams prm = a->prm;
   prm.omega = 1.0 / a->tau[L];
   {

@@ -77,16 +77,16 @@ __device__ __forceinline__ void collide_push(typename Store<T>::R (&f)[Q], int l
                                              const uint16_t* __restrict__ tab,
                                              const int32_t* __restrict__ nb,
                                              const uint64_t* __restrict__ sm_nb,
-                                             T* __restrict__ fout, const StepParams& prm) {
+                                             T* __restrict__ fout, size_t stride, double omega,
+                                             const FaceParams& faces) {
   using V = VS<D, Q>;
   using S = Store<T>;
   using R = typename S::R;
   constexpr int M = Block<D>::M;
-  const size_t stride = prm.stride;
   R rho, ux, uy, uz;
   moments<D, Q>(f, rho, ux, uy, uz);
   const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
-  const R om = R(prm.omega);
+  const R om = R(omega);
   const int own = b * M + l;
   static_for<0, Q>([&](auto P) {
     constexpr int p = P;
@@ -110,15 +110,15 @@ __device__ __forceinline__ void collide_push(typename Store<T>::R (&f)[Q], int l
         R v = fs;   // NONE (interface) or solid: halfway bounce-back
         if (tgt <= -2) {
           const int face = -2 - tgt;
-          if (prm.faces.kind[face] == FACE_OUTLET) {
+          if (faces.kind[face] == FACE_OUTLET) {
             R cu = R(0);
             if constexpr (cx != 0) cu += cx > 0 ? ux : -ux;
             if constexpr (cy != 0) cu += cy > 0 ? uy : -uy;
             if constexpr (cz != 0) cu += cz > 0 ? uz : -uz;
             constexpr double wp = V::w[p];
-            v = -fs + R(2.0 * wp * prm.faces.rho_w[face]) * (R(1) + R(4.5) * cu * cu - usq15);
+            v = -fs + R(2.0 * wp * faces.rho_w[face]) * (R(1) + R(4.5) * cu * cu - usq15);
           } else {
-            v = fs + R(prm.faces.bb[face][p]);
+            v = fs + R(faces.bb[face][p]);
           }
         }
         fout[(size_t)pb * stride + own] = S::template save<D, Q, pb>(v);
@@ -187,10 +187,11 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS>()
   });
   if constexpr (TAB_SMEM)
     collide_push<D, Q, T, SOLID, true>(f, l, b, s_tab, s_nb[slot], SOLID ? s_sm[slot] : nullptr,
-                                       fout, prm);
+                                       fout, prm.stride, prm.omega, prm.faces);
   else
     collide_push<D, Q, T, SOLID, false>(f, l, b, g_stream_table<D, Q>.e, s_nb[slot],
-                                        SOLID ? s_sm[slot] : nullptr, fout, prm);
+                                        SOLID ? s_sm[slot] : nullptr, fout, prm.stride,
+                                        prm.omega, prm.faces);
 }
 
 // ================================== pipelined persistent collide + stream
@@ -300,7 +301,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 8 && Q == 27) ? 1 : 2)
       R f[Q];
       static_for<0, Q>([&](auto P) { f[P] = S::template load<D, Q, P>(sblk[P * M + l]); });
       collide_push<D, Q, T, SOLID, true>(f, l, b, s_tab, s_nb[slot],
-                                         SOLID ? s_sm[slot] : nullptr, fout, prm);
+                                         SOLID ? s_sm[slot] : nullptr, fout, prm.stride,
+                                         prm.omega, prm.faces);
     }
     __syncthreads();
     stage = (stage + 1) % STAGES;
@@ -314,41 +316,38 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 8 && Q == 27) ? 1 : 2)
 // each child c, fine cell (I,J,K) takes the multilinear interpolant of the
 // 2^D parent cells of quadrant c at local coordinates -1/4 + I/2.  Writes the
 // ghost cells of every child (mode_all = 0) or every cell (mode_all = 1).
+template <int D, int Q, class T>
+__device__ __forceinline__ void interp_stage(typename Store<T>::R (*sF)[Block<D>::M],
+                                             const T* __restrict__ fpar, size_t stride, int P,
+                                             int l, double ratio) {
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int M = Block<D>::M;
+  const size_t base = (size_t)P * M + l;
+  R f[Q];
+  static_for<0, Q>([&](auto Pp) {
+    f[Pp] = S::template load<D, Q, Pp>(fpar[(size_t)Pp * stride + base]);
+  });
+  R rho, ux, uy, uz;
+  moments<D, Q>(f, rho, ux, uy, uz);
+  const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+  const R r = R(ratio);
+  static_for<0, Q>([&](auto Pp) {
+    const R e = feq<D, Q, Pp>(rho, ux, uy, uz, usq15);
+    sF[Pp][l] = e + (f[Pp] - e) * r;
+  });
+}
+
 template <int D, int Q, class T, bool SOLID>
-__global__ void __launch_bounds__(128)
-    k_interp(const int32_t* __restrict__ list, int n, const T* __restrict__ fpar,
-             T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
-             const uint64_t* __restrict__ cellmask, const uint64_t* __restrict__ solidmask,
-             double ratio, int mode_all) {
+__device__ __forceinline__ void interp_children(const typename Store<T>::R (*sF)[Block<D>::M],
+                                                int l, T* __restrict__ fch, size_t stride,
+                                                int c0, const uint64_t* __restrict__ cellmask,
+                                                const uint64_t* __restrict__ solidmask,
+                                                int mode_all) {
   using S = Store<T>;
   using R = typename S::R;
   constexpr int M = Block<D>::M;
   constexpr int NC = Block<D>::NC;
-  constexpr int BPC = 128 / M;
-  __shared__ R sF[BPC][Q][M];
-  const int slot = threadIdx.x / M;
-  const int l = threadIdx.x - slot * M;
-  const int bi = blockIdx.x * BPC + slot;
-  const bool valid = bi < n;
-  int P = 0;
-  if (valid) {
-    P = list[bi];
-    const size_t base = (size_t)P * M + l;
-    R f[Q];
-    static_for<0, Q>([&](auto Pp) {
-      f[Pp] = S::template load<D, Q, Pp>(fpar[(size_t)Pp * stride + base]);
-    });
-    R rho, ux, uy, uz;
-    moments<D, Q>(f, rho, ux, uy, uz);
-    const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
-    const R r = R(ratio);
-    static_for<0, Q>([&](auto Pp) {
-      const R e = feq<D, Q, Pp>(rho, ux, uy, uz, usq15);
-      sF[slot][Pp][l] = e + (f[Pp] - e) * r;
-    });
-  }
-  __syncthreads();
-  if (!valid) return;
   const int i = Block<D>::ci(l), j = Block<D>::cj(l), k = Block<D>::ck(l);
   const R x = R(-0.25) + R(0.5) * R(i);
   const R y = R(-0.25) + R(0.5) * R(j);
@@ -360,7 +359,6 @@ __global__ void __launch_bounds__(128)
     if (D == 3) wv *= (a & 4) ? z : R(1) - z;
     wgt[a] = wv;
   }
-  const int c0 = child0[P];
   for (int c = 0; c < NC; ++c) {
     const int ch = c0 + c;
     if (!mode_all) {
@@ -381,10 +379,32 @@ __global__ void __launch_bounds__(128)
     static_for<0, Q>([&](auto Pp) {
       R v = R(0);
 #pragma unroll
-      for (int a = 0; a < NC; ++a) v += wgt[a] * sF[slot][Pp][corner[a]];
+      for (int a = 0; a < NC; ++a) v += wgt[a] * sF[Pp][corner[a]];
       fch[(size_t)Pp * stride + base] = S::template save<D, Q, Pp>(v);
     });
   }
+}
+
+template <int D, int Q, class T, bool SOLID>
+__global__ void __launch_bounds__(128)
+    k_interp(const int32_t* __restrict__ list, int n, const T* __restrict__ fpar,
+             T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
+             const uint64_t* __restrict__ cellmask, const uint64_t* __restrict__ solidmask,
+             double ratio, int mode_all) {
+  using R = typename Store<T>::R;
+  constexpr int M = Block<D>::M;
+  constexpr int BPC = 128 / M;
+  __shared__ R sF[BPC][Q][M];
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int bi = blockIdx.x * BPC + slot;
+  const bool valid = bi < n;
+  const int P = valid ? list[bi] : 0;
+  if (valid) interp_stage<D, Q, T>(sF[slot], fpar, stride, P, l, ratio);
+  __syncthreads();
+  if (!valid) return;
+  interp_children<D, Q, T, SOLID>(sF[slot], l, fch, stride, child0[P], cellmask, solidmask,
+                                  mode_all);
 }
 
 // ===================================================== fine-to-coarse averaging
@@ -393,25 +413,18 @@ __global__ void __launch_bounds__(128)
 // averaged.  mode_sync = 0 writes parent cells over interface children;
 // mode_sync = 1 writes every parent cell whose children are not ghosts.
 template <int D, int Q, class T, bool SOLID>
-__global__ void __launch_bounds__(128)
-    k_average(const int32_t* __restrict__ list, int n, T* __restrict__ fpar,
-              const T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
-              const uint64_t* __restrict__ cellmask, const int32_t* __restrict__ status,
-              const uint64_t* __restrict__ solidmask, double ratio, int mode_sync) {
+__device__ __forceinline__ void average_cell(int P, int l, T* __restrict__ fpar,
+                                             const T* __restrict__ fch, size_t stride, int c0,
+                                             const uint64_t* __restrict__ cellmask,
+                                             const uint64_t* __restrict__ solidmask,
+                                             double ratio, int mode_sync) {
   using S = Store<T>;
   using R = typename S::R;
   constexpr int M = Block<D>::M;
   constexpr int NC = Block<D>::NC;
-  constexpr int BPC = 128 / M;
-  const int slot = threadIdx.x / M;
-  const int l = threadIdx.x - slot * M;
-  const int bi = blockIdx.x * BPC + slot;
-  if (bi >= n) return;
-  const int P = list[bi];
-  if (mode_sync && status[P] < ST_REFINED) return;
   const int i = Block<D>::ci(l), j = Block<D>::cj(l), k = Block<D>::ck(l);
   const int c = (i >> 1) + 2 * (j >> 1) + (D == 3 ? 4 * (k >> 1) : 0);
-  const int ch = child0[P] + c;
+  const int ch = c0 + c;
   const int fi = 2 * (i & 1), fj = 2 * (j & 1), fk = 2 * (k & 1);
   // all 2^D children of a parent cell share one class; test the first
   const int f0 = Block<D>::cell(fi, fj, fk);
@@ -444,6 +457,115 @@ __global__ void __launch_bounds__(128)
   static_for<0, Q>([&](auto Pp) {
     fpar[(size_t)Pp * stride + base] = S::template save<D, Q, Pp>(acc[Pp] * inv);
   });
+}
+
+template <int D, int Q, class T, bool SOLID>
+__global__ void __launch_bounds__(128)
+    k_average(const int32_t* __restrict__ list, int n, T* __restrict__ fpar,
+              const T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
+              const uint64_t* __restrict__ cellmask, const int32_t* __restrict__ status,
+              const uint64_t* __restrict__ solidmask, double ratio, int mode_sync) {
+  constexpr int M = Block<D>::M;
+  constexpr int BPC = 128 / M;
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int bi = blockIdx.x * BPC + slot;
+  if (bi >= n) return;
+  const int P = list[bi];
+  if (mode_sync && status[P] < ST_REFINED) return;
+  average_cell<D, Q, T, SOLID>(P, l, fpar, fch, stride, child0[P], cellmask, solidmask, ratio,
+                               mode_sync);
+}
+
+// ================================================ batched instances (lock-step)
+// Work items pack (instance, block) as inst << BATCH_SHIFT | block; each
+// instance's buffers, tables and per-level factors come from its descriptor.
+template <int D, int Q, class T, int THREADS>
+__global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS>()))
+    k_collide_stream_batch(const uint32_t* __restrict__ items, int n,
+                           const InstDesc* __restrict__ descs, int level, int which_in) {
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int M = Block<D>::M;
+  constexpr int NCODE = D == 2 ? 9 : 27;
+  constexpr int CENTER = D == 2 ? 4 : 13;
+  constexpr int BPC = THREADS / M;
+  __shared__ int32_t s_nb[BPC][NCODE];
+  __shared__ int32_t s_inst[BPC];
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int first = blockIdx.x * BPC;
+  for (int t = threadIdx.x; t < BPC * NCODE; t += THREADS) {
+    const int s = t / NCODE, code = t - s * NCODE;
+    const int bi = first + s;
+    int v = NONE;
+    if (bi < n) {
+      const uint32_t it = __ldg(items + bi);
+      const int inst = (int)(it >> BATCH_SHIFT);
+      const int b = (int)(it & BATCH_MASK);
+      v = __ldg(descs[inst].nbr + (size_t)b * NBR_STRIDE + geo_to_k<D>(code));
+      if (code == 0) s_inst[s] = inst;
+    }
+    s_nb[s][code] = v;
+  }
+  __syncthreads();
+  if (first + slot >= n) return;
+  const InstDesc& d = descs[s_inst[slot]];
+  const int b = s_nb[slot][CENTER];
+  const T* __restrict__ fin = (const T*)d.f[which_in];
+  T* __restrict__ fout = (T*)d.f[which_in ^ 1];
+  const size_t stride = d.stride;
+  const int own = b * M + l;
+  R f[Q];
+  static_for<0, Q>([&](auto P) {
+    f[P] = S::template load<D, Q, P>(fin[(size_t)P * stride + own]);
+  });
+  collide_push<D, Q, T, false, false>(f, l, b, g_stream_table<D, Q>.e, s_nb[slot], nullptr, fout,
+                                      stride, d.omega[level], d.faces);
+}
+
+template <int D, int Q, class T>
+__global__ void __launch_bounds__(128)
+    k_interp_batch(const uint32_t* __restrict__ items, int n, const InstDesc* __restrict__ descs,
+                   int level, int which_par, int which_ch) {
+  using R = typename Store<T>::R;
+  constexpr int M = Block<D>::M;
+  constexpr int BPC = 128 / M;
+  __shared__ R sF[BPC][Q][M];
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int bi = blockIdx.x * BPC + slot;
+  const bool valid = bi < n;
+  int inst = 0, P = 0;
+  if (valid) {
+    const uint32_t it = __ldg(items + bi);
+    inst = (int)(it >> BATCH_SHIFT);
+    P = (int)(it & BATCH_MASK);
+    const InstDesc& d = descs[inst];
+    interp_stage<D, Q, T>(sF[slot], (const T*)d.f[which_par], d.stride, P, l, d.r_cf[level]);
+  }
+  __syncthreads();
+  if (!valid) return;
+  const InstDesc& d = descs[inst];
+  interp_children<D, Q, T, false>(sF[slot], l, (T*)d.f[which_ch], d.stride, d.child0[P],
+                                  d.cellmask, nullptr, 0);
+}
+
+template <int D, int Q, class T>
+__global__ void __launch_bounds__(128)
+    k_average_batch(const uint32_t* __restrict__ items, int n, const InstDesc* __restrict__ descs,
+                    int level, int which_par, int which_ch) {
+  constexpr int M = Block<D>::M;
+  constexpr int BPC = 128 / M;
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int bi = blockIdx.x * BPC + slot;
+  if (bi >= n) return;
+  const uint32_t it = __ldg(items + bi);
+  const InstDesc& d = descs[it >> BATCH_SHIFT];
+  const int P = (int)(it & BATCH_MASK);
+  average_cell<D, Q, T, false>(P, l, (T*)d.f[which_par], (const T*)d.f[which_ch], d.stride,
+                               d.child0[P], d.cellmask, nullptr, d.r_fc[level], 0);
 }
 
 // ================================================================ criterion
@@ -871,10 +993,34 @@ struct Launch {
                                                   omega, dx, partial);
     return grid;
   }
+  static void collide_stream_batch(cudaStream_t s, const uint32_t* items, int n,
+                                   const InstDesc* descs, int level, int which_in, int variant) {
+    if (n <= 0) return;
+    if (variant == 4 || variant == 5)
+      k_collide_stream_batch<D, Q, T, 256><<<grid_for(n, 256 / M), 256, 0, s>>>(
+          items, n, descs, level, which_in);
+    else
+      k_collide_stream_batch<D, Q, T, 512><<<grid_for(n, 512 / M), 512, 0, s>>>(
+          items, n, descs, level, which_in);
+  }
+  static void interp_batch(cudaStream_t s, const uint32_t* items, int n, const InstDesc* descs,
+                           int level, int which_par, int which_ch) {
+    if (n <= 0) return;
+    k_interp_batch<D, Q, T><<<grid_for(n, 128 / M), 128, 0, s>>>(items, n, descs, level,
+                                                                   which_par, which_ch);
+  }
+  static void average_batch(cudaStream_t s, const uint32_t* items, int n, const InstDesc* descs,
+                            int level, int which_par, int which_ch) {
+    if (n <= 0) return;
+    k_average_batch<D, Q, T><<<grid_for(n, 128 / M), 128, 0, s>>>(items, n, descs, level,
+                                                                    which_par, which_ch);
+  }
+
   static const LbmOps* ops() {
-    static const LbmOps o = {setup, collide_stream, interp,   average,      criterion,
-                             export_f,       import_f, export_rho_u, init_rest,
-                             mass_partial,   force_partial};
+    static const LbmOps o = {setup,         collide_stream, interp,   average,
+                             criterion,     export_f,       import_f, export_rho_u,
+                             init_rest,     mass_partial,   force_partial,
+                             collide_stream_batch, interp_batch, average_batch};
     return &o;
   }
 };

@@ -14,6 +14,24 @@ struct FaceParams {
   double bb[6][27];     // bounce-back term -2 w_p rho_w (c_p . u_w) / cs^2
 };
 
+// Descriptor of one instance inside a batch (Section 4.1 level step applied to
+// many forests in lock-step).  Work items pack inst << BATCH_SHIFT | block.
+constexpr int BATCH_SHIFT = 25;
+constexpr uint32_t BATCH_MASK = (1u << BATCH_SHIFT) - 1u;
+constexpr int BATCH_MAX_LEVELS = 8;
+
+struct InstDesc {
+  void* f[2];                       // population buffers A / B
+  const int32_t* nbr;
+  const int32_t* child0;
+  const uint64_t* cellmask;
+  size_t stride;                    // capacity * M
+  double omega[BATCH_MAX_LEVELS];   // 1 / tau_L
+  double r_cf[BATCH_MAX_LEVELS];    // tau_{L+1} / (2 tau_L)
+  double r_fc[BATCH_MAX_LEVELS];    // 2 tau_L / tau_{L+1}
+  FaceParams faces;
+};
+
 struct StepParams {
   size_t stride;        // elements between population planes (capacity * M)
   double omega;         // 1 / tau_L
@@ -60,6 +78,14 @@ struct LbmOps {
   int (*force_partial)(cudaStream_t, const int32_t* list, int n, const void* f, size_t stride,
                        const int32_t* nbr, const int32_t* status, const uint64_t* solidmask,
                        double omega, double dx, double* partial);
+  // batched instances: one launch over an instance-major list of work items;
+  // buffer A / B choice per launch (every instance of a batch shares parities)
+  void (*collide_stream_batch)(cudaStream_t, const uint32_t* items, int n, const InstDesc* descs,
+                               int level, int which_in, int variant);
+  void (*interp_batch)(cudaStream_t, const uint32_t* items, int n, const InstDesc* descs,
+                       int level, int which_par, int which_ch);
+  void (*average_batch)(cudaStream_t, const uint32_t* items, int n, const InstDesc* descs,
+                        int level, int which_par, int which_ch);
 };
 
 const LbmOps* lbm_ops_d2q9(int storage);

@@ -1,0 +1,108 @@
+"""Batched instances: several forests of different sizes and depths advanced
+in lock-step by one launch sequence must give exactly the populations of the
+same forests advanced one by one (the arithmetic per cell is identical), and
+one member must match the CPU oracle."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.lattice import equilibrium
+from oracle.solver import ForestLBM
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_08085_gb300 import build as b
+    b.build()
+
+
+CFGS = [
+    lambda: W.cavity(dim=3, q=19, n=8, max_levels=2, re=200.0, max_blocks=8 * 12),
+    lambda: W.cavity(dim=3, q=19, n=12, ny=8, nz=8, max_levels=3, re=400.0, max_blocks=12 * 40),
+    lambda: W.cavity(dim=3, q=19, n=16, max_levels=1, re=800.0, max_blocks=64),
+]
+
+
+def member(cfg, storage, marks_seq, state):
+    from paper_2308_08085_gb300 import AmrLBM
+    m = AmrLBM(cfg, storage=storage)
+    for mk in marks_seq:
+        m.adapt(torch.from_numpy(mk).cuda())
+    m.set_populations(state)
+    return m
+
+
+def seeded(cfg, seed):
+    """Marks (two rounds) and a random state for a config, from the oracle
+    mesh so that the same marks apply to every copy."""
+    ref = ForestLBM(cfg)
+    seq = []
+    for r in range(2):
+        mk = np.zeros(cfg["max_blocks"], np.int8)
+        leaves = [b for b in ref.mesh.active_ids() if ref.mesh.status[b] == 1]
+        mk[leaves[: max(1, len(leaves) // 3)]] = 1
+        ref.adapt(mk)
+        seq.append(mk)
+    n = cfg["max_blocks"] * ref.m
+    rho, u = W.random_macro(seed, n, 3)
+    f = equilibrium(ref.vs, rho, u) + W.random_noise(seed + 1, (n, ref.vs.q), 1e-3)
+    f = f.reshape(cfg["max_blocks"], ref.m, ref.vs.q)
+    ref.f[:] = f
+    return ref, seq, f
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_batch_equals_individual_runs(storage):
+    from paper_2308_08085_gb300 import AmrBatch
+    cfgs = [mk() for mk in CFGS]
+    data = [seeded(c, 40 + i) for i, c in enumerate(cfgs)]
+    batched = [member(c, storage, seq, f) for c, (_, seq, f) in zip(cfgs, data)]
+    single = [member(c, storage, seq, f) for c, (_, seq, f) in zip(cfgs, data)]
+    batch = AmrBatch(batched)
+    batch.step(3)
+    for m in single:
+        m.step(3)
+    for b, s in zip(batched, single):
+        assert np.array_equal(b.populations(), s.populations())
+    # adapt every member with its criterion, re-batch and continue
+    for b, s in zip(batched, single):
+        b.adapt()
+        s.adapt()
+    batch.refresh()
+    batch.step(2)
+    for m in single:
+        m.step(2)
+    for b, s in zip(batched, single):
+        assert np.array_equal(b.populations(), s.populations())
+    # a member stepped outside the batch breaks lock-step: refused
+    batched[0].step(1)
+    from paper_2308_08085_gb300.amr import AmrError
+    with pytest.raises(AmrError):
+        batch.step(1)
+    batch.close()
+
+
+def test_batch_member_matches_oracle_and_autotune():
+    from paper_2308_08085_gb300 import AmrBatch
+    cfgs = [mk() for mk in CFGS]
+    data = [seeded(c, 60 + i) for i, c in enumerate(cfgs)]
+    members = [member(c, "f64", seq, f) for c, (_, seq, f) in zip(cfgs, data)]
+    batch = AmrBatch(members)
+    v = batch.autotune(trial_steps=1)           # advances every member by 2 x (1 + 1) steps
+    assert v in (4, 6)
+    batch.step(1)
+    ref = data[1][0]
+    ref.step(5)
+    ref.sync()
+    members[1].rho_u()
+    ids = ref.mesh.active_ids()
+    got = members[1].populations()[ids]
+    err = np.linalg.norm(got - ref.f[ids]) / np.linalg.norm(ref.f[ids])
+    assert err <= 1e-12, err
+    assert batch.launches() > 0
+    batch.close()
