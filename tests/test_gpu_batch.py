@@ -1,7 +1,8 @@
 """Batched instances: several forests of different sizes and depths advanced
-in lock-step by one launch sequence must give exactly the populations of the
-same forests advanced one by one (the arithmetic per cell is identical), and
-one member must match the CPU oracle."""
+in lock-step by one launch sequence must give the populations of the same
+forests advanced one by one -- the same arithmetic per cell, compiled into
+different kernels, so equal up to the compiler's fused multiply-add choices
+(rounding-level differences) -- and one member must match the CPU oracle."""
 import numpy as np
 import pytest
 
@@ -56,6 +57,13 @@ def seeded(cfg, seed):
     return ref, seq, f
 
 
+ROUNDING = {"f32": 1e-6, "f64": 1e-13}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
 @pytest.mark.parametrize("storage", ["f32", "f64"])
 def test_batch_equals_individual_runs(storage):
     from paper_2308_08085_gb300 import AmrBatch
@@ -68,7 +76,7 @@ def test_batch_equals_individual_runs(storage):
     for m in single:
         m.step(3)
     for b, s in zip(batched, single):
-        assert np.array_equal(b.populations(), s.populations())
+        assert rel(b.populations(), s.populations()) <= ROUNDING[storage]
     # adapt every member with its criterion, re-batch and continue
     for b, s in zip(batched, single):
         b.adapt()
@@ -78,7 +86,8 @@ def test_batch_equals_individual_runs(storage):
     for m in single:
         m.step(2)
     for b, s in zip(batched, single):
-        assert np.array_equal(b.populations(), s.populations())
+        assert rel(b.populations(), s.populations()) <= ROUNDING[storage]
+        assert np.array_equal(b.blocks()["status"], s.blocks()["status"])
     # a member stepped outside the batch breaks lock-step: refused
     batched[0].step(1)
     from paper_2308_08085_gb300.amr import AmrError
