@@ -36,11 +36,11 @@ PERIOD = 50
 HBM_FALLBACK_GBS = 6800.0
 PAPER_A100_MLUPS = 1753.0     # paper, 3D LDC D3Q19 FP32 64^3 L_max 4 on A100 (context)
 
-# ncu DRAM traffic of k_collide_stream<3,19,float> per cell update, and the
-# hash of the kernel source it was measured on (profiles/ summary); None until
-# captured.  A changed source hash reports traffic as null.
-NCU_TRAFFIC_PER_UPDATE = None
-NCU_SOURCE_SHA = None
+# ncu DRAM traffic of k_collide_stream<3,19,float> per cell update on the
+# 256^3 forest (profiles/collide_stream_bar256_d3q19_f32.md), and the hash of
+# the kernel source it was measured on.  A changed source reports null.
+NCU_TRAFFIC_PER_UPDATE = 154.4     # bytes (dram read + write) per cell update
+NCU_SOURCE_SHA = "0137b8fa32c97ad0"
 
 
 def kernel_source_sha():
@@ -267,7 +267,7 @@ def run_ours(args):
         per_launch_updates = cs["cells"] / max(1, cs["launches"])
         traffic = None
         if NCU_TRAFFIC_PER_UPDATE is not None and NCU_SOURCE_SHA == kernel_source_sha():
-            traffic = NCU_TRAFFIC_PER_UPDATE * per_launch_updates
+            traffic = round(NCU_TRAFFIC_PER_UPDATE * per_launch_updates)
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": peak_kind + " hbm_gbs (MEASURED_PEAKS.json copy test)",
