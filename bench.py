@@ -528,6 +528,134 @@ def run_batched(args):
     return out
 
 
+# ---------------------------------------------------------- learned workload
+def run_learned(args):
+    """Learned refinement proposal on the channel past a square prism (D3Q27,
+    FP32, distance + vorticity criterion).  Training pairs: block summaries at
+    t and the plain criterion's refine flag at t + 20 coarse steps, from seeded
+    runs (seed s sets Re = 100 (0.8 + 0.05 s)); seeds 1-6 train, 7-8 test.
+    Evaluation from one spun-up state: plain criterion every 50 coarse steps
+    against proposal + criterion every 200 (and criterion alone every 200).
+    Missed-refinement rate: leaves the plain criterion flags 20 steps after
+    an adaptation that are still leaves."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2308_08085_gb300 import AmrLBM, Mlp
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    nx = args.cyl_nx
+    sc = nx / 256
+
+    def cfg_for(seed):
+        return W.channel_cylinder(q=27, nx=nx, ny=int(64 * sc), nz=int(64 * sc), side=8 * sc,
+                                  cx=64 * sc, cy=32 * sc, re=100.0 * (0.8 + 0.05 * seed),
+                                  max_levels=args.cyl_levels, max_blocks=args.cyl_cap)
+
+    def spun_up(seed):
+        sim = AmrLBM(cfg_for(seed), storage="f32")
+        for _ in range(args.learn_spin):
+            sim.step(50)
+            sim.adapt()
+        return sim
+
+    # ---- training pairs
+    per_seed = args.learn_pairs // 8
+    xs, ys, seeds = [], [], []
+    for seed in range(1, 9):
+        sim = spun_up(seed)
+        px, py = [], []
+        for _ in range(args.learn_windows):
+            feats = sim.features()
+            leaf = torch.from_numpy(sim.blocks()["status"] == 1).to(dev)
+            sim.step(20)
+            flag = sim.criterion_marks() > 0
+            px.append(feats[leaf])
+            py.append(flag[leaf].float())
+            sim.step(30)
+            sim.adapt()
+        x = torch.cat(px)
+        y = torch.cat(py)
+        stride = max(1, x.shape[0] // per_seed)
+        xs.append(x[::stride][:per_seed].contiguous())
+        ys.append(y[::stride][:per_seed].contiguous())
+        seeds.append(seed)
+        sim.close()
+        torch.cuda.empty_cache()
+    xtr, ytr = torch.cat(xs[:6]).contiguous(), torch.cat(ys[:6]).contiguous()
+    xte, yte = torch.cat(xs[6:]).contiguous(), torch.cat(ys[6:]).contiguous()
+    pos = float(ytr.sum())
+    pw = max(1.0, (ytr.numel() - pos) / max(pos, 1.0))
+    net = Mlp(dev, seed=0)
+    t0 = time.perf_counter()
+    losses = [net.train_epoch(xtr, ytr, batch=1024, lr=2e-3, pos_weight=pw, seed=e)
+              for e in range(args.learn_epochs)]
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    pr = net.infer(xte) > args.learn_threshold
+    tp = float((pr & (yte > 0.5)).sum())
+    test = {"pairs": int(xte.shape[0]), "positives": int(yte.sum()),
+            "recall": tp / max(1.0, float(yte.sum())),
+            "precision": tp / max(1.0, float(pr.sum())),
+            "accuracy": float((pr.float() == yte).float().mean())}
+
+    # ---- evaluation from one spun-up state (deterministic: equal histories)
+    def evaluate(mode):
+        sim = spun_up(9)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        period = 50 if mode == "plain" else 200
+        ups_sum, t_ms, flagged, missed, adapts = 0.0, 0.0, 0, 0, 0
+        steps = 0
+        while steps < args.learn_eval_steps:
+            e0.record(stream)
+            if mode == "learned":
+                marks = sim.propose_marks(net.half, args.learn_threshold, True)
+                sim.adapt(marks)
+            else:
+                sim.adapt()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_ms += e0.elapsed_time(e1)
+            adapts += 1
+            ups = sim.updates_per_coarse_step()
+            # 20 steps on, the plain criterion's verdict (the check itself is untimed)
+            e0.record(stream)
+            sim.step(20)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_ms += e0.elapsed_time(e1)
+            fl = (sim.criterion_marks() > 0).cpu().numpy()
+            leaf = sim.blocks()["status"] == 1
+            flagged += int(fl.sum())
+            missed += int((fl & leaf).sum())
+            e0.record(stream)
+            sim.step(period - 20)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_ms += e0.elapsed_time(e1)
+            ups_sum += ups * period
+            steps += period
+        out = {"mlups_incl_adapt": round(ups_sum / (t_ms / 1e3) / 1e6, 1),
+               "adaptations": adapts, "coarse_steps": steps,
+               "flagged_at_t_plus_20": flagged,
+               "missed_refinement_rate": missed / max(1, flagged),
+               "blocks_end": sim.counts()["n_ids"]}
+        sim.close()
+        torch.cuda.empty_cache()
+        return out
+
+    ev = {m: evaluate(m) for m in ("plain", "learned", "criterion_every_200")}
+    return {"workload": "learned refinement proposal, channel past a square prism D3Q27 FP32, "
+                        "%dx%dx%d root, L_max %d" % (nx, int(64 * sc), int(64 * sc),
+                                                     args.cyl_levels),
+            "pairs_train": int(xtr.shape[0]), "pairs_test": test["pairs"],
+            "pos_weight": round(pw, 2), "epochs": args.learn_epochs,
+            "loss_first_last": [round(losses[0], 4), round(losses[-1], 4)],
+            "train_seconds": round(t_train, 3), "threshold": args.learn_threshold,
+            "test": test, "evaluation": ev}
+
+
 # ----------------------------------------------------------- reference arm
 def run_reference(args):
     world, rank, local = dist_setup()
@@ -571,7 +699,14 @@ def main():
     ap.add_argument("--cpu-worker", action="store_true")
     ap.add_argument("--variant", type=int, default=0,
                     help="collide-stream kernel: 0 auto, 1 one-pass, 2/3 pipelined stages")
-    ap.add_argument("--workload", default="cavity", choices=["cavity", "cylinder", "batched"])
+    ap.add_argument("--workload", default="cavity",
+                    choices=["cavity", "cylinder", "batched", "learned"])
+    ap.add_argument("--learn-pairs", type=int, default=200_000)
+    ap.add_argument("--learn-spin", type=int, default=4)
+    ap.add_argument("--learn-windows", type=int, default=4)
+    ap.add_argument("--learn-epochs", type=int, default=12)
+    ap.add_argument("--learn-threshold", type=float, default=0.5)
+    ap.add_argument("--learn-eval-steps", type=int, default=800)
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--cyl-nx", type=int, default=256)
     ap.add_argument("--cyl-levels", type=int, default=5)
@@ -591,6 +726,9 @@ def main():
         return
     if args.workload == "batched":
         print(json.dumps(run_batched(args)))
+        return
+    if args.workload == "learned":
+        print(json.dumps(run_learned(args)))
         return
     if args.bar_only:
         import torch

@@ -194,6 +194,9 @@ int amr_adapt(amr_t* a, const int8_t* dev_marks, amr_adapt_stats* out);
                            rho V and rho u V, V = cell volume (root units)     */
 #define AMR_FORCE 11    /* double [3]: momentum-exchange force on the solid
                            (Section 5.3), physical units of dx                 */
+#define AMR_FEATURES 12 /* float [B][27]: block summaries of the learned
+                           refinement proposal (3D only; after a sync; 0 for
+                           blocks outside the mesh), see amr_propose_marks     */
 
 /* Copy field `what` into `dst` (device pointer if dst_on_device, else host).
  * dst == NULL returns the required bytes.  Returns bytes written or a
@@ -252,6 +255,63 @@ int amr_mass_audit_noalloc(int dim, int q, int storage, int64_t n_blocks,
 
 /* Release host-side state (the arena stays owned by the caller). */
 int amr_free(amr_t* a);
+
+/* ------------------------------------------------ learned refinement proposal
+ * Not in the paper: a per-block MLP (27 -> 64 -> 64 -> 1, ReLU, sigmoid)
+ * proposes refinement ahead of the vorticity criterion so that adaptation can
+ * run less often; the plain criterion stays the fallback.  Inputs are the 27
+ * block summaries of AMR_FEATURES: for the velocity-gradient components
+ * du_a/dx_b their block mean and max |.|, mean and max-min of rho, mean
+ * velocity and max |u|, mean and max |vorticity|, level / L_max (gradient and
+ * vorticity entries compressed as sign(x) log(1 + |x|)).  Parameters are a flat
+ * float array of amr_mlp_param_count() entries: W1[64][27], b1[64],
+ * W2[64][64], b2[64], w3[64], b3 (FP32 master), plus an FP16 copy of the same
+ * layout that inference reads.  All pointers are device pointers. */
+#define AMR_MLP_INPUTS 27
+#define AMR_MLP_HIDDEN 64
+
+typedef struct {
+  float* params;       /* FP32 master weights                                */
+  float* adam_m;       /* Adam first moments (zero-initialised by the caller) */
+  float* adam_v;       /* Adam second moments (zero-initialised)             */
+  void* params_half;   /* FP16 copy, refreshed by every update               */
+  float* grad;         /* scratch: summed gradient of a minibatch            */
+  float* loss;         /* scratch: one float                                 */
+  int64_t step;        /* Adam step counter (host side, updated)             */
+} amr_mlp_state;
+
+int amr_mlp_param_count(void);
+/* Glorot-uniform weights and zero biases from a counter-based generator;
+ * writes the FP16 copy too when params_half is not NULL. */
+int amr_mlp_init(float* params, void* params_half, uint64_t seed, void* stream);
+/* Summed gradient (into grad[param_count]) and summed loss (into *loss) of the
+ * class-weighted binary cross-entropy  pw y softplus(-z) + (1-y) softplus(z)
+ * over n samples x[n][27], labels y[n] in {0, 1}; nothing is updated. */
+int amr_mlp_grad(const float* params, const float* x, const float* y, int64_t n, float pos_weight,
+                 float* grad, float* loss, void* stream);
+/* One epoch of minibatch Adam (beta 0.9 / 0.999, eps 1e-8) over n samples in
+ * an order fixed by epoch_seed; *mean_loss (host, may be NULL; synchronises)
+ * receives the mean loss of the epoch. */
+int amr_mlp_train_epoch(const amr_mlp_state* st, const float* x, const float* y, int64_t n,
+                        int batch, float lr, float pos_weight, uint64_t epoch_seed,
+                        double* mean_loss, void* stream);
+/* prob[i] = sigmoid(MLP(x[i])) with the FP16 weights, i < n. */
+int amr_mlp_infer(const void* params_half, const float* x, int64_t n, float* prob, void* stream);
+
+/* The plain criterion as a dry run: sync, vorticity criterion and distance
+ * rule; writes the raw marks (+1 / +2 refine a leaf, -1 coarsen a REFINED
+ * block, 0) of every block to dev_marks[max_blocks]; the mesh is unchanged.
+ * Synchronous. */
+int amr_criterion_marks(amr_t* a, int8_t* dev_marks);
+
+/* Refinement proposal: sync, block summaries, the MLP (FP16 weights) on every
+ * leaf; a leaf with probability > threshold is marked +1.  With
+ * with_criterion != 0 the marks of the plain criterion are merged in (a
+ * refine mark from either source refines; coarsening comes from the
+ * criterion).  Writes dev_marks[max_blocks] for amr_adapt.  3D only.
+ * Synchronous. */
+int amr_propose_marks(amr_t* a, const void* params_half, float threshold, int with_criterion,
+                      int8_t* dev_marks);
 
 /* ---------------------------------------------------------- batched instances
  * Many independent instances (same velocity set and storage, no solid) are

@@ -21,7 +21,8 @@ STORAGE = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 FACE = {"noslip": 0, "moving": 1, "outlet": 2, "periodic": 3}
 # field selectors
 AMR_RHO_U, AMR_F, AMR_BLOCKS, AMR_COORDS, AMR_NBR, AMR_NBR_CHILD, AMR_IDSETS, AMR_GAPS, \
-    AMR_MASKS, AMR_COUNTS, AMR_MASS, AMR_FORCE = range(12)
+    AMR_MASKS, AMR_COUNTS, AMR_MASS, AMR_FORCE, AMR_FEATURES = range(13)
+MLP_INPUTS, MLP_HIDDEN = 27, 64
 
 EXPORTED = ["amr_arena_bytes", "amr_init", "amr_step", "amr_adapt", "amr_fields",
             "amr_set_fields", "amr_profile", "amr_profile_read", "amr_free", "amr_strerror",
@@ -50,6 +51,12 @@ class AmrAdaptStats(ctypes.Structure):
                 ("n_refined", ctypes.c_int64), ("n_coarsened", ctypes.c_int64),
                 ("n_blocks", ctypes.c_int64), ("capacity_error", ctypes.c_int32),
                 ("pad_", ctypes.c_int32), ("ms_total", ctypes.c_double)]
+
+
+class AmrMlpState(ctypes.Structure):
+    _fields_ = [("params", ctypes.c_void_p), ("adam_m", ctypes.c_void_p),
+                ("adam_v", ctypes.c_void_p), ("params_half", ctypes.c_void_p),
+                ("grad", ctypes.c_void_p), ("loss", ctypes.c_void_p), ("step", ctypes.c_int64)]
 
 
 class AmrKernelProfile(ctypes.Structure):
@@ -91,6 +98,25 @@ def load_library(path=LIB_PATH):
     lib.amr_strerror.restype = ctypes.c_char_p
     lib.amr_last_error.argtypes = []
     lib.amr_last_error.restype = ctypes.c_char_p
+    lib.amr_mlp_param_count.argtypes = []
+    lib.amr_mlp_param_count.restype = i32
+    lib.amr_mlp_init.argtypes = [vp, vp, ctypes.c_uint64, vp]
+    lib.amr_mlp_init.restype = i32
+    lib.amr_mlp_grad.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, vp, vp]
+    lib.amr_mlp_grad.restype = i32
+    lib.amr_mlp_train_epoch.argtypes = [ctypes.POINTER(AmrMlpState), vp, vp, i64, i32,
+                                        ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
+                                        ctypes.POINTER(ctypes.c_double), vp]
+    lib.amr_mlp_train_epoch.restype = i32
+    lib.amr_mlp_infer.argtypes = [vp, vp, i64, vp, vp]
+    lib.amr_mlp_infer.restype = i32
+    lib.amr_criterion_marks.argtypes = [vp, vp]
+    lib.amr_criterion_marks.restype = i32
+    lib.amr_propose_marks.argtypes = [vp, vp, ctypes.c_float, i32, vp]
+    lib.amr_propose_marks.restype = i32
+    lib.amr_mass_audit_noalloc.argtypes = [i32, i32, i32, i64, vp, vp, ctypes.c_uint32, vp, vp,
+                                           vp, vp]
+    lib.amr_mass_audit_noalloc.restype = i32
     pp = ctypes.POINTER(vp)
     lib.amr_batch_arena_bytes.argtypes = [pp, i32]
     lib.amr_batch_arena_bytes.restype = sz
@@ -294,6 +320,29 @@ class AmrLBM:
     def launches(self):
         return self.counts()["launches"]
 
+    def features(self):
+        """Block summaries [cap, 27] (float32, device tensor; runs a sync)."""
+        import torch
+        return self.fields_device(AMR_FEATURES, torch.float32).reshape(self.cap, MLP_INPUTS)
+
+    def criterion_marks(self):
+        """Marks of the plain criterion without adapting (int8 device tensor)."""
+        import torch
+        out = torch.zeros(self.cap, dtype=torch.int8, device=self.device)
+        self._check(self.lib.amr_criterion_marks(self.h, ctypes.c_void_p(out.data_ptr())),
+                    "amr_criterion_marks")
+        return out
+
+    def propose_marks(self, params_half, threshold=0.5, with_criterion=True):
+        """Marks from the learned proposal (merged with the plain criterion)."""
+        import torch
+        out = torch.zeros(self.cap, dtype=torch.int8, device=self.device)
+        self._check(self.lib.amr_propose_marks(self.h, ctypes.c_void_p(params_half.data_ptr()),
+                                               float(threshold), 1 if with_criterion else 0,
+                                               ctypes.c_void_p(out.data_ptr())),
+                    "amr_propose_marks")
+        return out
+
     def updates_per_coarse_step(self):
         """Leaf-cell updates of one coarse step (Section 5.1 definition)."""
         c = self.counts()
@@ -365,3 +414,61 @@ class AmrBatch:
             self.close()
         except Exception:
             pass
+
+
+class Mlp:
+    """Per-block MLP of the learned refinement proposal (device tensors)."""
+
+    def __init__(self, device, seed=0, stream=None):
+        import torch
+        self.lib = lib = load_library()
+        self.n = lib.amr_mlp_param_count()
+        f32 = dict(dtype=torch.float32, device=device)
+        self.params = torch.empty(self.n, **f32)
+        self.half = torch.empty(self.n, dtype=torch.float16, device=device)
+        self.m = torch.zeros(self.n, **f32)
+        self.v = torch.zeros(self.n, **f32)
+        self.grad = torch.zeros(self.n, **f32)
+        self.loss = torch.zeros(1, **f32)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.state = AmrMlpState(self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(),
+                                 self.half.data_ptr(), self.grad.data_ptr(),
+                                 self.loss.data_ptr(), 0)
+        rc = lib.amr_mlp_init(ctypes.c_void_p(self.params.data_ptr()),
+                              ctypes.c_void_p(self.half.data_ptr()), int(seed),
+                              ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_mlp_init")
+
+    def train_epoch(self, x, y, batch=1024, lr=1e-3, pos_weight=1.0, seed=0):
+        out = ctypes.c_double(0.0)
+        rc = self.lib.amr_mlp_train_epoch(ctypes.byref(self.state), ctypes.c_void_p(x.data_ptr()),
+                                          ctypes.c_void_p(y.data_ptr()), int(x.shape[0]),
+                                          int(batch), float(lr), float(pos_weight), int(seed),
+                                          ctypes.byref(out),
+                                          ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_mlp_train_epoch")
+        return out.value
+
+    def grad_of(self, x, y, pos_weight=1.0):
+        rc = self.lib.amr_mlp_grad(ctypes.c_void_p(self.params.data_ptr()),
+                                   ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                   int(x.shape[0]), float(pos_weight),
+                                   ctypes.c_void_p(self.grad.data_ptr()),
+                                   ctypes.c_void_p(self.loss.data_ptr()),
+                                   ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_mlp_grad")
+        return self.grad, self.loss
+
+    def infer(self, x):
+        import torch
+        prob = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        rc = self.lib.amr_mlp_infer(ctypes.c_void_p(self.half.data_ptr()),
+                                    ctypes.c_void_p(x.data_ptr()), int(x.shape[0]),
+                                    ctypes.c_void_p(prob.data_ptr()),
+                                    ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_mlp_infer")
+        return prob

@@ -38,6 +38,8 @@ struct Instance {
   uint32_t* nonemask = nullptr;    // bit k set when nbr[b][k] == NONE
   uint64_t* solidmask = nullptr;   // bit l set when cell l is solid
   uint64_t* cellmask = nullptr;    // [cap][2]: ghost cells, interface cells (bit l)
+  float* features = nullptr;       // [cap][27] block summaries
+  float* prob = nullptr;           // [cap] proposal probabilities
   int32_t *idset = nullptr, *active = nullptr, *parents = nullptr;   // [lmax][cap]
   int32_t* gap = nullptr;          // [cap]
   int8_t* marks = nullptr;         // [cap]
@@ -91,6 +93,9 @@ int mesh_adapt(Instance* a, bool external, amr_adapt_stats* st);
 int mesh_export(Instance* a, int what, void* dst_dev);
 int mesh_refresh_lists(Instance* a);
 int mesh_distance_marks(Instance* a);
+// mlp.cu
+void mlp_infer_list(cudaStream_t s, const void* params_half, const float* x, const int32_t* list,
+                    int64_t n, float* prob);
 int64_t mesh_export_bytes(const Instance* a, int what);
 
 #define AMR_CUDA(call)                                                             \

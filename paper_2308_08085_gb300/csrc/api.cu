@@ -122,6 +122,8 @@ static Layout layout_for(const amr_config* c) {
       64 * 4,                                  // 22 wall_code
       STAGING_BYTES,                           // 23 staging
       (size_t)cap * 16,                        // 24 cellmask
+      (size_t)cap * 27 * 4,                    // 25 features
+      (size_t)cap * 4,                         // 26 proposal probabilities
   };
   size_t off = 0;
   int i = 0;
@@ -336,6 +338,49 @@ static void level_sync(Instance* a) {
   }
 }
 
+// Vorticity criterion of every level and the distance rule into a->marks.
+static int criterion_into_marks(Instance* a) {
+  AMR_CUDA(cudaMemsetAsync(a->marks, 0, a->cap, a->stream));
+  for (int L = 0; L < a->lmax; ++L) {
+    if (a->n_ids[L] == 0) continue;
+    const double inv_dx = a->cfg.nx * std::ldexp(1.0, L) / a->cfg.length_x;
+    a->ops->criterion(a->stream, a->idset + (size_t)L * a->cap, (int)a->n_ids[L],
+                      a->fbuf(L, 0), a->stride(), a->status, L, a->lmax, inv_dx,
+                      a->cfg.crit_start, a->cfg.crit_inc, a->marks, a->w2);
+    a->launches += 1;
+  }
+  AMR_CUDA(cudaGetLastError());
+  return mesh_distance_marks(a);
+}
+
+// Block summaries of every block in the ID sets into a->features.
+static int features_all(Instance* a) {
+  if (a->dim != 3) {
+    set_error("block summaries are defined for 3D forests");
+    return AMR_E_INVAL;
+  }
+  AMR_CUDA(cudaMemsetAsync(a->features, 0, sizeof(float) * 27 * a->cap, a->stream));
+  for (int L = 0; L < a->lmax; ++L) {
+    if (a->n_ids[L] == 0) continue;
+    const double inv_dx = a->cfg.nx * std::ldexp(1.0, L) / a->cfg.length_x;
+    a->ops->features(a->stream, a->idset + (size_t)L * a->cap, (int)a->n_ids[L], a->fbuf(L, 0),
+                     a->stride(), L, a->lmax, inv_dx, a->features);
+    a->launches += 1;
+  }
+  AMR_CUDA(cudaGetLastError());
+  return AMR_OK;
+}
+
+// leaves with probability above the threshold get a refine mark (+1) unless
+// they already carry one
+__global__ void k_propose(const int32_t* list, int n, const int32_t* status, const float* prob,
+                          float threshold, int8_t* marks) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = list[i];
+  if (status[b] == 1 && prob[b] > threshold && marks[b] <= 0) marks[b] = 1;
+}
+
 __global__ void k_sum_partials(int n, int nv, const double* partial, double* out) {
   __shared__ double s[256];
   for (int v = 0; v < nv; ++v) {
@@ -449,6 +494,8 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
   a->wall_code = (int32_t*)(base + L.off[i++]);
   a->staging = base + L.off[i++];
   a->cellmask = (uint64_t*)(base + L.off[i++]);
+  a->features = (float*)(base + L.off[i++]);
+  a->prob = (float*)(base + L.off[i++]);
 
   const double tau0 = 3.0 * cfg->nu0 + 0.5;
   for (int l = 0; l < a->lmax; ++l) a->tau[l] = 0.5 + std::ldexp(tau0 - 0.5, l);
@@ -548,17 +595,8 @@ int amr_adapt(amr_t* h, const int8_t* dev_marks, amr_adapt_stats* out) {
   if (dev_marks) {
     AMR_CUDA(cudaMemcpyAsync(a->marks, dev_marks, a->cap, cudaMemcpyDeviceToDevice, a->stream));
   } else {
-    AMR_CUDA(cudaMemsetAsync(a->marks, 0, a->cap, a->stream));
-    for (int L = 0; L < a->lmax; ++L) {
-      if (a->n_ids[L] == 0) continue;
-      const double inv_dx = a->cfg.nx * std::ldexp(1.0, L) / a->cfg.length_x;
-      a->ops->criterion(a->stream, a->idset + (size_t)L * a->cap, (int)a->n_ids[L],
-                        a->fbuf(L, 0), a->stride(), a->status, L, a->lmax, inv_dx,
-                        a->cfg.crit_start, a->cfg.crit_inc, a->marks, a->w2);
-      a->launches += 1;
-    }
-    const int drc = mesh_distance_marks(a);
-    if (drc != AMR_OK) return drc;
+    const int crc = criterion_into_marks(a);
+    if (crc != AMR_OK) return crc;
   }
   AMR_CUDA(cudaGetLastError());
   int rc = mesh_adapt(a, dev_marks != nullptr, &st);
@@ -585,6 +623,7 @@ int64_t amr_fields(amr_t* h, int what, void* dst, size_t dst_bytes, int dst_on_d
     case AMR_COUNTS: need = (4 + 4 * (int64_t)a->lmax) * 8; break;
     case AMR_MASS: need = (1 + D) * 8; break;
     case AMR_FORCE: need = 3 * 8; break;
+    case AMR_FEATURES: need = cap * 27 * 4; break;
     default: need = mesh_export_bytes(a, what);
   }
   if (need < 0) {
@@ -657,6 +696,18 @@ int64_t amr_fields(amr_t* h, int what, void* dst, size_t dst_bytes, int dst_on_d
           set_error("mass audit found a non-finite value");
           return AMR_E_UNSTABLE;
         }
+    }
+    return need;
+  }
+  if (what == AMR_FEATURES) {
+    level_sync(a);
+    const int frc = features_all(a);
+    if (frc != AMR_OK) return frc;
+    if (dst_on_device) {
+      AMR_CUDA(cudaMemcpyAsync(dst, a->features, need, cudaMemcpyDeviceToDevice, s));
+    } else {
+      AMR_CUDA(cudaMemcpyAsync(dst, a->features, need, cudaMemcpyDeviceToHost, s));
+      AMR_CUDA(cudaStreamSynchronize(s));
     }
     return need;
   }
@@ -753,6 +804,42 @@ int amr_set_fields(amr_t* h, int what, const void* src, size_t src_bytes, int sr
     }
   }
   AMR_CUDA(cudaGetLastError());
+  return AMR_OK;
+}
+
+int amr_criterion_marks(amr_t* h, int8_t* dev_marks) {
+  Handle* a = reinterpret_cast<Handle*>(h);
+  if (!a || !dev_marks) return AMR_E_INVAL;
+  level_sync(a);
+  const int rc = criterion_into_marks(a);
+  if (rc != AMR_OK) return rc;
+  AMR_CUDA(cudaMemcpyAsync(dev_marks, a->marks, a->cap, cudaMemcpyDeviceToDevice, a->stream));
+  AMR_CUDA(cudaStreamSynchronize(a->stream));
+  return AMR_OK;
+}
+
+int amr_propose_marks(amr_t* h, const void* params_half, float threshold, int with_criterion,
+                      int8_t* dev_marks) {
+  Handle* a = reinterpret_cast<Handle*>(h);
+  if (!a || !params_half || !dev_marks) return AMR_E_INVAL;
+  level_sync(a);
+  int rc = with_criterion ? criterion_into_marks(a) : AMR_OK;
+  if (rc != AMR_OK) return rc;
+  if (!with_criterion) AMR_CUDA(cudaMemsetAsync(a->marks, 0, a->cap, a->stream));
+  rc = features_all(a);
+  if (rc != AMR_OK) return rc;
+  for (int L = 0; L < a->lmax; ++L) {
+    const int64_t n = a->n_ids[L];
+    if (n == 0) continue;
+    const int32_t* ids = a->idset + (size_t)L * a->cap;
+    mlp_infer_list(a->stream, params_half, a->features, ids, n, a->prob);
+    k_propose<<<(int)((n + 255) / 256), 256, 0, a->stream>>>(ids, (int)n, a->status, a->prob,
+                                                             threshold, a->marks);
+    a->launches += 2;
+  }
+  AMR_CUDA(cudaGetLastError());
+  AMR_CUDA(cudaMemcpyAsync(dev_marks, a->marks, a->cap, cudaMemcpyDeviceToDevice, a->stream));
+  AMR_CUDA(cudaStreamSynchronize(a->stream));
   return AMR_OK;
 }
 

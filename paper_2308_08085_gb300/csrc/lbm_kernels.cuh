@@ -648,6 +648,118 @@ __global__ void __launch_bounds__(128)
   if (w2out) w2out[b] = w2d;
 }
 
+
+// ============================================ block summaries (27 features)
+// Inputs of the learned refinement proposal, per 4^3 block after the level
+// synchronisation: for the 9 velocity-gradient components G_ab = du_a/dx_b
+// (block-local first-order differences as in the criterion, physical units)
+// their mean and max |.|; mean and max-min of rho; mean u_x, u_y, u_z and
+// max |u|; mean and max |w|; level / L_max.  Gradient and vorticity entries
+// are compressed as sign(x) log(1 + |x|); density entries are (rho - 1) * 100
+// and (max - min) * 100; velocities are scaled by 20.
+constexpr int N_FEATURES = 27;
+
+__device__ __forceinline__ float squash(float x) { return copysignf(log1pf(fabsf(x)), x); }
+
+template <int Q, class T>
+__global__ void __launch_bounds__(128)
+    k_features(const int32_t* __restrict__ list, int n, const T* __restrict__ f, size_t stride,
+               int level, int lmax, double inv_dx, float* __restrict__ out) {
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int D = 3, M = 64, BPC = 2, NV = 15;
+  __shared__ float su[BPC][4][M];            // ux, uy, uz, rho
+  __shared__ float sv[BPC][NV][M];           // per-cell values to reduce
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int bi = blockIdx.x * BPC + slot;
+  const bool valid = bi < n;
+  int b = 0;
+  if (valid) {
+    b = list[bi];
+    R fl[Q];
+    static_for<0, Q>([&](auto P) {
+      fl[P] = S::template load<D, Q, P>(f[(size_t)P * stride + (size_t)b * M + l]);
+    });
+    R rho, ux, uy, uz;
+    moments<D, Q>(fl, rho, ux, uy, uz);
+    su[slot][0][l] = (float)ux;
+    su[slot][1][l] = (float)uy;
+    su[slot][2][l] = (float)uz;
+    su[slot][3][l] = (float)rho;
+  }
+  __syncthreads();
+  if (valid) {
+    const int i = l & 3, j = (l >> 2) & 3, k = l >> 4;
+    const float s = (float)inv_dx;
+    float G[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        const int pos = ax == 0 ? i : (ax == 1 ? j : k);
+        const int st = ax == 0 ? 1 : (ax == 1 ? 4 : 16);
+        const float d = pos < 3 ? su[slot][c][l + st] - su[slot][c][l]
+                                : su[slot][c][l] - su[slot][c][l - st];
+        G[3 * c + ax] = d * s;
+      }
+    const float wx = G[7] - G[5], wy = G[2] - G[6], wz = G[3] - G[1];
+    const float ux = su[slot][0][l], uy = su[slot][1][l], uz = su[slot][2][l];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) sv[slot][q][l] = G[q];
+    sv[slot][9][l] = su[slot][3][l];
+    sv[slot][10][l] = ux;
+    sv[slot][11][l] = uy;
+    sv[slot][12][l] = uz;
+    sv[slot][13][l] = sqrtf(ux * ux + uy * uy + uz * uz);
+    sv[slot][14][l] = sqrtf(wx * wx + wy * wy + wz * wz);
+  }
+  __syncthreads();
+  if (!valid || l >= N_FEATURES) return;
+  // thread l reduces feature l over the block's 64 cells
+  const int q = l;
+  float acc;
+  if (q < 9) {                                   // mean of G_q
+    acc = 0.f;
+    for (int c = 0; c < M; ++c) acc += sv[slot][q][c];
+    acc = squash(acc / M);
+  } else if (q < 18) {                           // max |G_q|
+    acc = 0.f;
+    for (int c = 0; c < M; ++c) acc = fmaxf(acc, fabsf(sv[slot][q - 9][c]));
+    acc = squash(acc);
+  } else if (q == 18) {                          // mean rho
+    acc = 0.f;
+    for (int c = 0; c < M; ++c) acc += sv[slot][9][c];
+    acc = (acc / M - 1.f) * 100.f;
+  } else if (q == 19) {                          // max - min rho
+    float lo = sv[slot][9][0], hi = lo;
+    for (int c = 1; c < M; ++c) {
+      lo = fminf(lo, sv[slot][9][c]);
+      hi = fmaxf(hi, sv[slot][9][c]);
+    }
+    acc = (hi - lo) * 100.f;
+  } else if (q < 23) {                           // mean u_x, u_y, u_z
+    acc = 0.f;
+    for (int c = 0; c < M; ++c) acc += sv[slot][10 + (q - 20)][c];
+    acc = acc / M * 20.f;
+  } else if (q == 23) {                          // max |u|
+    acc = 0.f;
+    for (int c = 0; c < M; ++c) acc = fmaxf(acc, sv[slot][13][c]);
+    acc *= 20.f;
+  } else if (q == 24) {                          // mean |w|
+    acc = 0.f;
+    for (int c = 0; c < M; ++c) acc += sv[slot][14][c];
+    acc = squash(acc / M);
+  } else if (q == 25) {                          // max |w|
+    acc = 0.f;
+    for (int c = 0; c < M; ++c) acc = fmaxf(acc, sv[slot][14][c]);
+    acc = squash(acc);
+  } else {                                       // level / L_max
+    acc = (float)level / (float)lmax;
+  }
+  out[(size_t)b * N_FEATURES + q] = acc;
+}
+
 // ============================================================ exports/imports
 template <int D, int Q, class T>
 __global__ void k_export_f(int64_t cap, int64_t b0, int64_t nb, const T* __restrict__ fa,
@@ -993,6 +1105,15 @@ struct Launch {
                                                   omega, dx, partial);
     return grid;
   }
+  static void features(cudaStream_t s, const int32_t* list, int n, const void* f, size_t stride,
+                       int level, int lmax, double inv_dx, float* out) {
+    if constexpr (D == 3) {
+      if (n > 0)
+        k_features<Q, T><<<grid_for(n, 2), 128, 0, s>>>(list, n, (const T*)f, stride, level, lmax,
+                                                        inv_dx, out);
+    }
+  }
+
   static void collide_stream_batch(cudaStream_t s, const uint32_t* items, int n,
                                    const InstDesc* descs, int level, int which_in, int variant) {
     if (n <= 0) return;
@@ -1020,7 +1141,7 @@ struct Launch {
     static const LbmOps o = {setup,         collide_stream, interp,   average,
                              criterion,     export_f,       import_f, export_rho_u,
                              init_rest,     mass_partial,   force_partial,
-                             collide_stream_batch, interp_batch, average_batch};
+                             collide_stream_batch, interp_batch, average_batch, features};
     return &o;
   }
 };

@@ -86,6 +86,9 @@ struct LbmOps {
                        int level, int which_par, int which_ch);
   void (*average_batch)(cudaStream_t, const uint32_t* items, int n, const InstDesc* descs,
                         int level, int which_par, int which_ch);
+  // 27 block summaries of the learned refinement proposal (3D only)
+  void (*features)(cudaStream_t, const int32_t* list, int n, const void* f, size_t stride,
+                   int level, int lmax, double inv_dx, float* out);
 };
 
 const LbmOps* lbm_ops_d2q9(int storage);
