@@ -553,11 +553,13 @@ def run_learned(args):
                                   cx=64 * sc, cy=32 * sc, re=100.0 * (0.8 + 0.05 * seed),
                                   max_levels=args.cyl_levels, max_blocks=args.cyl_cap)
 
+    cap_errors = {"spin": 0}
+
     def spun_up(seed):
         sim = AmrLBM(cfg_for(seed), storage="f32")
         for _ in range(args.learn_spin):
             sim.step(50)
-            sim.adapt()
+            cap_errors["spin"] += sim.adapt()[0] != 0
         return sim
 
     # ---- training pairs
@@ -568,6 +570,7 @@ def run_learned(args):
         px, py = [], []
         for _ in range(args.learn_windows):
             feats = sim.features()
+
             leaf = torch.from_numpy(sim.blocks()["status"] == 1).to(dev)
             sim.step(20)
             flag = sim.criterion_marks() > 0
@@ -605,15 +608,16 @@ def run_learned(args):
         sim = spun_up(9)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         period = 50 if mode == "plain" else 200
-        ups_sum, t_ms, flagged, missed, adapts = 0.0, 0.0, 0, 0, 0
+        ups_sum, t_ms, flagged, missed, adapts, cap_err = 0.0, 0.0, 0, 0, 0, 0
         steps = 0
         while steps < args.learn_eval_steps:
             e0.record(stream)
             if mode == "learned":
                 marks = sim.propose_marks(net.half, args.learn_threshold, True)
-                sim.adapt(marks)
+                rc, _ = sim.adapt(marks)
             else:
-                sim.adapt()
+                rc, _ = sim.adapt()
+            cap_err += rc != 0
             e1.record(stream)
             torch.cuda.synchronize()
             t_ms += e0.elapsed_time(e1)
@@ -640,6 +644,7 @@ def run_learned(args):
                "adaptations": adapts, "coarse_steps": steps,
                "flagged_at_t_plus_20": flagged,
                "missed_refinement_rate": missed / max(1, flagged),
+               "capacity_errors": cap_err,
                "blocks_end": sim.counts()["n_ids"]}
         sim.close()
         torch.cuda.empty_cache()
@@ -653,7 +658,8 @@ def run_learned(args):
             "pos_weight": round(pw, 2), "epochs": args.learn_epochs,
             "loss_first_last": [round(losses[0], 4), round(losses[-1], 4)],
             "train_seconds": round(t_train, 3), "threshold": args.learn_threshold,
-            "test": test, "evaluation": ev}
+            "test": test, "capacity_errors_spin_up": int(cap_errors["spin"]),
+            "evaluation": ev}
 
 
 # ----------------------------------------------------------- reference arm
