@@ -208,9 +208,15 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
+    step_updates = []
+    active_updates = 0
     for k in range(args.steps):
         flush.fill_(k & 0xFF)                      # untimed: evict L2 between steps
-        updates += PERIOD * sim.updates_per_coarse_step()
+        step_updates.append(PERIOD * sim.updates_per_coarse_step())
+        updates += step_updates[-1]
+        cnt = sim.counts()
+        active_updates += PERIOD * sum((2 ** L) * cnt["n_active"][L] * sim.m
+                                       for L in range(sim.lmax))
         e0, e1, e2 = ev[k]
         e0.record(stream)
         sim.step(PERIOD)
@@ -223,6 +229,10 @@ def run_ours(args):
     clk = clocks.stop()
     launches = sim.counts()["launches"] - launches0     # this library's kernels only
     t_total = sum(e0.elapsed_time(e2) for e0, _, e2 in ev) / 1e3
+    # windows of two timed steps (100 coarse steps each, adaptation included)
+    win = [(step_updates[i] + step_updates[i + 1])
+           / ((ev[i][0].elapsed_time(ev[i][2]) + ev[i + 1][0].elapsed_time(ev[i + 1][2])) / 1e3)
+           / 1e6 for i in range(0, args.steps - 1, 2)]
     t_solver = sum(e0.elapsed_time(e1) for e0, e1, _ in ev) / 1e3
     prof = sim.profile_read(reset=True)
     sim.profile(0)
@@ -276,13 +286,23 @@ def run_ours(args):
                 "sampled_launches": cs["launches"],
                 "avg_launch_ms": round(cs["ms"] / max(1, cs["launches"]), 5),
                 "avg_updates_per_launch": round(per_launch_updates, 1)}
-    share = {k: round(v["ms"], 4) for k, v in prof.items()}
+    # every profiled kernel kind over the sampled coarse steps: time share and
+    # achieved algorithmic bandwidth (interpolation: 2^D parent cells per child
+    # with ghost cells read + ghost cells written; averaging: interface fine
+    # cells read + one parent cell per 2^D written)
+    t_prof = sum(v["ms"] for v in prof.values()) or 1.0
+    share = {k: {"ms": round(v["ms"], 4), "share": round(v["ms"] / t_prof, 4),
+                 "launches": v["launches"],
+                 "gbs": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None,
+                 "frac": round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / peak, 4) if v["ms"] > 0 else None}
+             for k, v in prof.items()}
 
     # single-level periodic 256^3 D3Q19 FP32 forest: the stencil's roofline bar
     bar = None
     if not args.no_bar:
         del flush
-        bar = run_bar(args, AmrLBM, W, torch, dev, stream)
+        bar = {order: run_bar(args, AmrLBM, W, torch, dev, stream, order)
+               for order in ("lexicographic", "morton", "shuffled")}
 
     out = None
     if rank == 0:
@@ -306,9 +326,15 @@ def run_ours(args):
                 "blocks_per_level_end": end_counts["n_ids"],
                 "leaf_updates_per_coarse_step_end": sim.updates_per_coarse_step(),
                 "solver_mlups_excl_adapt": round(updates / t_solver / 1e6, 2),
+                "window_mlups": [round(w, 1) for w in win],
+                "median_window_mlups": round(float(sorted(win)[len(win) // 2]), 1) if win else None,
+                "active_cell_mlups": round(active_updates / t_total / 1e6, 2),
+                "mlups_count": "leaf-cell updates, sum_L 2^L (N_L - N_(L+1)/N_c) M (Section 5.1); "
+                               "active_cell_mlups also counts the refined blocks advanced at the "
+                               "coarse-fine interface",
                 "adapt_share": round(1 - t_solver / t_total, 4),
                 "capacity_errors": int(capacity_errors),
-                "kernel_ms_last_sampled": share,
+                "kernels_sampled": share,
                 "baseline": "paper A100 mean MLUPS 1753 (D3Q19 FP32 64^3, L_max 4): context",
                 "uniform_bar": bar,
             },
@@ -328,10 +354,16 @@ def run_ours(args):
     return out
 
 
-def run_bar(args, AmrLBM, W, torch, dev, stream):
+def run_bar(args, AmrLBM, W, torch, dev, stream, order="lexicographic"):
     """Single-level periodic D3Q19 FP32 forest of 256^3 cells (2 x 1.27 GB of
-    populations, far above L2): fused collide-stream only."""
+    populations, far above L2): fused collide-stream only.  `order` numbers
+    the root blocks lexicographically, along the Morton curve or by a seeded
+    shuffle (block IDs then carry no spatial locality)."""
     cfg = W.config_uniform_bar(256)
+    if order == "morton":
+        cfg["root_ids"] = W.morton_root_ids(cfg)
+    elif order == "shuffled":
+        cfg["root_ids"] = W.shuffled_root_ids(cfg, 0)
     sim = AmrLBM(cfg, storage="f32", kernel_variant=args.variant)
     sim.step(3)
     sim.profile(1)
@@ -348,7 +380,7 @@ def run_bar(args, AmrLBM, W, torch, dev, stream):
     peak, _ = measured_peaks()
     ups = 256 ** 3
     kernel_gbs = prof["bytes"] / (prof["ms"] / 1e3) / 1e9
-    return {"cells": ups, "variant": args.variant,
+    return {"cells": ups, "variant": args.variant, "root_order": order,
             "mlups": round(ups * n / (e0.elapsed_time(e1) / 1e3) / 1e6, 1),
             "kernel_gbs": round(kernel_gbs, 1), "frac": round(kernel_gbs / peak, 4)}
 
@@ -377,7 +409,7 @@ def run_cylinder(args):
     area = (side / nx) * (cfg["nz"] / nx)           # D * H in physical units (length_x = 1)
     results, ref = {}, None
     for storage in args.cyl_storages.split(","):
-        sim = AmrLBM(cfg, storage=storage)
+        sim = AmrLBM(cfg, storage=storage, kernel_variant=args.variant)
         for _ in range(args.cyl_levels):            # static distance-refined mesh
             sim.adapt()
         counts = sim.counts()
@@ -706,7 +738,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=64)
@@ -733,6 +765,9 @@ def main():
     ap.add_argument("--cyl-storages", default="f64,f32,bf16,f16")
     ap.add_argument("--bar-only", action="store_true",
                     help="only the single-level 256^3 D3Q19 FP32 forest (profiling)")
+    ap.add_argument("--bar-order", default="lexicographic",
+                    choices=["lexicographic", "morton", "shuffled"],
+                    help="root-block numbering of the --bar-only forest")
     args = ap.parse_args()
     if args.cpu_worker:
         cpu_worker(args)
@@ -754,7 +789,7 @@ def main():
         from paper_2308_08085_gb300 import AmrLBM
         torch.cuda.set_device(0)
         print(json.dumps(run_bar(args, AmrLBM, W, torch, torch.device("cuda", 0),
-                                 torch.cuda.current_stream())))
+                                 torch.cuda.current_stream(), args.bar_order)))
         return
     if args.impl == "reference":
         out = run_reference(args)

@@ -104,14 +104,31 @@ typedef struct {
                               512-thread CTAs, push table read through L1;
                               1: 512 threads, table in shared memory; 4: 256
                               threads, shared; 5: 256 threads, L1; 2 / 3: 2- /
-                              3-stage cp.async pipeline in a persistent grid  */
+                              3-stage cp.async pipeline in a persistent grid;
+                              7: as 6 with 512 more resident threads per SM
+                              (tighter register budget)                        */
   double refine_dist;      /* distance refinement (Section 4.4): a leaf on level
                               L within refine_dist / 2^L (physical units) of a
                               target is marked for refinement; 0 = off        */
   int32_t refine_dist_targets; /* bit 0: the solid prism, bit 1: outlet faces */
   int32_t refine_dist_freeze;  /* 1: blocks refined by distance become
                                   AMR_ST_REFINED_PERMANENT                    */
+  const int32_t* root_ids; /* NULL: root block IDs in lexicographic order of
+                              their position, b = bx + nbx (by + nby bz).
+                              Else a host array of the n_root root blocks
+                              (read by amr_init only): root_ids[i] is the ID
+                              of the root at lexicographic position i; it must
+                              be a permutation of 0 .. n_root-1 (AMR_E_INVAL
+                              otherwise).  The ID set of level 0 stays in
+                              ascending ID order, so the order of the IDs is
+                              the order of the blocks in memory.             */
+  int32_t interp;          /* coarse-to-fine interpolation (Section 3.4):
+                              AMR_INTERP_LINEAR (0) or AMR_INTERP_CUBIC (3)  */
+  int32_t pad_;
 } amr_config;
+
+#define AMR_INTERP_LINEAR 0
+#define AMR_INTERP_CUBIC 3
 
 typedef struct {
   int64_t n_marked_refine;   /* eligible refine marks before capacity check  */
@@ -128,9 +145,10 @@ typedef struct {
   char name[32];         /* kernel class                                     */
   int64_t launches;
   double ms;             /* summed CUDA-event durations                      */
-  double bytes;          /* summed algorithmic bytes (2 Q N_p per update for
-                            collide-stream)                                  */
-  double cells;          /* summed cell updates                              */
+  double bytes;          /* summed algorithmic bytes (see amr_profile)       */
+  double cells;          /* summed cells: updates (collide-stream), ghost
+                            cells written (interp), interface fine cells read
+                            (average)                                        */
 } amr_kernel_profile;
 
 typedef struct amr_t amr_t;
@@ -215,7 +233,12 @@ int amr_set_fields(amr_t* a, int what, const void* src, size_t src_bytes,
  * sample, the launches of the most recently replayed coarse step.
  * amr_profile_read synchronises, fills up to `max` entries (collide_stream,
  * interp, average) and returns how many kernel classes exist; reset != 0
- * clears the sums.  Bytes are algorithmic: 2 Q N_p per cell update. */
+ * clears the sums.  Bytes are algorithmic, N_p bytes per stored population:
+ * collide-stream 2 Q N_p per cell update (Section 4.2, read and write once);
+ * interp Q N_p per ghost cell written plus 2^D Q N_p per child block with
+ * ghost cells (its parent cells, Section 3.4.1); average Q N_p per interface
+ * fine cell read plus Q N_p per parent cell written, one per 2^D fine cells
+ * (Section 3.4.3). */
 int amr_profile(amr_t* a, int mode);
 int amr_profile_read(amr_t* a, amr_kernel_profile* out, int max, int reset);
 

@@ -13,7 +13,10 @@ Conventions (readings of the paper where it is silent or garbled)
   X_parent + (cx, cy, cz) * w_child, where w_child is half the parent block
   width (Algorithm 1 with dx_root read as the root *block* width).
   Coordinates are in root-cell units; all offsets are exact binary fractions.
-* Root blocks are numbered x-fastest: b = bx + nbx (by + nby bz).
+* Root blocks are numbered x-fastest, b = bx + nbx (by + nby bz), unless the
+  configuration gives `root_ids`: root_ids[i] is then the ID of the root at
+  x-fastest position i (a relabelling only; the ID set of level 0 stays in
+  ascending ID order).
 * nbr[b][k] for the 3^dim directions in velocity-set order (D2Q9 / D3Q27):
   the ID of the same-level block at X_b + e_k * width, nbr[b][0] = b,
   NONE (-1) when no block of that level covers that position, or a boundary
@@ -105,10 +108,14 @@ class Forest:
         d = self.dim
         n0 = int(np.prod(self.nroot))
         self.n_root = n0
-        for b in range(n0):
-            bx = b % self.nroot[0]
-            by = (b // self.nroot[0]) % self.nroot[1]
-            pos = [bx, by] + ([b // (self.nroot[0] * self.nroot[1])] if d == 3 else [])
+        ids = self.cfg.get("root_ids")
+        ids = list(range(n0)) if ids is None else [int(v) for v in ids]
+        assert sorted(ids) == list(range(n0)), "root_ids must be a permutation"
+        for i in range(n0):
+            b = ids[i]
+            bx = i % self.nroot[0]
+            by = (i // self.nroot[0]) % self.nroot[1]
+            pos = [bx, by] + ([i // (self.nroot[0] * self.nroot[1])] if d == 3 else [])
             self.X[b] = np.array(pos, np.float64) * BLOCK_EDGE
             self.level[b] = 0
             self.status[b] = UNREFINED

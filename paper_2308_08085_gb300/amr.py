@@ -43,7 +43,9 @@ class AmrConfig(ctypes.Structure):
                 ("length_x", ctypes.c_double), ("solid", ctypes.c_double * 4),
                 ("faces", AmrFace * 6), ("use_graphs", ctypes.c_int32),
                 ("kernel_variant", ctypes.c_int32), ("refine_dist", ctypes.c_double),
-                ("refine_dist_targets", ctypes.c_int32), ("refine_dist_freeze", ctypes.c_int32)]
+                ("refine_dist_targets", ctypes.c_int32), ("refine_dist_freeze", ctypes.c_int32),
+                ("root_ids", ctypes.POINTER(ctypes.c_int32)), ("interp", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
 
 class AmrAdaptStats(ctypes.Structure):
@@ -169,6 +171,12 @@ def make_config(cfg, storage="f32", use_graphs=True, kernel_variant=0):
     c.refine_dist = float(cfg.get("refine_dist", 0.0))
     c.refine_dist_targets = int(cfg.get("refine_dist_targets", 0))
     c.refine_dist_freeze = int(cfg.get("refine_dist_freeze", 0))
+    ids = cfg.get("root_ids")
+    if ids is not None:
+        arr = np.ascontiguousarray(ids, dtype=np.int32)
+        c._root_ids = arr                               # kept alive with the struct
+        c.root_ids = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    c.interp = {"linear": 0, "cubic": 3}[cfg.get("interp", "linear")]
     return c
 
 

@@ -53,6 +53,11 @@ struct Instance {
   // host mirror of the mesh sizes and time-stepping state
   int64_t n_ids[AMR_MAX_LEVELS] = {}, n_active[AMR_MAX_LEVELS] = {},
           n_parents[AMR_MAX_LEVELS] = {}, n_leaves[AMR_MAX_LEVELS] = {};
+  // per level L: over the children of level L's exchanging parents, the
+  // children holding ghost cells, their ghost cells and their interface cells
+  // (the algorithmic work of interpolation into and averaging from level L+1)
+  int64_t n_ghost_children[AMR_MAX_LEVELS] = {}, n_ghost_cells[AMR_MAX_LEVELS] = {},
+          n_iface_cells[AMR_MAX_LEVELS] = {};
   int64_t n_gaps = 0;
   int64_t coarse_steps = 0;
   int64_t launches = 0;            // kernels launched by this instance
@@ -84,6 +89,9 @@ struct Instance {
     return f[((cur >> level) & 1u) ^ (unsigned)which];
   }
 };
+
+// dcount slot of the device wait-timeout flag (StepParams::wait_flag)
+constexpr int kWaitFlagSlot = 16;
 
 enum ProfileKind { PK_COLLIDE = 0, PK_INTERP = 1, PK_AVERAGE = 2, PK_COUNT = 3 };
 

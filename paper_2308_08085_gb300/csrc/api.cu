@@ -16,7 +16,7 @@
 #include "amr_internal.h"
 #include "lattice.cuh"
 
-static_assert(sizeof(amr_config) == 360, "amr_config layout is part of the ABI");
+static_assert(sizeof(amr_config) == 376, "amr_config layout is part of the ABI");
 static_assert(sizeof(amr_adapt_stats) == 56, "amr_adapt_stats layout is part of the ABI");
 static_assert(sizeof(amr_kernel_profile) == 64, "amr_kernel_profile layout is part of the ABI");
 
@@ -92,6 +92,21 @@ static int validate(const amr_config* c, std::string* why) {
     return AMR_E_INVAL;
   }
   if (c->max_blocks > (int64_t(1) << 31) / 64) { *why = "max_blocks too large"; return AMR_E_INVAL; }
+  if (c->interp != AMR_INTERP_LINEAR && c->interp != AMR_INTERP_CUBIC) {
+    *why = "interp must be AMR_INTERP_LINEAR or AMR_INTERP_CUBIC";
+    return AMR_E_INVAL;
+  }
+  if (c->root_ids) {
+    std::vector<char> seen((size_t)n_root, 0);
+    for (int64_t i = 0; i < n_root; ++i) {
+      const int32_t v = c->root_ids[i];
+      if (v < 0 || v >= n_root || seen[(size_t)v]) {
+        *why = "root_ids must be a permutation of 0 .. n_root-1";
+        return AMR_E_INVAL;
+      }
+      seen[(size_t)v] = 1;
+    }
+  }
   return AMR_OK;
 }
 
@@ -243,7 +258,11 @@ static void advance(Instance* a, int L) {
   const bool fine = L + 1 < a->lmax && a->n_ids[L + 1] > 0;
   const int64_t np = a->n_parents[L];
   if (fine && np > 0) {
-    ProfScope ps(a, PK_INTERP, 0.0, 0.0);
+    // algorithmic bytes: the 2^D parent cells under each child with ghost
+    // cells (read) and the ghost cells (written)
+    const double cells = (double)a->n_ghost_cells[L];
+    ProfScope ps(a, PK_INTERP,
+                 ((double)a->n_ghost_children[L] * a->nc + cells) * a->q * a->elem, cells);
     a->ops->interp(a->stream, a->parents + (size_t)L * a->cap, (int)np, a->fbuf(L, 0),
                    a->fbuf(L + 1, 0), a->stride(), a->child0, a->cellmask, a->solidmask,
                    ratio_cf(a, L), 0, a->solid);
@@ -254,7 +273,10 @@ static void advance(Instance* a, int L) {
     advance(a, L + 1);
     advance(a, L + 1);
     if (np > 0) {
-      ProfScope ps(a, PK_AVERAGE, 0.0, 0.0);
+      // algorithmic bytes: interface fine cells (read) and their parent
+      // cells, one per 2^D children (written)
+      const double cells = (double)a->n_iface_cells[L];
+      ProfScope ps(a, PK_AVERAGE, cells * (1.0 + 1.0 / a->nc) * a->q * a->elem, cells);
       a->ops->average(a->stream, a->parents + (size_t)L * a->cap, (int)np, a->fbuf(L, 0),
                       a->fbuf(L + 1, 0), a->stride(), a->child0, a->cellmask, a->status,
                       a->solidmask, ratio_fc(a, L), 0, a->solid);
@@ -402,6 +424,19 @@ __global__ void k_sum_partials(int n, int nv, const double* partial, double* out
 using namespace amr;
 
 // ====================================================================== ABI
+// A kernel whose bounded wait gave up sets this device counter; the next
+// synchronising call (amr_adapt, amr_fields to host memory) reports it.
+static int take_wait_flag(Instance* a) {
+  int32_t v = 0;
+  AMR_CUDA(cudaMemcpyAsync(&v, a->dcount + kWaitFlagSlot, sizeof(v), cudaMemcpyDeviceToHost,
+                           a->stream));
+  AMR_CUDA(cudaStreamSynchronize(a->stream));
+  if (v == 0) return AMR_OK;
+  AMR_CUDA(cudaMemsetAsync(a->dcount + kWaitFlagSlot, 0, sizeof(int32_t), a->stream));
+  set_error("a bounded wait for staged populations timed out in the collide-stream kernel");
+  return AMR_E_TIMEOUT;
+}
+
 extern "C" {
 
 const char* amr_strerror(int code) {
@@ -518,6 +553,7 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
   std::memset(&a->prm, 0, sizeof(a->prm));
   a->prm.stride = a->stride();
   a->prm.variant = cfg->kernel_variant;
+  a->prm.wait_flag = a->dcount + kWaitFlagSlot;
   if (a->ops->setup() != 0) {
     set_error(std::string("kernel setup: ") + cudaGetErrorString(cudaGetLastError()));
     delete a;
@@ -544,10 +580,15 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
     set_error("wall code upload failed");
     rc = AMR_E_CUDA;
   }
+  if (rc == AMR_OK && cudaMemsetAsync(a->dcount, 0, 64 * sizeof(int32_t), a->stream) != cudaSuccess) {
+    set_error("counter reset failed");
+    rc = AMR_E_CUDA;
+  }
   if (rc == AMR_OK) {
     a->ops->init_rest(a->stream, a->cap, a->f[0]);
     a->ops->init_rest(a->stream, a->cap, a->f[1]);
     rc = mesh_init_root(a);
+    a->cfg.root_ids = nullptr;   // read by amr_init only
   }
   if (rc == AMR_OK && cudaStreamSynchronize(a->stream) != cudaSuccess) {
     set_error(std::string("init: ") + cudaGetErrorString(cudaGetLastError()));
@@ -603,6 +644,7 @@ int amr_adapt(amr_t* h, const int8_t* dev_marks, amr_adapt_stats* out) {
   if (rc != AMR_OK) return rc;
   destroy_graphs(a);
   AMR_CUDA(cudaStreamSynchronize(a->stream));
+  if (int wrc = take_wait_flag(a)) return wrc;
   int64_t nb = 0;
   for (int L = 0; L < a->lmax; ++L) nb += a->n_ids[L];
   st.n_blocks = nb;
@@ -631,6 +673,8 @@ int64_t amr_fields(amr_t* h, int what, void* dst, size_t dst_bytes, int dst_on_d
     return AMR_E_INVAL;
   }
   if (!dst) return need;
+  if (!dst_on_device)
+    if (int wrc = take_wait_flag(a)) return wrc;
   if ((int64_t)dst_bytes < need) {
     set_error("destination too small: need " + std::to_string(need) + " bytes");
     return AMR_E_INVAL;

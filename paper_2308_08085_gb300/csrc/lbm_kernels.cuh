@@ -47,7 +47,7 @@ template <int D, int Q>
 struct StreamTable {
   uint16_t e[Q * Block<D>::M];
 };
-template <int D, int Q>
+template <int D, int Q, bool BY_K = false>
 constexpr StreamTable<D, Q> make_stream_table() {
   StreamTable<D, Q> t{};
   constexpr int M = Block<D>::M;
@@ -59,7 +59,8 @@ constexpr StreamTable<D, Q> make_stream_table() {
       const int sx = ti < 0 ? -1 : (ti > 3 ? 1 : 0);
       const int sy = tj < 0 ? -1 : (tj > 3 ? 1 : 0);
       const int sz = tk < 0 ? -1 : (tk > 3 ? 1 : 0);
-      const int code = (sx + 1) + 3 * (sy + 1) + (D == 3 ? 9 * (sz + 1) : 0);
+      const int code = BY_K ? Nbr<D>::dir_of(sx, sy, sz)
+                            : (sx + 1) + 3 * (sy + 1) + (D == 3 ? 9 * (sz + 1) : 0);
       const int cell = (ti & 3) + 4 * (tj & 3) + (D == 3 ? 16 * (tk & 3) : 0);
       t.e[p * M + l] = (uint16_t)(code | (cell << 5));
     }
@@ -67,6 +68,10 @@ constexpr StreamTable<D, Q> make_stream_table() {
 }
 template <int D, int Q>
 __device__ const StreamTable<D, Q> g_stream_table = make_stream_table<D, Q>();
+// the same targets with the neighbour index k of the block's nbr row in place
+// of the geometric code (for kernels that use the raw row)
+template <int D, int Q>
+__device__ const StreamTable<D, Q> g_stream_table_k = make_stream_table<D, Q, true>();
 
 // One BGK collision + push of a cell whose populations are f[]: the common
 // body of both collide-stream kernels.  `tab` is the stream table, in shared
@@ -137,15 +142,17 @@ __device__ __forceinline__ void collide_push(typename Store<T>::R (&f)[Q], int l
 // anti-bounce-back outlet value (Section 2 boundary equations).
 // resident warps per SM targeted by the one-pass kernel: 48 for FP32 math
 // with Q <= 19 (40 registers), fewer for the larger register footprints
-template <class T, int Q, int THREADS>
+// (+ 512 threads per SM with DENSE: a tighter register budget that may spill)
+template <class T, int Q, int THREADS, bool DENSE = false>
 constexpr int one_pass_min_blocks() {
-  const int threads_per_sm = sizeof(typename Store<T>::R) == 4 ? (Q <= 19 ? 1536 : 1024)
-                                                                : (Q <= 19 ? 1024 : 512);
+  const int threads_per_sm = (sizeof(typename Store<T>::R) == 4 ? (Q <= 19 ? 1536 : 1024)
+                                                                 : (Q <= 19 ? 1024 : 512)) +
+                             (DENSE ? 512 : 0);
   return threads_per_sm / THREADS > 0 ? threads_per_sm / THREADS : 1;
 }
 
-template <int D, int Q, class T, bool SOLID, int THREADS, bool TAB_SMEM>
-__global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS>()))
+template <int D, int Q, class T, bool SOLID, int THREADS, bool TAB_SMEM, bool DENSE = false>
+__global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, DENSE>()))
     k_collide_stream(const int32_t* __restrict__ list, int n, const T* __restrict__ fin,
                      T* __restrict__ fout, const int32_t* __restrict__ nbr,
                      const uint64_t* __restrict__ solidmask, StepParams prm) {
@@ -308,6 +315,182 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 8 && Q == 27) ? 1 : 2)
     stage = (stage + 1) % STAGES;
   }
   cp_async_wait<0>();
+}
+
+// ============================ bulk-copy staged persistent collide + stream
+// Same arithmetic as k_collide_stream.  Each CTA walks tiles of THREADS/M
+// blocks (tile = blockIdx.x + k gridDim.x, one cell per thread).  Warp 0
+// stages a tile into shared memory with bulk asynchronous copies
+// (cp.async.bulk, completion counted in bytes on the stage's mbarrier): the Q
+// population planes of each block (M N_p contiguous bytes each) and its
+// 128-byte neighbour row.  STAGES tiles are in flight while the CTA collides
+// the current one out of shared memory and pushes it to global memory.  The
+// loads occupy no registers and no load instructions of the computing
+// threads.  Every wait on an mbarrier is bounded (about a second); a CTA
+// that gives up sets *wait_flag, waits (bounded) for its copies in flight
+// and returns.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase of `parity` to complete: false after ~2^31 cycles
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_test(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+template <int D, int Q, class T, int THREADS>
+struct BulkTile {
+  static constexpr int M = Block<D>::M;
+  static constexpr int TB = THREADS / M;                       // blocks per tile
+  static constexpr int PLANE = M * (int)sizeof(T);             // bytes, multiple of 16
+  static constexpr int POPS = TB * Q * PLANE;                  // [TB][Q][M] values
+  static constexpr int ROW = NBR_STRIDE * 4;                   // one neighbour row
+  static constexpr int STAGE = POPS + TB * ROW;
+  static constexpr size_t smem(int stages) { return (size_t)stages * STAGE + 8 * (size_t)stages; }
+  static_assert(PLANE % 16 == 0 && ROW % 16 == 0, "bulk copies move multiples of 16 bytes");
+  static_assert(TB <= 32, "one lane of warp 0 per block of a tile");
+};
+
+template <int D, int Q, class T, int THREADS, int STAGES>
+__global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 2 : 4))
+    k_collide_stream_bulk(const int32_t* __restrict__ list, int n, const T* __restrict__ fin,
+                          T* __restrict__ fout, const int32_t* __restrict__ nbr,
+                          StepParams prm) {
+  using BT = BulkTile<D, Q, T, THREADS>;
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int M = BT::M, TB = BT::TB;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + STAGES * (size_t)BT::STAGE);
+  __shared__ int s_contig[STAGES];   // 1: the stage was filled by one copy per plane
+  const int n_tiles = (n + TB - 1) / TB;
+  const int lane = threadIdx.x & 31;
+  const bool producer = threadIdx.x < 32;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < STAGES; ++st) mbar_init(smem_addr(bars + st), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // warp 0: request tile `tile` into stage `st`
+  auto issue = [&](int tile, int st) {
+    const int first = tile * TB;
+    const int nb = min(TB, n - first);
+    const uint32_t bar = smem_addr(bars + st);
+    unsigned char* base = smem_raw + (size_t)st * BT::STAGE;
+    const int my_b = lane < nb ? __ldg(list + first + lane) : 0;
+    const int b0 = __shfl_sync(0xffffffffu, my_b, 0);
+    // consecutive IDs (sibling groups, uniform forests): one copy per plane
+    const bool contig = __all_sync(0xffffffffu, lane >= nb || my_b == b0 + lane);
+    if (lane == 0) s_contig[st] = contig ? 1 : 0;   // published by the arrive below
+    fence_proxy_async_smem();   // earlier generic reads of this stage before the async writes
+    __syncwarp();
+    if (lane == 0) mbar_expect_tx(bar, (uint32_t)nb * (Q * BT::PLANE + BT::ROW));
+    __syncwarp();
+    if (contig) {
+      for (int p = lane; p <= Q; p += 32) {
+        if (p < Q)
+          bulk_load(smem_addr(base + (size_t)p * BT::PLANE * TB),
+                    fin + (size_t)p * prm.stride + (size_t)b0 * M, nb * BT::PLANE, bar);
+        else
+          bulk_load(smem_addr(base + BT::POPS), nbr + (size_t)b0 * NBR_STRIDE, nb * BT::ROW, bar);
+      }
+      return;
+    }
+#pragma unroll 1
+    for (int s = 0; s < nb; ++s) {
+      const int b = __shfl_sync(0xffffffffu, my_b, s);
+      for (int p = lane; p <= Q; p += 32) {
+        if (p < Q)
+          bulk_load(smem_addr(base + (size_t)(s * Q + p) * BT::PLANE),
+                    fin + (size_t)p * prm.stride + (size_t)b * M, BT::PLANE, bar);
+        else
+          bulk_load(smem_addr(base + BT::POPS + s * BT::ROW), nbr + (size_t)b * NBR_STRIDE,
+                    BT::ROW, bar);
+      }
+    }
+  };
+
+  int k_issued = 0;   // tiles of this CTA requested so far
+  if (producer)
+    for (; k_issued < STAGES && blockIdx.x + k_issued * (int)gridDim.x < n_tiles; ++k_issued)
+      issue(blockIdx.x + k_issued * gridDim.x, k_issued);
+  if (producer) k_issued = __shfl_sync(0xffffffffu, k_issued, 0);
+
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  int k = 0;
+  bool failed = false;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
+    const int st = k % STAGES;
+    const uint32_t parity = (uint32_t)(k / STAGES) & 1u;
+    const bool ok = mbar_wait(smem_addr(bars + st), parity);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const unsigned char* base = smem_raw + (size_t)st * BT::STAGE;
+    if (tile * TB + slot < n) {
+      const int32_t* row = reinterpret_cast<const int32_t*>(base + BT::POPS + slot * BT::ROW);
+      // plane-major [Q][TB][M] after a contiguous copy, else block-major [TB][Q][M]
+      const bool contig = s_contig[st] != 0;
+      const T* sf = reinterpret_cast<const T*>(base) + (contig ? (size_t)slot * M : (size_t)slot * Q * M);
+      const int pstride = contig ? TB * M : M;
+      R f[Q];
+      static_for<0, Q>([&](auto P) { f[P] = S::template load<D, Q, P>(sf[P * pstride + l]); });
+      collide_push<D, Q, T, false, false>(f, l, row[0], g_stream_table_k<D, Q>.e, row, nullptr,
+                                          fout, prm.stride, prm.omega, prm.faces);
+    }
+    __syncthreads();   // stage st is free again
+    const int next = tile + STAGES * (int)gridDim.x;
+    if (producer && next < n_tiles) {
+      issue(next, st);
+      ++k_issued;
+    }
+  }
+  if (failed) {
+    // give up: report, then let the copies already requested land (bounded)
+    if (threadIdx.x == 0) {
+      atomicExch(prm.wait_flag, 1);
+      for (int j = k; j < k_issued; ++j)
+        (void)mbar_wait(smem_addr(bars + (j % STAGES)), (uint32_t)(j / STAGES) & 1u);
+    }
+    __syncthreads();
+  }
 }
 
 // =========================================== coarse-to-fine linear interpolation
@@ -974,6 +1157,25 @@ struct Launch {
     return 0;
   }
 
+  // persistent grids of the bulk-copy kernel: [threads 256/512][stages 2..4]
+  static inline int bulk_grid[2][3] = {{0, 0, 0}, {0, 0, 0}};
+
+  template <int THREADS, int STAGES>
+  static int setup_bulk(int sms) {
+    using BT = BulkTile<D, Q, T, THREADS>;
+    const size_t bytes = BT::smem(STAGES);
+    const void* fn = (const void*)k_collide_stream_bulk<D, Q, T, THREADS, STAGES>;
+    if (bytes > 227 * 1024) return 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
+      return -1;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, THREADS, bytes) != cudaSuccess)
+      return -1;
+    bulk_grid[THREADS == 512 ? 1 : 0][STAGES - 2] = per_sm > 0 ? per_sm * sms : 0;
+    return 0;
+  }
+
   static int setup() {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;
@@ -981,7 +1183,23 @@ struct Launch {
     if (setup_one<false, 2>(sms) || setup_one<true, 2>(sms) || setup_one<false, 3>(sms) ||
         setup_one<true, 3>(sms))
       return -1;
+    if (setup_bulk<512, 2>(sms) || setup_bulk<512, 3>(sms) || setup_bulk<512, 4>(sms) ||
+        setup_bulk<256, 2>(sms) || setup_bulk<256, 3>(sms) || setup_bulk<256, 4>(sms))
+      return -1;
     return 0;
+  }
+
+  template <int THREADS, int STAGES>
+  static bool launch_bulk(cudaStream_t s, const int32_t* list, int n, const void* fin, void* fout,
+                          const int32_t* nbr, const StepParams& prm) {
+    using BT = BulkTile<D, Q, T, THREADS>;
+    const int g = bulk_grid[THREADS == 512 ? 1 : 0][STAGES - 2];
+    if (g <= 0) return false;
+    const int n_tiles = (n + BT::TB - 1) / BT::TB;
+    k_collide_stream_bulk<D, Q, T, THREADS, STAGES>
+        <<<std::min(n_tiles, g), THREADS, BT::smem(STAGES), s>>>(list, n, (const T*)fin,
+                                                                (T*)fout, nbr, prm);
+    return true;
   }
 
   template <bool SOLID, int STAGES>
@@ -1016,28 +1234,46 @@ struct Launch {
       }
       return;
     }
+    // bulk-copy staged persistent kernel (no solid cells): 8 / 9 / 10: 512
+    // threads, 2 / 3 / 4 stages; 11 / 12 / 13: 256 threads, 2 / 3 / 4 stages
+    if (!sol && prm.variant >= 8 && prm.variant <= 13) {
+      bool done = false;
+      switch (prm.variant) {
+        case 8: done = launch_bulk<512, 2>(s, list, n, fin, fout, nbr, prm); break;
+        case 9: done = launch_bulk<512, 3>(s, list, n, fin, fout, nbr, prm); break;
+        case 10: done = launch_bulk<512, 4>(s, list, n, fin, fout, nbr, prm); break;
+        case 11: done = launch_bulk<256, 2>(s, list, n, fin, fout, nbr, prm); break;
+        case 12: done = launch_bulk<256, 3>(s, list, n, fin, fout, nbr, prm); break;
+        default: done = launch_bulk<256, 4>(s, list, n, fin, fout, nbr, prm); break;
+      }
+      if (done) return;
+    }
     // one-pass kernel: 1: 512 threads, table in shared memory; 4: 256 threads,
     // shared; 5: 256 threads, table read through L1; 6 and 0 (auto, the fastest
-    // on the 256^3 forest): 512 threads, table through L1
+    // on the 256^3 forest): 512 threads, table through L1; 7: as 6 with 512
+    // more resident threads per SM (tighter register budget)
     const int v = prm.variant;
     if (sol) {
       if (v == 1) one_pass<true, 512, true>(s, list, n, fin, fout, nbr, sm, prm);
       else if (v == 4) one_pass<true, 256, true>(s, list, n, fin, fout, nbr, sm, prm);
       else if (v == 5) one_pass<true, 256, false>(s, list, n, fin, fout, nbr, sm, prm);
+      else if (v == 7) one_pass<true, 512, false, true>(s, list, n, fin, fout, nbr, sm, prm);
       else one_pass<true, 512, false>(s, list, n, fin, fout, nbr, sm, prm);
     } else {
       if (v == 1) one_pass<false, 512, true>(s, list, n, fin, fout, nbr, sm, prm);
       else if (v == 4) one_pass<false, 256, true>(s, list, n, fin, fout, nbr, sm, prm);
       else if (v == 5) one_pass<false, 256, false>(s, list, n, fin, fout, nbr, sm, prm);
+      else if (v == 7) one_pass<false, 512, false, true>(s, list, n, fin, fout, nbr, sm, prm);
       else one_pass<false, 512, false>(s, list, n, fin, fout, nbr, sm, prm);
     }
   }
 
-  template <bool SOLID, int THREADS, bool TAB_SMEM>
+  template <bool SOLID, int THREADS, bool TAB_SMEM, bool DENSE = false>
   static void one_pass(cudaStream_t s, const int32_t* list, int n, const void* fin, void* fout,
                        const int32_t* nbr, const uint64_t* sm, const StepParams& prm) {
-    k_collide_stream<D, Q, T, SOLID, THREADS, TAB_SMEM><<<grid_for(n, THREADS / M), THREADS, 0, s>>>(
-        list, n, (const T*)fin, (T*)fout, nbr, sm, prm);
+    k_collide_stream<D, Q, T, SOLID, THREADS, TAB_SMEM, DENSE>
+        <<<grid_for(n, THREADS / M), THREADS, 0, s>>>(list, n, (const T*)fin, (T*)fout, nbr, sm,
+                                                      prm);
   }
   static void interp(cudaStream_t s, const int32_t* list, int n, const void* fpar, void* fch,
                      size_t stride, const int32_t* child0, const uint64_t* nm, const uint64_t* sm,

@@ -37,6 +37,7 @@ struct StepParams {
   double omega;         // 1 / tau_L
   int variant;          // collide-stream kernel variant (amr_config.kernel_variant)
   FaceParams faces;
+  int32_t* wait_flag;   // device int set to 1 by a kernel whose bounded wait gave up
 };
 
 struct LbmOps {

@@ -172,12 +172,16 @@ static inline int blocks_for(int64_t n, int t = 256) {
 // ============================================================== root grid
 // Root blocks b = bx + nbx (by + nby bz) at 4 * (bx, by, bz); neighbours by
 // position with periodic wrap, else the wall code of the crossed faces.
+// id_of_pos / pos_of_id: the root numbering (root ID of a lexicographic
+// position and its inverse), or null for the lexicographic numbering.
 template <int D>
 __global__ void k_init_root(int64_t cap, int n_root, int nbx, int nby, int nbz,
                             unsigned periodic, const int32_t* __restrict__ wall_code,
-                            int32_t* level, int32_t* status, int32_t* child0, int32_t* parent,
-                            float* X, int32_t* nbr, uint32_t* nonemask, uint64_t* cellmask,
-                            int32_t* gap, int32_t* idset0) {
+                            const int32_t* __restrict__ id_of_pos,
+                            const int32_t* __restrict__ pos_of_id, int32_t* level,
+                            int32_t* status, int32_t* child0, int32_t* parent, float* X,
+                            int32_t* nbr, uint32_t* nonemask, uint64_t* cellmask, int32_t* gap,
+                            int32_t* idset0) {
   using NV = typename Nbr<D>::V;
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= cap) return;
@@ -197,7 +201,9 @@ __global__ void k_init_root(int64_t cap, int n_root, int nbx, int nby, int nbz,
   idset0[b] = (int32_t)b;
   level[b] = 0;
   status[b] = ST_UNREFINED;
-  const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((int64_t)nbx * nby));
+  const int64_t pos = pos_of_id ? pos_of_id[b] : b;
+  const int bx = (int)(pos % nbx), by = (int)((pos / nbx) % nby),
+            bz = (int)(pos / ((int64_t)nbx * nby));
   X[3 * b] = 4.f * bx;
   X[3 * b + 1] = 4.f * by;
   X[3 * b + 2] = D == 3 ? 4.f * bz : 0.f;
@@ -216,8 +222,8 @@ __global__ void k_init_root(int64_t cap, int n_root, int nbx, int nby, int nbz,
         }
       }
     }
-    row[P] = crossed ? wall_code[crossed]
-                     : (int32_t)(pos[0] + nbx * (pos[1] + (int64_t)nby * (D == 3 ? pos[2] : 0)));
+    const int64_t npos = pos[0] + nbx * (pos[1] + (int64_t)nby * (D == 3 ? pos[2] : 0));
+    row[P] = crossed ? wall_code[crossed] : (id_of_pos ? id_of_pos[npos] : (int32_t)npos);
   });
 }
 
@@ -528,10 +534,23 @@ static int init_root_t(Instance* a) {
   unsigned periodic = 0;
   for (int ax = 0; ax < D; ++ax)
     if (a->cfg.faces[2 * ax].kind == AMR_FACE_PERIODIC) periodic |= 1u << ax;
+  const int32_t *id_of_pos = nullptr, *pos_of_id = nullptr;
+  if (a->cfg.root_ids) {
+    // both directions of the numbering, staged in the adaptation scratch lists
+    std::vector<int32_t> inv((size_t)a->n_root);
+    for (int64_t i = 0; i < a->n_root; ++i) inv[(size_t)a->cfg.root_ids[i]] = (int32_t)i;
+    AMR_CUDA(cudaMemcpyAsync(a->tmp0, a->cfg.root_ids, sizeof(int32_t) * a->n_root,
+                             cudaMemcpyHostToDevice, s));
+    AMR_CUDA(cudaMemcpyAsync(a->tmp1, inv.data(), sizeof(int32_t) * a->n_root,
+                             cudaMemcpyHostToDevice, s));
+    AMR_CUDA(cudaStreamSynchronize(s));   // inv is a host temporary
+    id_of_pos = a->tmp0;
+    pos_of_id = a->tmp1;
+  }
   k_init_root<D><<<blocks_for(a->cap), 256, 0, s>>>(
       a->cap, (int)a->n_root, a->nroot[0], a->nroot[1], a->nroot[2], periodic, a->wall_code,
-      a->level, a->status, a->child0, a->parent, a->X, a->nbr, a->nonemask, a->cellmask, a->gap,
-      a->idset);
+      id_of_pos, pos_of_id, a->level, a->status, a->child0, a->parent, a->X, a->nbr, a->nonemask,
+      a->cellmask, a->gap, a->idset);
   AMR_CUDA(cudaGetLastError());
   AMR_CUDA(cudaMemsetAsync(a->solidmask, 0, sizeof(uint64_t) * a->cap, s));
   if (a->solid) {
@@ -549,6 +568,36 @@ static int init_root_t(Instance* a) {
 
 int mesh_init_root(Instance* a) { return a->dim == 2 ? init_root_t<2>(a) : init_root_t<3>(a); }
 
+// Per parent of a level's exchange list: how many of its children hold ghost
+// cells, and the ghost and interface cells of its children (popcounts of the
+// children's cell masks), summed into out[0..2].
+__global__ void __launch_bounds__(256)
+    k_exchange_cells(const int32_t* __restrict__ parents, int n,
+                     const int32_t* __restrict__ child0, const uint64_t* __restrict__ cellmask,
+                     int nc, unsigned long long* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long kids = 0, ghost = 0, iface = 0;
+  if (i < n) {
+    const int c0 = child0[parents[i]];
+    for (int c = 0; c < nc; ++c) {
+      const uint64_t g = cellmask[2 * (size_t)(c0 + c)];
+      kids += g != 0ull;
+      ghost += __popcll(g);
+      iface += __popcll(cellmask[2 * (size_t)(c0 + c) + 1]);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    kids += __shfl_down_sync(0xffffffffu, kids, o);
+    ghost += __shfl_down_sync(0xffffffffu, ghost, o);
+    iface += __shfl_down_sync(0xffffffffu, iface, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (kids | ghost | iface)) {
+    atomicAdd(out, kids);
+    atomicAdd(out + 1, ghost);
+    atomicAdd(out + 2, iface);
+  }
+}
+
 int mesh_refresh_lists(Instance* a) {
   for (int L = 0; L < a->lmax; ++L) {
     int32_t* ids = a->idset + (size_t)L * a->cap;
@@ -558,6 +607,26 @@ int mesh_refresh_lists(Instance* a) {
     AMR_TRY(compact(a, n, act, VList{ids}, a->active + (size_t)L * a->cap, &a->n_active[L]));
     AMR_TRY(compact(a, n, par, VList{ids}, a->parents + (size_t)L * a->cap, &a->n_parents[L]));
     AMR_TRY(compact(a, n, PLeaf{ids, a->status}, VIdent{}, nullptr, &a->n_leaves[L], 0, false));
+  }
+  // exchange work per level, for the profile's algorithmic bytes
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(a->red);
+  AMR_CUDA(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long) * a->lmax, a->stream));
+  for (int L = 0; L + 1 < a->lmax; ++L) {
+    if (a->n_parents[L] == 0) continue;
+    k_exchange_cells<<<blocks_for(a->n_parents[L]), 256, 0, a->stream>>>(
+        a->parents + (size_t)L * a->cap, (int)a->n_parents[L], a->child0, a->cellmask, a->nc,
+        cnt + 3 * L);
+    a->launches += 1;
+  }
+  AMR_CUDA(cudaGetLastError());
+  unsigned long long h[3 * AMR_MAX_LEVELS] = {};
+  AMR_CUDA(cudaMemcpyAsync(h, cnt, 3 * sizeof(unsigned long long) * a->lmax,
+                           cudaMemcpyDeviceToHost, a->stream));
+  AMR_CUDA(cudaStreamSynchronize(a->stream));
+  for (int L = 0; L < a->lmax; ++L) {
+    a->n_ghost_children[L] = (int64_t)h[3 * L];
+    a->n_ghost_cells[L] = (int64_t)h[3 * L + 1];
+    a->n_iface_cells[L] = (int64_t)h[3 * L + 2];
   }
   return AMR_OK;
 }

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_config_struct_layout_matches_header(lib):
     from paper_2308_08085_gb300.amr import AmrAdaptStats, AmrConfig, AmrKernelProfile
-    assert ctypes.sizeof(AmrConfig) == 360
+    assert ctypes.sizeof(AmrConfig) == 376
     assert ctypes.sizeof(AmrAdaptStats) == 56
     assert ctypes.sizeof(AmrKernelProfile) == 64
 

@@ -64,12 +64,14 @@ SINGLE = [
 ]
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", list(range(1, 14)))
 @pytest.mark.parametrize("name,mk,storages", SINGLE, ids=[c[0] for c in SINGLE])
 def test_single_level_collide_stream(name, mk, storages, variant):
     """Every collide-stream kernel variant: one-pass with 512 / 256 threads and
-    the push table in shared memory or read through L1 (1, 4, 5, 6), and the
-    pipelined persistent kernel with 2 / 3 cp.async stages (2, 3)."""
+    the push table in shared memory or read through L1 (1, 4, 5, 6, 7), the
+    pipelined persistent kernel with 2 / 3 cp.async stages (2, 3), and the
+    persistent kernel staged by bulk asynchronous copies with 512 / 256
+    threads and 2 to 4 stages (8 to 13; prism cases use the one-pass kernel)."""
     for storage in storages:
         cfg = mk()
         ref = ForestLBM(cfg)
@@ -87,12 +89,24 @@ def test_single_level_collide_stream(name, mk, storages, variant):
 
 
 # ----------------------------------------------------------- mesh tables
+def with_roots(cfg, ids):
+    cfg = dict(cfg)
+    cfg["root_ids"] = ids(cfg)
+    return cfg
+
+
 MESHES = [
     ("2d_cavity_3x3", lambda: W.cavity(dim=2, n=12, max_levels=4, max_blocks=9 * 40)),
     ("2d_periodic_2x3", lambda: W.periodic_box(dim=2, n=8, ny=12, max_levels=3, max_blocks=200)),
     ("3d_cavity_2x2x2", lambda: W.cavity(dim=3, n=8, max_levels=3, max_blocks=8 * 30)),
     ("3d_periodic_3x2x2", lambda: W.periodic_box(dim=3, n=12, ny=8, nz=8, max_levels=3,
                                                  max_blocks=12 * 25)),
+    ("2d_cavity_4x3_shuffled", lambda: with_roots(
+        W.cavity(dim=2, n=16, ny=12, max_levels=3, max_blocks=12 * 20),
+        lambda c: W.shuffled_root_ids(c, 5))),
+    ("3d_periodic_3x2x2_morton", lambda: with_roots(
+        W.periodic_box(dim=3, n=12, ny=8, nz=8, max_levels=3, max_blocks=12 * 25),
+        W.morton_root_ids)),
 ]
 
 
@@ -211,7 +225,8 @@ def test_three_level_step_2d(storage):
 
 
 @pytest.mark.parametrize("q,storage,variant", [(19, "f64", 1), (19, "f32", 1), (27, "f64", 1),
-                                               (19, "f32", 2), (27, "f32", 3)])
+                                               (19, "f32", 2), (27, "f32", 3), (19, "f32", 8),
+                                               (19, "f64", 9), (27, "f32", 10), (19, "f32", 13)])
 def test_two_level_step_3d(q, storage, variant):
     cfg = W.cavity(dim=3, q=q, n=12, ny=8, nz=8, max_levels=3, max_blocks=12 * 40)
     sel = leaves_where(lambda m, b: m.X[b][2] >= 4 and m.X[b][0] >= 4)
@@ -265,6 +280,22 @@ def test_cavity2d_criterion_end_to_end_f64():
 
 def test_cavity3d_criterion_end_to_end_f64():
     cfg = W.cavity(dim=3, q=19, n=16, re=100.0, max_levels=3, max_blocks=64 * 20)
+    ref, gpu = run_pair(cfg, "f64", 60, 20)
+    compare_tables(gpu, ref.mesh)
+    assert sum(ref.mesh.counts()[1:]) > 0
+    ref.sync()
+    gpu.rho_u()
+    ids = ref.mesh.active_ids()
+    assert rel_l2(gpu.populations()[ids], ref.f[ids]) <= 1e-12
+    gpu.close()
+
+
+def test_shuffled_roots_criterion_end_to_end_f64():
+    """Root blocks numbered by a seeded permutation (block IDs no longer follow
+    space): tables bit-exact and fields within 1e-12 through criterion-driven
+    adaptation."""
+    cfg = with_roots(W.cavity(dim=3, q=19, n=16, re=100.0, max_levels=3, max_blocks=64 * 20),
+                     lambda c: W.shuffled_root_ids(c, 17))
     ref, gpu = run_pair(cfg, "f64", 60, 20)
     compare_tables(gpu, ref.mesh)
     assert sum(ref.mesh.counts()[1:]) > 0

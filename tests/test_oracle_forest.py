@@ -198,10 +198,22 @@ def geometric_nbr(mesh: Forest, b):
     return out
 
 
+def with_roots(cfg, ids):
+    cfg = dict(cfg)
+    cfg["root_ids"] = ids(cfg)
+    return cfg
+
+
 MESHES = [
     ("2d_cavity_3x3", lambda: W.cavity(dim=2, n=12, max_levels=4, max_blocks=9 * 40)),
     ("2d_periodic_2x3", lambda: W.periodic_box(dim=2, n=8, ny=12, max_levels=3, max_blocks=200)),
     ("3d_cavity_2x2x2", lambda: W.cavity(dim=3, n=8, max_levels=3, max_blocks=8 * 30)),
+    ("2d_cavity_4x3_shuffled", lambda: with_roots(
+        W.cavity(dim=2, n=16, ny=12, max_levels=3, max_blocks=12 * 20),
+        lambda c: W.shuffled_root_ids(c, 5))),
+    ("3d_periodic_3x2x2_morton", lambda: with_roots(
+        W.periodic_box(dim=3, n=12, ny=8, nz=8, max_levels=3, max_blocks=12 * 25),
+        W.morton_root_ids)),
 ]
 
 
@@ -540,3 +552,55 @@ def test_frozen_blocks_are_never_coarsened():
     res = mesh.adapt(m)
     assert res["n_coarsened"] == 1 and mesh.status[0] == 4 and mesh.status[1] == UNREFINED
     brute_force_check(mesh)
+
+
+# ------------------------------------------------------- root numbering
+def test_morton_root_ids_follow_the_z_curve():
+    cfg = W.periodic_box(dim=3, n=16, max_levels=1)
+    ids = W.morton_root_ids(cfg)
+    assert sorted(ids.tolist()) == list(range(64))
+    pos = W.root_positions(cfg)
+    by_id = pos[np.argsort(ids)]                      # position of ID 0, 1, ...
+    # each aligned group of 8 IDs is a 2x2x2 cube, each of 64 a 4x4x4 cube
+    for g in range(8):
+        cube = by_id[8 * g:8 * g + 8]
+        assert np.all(cube.max(0) - cube.min(0) == 1)
+    assert np.array_equal(by_id[:8].min(0), [0, 0, 0])
+    assert np.array_equal(by_id[1], [1, 0, 0]) and np.array_equal(by_id[2], [0, 1, 0])
+    assert np.array_equal(by_id[4], [0, 0, 1])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_root_numbering_is_a_relabelling(dim):
+    """Fields of a two-level forest with shuffled root IDs equal, position by
+    position and bit for bit, those of the lexicographic numbering."""
+    base = (W.cavity(dim=2, q=9, n=16, ny=12, max_levels=2, max_blocks=12 * 6) if dim == 2 else
+            W.cavity(dim=3, q=19, n=12, ny=8, nz=8, max_levels=2, max_blocks=12 * 10))
+    runs, roots = [], []
+    for ids in (None, W.shuffled_root_ids(base, 11)):
+        cfg = dict(base)
+        if ids is not None:
+            cfg["root_ids"] = ids
+        lbm = ForestLBM(cfg)
+        m = np.zeros(cfg["max_blocks"], np.int8)
+        for b in range(lbm.mesh.n_root):                  # refine by position
+            if lbm.mesh.X[b][0] >= 4 and lbm.mesh.X[b][1] >= 4:
+                m[b] = 1
+        lbm.adapt(m)
+        # the same state, a function of the cell position
+        for b in lbm.mesh.active_ids():
+            x = lbm.cell_centres(b)
+            rho = 1.0 + 0.01 * np.sin(0.7 * x[:, 0]) * np.cos(0.4 * x[:, 1])
+            u = 0.02 * np.stack([np.sin(0.3 * x[:, (a + 1) % dim] + a) for a in range(dim)], 1)
+            lbm.f[b] = equilibrium(lbm.vs, rho, u)
+        lbm.step(3)
+        out = {}
+        for b in lbm.mesh.active_ids():
+            key = tuple(np.round(lbm.mesh.X[b] * 8).astype(np.int64)) + (int(lbm.mesh.level[b]),)
+            out[key] = lbm.f[b].copy()
+        runs.append(out)
+        roots.append(lbm.mesh.X[:lbm.mesh.n_root].copy())
+    assert not np.array_equal(roots[0], roots[1])          # the IDs did move
+    assert runs[0].keys() == runs[1].keys() and len(runs[0]) > 0
+    for k in runs[0]:
+        assert np.array_equal(runs[0][k], runs[1][k]), k

@@ -133,6 +133,52 @@ def random_marks(seed, n, p_refine=0.3, p_coarsen=0.3):
     return m
 
 
+def slab_marks(level, status, corner_z, lvl, width, centre, half, p_extra, seed):
+    """Seeded refinement marks for a layered mesh: every leaf (status 1) of
+    level `lvl` whose block centre lies within `half` (root-cell units) of the
+    plane z = centre, plus each other leaf of that level with probability
+    `p_extra`.  Inputs are per-ID tables (level, status, corner z) of equal
+    length; `width` is the block width of level `lvl`."""
+    level, status = np.asarray(level), np.asarray(status)
+    zc = np.asarray(corner_z, np.float64) + 0.5 * width
+    leaf = (level == lvl) & (status == 1)
+    x = rng(seed).random(len(level))
+    m = np.zeros(len(level), dtype=np.int8)
+    m[leaf & ((np.abs(zc - centre) < half) | (x < p_extra))] = 1
+    return m
+
+
+def root_positions(cfg):
+    """Integer positions (bx, by[, bz]) of the root blocks in x-fastest order."""
+    d = cfg["dim"]
+    n = [cfg["nx"] // 4, cfg["ny"] // 4] + ([cfg["nz"] // 4] if d == 3 else [])
+    idx = np.arange(int(np.prod(n)))
+    pos = [idx % n[0], (idx // n[0]) % n[1]]
+    if d == 3:
+        pos.append(idx // (n[0] * n[1]))
+    return np.stack(pos, axis=1)
+
+
+def morton_root_ids(cfg):
+    """root_ids numbering the root blocks along the Morton (Z-order) curve:
+    the ID of the root at x-fastest position i is its rank in bit-interleaved
+    order of (bx, by[, bz])."""
+    pos = root_positions(cfg)
+    key = np.zeros(len(pos), np.int64)
+    for bit in range(21):
+        for ax in range(pos.shape[1]):
+            key |= ((pos[:, ax] >> bit) & 1).astype(np.int64) << (bit * pos.shape[1] + ax)
+    ids = np.empty(len(pos), np.int32)
+    ids[np.argsort(key, kind="stable")] = np.arange(len(pos), dtype=np.int32)
+    return ids
+
+
+def shuffled_root_ids(cfg, seed):
+    """root_ids of a seeded random numbering of the root blocks."""
+    n = len(root_positions(cfg))
+    return rng(seed).permutation(n).astype(np.int32)
+
+
 # ------------------------------------------------------- named configurations
 
 def config_c0():
