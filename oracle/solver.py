@@ -22,6 +22,15 @@ Readings of the paper (where it is silent or garbled)
   bilinear / trilinear polynomial over the 2^dim parent cells of the child's
   quadrant is used, child cell I at local coordinate -1/4 + I/2 (cells at
   -1/4 and 5/4 are extrapolated).
+* Cubic interpolation (Section 3.4.2): the polynomial with exponents 0..3 in
+  each direction through all 4^dim rescaled parent cells, on the unit
+  square / cube spanned by the parent's corner cell centres (parent cell m at
+  m/3); child c's cell I at -1/12 + I/6 + c_d 2/3.  The coefficients come from
+  the inverted Vandermonde matrix of the 4^dim sampling points, as the paper
+  describes; the same interpolant then writes the ghost cells (normal step,
+  synchronisation) and every cell of new children.  The printed upper limit
+  of the k sum (3^(N_d - 2)) is read as 3 in 3D and as the single term k = 0
+  in 2D.
 * Averaging: K' = mod(l/16, 2) (the printed mod((l/16)/2, 2) is garbled); the
   sum runs over the N_c children of a parent cell.
 * Normal step: interpolation writes the ghost cells of level L+1 from level L
@@ -49,6 +58,8 @@ Readings of the paper (where it is silent or garbled)
 * Solid cells always hold the rest equilibrium: they are not collided,
   streamed, interpolated into or averaged into.
 """
+from fractions import Fraction
+
 import numpy as np
 
 from .forest import (BLOCK_EDGE, GHOST, INTERFACE, NONE, REFINED, UNREFINED,
@@ -192,6 +203,31 @@ class ForestLBM:
                            + a_xz * X * Z + a_xyz * X * Y * Z)
         return W
 
+    def _cubic_weights(self):
+        """W[c][cell, V]: weight of parent cell V for cell `cell` of child c
+        under cubic interpolation.  Sampling point U = (m, n[, l]) sits at
+        (m/3, n/3[, l/3]); A[U, V] = x^i y^j [z^k] for V = (i, j[, k]); the
+        coefficients are alpha = A^-1 F and the child value sum_V alpha_V
+        x^i y^j [z^k] at x_local = -1/12 + I/6 + c_d 2/3."""
+        d, m = self.dim, self.m
+        lc = [[int(v) for v in row] for row in self.lc]          # (i, j, k) of V, (m, n, l) of U
+        # the Vandermonde matrix is ill-conditioned (about 1e6 in 3D): it is
+        # inverted in exact rational arithmetic, then the weights are rounded
+        A = [[_prod(Fraction(u[a], 3) ** v[a] for a in range(d)) for v in lc] for u in lc]
+        Ainv = _inverse(A)
+        W = []
+        for c in range(2 ** d):
+            off = [(c >> ax) & 1 for ax in range(d)]
+            x = [[Fraction(-1, 12) + Fraction(I[a], 6) + Fraction(2 * off[a], 3)
+                  for a in range(d)] for I in lc]                # child cells
+            Wc = np.empty((m, m))
+            for cell in range(m):
+                phi = [_prod(x[cell][a] ** v[a] for a in range(d)) for v in lc]
+                for U in range(m):
+                    Wc[cell, U] = float(sum(phi[V] * Ainv[V][U] for V in range(m)))
+            W.append(Wc)
+        return W
+
     def quadrant_cells(self, c):
         """Parent cell index of corner a of child quadrant c."""
         d = self.dim
@@ -203,18 +239,29 @@ class ForestLBM:
         return np.array(out, np.int64)
 
     def interpolate(self, blocks, mode):
-        """Coarse-to-fine linear interpolation into `blocks` (level >= 1):
+        """Coarse-to-fine interpolation (linear, or cubic when the
+        configuration says interp = 'cubic') into `blocks` (level >= 1):
         mode 'ghost' writes ghost cells, 'all' writes every cell."""
         mesh = self.mesh
+        cubic = self.cfg.get("interp", "linear") == "cubic"
         if not hasattr(self, "_W"):
             self._W = self._interp_weights()
+        if cubic and not hasattr(self, "_W3"):
+            if self.dim not in _CUBIC_W:
+                _CUBIC_W[self.dim] = self._cubic_weights()
+            self._W3 = _CUBIC_W[self.dim]
         for b in blocks:
             par = mesh.parent[b]
             lf = mesh.level[b]
             ratio = self.tau[lf] / (2.0 * self.tau[lf - 1])
-            corners = self.quadrant_cells(b - mesh.child0[par])
-            F = self._rescaled(self.f[par][corners], ratio)    # [2^d, Q]
-            vals = self._W @ F                                 # [M, Q]
+            c = b - mesh.child0[par]
+            if cubic:
+                F = self._rescaled(self.f[par], ratio)          # [M, Q] all parent cells
+                vals = self._W3[c] @ F                          # [M, Q]
+            else:
+                corners = self.quadrant_cells(c)
+                F = self._rescaled(self.f[par][corners], ratio)    # [2^d, Q]
+                vals = self._W @ F                                 # [M, Q]
             if mode == "ghost":
                 sel = mesh.cell_classes(b) == GHOST
             else:
@@ -429,3 +476,29 @@ class ForestLBM:
             if n >= 0 and np.any(self.solid[n]):
                 return True
         return False
+
+
+_CUBIC_W = {}   # cubic interpolation weights by dimension (exact, then rounded)
+
+
+def _prod(it):
+    out = Fraction(1)
+    for v in it:
+        out *= v
+    return out
+
+
+def _inverse(A):
+    """Inverse of a square matrix of Fractions by Gauss-Jordan elimination."""
+    n = len(A)
+    M = [list(row) + [Fraction(int(i == j)) for j in range(n)] for i, row in enumerate(A)]
+    for col in range(n):
+        piv = next(r for r in range(col, n) if M[r][col] != 0)
+        M[col], M[piv] = M[piv], M[col]
+        pv = M[col][col]
+        M[col] = [v / pv for v in M[col]]
+        for r in range(n):
+            if r != col and M[r][col] != 0:
+                f = M[r][col]
+                M[r] = [a - f * b for a, b in zip(M[r], M[col])]
+    return [row[n:] for row in M]

@@ -320,6 +320,65 @@ def two_level_lbm(cfg, refine_ids):
     return lbm
 
 
+@pytest.mark.parametrize("dim,q", [(2, 9), (3, 19)])
+def test_cubic_interpolation_exact_on_cubic_equilibria(dim, q):
+    """Cubic interpolation (Section 3.4.2) reproduces every population of an
+    equilibrium whose density and velocity are affine in space: f_eq(rho(x),
+    u(x)) has degree <= 3 in each coordinate, and rescaling leaves an
+    equilibrium unchanged.  Positions come from the forest geometry (cell
+    centres of parent and children), not from the interpolation code; linear
+    interpolation must miss the same data."""
+    errs = {}
+    for kind in ("cubic", "linear"):
+        cfg = W.periodic_box(dim=dim, q=q, n=8, max_levels=2, max_blocks=None)
+        cfg["interp"] = kind
+        lbm = ForestLBM(cfg)
+        g = np.random.default_rng(4)
+        a_rho, b_rho = 1.0, 0.01 * g.standard_normal(dim)
+        a_u, B_u = 0.02 * g.standard_normal(dim), 0.006 * g.standard_normal((dim, dim))
+
+        def state(x):
+            return equilibrium(lbm.vs, a_rho + x @ b_rho, a_u + x @ B_u.T)
+
+        par = 0
+        lbm.f[par] = state(lbm.cell_centres(par))
+        m = np.zeros(lbm.mesh.cap, np.int8)
+        m[par] = 1
+        res = lbm.mesh.adapt(m)
+        kids = res["new_children"]
+        assert len(kids) == 2 ** dim
+        lbm.interpolate(kids, "all")
+        errs[kind] = max(np.abs(lbm.f[c] - state(lbm.cell_centres(c))).max() for c in kids)
+    assert errs["cubic"] <= 1e-13, errs
+    assert errs["linear"] >= 1e-7, errs
+
+
+def test_cubic_weights_are_tensor_lagrange():
+    """The Vandermonde-inverse weights equal the product of the 1D cubic
+    Lagrange bases on the nodes 0, 1/3, 2/3, 1 (the unique interpolant in the
+    tensor-product cubic space)."""
+    lbm = ForestLBM(W.periodic_box(dim=3, q=19, n=8, max_levels=2))
+    Ws = lbm._cubic_weights()
+    nodes = np.array([0.0, 1.0, 2.0, 3.0]) / 3.0
+
+    def lag(x, mnode):
+        out = 1.0
+        for j in range(4):
+            if j != mnode:
+                out *= (x - nodes[j]) / (nodes[mnode] - nodes[j])
+        return out
+
+    for c in (0, 5, 7):
+        off = [(c >> ax) & 1 for ax in range(3)]
+        for cell in (0, 21, 63):
+            I = [cell % 4, (cell // 4) % 4, cell // 16]
+            x = [-1 / 12 + I[a] / 6 + off[a] * 2 / 3 for a in range(3)]
+            for U in (0, 17, 42, 63):
+                mm = [U % 4, (U // 4) % 4, U // 16]
+                want = lag(x[0], mm[0]) * lag(x[1], mm[1]) * lag(x[2], mm[2])
+                assert abs(Ws[c][cell, U] - want) <= 1e-14, (c, cell, U)
+
+
 def test_interpolation_preserves_equilibrium():
     cfg = W.periodic_box(dim=3, q=19, n=8, max_levels=2, nu0=0.02)
     lbm = ForestLBM(cfg)
@@ -389,8 +448,9 @@ def test_averaging_children_are_geometric():
 
 
 # ------------------------------------------------------- level stepping
-def couette_two_level(ratio_scale=None, steps=2600):
+def couette_two_level(ratio_scale=None, steps=2600, interp="linear"):
     cfg = W.cavity(dim=2, q=9, n=16, max_levels=2, max_blocks=16 + 8 * 4)
+    cfg["interp"] = interp
     cfg["faces"] = [("periodic", (0, 0, 0)), ("periodic", (0, 0, 0)),
                     ("noslip", (0, 0, 0)), ("moving", (0.05, 0.0, 0.0))]
     cfg["nu0"] = 0.25
@@ -424,10 +484,17 @@ def test_two_level_couette_linear():
     assert couette_two_level(1.0, steps=1000) > 1e-5
 
 
-def test_taylor_green_two_level():
+def test_two_level_couette_linear_cubic():
+    # cubic interpolation reproduces the linear profile as well
+    assert couette_two_level(None, interp="cubic") < 1e-10
+
+
+@pytest.mark.parametrize("interp", ["linear", "cubic"])
+def test_taylor_green_two_level(interp):
     N, tau_root = 32, 0.8
     nu0 = CS2 * (tau_root - 0.5)
     cfg = W.periodic_box(dim=2, q=9, n=N, nu0=nu0, max_levels=2, max_blocks=64 + 4 * 64)
+    cfg["interp"] = interp
     lbm = ForestLBM(cfg)
     k = 2 * np.pi / N
     U = 0.01
