@@ -28,7 +28,12 @@ Readings of the paper (where it is silent or garbled)
   m/3); child c's cell I at -1/12 + I/6 + c_d 2/3.  The coefficients come from
   the inverted Vandermonde matrix of the 4^dim sampling points, as the paper
   describes; the same interpolant then writes the ghost cells (normal step,
-  synchronisation) and every cell of new children.  The printed upper limit
+  synchronisation) and every cell of new children.  The stencil spans parent
+  cells over interior children, which the normal step leaves covered (the
+  paper does not say what they hold): with cubic interpolation the end of
+  each level step averages every parent cell whose children are not ghosts
+  (the averaging of the synchronisation) instead of only those over
+  interface children, so the stencil reads restricted fine data.  The printed upper limit
   of the k sum (3^(N_d - 2)) is read as 3 in 3D and as the single term k = 0
   in 2D.
 * Averaging: K' = mod(l/16, 2) (the printed mod((l/16)/2, 2) is garbled); the
@@ -309,7 +314,14 @@ class ForestLBM:
         if has_fine:
             self.advance(level + 1)
             self.advance(level + 1)
-            self.average(mesh.boundary_children(level + 1), "interface")
+            if self.cfg.get("interp", "linear") == "cubic":
+                # the cubic stencil is the whole parent block: its cells over
+                # interior children are averaged too
+                kids = [mesh.child0[p] + c for p in mesh.parent_list(level)
+                        for c in range(mesh.nc)]
+                self.average(kids, "sync")
+            else:
+                self.average(mesh.boundary_children(level + 1), "interface")
 
     def step(self, n=1):
         for _ in range(n):

@@ -41,6 +41,11 @@ struct Instance {
   float* features = nullptr;       // [cap][27] block summaries
   float* prob = nullptr;           // [cap] proposal probabilities
   int32_t *idset = nullptr, *active = nullptr, *parents = nullptr;   // [lmax][cap]
+  // [lmax][cap]: the blocks of each level in tree order -- roots by position
+  // (x fastest), then the children of each refined block in child order; the
+  // active and parent lists are taken from it, so blocks that are neighbours
+  // in space are advanced close together in time whatever their IDs
+  int32_t* order = nullptr;
   int32_t* gap = nullptr;          // [cap]
   int8_t* marks = nullptr;         // [cap]
   double* w2 = nullptr;            // [cap] criterion block maxima
@@ -83,6 +88,8 @@ struct Instance {
   struct Acc { int64_t launches = 0; double ms = 0, bytes = 0, cells = 0; };
   Acc acc[8];
 
+  // interpolation mode bit of LbmOps::interp for this configuration
+  int interp_bits() const { return cfg.interp == AMR_INTERP_CUBIC ? 2 : 0; }
   size_t f_bytes() const { return (size_t)cap * M * q * elem; }
   size_t stride() const { return (size_t)cap * M; }
   void* fbuf(int level, int which) const {   // which: 0 current, 1 other

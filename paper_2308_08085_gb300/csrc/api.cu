@@ -139,6 +139,7 @@ static Layout layout_for(const amr_config* c) {
       (size_t)cap * 16,                        // 24 cellmask
       (size_t)cap * 27 * 4,                    // 25 features
       (size_t)cap * 4,                         // 26 proposal probabilities
+      (size_t)lmax * cap * 4,                  // 27 tree order of each level
   };
   size_t off = 0;
   int i = 0;
@@ -265,7 +266,7 @@ static void advance(Instance* a, int L) {
                  ((double)a->n_ghost_children[L] * a->nc + cells) * a->q * a->elem, cells);
     a->ops->interp(a->stream, a->parents + (size_t)L * a->cap, (int)np, a->fbuf(L, 0),
                    a->fbuf(L + 1, 0), a->stride(), a->child0, a->cellmask, a->solidmask,
-                   ratio_cf(a, L), 0, a->solid);
+                   ratio_cf(a, L), a->interp_bits(), a->solid);
     a->launches += 1;
   }
   collide_stream_level(a, L);
@@ -277,9 +278,13 @@ static void advance(Instance* a, int L) {
       // cells, one per 2^D children (written)
       const double cells = (double)a->n_iface_cells[L];
       ProfScope ps(a, PK_AVERAGE, cells * (1.0 + 1.0 / a->nc) * a->q * a->elem, cells);
+      // cubic interpolation samples every cell of the parent, so with it the
+      // parent cells over interior children are averaged as well (mode 1:
+      // every cell whose children are not ghosts), else only those over
+      // interface children (mode 0)
       a->ops->average(a->stream, a->parents + (size_t)L * a->cap, (int)np, a->fbuf(L, 0),
                       a->fbuf(L + 1, 0), a->stride(), a->child0, a->cellmask, a->status,
-                      a->solidmask, ratio_fc(a, L), 0, a->solid);
+                      a->solidmask, ratio_fc(a, L), a->interp_bits() ? 1 : 0, a->solid);
       a->launches += 1;
     }
   }
@@ -355,7 +360,7 @@ static void level_sync(Instance* a) {
     if (a->n_parents[L] == 0) continue;
     a->ops->interp(a->stream, a->parents + (size_t)L * a->cap, (int)a->n_parents[L],
                    a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0, a->cellmask,
-                   a->solidmask, ratio_cf(a, L), 0, a->solid);
+                   a->solidmask, ratio_cf(a, L), a->interp_bits(), a->solid);
     a->launches += 1;
   }
 }
@@ -531,6 +536,7 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
   a->cellmask = (uint64_t*)(base + L.off[i++]);
   a->features = (float*)(base + L.off[i++]);
   a->prob = (float*)(base + L.off[i++]);
+  a->order = (int32_t*)(base + L.off[i++]);
 
   const double tau0 = 3.0 * cfg->nu0 + 0.5;
   for (int l = 0; l < a->lmax; ++l) a->tau[l] = 0.5 + std::ldexp(tau0 - 0.5, l);

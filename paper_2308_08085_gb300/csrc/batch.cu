@@ -221,6 +221,10 @@ int amr_batch_create(amr_t* const* instances, int n, void* dev_arena, size_t are
       set_error("batch members may not have a solid prism");
       return AMR_E_INVAL;
     }
+    if (a->cfg.interp != AMR_INTERP_LINEAR) {
+      set_error("batch members use linear interpolation");
+      return AMR_E_INVAL;
+    }
     if (a->cap > (int64_t)BATCH_MASK) {
       set_error("batch member capacity exceeds 2^25 blocks");
       return AMR_E_INVAL;

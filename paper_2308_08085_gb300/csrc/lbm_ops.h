@@ -49,9 +49,11 @@ struct LbmOps {
                          const int32_t* nbr, const uint64_t* solidmask, const StepParams& prm,
                          bool solid);
   // coarse-to-fine linear interpolation: parents in `list`, into their children
+  // (mode bit 0: every cell of the children, else their ghost cells; bit 1:
+  // cubic instead of linear interpolation)
   void (*interp)(cudaStream_t, const int32_t* list, int n, const void* fpar, void* fch,
                  size_t stride, const int32_t* child0, const uint64_t* cellmask,
-                 const uint64_t* solidmask, double ratio, int mode_all, bool solid);
+                 const uint64_t* solidmask, double ratio, int mode, bool solid);
   // fine-to-coarse averaging into the parents in `list`
   void (*average)(cudaStream_t, const int32_t* list, int n, void* fpar, const void* fch,
                   size_t stride, const int32_t* child0, const uint64_t* cellmask,

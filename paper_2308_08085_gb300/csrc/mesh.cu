@@ -107,6 +107,11 @@ struct PAlive {
   const int32_t* status;
   __device__ bool operator()(int i) const { return status[list[i]] != ST_INACTIVE; }
 };
+struct PHasKids {
+  const int32_t* list;
+  const int32_t* child0;
+  __device__ bool operator()(int i) const { return child0[list[i]] >= 0; }
+};
 struct PLeaf {
   const int32_t* list;
   const int32_t* status;
@@ -181,7 +186,7 @@ __global__ void k_init_root(int64_t cap, int n_root, int nbx, int nby, int nbz,
                             const int32_t* __restrict__ pos_of_id, int32_t* level,
                             int32_t* status, int32_t* child0, int32_t* parent, float* X,
                             int32_t* nbr, uint32_t* nonemask, uint64_t* cellmask, int32_t* gap,
-                            int32_t* idset0) {
+                            int32_t* idset0, int32_t* order0) {
   using NV = typename Nbr<D>::V;
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= cap) return;
@@ -202,6 +207,7 @@ __global__ void k_init_root(int64_t cap, int n_root, int nbx, int nby, int nbz,
   level[b] = 0;
   status[b] = ST_UNREFINED;
   const int64_t pos = pos_of_id ? pos_of_id[b] : b;
+  order0[pos] = (int32_t)b;
   const int bx = (int)(pos % nbx), by = (int)((pos / nbx) % nby),
             bz = (int)(pos / ((int64_t)nbx * nby));
   X[3 * b] = 4.f * bx;
@@ -550,7 +556,7 @@ static int init_root_t(Instance* a) {
   k_init_root<D><<<blocks_for(a->cap), 256, 0, s>>>(
       a->cap, (int)a->n_root, a->nroot[0], a->nroot[1], a->nroot[2], periodic, a->wall_code,
       id_of_pos, pos_of_id, a->level, a->status, a->child0, a->parent, a->X, a->nbr, a->nonemask,
-      a->cellmask, a->gap, a->idset);
+      a->cellmask, a->gap, a->idset, a->order);
   AMR_CUDA(cudaGetLastError());
   AMR_CUDA(cudaMemsetAsync(a->solidmask, 0, sizeof(uint64_t) * a->cap, s));
   if (a->solid) {
@@ -600,13 +606,35 @@ __global__ void __launch_bounds__(256)
 
 int mesh_refresh_lists(Instance* a) {
   for (int L = 0; L < a->lmax; ++L) {
-    int32_t* ids = a->idset + (size_t)L * a->cap;
+    int32_t* ord = a->order + (size_t)L * a->cap;
     const int64_t n = a->n_ids[L];
-    PActive act{ids, a->status, a->child0, a->nonemask, a->nc, false};
-    PActive par{ids, a->status, a->child0, a->nonemask, a->nc, true};
-    AMR_TRY(compact(a, n, act, VList{ids}, a->active + (size_t)L * a->cap, &a->n_active[L]));
-    AMR_TRY(compact(a, n, par, VList{ids}, a->parents + (size_t)L * a->cap, &a->n_parents[L]));
-    AMR_TRY(compact(a, n, PLeaf{ids, a->status}, VIdent{}, nullptr, &a->n_leaves[L], 0, false));
+    if (L > 0) {
+      // tree order of level L: the children of the refined blocks of level
+      // L-1, taken in that level's tree order (roots were placed at init)
+      const int32_t* up = a->order + (size_t)(L - 1) * a->cap;
+      int64_t n_ref = 0;
+      AMR_TRY(compact(a, a->n_ids[L - 1], PHasKids{up, a->child0}, VList{up}, a->tmp2, &n_ref));
+      if (n_ref * a->nc != n) {
+        set_error("tree order: the children of level " + std::to_string(L - 1) +
+                  " do not match the ID set of level " + std::to_string(L));
+        return AMR_E_CUDA;
+      }
+      if (n_ref > 0) {
+        if (a->dim == 2)
+          k_append_children<2><<<blocks_for(n), 256, 0, a->stream>>>(a->tmp2, (int)n_ref,
+                                                                       a->child0, ord);
+        else
+          k_append_children<3><<<blocks_for(n), 256, 0, a->stream>>>(a->tmp2, (int)n_ref,
+                                                                       a->child0, ord);
+        a->launches += 1;
+        AMR_CUDA(cudaGetLastError());
+      }
+    }
+    PActive act{ord, a->status, a->child0, a->nonemask, a->nc, false};
+    PActive par{ord, a->status, a->child0, a->nonemask, a->nc, true};
+    AMR_TRY(compact(a, n, act, VList{ord}, a->active + (size_t)L * a->cap, &a->n_active[L]));
+    AMR_TRY(compact(a, n, par, VList{ord}, a->parents + (size_t)L * a->cap, &a->n_parents[L]));
+    AMR_TRY(compact(a, n, PLeaf{ord, a->status}, VIdent{}, nullptr, &a->n_leaves[L], 0, false));
   }
   // exchange work per level, for the profile's algorithmic bytes
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(a->red);
@@ -751,7 +779,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     AMR_CUDA(cudaGetLastError());
     const double ratio = a->tau[L + 1] / (2.0 * a->tau[L]);
     a->ops->interp(s, C + offR[L], (int)nRL[L], a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(),
-                   a->child0, a->cellmask, a->solidmask, ratio, 1, a->solid);
+                   a->child0, a->cellmask, a->solidmask, ratio, 1 | a->interp_bits(), a->solid);
     a->launches += 1;
     AMR_CUDA(cudaGetLastError());
   }

@@ -115,3 +115,14 @@ def test_batch_member_matches_oracle_and_autotune():
     assert err <= 1e-12, err
     assert batch.launches() > 0
     batch.close()
+
+
+def test_batch_rejects_cubic_members():
+    from paper_2308_08085_gb300 import AmrBatch, AmrLBM
+    from paper_2308_08085_gb300.amr import AmrError
+    cfg = W.cavity(dim=3, q=19, n=8, max_levels=2, max_blocks=8 * 12)
+    cfg["interp"] = "cubic"
+    m = AmrLBM(cfg, storage="f32")
+    with pytest.raises(AmrError):
+        AmrBatch([m])
+    m.close()

@@ -229,6 +229,10 @@ def test_three_level_step_2d(storage):
                                                (19, "f64", 9), (27, "f32", 10), (19, "f32", 13)])
 def test_two_level_step_3d(q, storage, variant):
     cfg = W.cavity(dim=3, q=q, n=12, ny=8, nz=8, max_levels=3, max_blocks=12 * 40)
+    two_level_case(cfg, storage, variant)
+
+
+def two_level_case(cfg, storage, variant=0):
     sel = leaves_where(lambda m, b: m.X[b][2] >= 4 and m.X[b][0] >= 4)
     ref = ForestLBM(cfg)
     gpu = new_gpu(cfg, storage, variant)
@@ -344,6 +348,50 @@ def test_cylinder_distance_rule_force_end_to_end():
     f_ref = ref.mea_force()
     f_gpu = gpu.force()
     assert abs(f_ref[0]) > 0
+    assert np.max(np.abs(f_gpu - f_ref)) <= 1e-11 * np.max(np.abs(f_ref))
+    gpu.close()
+
+
+# ------------------------------------------------- cubic interpolation
+def cubic(cfg):
+    cfg = dict(cfg)
+    cfg["interp"] = "cubic"
+    return cfg
+
+
+@pytest.mark.parametrize("q,storage", [(19, "f64"), (19, "f32"), (27, "f64")])
+def test_cubic_two_level_step_3d(q, storage):
+    """Cubic coarse-to-fine interpolation (Section 3.4.2): ghost cells of the
+    normal step, every cell of new children, and the pre-adapt sync."""
+    cfg = cubic(W.cavity(dim=3, q=q, n=12, ny=8, nz=8, max_levels=3, max_blocks=12 * 40))
+    two_level_case(cfg, storage)
+
+
+def test_cubic_criterion_end_to_end_2d_f64():
+    cfg = cubic(W.cavity(dim=2, q=9, n=32, re=100.0, max_levels=3, max_blocks=64 * 24))
+    ref, gpu = run_pair(cfg, "f64", 200, 50)
+    compare_tables(gpu, ref.mesh)
+    assert sum(ref.mesh.counts()[1:]) > 0
+    ref.step(10)
+    gpu.step(10)
+    ref.sync()
+    gpu.rho_u()
+    ids = ref.mesh.active_ids()
+    assert rel_l2(gpu.populations()[ids], ref.f[ids]) <= 1e-12
+    gpu.close()
+
+
+def test_cubic_cylinder_end_to_end_f64():
+    """Cubic interpolation next to the solid prism (solid cells are skipped)."""
+    cfg = cubic(W.channel_cylinder(q=19, nx=48, ny=24, nz=8, side=4, cx=16, cy=12, max_levels=3,
+                                   max_blocks=72 * 30, refine_dist=0.15))
+    ref, gpu = run_pair(cfg, "f64", 40, 20)
+    compare_tables(gpu, ref.mesh)
+    ref.sync()
+    gpu.rho_u()
+    ids = ref.mesh.active_ids()
+    assert rel_l2(gpu.populations()[ids], ref.f[ids]) <= 1e-12
+    f_ref, f_gpu = ref.mea_force(), gpu.force()
     assert np.max(np.abs(f_gpu - f_ref)) <= 1e-11 * np.max(np.abs(f_ref))
     gpu.close()
 
