@@ -140,6 +140,7 @@ static Layout layout_for(const amr_config* c) {
       (size_t)cap * 27 * 4,                    // 25 features
       (size_t)cap * 4,                         // 26 proposal probabilities
       (size_t)lmax * cap * 4,                  // 27 tree order of each level
+      (size_t)lmax * cap * 4,                  // 28 blocks with a NONE neighbour, per level
   };
   size_t off = 0;
   int i = 0;
@@ -282,9 +283,15 @@ static void advance(Instance* a, int L) {
       // parent cells over interior children are averaged as well (mode 1:
       // every cell whose children are not ghosts), else only those over
       // interface children (mode 0)
-      a->ops->average(a->stream, a->parents + (size_t)L * a->cap, (int)np, a->fbuf(L, 0),
-                      a->fbuf(L + 1, 0), a->stride(), a->child0, a->cellmask, a->status,
-                      a->solidmask, ratio_fc(a, L), a->interp_bits() ? 1 : 0, a->solid);
+      if (a->interp_bits())
+        a->ops->average(a->stream, a->parents + (size_t)L * a->cap, (int)np, true,
+                        a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0, a->parent,
+                        a->cellmask, a->status, a->solidmask, ratio_fc(a, L), 1, a->solid);
+      else
+        a->ops->average(a->stream, a->bnd + (size_t)(L + 1) * a->cap, (int)a->n_bnd[L + 1],
+                        false, a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0,
+                        a->parent, a->cellmask, a->status, a->solidmask, ratio_fc(a, L), 0,
+                        a->solid);
       a->launches += 1;
     }
   }
@@ -351,9 +358,9 @@ static int build_graphs(Handle* h) {
 static void level_sync(Instance* a) {
   for (int L = a->lmax - 2; L >= 0; --L) {
     if (a->n_ids[L + 1] == 0) continue;
-    a->ops->average(a->stream, a->idset + (size_t)L * a->cap, (int)a->n_ids[L], a->fbuf(L, 0),
-                    a->fbuf(L + 1, 0), a->stride(), a->child0, a->cellmask, a->status,
-                    a->solidmask, ratio_fc(a, L), 1, a->solid);
+    a->ops->average(a->stream, a->idset + (size_t)L * a->cap, (int)a->n_ids[L], true,
+                    a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0, a->parent,
+                    a->cellmask, a->status, a->solidmask, ratio_fc(a, L), 1, a->solid);
     a->launches += 1;
   }
   for (int L = 0; L + 1 < a->lmax; ++L) {
@@ -537,6 +544,7 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
   a->features = (float*)(base + L.off[i++]);
   a->prob = (float*)(base + L.off[i++]);
   a->order = (int32_t*)(base + L.off[i++]);
+  a->bnd = (int32_t*)(base + L.off[i++]);
 
   const double tau0 = 3.0 * cfg->nu0 + 0.5;
   for (int l = 0; l < a->lmax; ++l) a->tau[l] = 0.5 + std::ldexp(tau0 - 0.5, l);

@@ -224,12 +224,14 @@ __global__ void __launch_bounds__(64)
 }
 
 // ===================================================== fine-to-coarse averaging
-// One thread per parent cell: the 2^D fine children (all of one child block)
-// are rescaled to the coarse level (f_eq + (f - f_eq) r, Section 3.4.3) and
-// averaged.  mode_sync = 0 writes parent cells over interface children;
-// mode_sync = 1 writes every parent cell whose children are not ghosts.
+// Section 3.4.3.  One thread per parent cell over a child: a child covers
+// 2^D parent cells (g = gx + 2 gy [+ 4 gz]), each the mean of a 2^D group
+// of the child's fine cells, which share one class.  A group is taken when
+// its cells are interface cells (mode_sync = 0) or not ghosts
+// (mode_sync = 1); its fine cells are rescaled to the coarse level
+// (f_eq + (f - f_eq) r) and averaged.
 template <int D, int Q, class T, bool SOLID>
-__device__ __forceinline__ void average_cell(int P, int l, T* __restrict__ fpar,
+__device__ __forceinline__ void average_cell(int P, int c, int g, T* __restrict__ fpar,
                                              const T* __restrict__ fch, size_t stride, int c0,
                                              const uint64_t* __restrict__ cellmask,
                                              const uint64_t* __restrict__ solidmask,
@@ -238,23 +240,22 @@ __device__ __forceinline__ void average_cell(int P, int l, T* __restrict__ fpar,
   using R = typename S::R;
   constexpr int M = Block<D>::M;
   constexpr int NC = Block<D>::NC;
-  const int i = Block<D>::ci(l), j = Block<D>::cj(l), k = Block<D>::ck(l);
-  const int c = (i >> 1) + 2 * (j >> 1) + (D == 3 ? 4 * (k >> 1) : 0);
   const int ch = c0 + c;
-  const int fi = 2 * (i & 1), fj = 2 * (j & 1), fk = 2 * (k & 1);
-  // all 2^D children of a parent cell share one class; test the first
-  const int f0 = Block<D>::cell(fi, fj, fk);
+  const int gx = g & 1, gy = (g >> 1) & 1, gz = (g >> 2) & 1;
+  const int f0 = Block<D>::cell(2 * gx, 2 * gy, 2 * gz);
   if (!mode_sync && !((__ldg(cellmask + 2 * (size_t)ch + 1) >> f0) & 1ull)) return;
   if (mode_sync && ((__ldg(cellmask + 2 * (size_t)ch) >> f0) & 1ull)) return;
+  const int pl = Block<D>::cell(2 * (c & 1) + gx, 2 * ((c >> 1) & 1) + gy,
+                                2 * ((c >> 2) & 1) + gz);
   if constexpr (SOLID) {
-    if ((__ldg(solidmask + P) >> l) & 1ull) return;
+    if ((__ldg(solidmask + P) >> pl) & 1ull) return;
   }
   const R r = R(ratio);
   R acc[Q];
   static_for<0, Q>([&](auto Pp) { acc[Pp] = R(0); });
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
-    const int fl = Block<D>::cell(fi + (s & 1), fj + ((s >> 1) & 1), fk + ((s >> 2) & 1));
+    const int fl = f0 + Block<D>::cell(s & 1, (s >> 1) & 1, (s >> 2) & 1);
     const size_t base = (size_t)ch * M + fl;
     R f[Q];
     static_for<0, Q>([&](auto Pp) {
@@ -268,28 +269,42 @@ __device__ __forceinline__ void average_cell(int P, int l, T* __restrict__ fpar,
       acc[Pp] += e + (f[Pp] - e) * r;
     });
   }
-  const size_t base = (size_t)P * M + l;
+  const size_t base = (size_t)P * M + pl;
   const R inv = R(1) / R(NC);
   static_for<0, Q>([&](auto Pp) {
     fpar[(size_t)Pp * stride + base] = S::template save<D, Q, Pp>(acc[Pp] * inv);
   });
 }
 
+// One thread per (child, parent cell): 128 threads = 128 / 2^D children.
+// by_parent: child item i is child i % N_c of list[i / N_c]; else child item
+// i is the block list[i] (a block with a NONE neighbour: the only blocks with
+// interface cells).
 template <int D, int Q, class T, bool SOLID>
 __global__ void __launch_bounds__(128)
-    k_average(const int32_t* __restrict__ list, int n, T* __restrict__ fpar,
-              const T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
+    k_average(const int32_t* __restrict__ list, int64_t n_items, bool by_parent,
+              T* __restrict__ fpar, const T* __restrict__ fch, size_t stride,
+              const int32_t* __restrict__ child0, const int32_t* __restrict__ parent,
               const uint64_t* __restrict__ cellmask, const int32_t* __restrict__ status,
               const uint64_t* __restrict__ solidmask, double ratio, int mode_sync) {
-  constexpr int M = Block<D>::M;
-  constexpr int BPC = 128 / M;
-  const int slot = threadIdx.x / M;
-  const int l = threadIdx.x - slot * M;
-  const int bi = blockIdx.x * BPC + slot;
-  if (bi >= n) return;
-  const int P = list[bi];
-  if (mode_sync && status[P] < ST_REFINED) return;
-  average_cell<D, Q, T, SOLID>(P, l, fpar, fch, stride, child0[P], cellmask, solidmask, ratio,
+  constexpr int NC = Block<D>::NC;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t item = t / NC;
+  const int g = (int)(t % NC);
+  if (item >= n_items) return;
+  int P, c, c0;
+  if (by_parent) {
+    P = list[item / NC];
+    c = (int)(item % NC);
+    c0 = child0[P];
+    if (c0 < 0 || (mode_sync && status[P] < ST_REFINED)) return;
+  } else {
+    const int ch = list[item];
+    P = parent[ch];
+    c0 = child0[P];
+    c = ch - c0;
+  }
+  average_cell<D, Q, T, SOLID>(P, c, g, fpar, fch, stride, c0, cellmask, solidmask, ratio,
                                mode_sync);
 }
 
@@ -367,21 +382,22 @@ __global__ void __launch_bounds__(128)
                                   d.cellmask, nullptr, 0);
 }
 
+// items are parents; child item i is child i % N_c of items[i / N_c]; one
+// thread per (child, parent cell)
 template <int D, int Q, class T>
 __global__ void __launch_bounds__(128)
-    k_average_batch(const uint32_t* __restrict__ items, int n, const InstDesc* __restrict__ descs,
-                    int level, int which_par, int which_ch) {
-  constexpr int M = Block<D>::M;
-  constexpr int BPC = 128 / M;
-  const int slot = threadIdx.x / M;
-  const int l = threadIdx.x - slot * M;
-  const int bi = blockIdx.x * BPC + slot;
-  if (bi >= n) return;
-  const uint32_t it = __ldg(items + bi);
+    k_average_batch(const uint32_t* __restrict__ items, int64_t n_items,
+                    const InstDesc* __restrict__ descs, int level, int which_par, int which_ch) {
+  constexpr int NC = Block<D>::NC;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t item = t / NC;
+  if (item >= n_items) return;
+  const uint32_t it = __ldg(items + item / NC);
   const InstDesc& d = descs[it >> BATCH_SHIFT];
   const int P = (int)(it & BATCH_MASK);
-  average_cell<D, Q, T, false>(P, l, (T*)d.f[which_par], (const T*)d.f[which_ch], d.stride,
-                               d.child0[P], d.cellmask, nullptr, d.r_fc[level], 0);
+  average_cell<D, Q, T, false>(P, (int)(item % NC), (int)(t % NC), (T*)d.f[which_par],
+                               (const T*)d.f[which_ch], d.stride, d.child0[P], d.cellmask,
+                               nullptr, d.r_fc[level], 0);
 }
 
 // ================================================================ criterion
@@ -932,18 +948,21 @@ struct Launch {
       k_interp<D, Q, T, false><<<grid, 128, 0, s>>>(list, n, (const T*)fpar, (T*)fch, stride,
                                                    child0, nm, sm, ratio, all);
   }
-  static void average(cudaStream_t s, const int32_t* list, int n, void* fpar, const void* fch,
-                      size_t stride, const int32_t* child0, const uint64_t* nm,
-                      const int32_t* status, const uint64_t* sm, double ratio, int mode_sync,
-                      bool solid) {
+  static void average(cudaStream_t s, const int32_t* list, int n, bool by_parent, void* fpar,
+                      const void* fch, size_t stride, const int32_t* child0,
+                      const int32_t* parent, const uint64_t* nm, const int32_t* status,
+                      const uint64_t* sm, double ratio, int mode_sync, bool solid) {
     if (n <= 0) return;
-    const int grid = grid_for(n, 128 / M);
+    const int64_t items = by_parent ? (int64_t)n * Block<D>::NC : (int64_t)n;
+    const int grid = (int)((items * Block<D>::NC + 127) / 128);
     if (solid && D == 3)
-      k_average<D, Q, T, true><<<grid, 128, 0, s>>>(list, n, (T*)fpar, (const T*)fch, stride,
-                                                   child0, nm, status, sm, ratio, mode_sync);
+      k_average<D, Q, T, true><<<grid, 128, 0, s>>>(list, items, by_parent, (T*)fpar,
+                                                   (const T*)fch, stride, child0, parent, nm,
+                                                   status, sm, ratio, mode_sync);
     else
-      k_average<D, Q, T, false><<<grid, 128, 0, s>>>(list, n, (T*)fpar, (const T*)fch, stride,
-                                                    child0, nm, status, sm, ratio, mode_sync);
+      k_average<D, Q, T, false><<<grid, 128, 0, s>>>(list, items, by_parent, (T*)fpar,
+                                                    (const T*)fch, stride, child0, parent, nm,
+                                                    status, sm, ratio, mode_sync);
   }
   static void criterion(cudaStream_t s, const int32_t* list, int n, const void* f, size_t stride,
                         const int32_t* status, int level, int lmax, double inv_dx, int ns, int ni,
@@ -1014,8 +1033,9 @@ struct Launch {
   static void average_batch(cudaStream_t s, const uint32_t* items, int n, const InstDesc* descs,
                             int level, int which_par, int which_ch) {
     if (n <= 0) return;
-    k_average_batch<D, Q, T><<<grid_for(n, 128 / M), 128, 0, s>>>(items, n, descs, level,
-                                                                    which_par, which_ch);
+    const int64_t kids = (int64_t)n * Block<D>::NC;
+    k_average_batch<D, Q, T><<<(int)((kids * Block<D>::NC + 127) / 128), 128, 0, s>>>(
+        items, kids, descs, level, which_par, which_ch);
   }
 
   static const LbmOps* ops() {

@@ -54,11 +54,14 @@ struct LbmOps {
   void (*interp)(cudaStream_t, const int32_t* list, int n, const void* fpar, void* fch,
                  size_t stride, const int32_t* child0, const uint64_t* cellmask,
                  const uint64_t* solidmask, double ratio, int mode, bool solid);
-  // fine-to-coarse averaging into the parents in `list`
-  void (*average)(cudaStream_t, const int32_t* list, int n, void* fpar, const void* fch,
-                  size_t stride, const int32_t* child0, const uint64_t* cellmask,
-                  const int32_t* status, const uint64_t* solidmask, double ratio, int mode_sync,
-                  bool solid);
+  // fine-to-coarse averaging: by_parent -- `list` holds parents, all their
+  // children are visited; else `list` holds children (boundary blocks of the
+  // fine level) and parent[] leads to their parents.  mode 0: parent cells
+  // over interface children, 1: over every non-ghost child (refined parents)
+  void (*average)(cudaStream_t, const int32_t* list, int n, bool by_parent, void* fpar,
+                  const void* fch, size_t stride, const int32_t* child0, const int32_t* parent,
+                  const uint64_t* cellmask, const int32_t* status, const uint64_t* solidmask,
+                  double ratio, int mode_sync, bool solid);
   // vorticity criterion marks (+1/-1/0) and block max |w|^2
   void (*criterion)(cudaStream_t, const int32_t* list, int n, const void* f, size_t stride,
                     const int32_t* status, int level, int lmax, double inv_dx, int n_start,

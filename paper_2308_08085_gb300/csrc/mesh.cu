@@ -107,6 +107,11 @@ struct PAlive {
   const int32_t* status;
   __device__ bool operator()(int i) const { return status[list[i]] != ST_INACTIVE; }
 };
+struct PNoneNbr {   // blocks with a missing same-level neighbour (NONE)
+  const int32_t* list;
+  const uint32_t* nonemask;
+  __device__ bool operator()(int i) const { return nonemask[list[i]] != 0u; }
+};
 struct PHasKids {
   const int32_t* list;
   const int32_t* child0;
@@ -635,6 +640,8 @@ int mesh_refresh_lists(Instance* a) {
     AMR_TRY(compact(a, n, act, VList{ord}, a->active + (size_t)L * a->cap, &a->n_active[L]));
     AMR_TRY(compact(a, n, par, VList{ord}, a->parents + (size_t)L * a->cap, &a->n_parents[L]));
     AMR_TRY(compact(a, n, PLeaf{ord, a->status}, VIdent{}, nullptr, &a->n_leaves[L], 0, false));
+    AMR_TRY(compact(a, n, PNoneNbr{ord, a->nonemask}, VList{ord}, a->bnd + (size_t)L * a->cap,
+                    &a->n_bnd[L]));
   }
   // exchange work per level, for the profile's algorithmic bytes
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(a->red);
