@@ -465,6 +465,152 @@ def run_cylinder(args):
             "results": results}
 
 
+# --------------------------------------------- FP32 against FP64 (cavity)
+def centreline_profiles(sim, n_pts=256):
+    """u_x along the vertical centreline (x = y = half width, z from bottom to
+    lid) and u_z along the horizontal centreline (y = z = half width, x from
+    wall to wall) of a 3D cavity, each sampled at n_pts evenly spaced points
+    from the leaf cell that contains the point (after the level
+    synchronisation)."""
+    import numpy as np
+    rho, u = sim.rho_u()
+    blk = sim.blocks()
+    X = sim.coords()
+    lev, st = blk["level"], blk["status"]
+    n = sim.cfg["nx"]
+    leaves = np.nonzero(st == 1)[0]
+    w = 4.0 / 2.0 ** lev[leaves]
+    lo = X[leaves]
+    hi = lo + w[:, None]
+    s = (np.arange(n_pts) + 0.5) * n / n_pts
+    h = n / 2.0
+
+    def sample(pts, comp):
+        out = np.empty(len(pts))
+        for i, pnt in enumerate(pts):
+            k = np.nonzero(np.all((lo <= pnt) & (pnt < hi), axis=1))[0][0]
+            b = leaves[k]
+            cell = np.floor((pnt - X[b]) / (w[k] / 4.0)).astype(int)
+            out[i] = u[b, cell[0] + 4 * cell[1] + 16 * cell[2], comp]
+        return out
+
+    vert = np.stack([np.full(n_pts, h), np.full(n_pts, h), s], 1)
+    horz = np.stack([s, np.full(n_pts, h), np.full(n_pts, h)], 1)
+    return sample(vert, 0), sample(horz, 2)
+
+
+def run_compare(args):
+    """The 3D cavity of the headline (64^3 root cells, D3Q19, Re 1000, L_max 4,
+    the vorticity criterion every 50 coarse steps) run from rest in FP64 and in
+    FP32 storage and arithmetic for --cmp-steps coarse steps; reports MLUPS of
+    each and the relative L2 difference of the centreline velocity profiles
+    (the two runs adapt on their own, so their meshes may differ)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2308_08085_gb300 import AmrLBM
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    out, prof = {}, {}
+    for storage in ("f64", "f32"):
+        cfg = W.config_c1(n=args.n, max_blocks=(args.n // 4) ** 3 * args.cap_factor)
+        sim = AmrLBM(cfg, storage=storage)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        updates, ms, cap_err = 0.0, 0.0, 0
+        for _ in range(args.cmp_steps // PERIOD):
+            updates += PERIOD * sim.updates_per_coarse_step()
+            e0.record(stream)
+            sim.step(PERIOD)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            rc, _ = sim.adapt()
+            cap_err += rc != 0
+        prof[storage] = centreline_profiles(sim)
+        out[storage] = {"mlups_excl_adapt": round(updates / (ms / 1e3) / 1e6, 1),
+                        "blocks_per_level": sim.counts()["n_ids"], "capacity_errors": cap_err}
+        sim.close()
+        torch.cuda.empty_cache()
+    a, b = prof["f32"], prof["f64"]
+    return {"workload": "3D lid-driven cavity D3Q19, %d^3 root cells, Re 1000, L_max 4, "
+                        "criterion every 50 coarse steps, from rest" % args.n,
+            "coarse_steps": (args.cmp_steps // PERIOD) * PERIOD, "runs": out,
+            "rel_l2_f32_vs_f64": {
+                "u_x_vertical_centreline": float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0])),
+                "u_z_horizontal_centreline": float(np.linalg.norm(a[1] - b[1]) / np.linalg.norm(b[1]))},
+            "profiles_f64": {"u_x_vertical": [round(v, 6) for v in b[0][::8]],
+                             "u_z_horizontal": [round(v, 6) for v in b[1][::8]]}}
+
+
+# ------------------------------------------------ Strouhal number (quasi-2D)
+def fit_sinusoid(t, y):
+    """Frequency, amplitude and mean of the sinusoid that fits y(t) best in
+    least squares: the FFT peak, refined by a scan of the residual of the
+    linear fit of (sin, cos, 1) at frequencies around it."""
+    import numpy as np
+    t = np.asarray(t, float)
+    y = np.asarray(y, float)
+    dt = t[1] - t[0]
+    spec = np.abs(np.fft.rfft(y - y.mean()))
+    freqs = np.fft.rfftfreq(len(y), dt)
+    k = int(np.argmax(spec[1:]) + 1)
+    best = None
+    for f in np.linspace(freqs[max(k - 1, 1)], freqs[min(k + 1, len(freqs) - 1)], 801):
+        A = np.stack([np.sin(2 * np.pi * f * t), np.cos(2 * np.pi * f * t), np.ones_like(t)], 1)
+        coef, res, _, _ = np.linalg.lstsq(A, y, rcond=None)
+        r = float(np.sum((A @ coef - y) ** 2))
+        if best is None or r < best[0]:
+            best = (r, f, float(np.hypot(coef[0], coef[1])), float(coef[2]))
+    return best[1], best[2], best[3]
+
+
+def run_strouhal(args):
+    """Quasi-2D flow past a square prism (the paper's FPSC case, Section 5.3):
+    D3Q19, 256 x 64 root cells, one block span with periodic z faces, prism
+    of side 8 one cell above the channel centre (to break the symmetry), Re
+    100, inlet 0.05, static distance refinement around the prism and the
+    outlet.  The lift coefficient is sampled every 16 coarse steps; after
+    --st-spinup coarse steps a sinusoid is fitted to it: St = f D / U."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2308_08085_gb300 import AmrLBM
+    torch.cuda.set_device(0)
+    side, u0, nx = 8.0, 0.05, 256
+    out = {}
+    for interp in args.st_interp.split(","):
+        cfg = W.channel_cylinder(q=19, nx=nx, ny=64, nz=4, side=side, cx=64, cy=33,
+                                 max_levels=args.st_levels, crit_start=100, crit_inc=1,
+                                 max_blocks=1024 * 40, span_periodic=True)
+        cfg["interp"] = interp
+        sim = AmrLBM(cfg, storage="f32")
+        for _ in range(args.st_levels):
+            sim.adapt()
+        area = (side / nx) * (cfg["nz"] / nx)
+        t, cl, cd = [], [], []
+        n = 0
+        t0 = time.perf_counter()
+        while n < args.st_steps:
+            sim.step(16)
+            n += 16
+            if n >= args.st_spinup:
+                fx, fy, _ = sim.force()
+                t.append(n)
+                cl.append(2.0 * fy / (u0 * u0 * area))
+                cd.append(2.0 * fx / (u0 * u0 * area))
+        wall = time.perf_counter() - t0
+        f, amp, mean = fit_sinusoid(t, cl)
+        out[interp] = {"St": round(f * side / u0, 4), "C_L_amplitude": round(amp, 4),
+                       "C_L_mean": round(mean, 4), "C_D_mean": round(float(np.mean(cd)), 4),
+                       "periods_fitted": round(f * (t[-1] - t[0]), 1),
+                       "blocks_per_level": sim.counts()["n_ids"],
+                       "wall_s": round(wall, 1)}
+        sim.close()
+    return {"workload": "quasi-2D channel past a square prism, D3Q19, 256x64 root cells, "
+                        "span one block (periodic), side 8, Re 100, L_max %d" % args.st_levels,
+            "coarse_steps": args.st_steps, "spinup": args.st_spinup, "results": out}
+
+
 # -------------------------------------------------------- batched workload
 def run_batched(args):
     """64 independent 3D cavities (D3Q19 FP32) with seeded uneven sizes (32^3 to
@@ -747,7 +893,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=64)
-    ap.add_argument("--cap-factor", type=int, default=64)
+    ap.add_argument("--cap-factor", type=int, default=128)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-bar", action="store_true")
@@ -755,7 +901,13 @@ def main():
     ap.add_argument("--variant", type=int, default=0,
                     help="collide-stream kernel: 0 auto, 1 one-pass, 2/3 pipelined stages")
     ap.add_argument("--workload", default="cavity",
-                    choices=["cavity", "cylinder", "batched", "learned"])
+                    choices=["cavity", "cylinder", "batched", "learned", "compare", "strouhal"])
+    ap.add_argument("--st-steps", type=int, default=16000)
+    ap.add_argument("--st-spinup", type=int, default=8000)
+    ap.add_argument("--st-levels", type=int, default=3)
+    ap.add_argument("--st-interp", default="linear,cubic")
+    ap.add_argument("--cmp-steps", type=int, default=10000,
+                    help="coarse steps of the FP32 / FP64 cavity comparison")
     ap.add_argument("--learn-pairs", type=int, default=200_000)
     ap.add_argument("--learn-spin", type=int, default=4)
     ap.add_argument("--learn-windows", type=int, default=4)
@@ -783,6 +935,12 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.workload == "cylinder":
         print(json.dumps(run_cylinder(args)))
+        return
+    if args.workload == "strouhal":
+        print(json.dumps(run_strouhal(args)))
+        return
+    if args.workload == "compare":
+        print(json.dumps(run_compare(args)))
         return
     if args.workload == "batched":
         print(json.dumps(run_batched(args)))

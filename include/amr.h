@@ -110,7 +110,8 @@ typedef struct {
   double refine_dist;      /* distance refinement (Section 4.4): a leaf on level
                               L within refine_dist / 2^L (physical units) of a
                               target is marked for refinement; 0 = off        */
-  int32_t refine_dist_targets; /* bit 0: the solid prism, bit 1: outlet faces */
+  int32_t refine_dist_targets; /* bit 0: the solid prism, bit 1: outlet faces,
+                                  bit 2: wall faces (no-slip and moving)      */
   int32_t refine_dist_freeze;  /* 1: blocks refined by distance become
                                   AMR_ST_REFINED_PERMANENT                    */
   const int32_t* root_ids; /* NULL: root block IDs in lexicographic order of
@@ -278,6 +279,25 @@ int amr_mass_audit_noalloc(int dim, int q, int storage, int64_t n_blocks,
 
 /* Release host-side state (the arena stays owned by the caller). */
 int amr_free(amr_t* a);
+
+/* ---------------------------------------------------- checkpoint / resume
+ * The paper keeps all state on the device and has no checkpoint; this is a
+ * service of the library.  A checkpoint is a host byte image of the whole
+ * instance: a header (format tag, the configuration fields that fix the
+ * arena layout, the host mirror of the mesh sizes, the coarse-step count and
+ * the level buffer parities) followed by the device arena.
+ * amr_checkpoint_bytes: the image size.  amr_checkpoint: synchronises and
+ * writes the image to host memory `dst` (caller-owned, >= the image size).
+ * amr_restore: loads an image into an instance created by amr_init with the
+ * same velocity set, storage, root grid, level count and capacity
+ * (AMR_E_INVAL otherwise, leaving the instance unchanged); graph use and
+ * stream may differ.  Stepping a restored instance with the same kernel
+ * variant reproduces the original bit for bit (other variants are compiled
+ * separately and may round differently).  Both calls are synchronous.
+ * Errors: AMR_E_INVAL, AMR_E_CUDA. */
+int64_t amr_checkpoint_bytes(amr_t* a);
+int amr_checkpoint(amr_t* a, void* dst, size_t dst_bytes);
+int amr_restore(amr_t* a, const void* src, size_t src_bytes);
 
 /* ------------------------------------------------ learned refinement proposal
  * Not in the paper: a per-block MLP (27 -> 64 -> 64 -> 1, ReLU, sigmoid)

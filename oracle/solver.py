@@ -52,7 +52,8 @@ Readings of the paper (where it is silent or garbled)
 * Distance rule (Section 4.4, used by the channel flow of Section 5.3): a leaf
   on level L whose block lies within d_spec / 2^L (physical) of a target -- the
   solid prism (Euclidean distance between the block square and the prism
-  square in the x-y plane) or an outlet face -- is marked for refinement
+  square in the x-y plane), an outlet face, or (a target the paper does not
+  use) a no-slip or moving wall face -- is marked for refinement
   (+2, frozen, when refine_dist_freeze); a refined block within that distance
   loses any coarsening mark.  Distances are compared squared, in root-cell
   units, without fused operations.
@@ -416,9 +417,10 @@ class ForestLBM:
             dy = max(y0 - (X[1] + w), X[1] - y1, 0.0)
             if dx * dx + dy * dy < thr2:
                 return True
-        if targets & 2:
+        if targets & 6:
+            kinds = (("outlet",) if targets & 2 else ()) + (("noslip", "moving") if targets & 4 else ())
             for fi, face in enumerate(cfg["faces"][:2 * self.dim]):
-                if face[0] != "outlet":
+                if face[0] not in kinds:
                     continue
                 a = fi // 2
                 d = (mesh.extent[a] - (X[a] + w)) if fi % 2 else X[a]

@@ -96,6 +96,12 @@ def load_library(path=LIB_PATH):
     lib.amr_profile_read.restype = i32
     lib.amr_free.argtypes = [vp]
     lib.amr_free.restype = i32
+    lib.amr_checkpoint_bytes.argtypes = [vp]
+    lib.amr_checkpoint_bytes.restype = i64
+    lib.amr_checkpoint.argtypes = [vp, vp, sz]
+    lib.amr_checkpoint.restype = i32
+    lib.amr_restore.argtypes = [vp, vp, sz]
+    lib.amr_restore.restype = i32
     lib.amr_strerror.argtypes = [i32]
     lib.amr_strerror.restype = ctypes.c_char_p
     lib.amr_last_error.argtypes = []
@@ -355,6 +361,22 @@ class AmrLBM:
         """Leaf-cell updates of one coarse step (Section 5.1 definition)."""
         c = self.counts()
         return sum((2 ** L) * c["n_leaves"][L] * self.m for L in range(self.lmax))
+
+    def checkpoint(self):
+        """Host image (numpy uint8) of the whole instance state."""
+        n = self.lib.amr_checkpoint_bytes(self.h)
+        if n < 0:
+            raise AmrError(n, "amr_checkpoint_bytes")
+        buf = np.empty(n, np.uint8)
+        self._check(self.lib.amr_checkpoint(self.h, buf.ctypes.data_as(ctypes.c_void_p), n),
+                    "amr_checkpoint")
+        return buf
+
+    def restore(self, image):
+        """Load a checkpoint image made by an instance of the same configuration."""
+        buf = np.ascontiguousarray(image, np.uint8)
+        self._check(self.lib.amr_restore(self.h, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes),
+                    "amr_restore")
 
     def close(self):
         if self.h:

@@ -155,7 +155,24 @@ static Layout layout_for(const amr_config* c) {
 struct Handle : Instance {
   void* staging = nullptr;
   cudaStream_t capture_stream = nullptr;
+  char* arena = nullptr;       // the caller's arena (layout_for offsets)
+  size_t arena_used = 0;       // bytes of it the layout occupies
 };
+
+// Header of a checkpoint image (amr_checkpoint): the configuration fields that
+// fix the arena layout, then the host mirror of the mesh and time state.
+struct CheckpointHeader {
+  char tag[8];
+  int32_t dim, q, storage, nx, ny, nz, max_levels, pad_;
+  int64_t max_blocks;
+  uint64_t arena_used;
+  int64_t n_ids[AMR_MAX_LEVELS], n_active[AMR_MAX_LEVELS], n_parents[AMR_MAX_LEVELS],
+      n_leaves[AMR_MAX_LEVELS], n_bnd[AMR_MAX_LEVELS], n_ghost_children[AMR_MAX_LEVELS],
+      n_ghost_cells[AMR_MAX_LEVELS], n_iface_cells[AMR_MAX_LEVELS];
+  int64_t n_gaps, coarse_steps;
+  uint32_t cur, pad2_;
+};
+static const char kCheckpointTag[8] = {'A', 'M', 'R', 'C', 'K', 'P', 'T', '1'};
 
 // ------------------------------------------------------------ profiling
 static const char* kPkNames[PK_COUNT] = {"collide_stream", "interp", "average"};
@@ -490,6 +507,8 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
     return AMR_E_ARENA;
   }
   Handle* a = new Handle();
+  a->arena = (char*)arena;
+  a->arena_used = L.total;
   a->cfg = *cfg;
   a->dim = cfg->dim;
   a->q = cfg->q;
@@ -927,6 +946,88 @@ int amr_profile_read(amr_t* h, amr_kernel_profile* out, int max, int reset) {
   if (reset)
     for (auto& acc : a->acc) acc = Instance::Acc{};
   return PK_COUNT;
+}
+
+int64_t amr_checkpoint_bytes(amr_t* h) {
+  Handle* a = reinterpret_cast<Handle*>(h);
+  if (!a) return AMR_E_INVAL;
+  return (int64_t)(sizeof(CheckpointHeader) + a->arena_used);
+}
+
+int amr_checkpoint(amr_t* h, void* dst, size_t dst_bytes) {
+  Handle* a = reinterpret_cast<Handle*>(h);
+  if (!a || !dst || dst_bytes < sizeof(CheckpointHeader) + a->arena_used) {
+    set_error("checkpoint destination missing or smaller than amr_checkpoint_bytes");
+    return AMR_E_INVAL;
+  }
+  drain_profile(a);
+  CheckpointHeader hd{};
+  std::memcpy(hd.tag, kCheckpointTag, sizeof(hd.tag));
+  hd.dim = a->cfg.dim;
+  hd.q = a->cfg.q;
+  hd.storage = a->cfg.storage;
+  hd.nx = a->cfg.nx;
+  hd.ny = a->cfg.ny;
+  hd.nz = a->cfg.nz;
+  hd.max_levels = a->cfg.max_levels;
+  hd.max_blocks = a->cfg.max_blocks;
+  hd.arena_used = a->arena_used;
+  for (int L = 0; L < AMR_MAX_LEVELS; ++L) {
+    hd.n_ids[L] = a->n_ids[L];
+    hd.n_active[L] = a->n_active[L];
+    hd.n_parents[L] = a->n_parents[L];
+    hd.n_leaves[L] = a->n_leaves[L];
+    hd.n_bnd[L] = a->n_bnd[L];
+    hd.n_ghost_children[L] = a->n_ghost_children[L];
+    hd.n_ghost_cells[L] = a->n_ghost_cells[L];
+    hd.n_iface_cells[L] = a->n_iface_cells[L];
+  }
+  hd.n_gaps = a->n_gaps;
+  hd.coarse_steps = a->coarse_steps;
+  hd.cur = a->cur;
+  AMR_CUDA(cudaStreamSynchronize(a->stream));
+  std::memcpy(dst, &hd, sizeof(hd));
+  AMR_CUDA(cudaMemcpy((char*)dst + sizeof(hd), a->arena, a->arena_used, cudaMemcpyDeviceToHost));
+  return AMR_OK;
+}
+
+int amr_restore(amr_t* h, const void* src, size_t src_bytes) {
+  Handle* a = reinterpret_cast<Handle*>(h);
+  if (!a || !src || src_bytes < sizeof(CheckpointHeader)) {
+    set_error("checkpoint image missing or truncated");
+    return AMR_E_INVAL;
+  }
+  CheckpointHeader hd;
+  std::memcpy(&hd, src, sizeof(hd));
+  const bool same = std::memcmp(hd.tag, kCheckpointTag, sizeof(hd.tag)) == 0 &&
+                    hd.dim == a->cfg.dim && hd.q == a->cfg.q && hd.storage == a->cfg.storage &&
+                    hd.nx == a->cfg.nx && hd.ny == a->cfg.ny && hd.nz == a->cfg.nz &&
+                    hd.max_levels == a->cfg.max_levels && hd.max_blocks == a->cfg.max_blocks &&
+                    hd.arena_used == a->arena_used &&
+                    src_bytes >= sizeof(hd) + a->arena_used;
+  if (!same) {
+    set_error("checkpoint image does not match this instance's configuration");
+    return AMR_E_INVAL;
+  }
+  drain_profile(a);
+  destroy_graphs(a);
+  AMR_CUDA(cudaStreamSynchronize(a->stream));
+  AMR_CUDA(cudaMemcpy(a->arena, (const char*)src + sizeof(hd), a->arena_used,
+                      cudaMemcpyHostToDevice));
+  for (int L = 0; L < AMR_MAX_LEVELS; ++L) {
+    a->n_ids[L] = hd.n_ids[L];
+    a->n_active[L] = hd.n_active[L];
+    a->n_parents[L] = hd.n_parents[L];
+    a->n_leaves[L] = hd.n_leaves[L];
+    a->n_bnd[L] = hd.n_bnd[L];
+    a->n_ghost_children[L] = hd.n_ghost_children[L];
+    a->n_ghost_cells[L] = hd.n_ghost_cells[L];
+    a->n_iface_cells[L] = hd.n_iface_cells[L];
+  }
+  a->n_gaps = hd.n_gaps;
+  a->coarse_steps = hd.coarse_steps;
+  a->cur = hd.cur;
+  return AMR_OK;
 }
 
 int amr_free(amr_t* h) {

@@ -456,7 +456,7 @@ __global__ void k_relink(const int32_t* list, int n, const int32_t* parent,
 __global__ void k_distance_marks(const int32_t* list, int n, int level, const int32_t* status,
                                  const float* X, int8_t* marks, double thr2, int targets,
                                  int has_solid, double sx0, double sx1, double sy0, double sy1,
-                                 unsigned outlet_faces, double ex, double ey, double ez,
+                                 unsigned face_mask, double ex, double ey, double ez,
                                  int freeze) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -469,11 +469,11 @@ __global__ void k_distance_marks(const int32_t* list, int n, int level, const in
     const double dy = fmax(fmax(__dsub_rn(sy0, __dadd_rn(y, w)), __dsub_rn(y, sy1)), 0.0);
     within = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) < thr2;
   }
-  if (targets & 2) {
+  if (targets & 6) {   // outlet faces (bit 1), wall faces (bit 2): face_mask
     const double lo[3] = {x, y, z};
     const double ext[3] = {ex, ey, ez};
     for (int f = 0; f < 6; ++f) {
-      if (!((outlet_faces >> f) & 1u)) continue;
+      if (!((face_mask >> f) & 1u)) continue;
       const int ax = f >> 1;
       const double d = (f & 1) ? __dsub_rn(ext[ax], __dadd_rn(lo[ax], w)) : lo[ax];
       if (__dmul_rn(d, d) < thr2) within = true;
@@ -488,16 +488,20 @@ __global__ void k_distance_marks(const int32_t* list, int n, int level, const in
 int mesh_distance_marks(Instance* a) {
   const amr_config& c = a->cfg;
   if (!(c.refine_dist > 0.0) || c.refine_dist_targets == 0) return AMR_OK;
-  unsigned outlets = 0;
-  for (int f = 0; f < 2 * a->dim; ++f)
-    if (c.faces[f].kind == AMR_FACE_OUTLET) outlets |= 1u << f;
+  unsigned faces = 0;   // the faces whose distance counts
+  for (int f = 0; f < 2 * a->dim; ++f) {
+    const int k = c.faces[f].kind;
+    if ((c.refine_dist_targets & 2) && k == AMR_FACE_OUTLET) faces |= 1u << f;
+    if ((c.refine_dist_targets & 4) && (k == AMR_FACE_NOSLIP || k == AMR_FACE_MOVING))
+      faces |= 1u << f;
+  }
   for (int L = 0; L < a->lmax; ++L) {
     if (a->n_ids[L] == 0) continue;
     const double thr = (c.refine_dist * c.nx / c.length_x) / std::ldexp(1.0, L);
     k_distance_marks<<<blocks_for(a->n_ids[L]), 256, 0, a->stream>>>(
         a->idset + (size_t)L * a->cap, (int)a->n_ids[L], L, a->status, a->X, a->marks, thr * thr,
         c.refine_dist_targets, c.has_solid, c.solid[0], c.solid[1], c.solid[2], c.solid[3],
-        outlets, (double)c.nx, (double)c.ny, (double)(a->dim == 3 ? c.nz : 0), c.refine_dist_freeze);
+        faces, (double)c.nx, (double)c.ny, (double)(a->dim == 3 ? c.nz : 0), c.refine_dist_freeze);
     a->launches += 1;
     AMR_CUDA(cudaGetLastError());
   }

@@ -1,7 +1,7 @@
 """Full-size parity cases: the 2D cavity run of 2000 coarse steps (64 x 64 root
 cells, D2Q9, FP64, L_max 3, the vorticity criterion every 100 steps) and one
 coarse step of the 3D cavity (64^3 root cells, D3Q19, L_max 4, capacity
-262,144 blocks) on a layered mesh with all four levels populated.
+524,288 blocks) on a layered mesh with all four levels populated.
 
 Shared by the GPU tests (`test_gpu_fullsize.py`) and by the script that
 writes their expected values from the oracle (`golden/make_fullsize.py`).
@@ -26,6 +26,16 @@ def c0_config():
     return W.config_c0()
 
 
+# 3D cavity of the headline configuration cut to 32^3 root cells (same Re,
+# L_max 4), 150 coarse steps with the criterion every 50
+C1CUT_PERIODS, C1CUT_EVERY = 3, 50
+C1CUT_SAMPLE_SEED = 79
+
+
+def c1cut_config():
+    return W.config_c1(n=32, max_blocks=(32 // 4) ** 3 * 80)
+
+
 # 3D cavity, one coarse step on a layered mesh
 C1_SLABS = ((12.0, 0.02), (8.0, 0.02), (2.0, 0.0))   # (half width, extra fraction) per level
 C1_CENTRE = 32.0
@@ -35,7 +45,7 @@ C1_SAMPLE_SEED = 78
 
 
 def c1_config():
-    return W.config_c1(n=64, max_blocks=(64 // 4) ** 3 * 64)
+    return W.config_c1(n=64, max_blocks=(64 // 4) ** 3 * 128)
 
 
 def c1_marks(level, status, corner_z, r):

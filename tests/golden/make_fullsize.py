@@ -1,13 +1,16 @@
 """Writes the expected values of the full-size parity cases (the cases are
 defined in tests/fullsize_cases.py) by running the oracle alone.
 
-    python tests/golden/make_fullsize.py [c0] [c1]
+    python tests/golden/make_fullsize.py [c0] [c1] [c1cut]
 
 c0_full_run.npz: the mesh-table digest and per-level block counts after each
   of the 20 adaptations of the 2D cavity run, the sampled block IDs, and their
   populations at the end of the run (after the last adaptation).
 c1_full_step.npz: the digest and counts of the layered 3D mesh, the sampled
   block IDs and their populations after one coarse step from the seeded state.
+c1cut_run.npz: the 3D cavity cut to 32^3 root cells, 150 coarse steps from
+  rest with the criterion every 50: the criterion's marks, digests and counts
+  of each adaptation, sampled blocks at the end.
 """
 import os
 import sys
@@ -40,6 +43,27 @@ def c0():
                         counts=np.array(counts, np.int64), ids=ids, f=ref.f[ids])
 
 
+def c1cut():
+    cfg = FC.c1cut_config()
+    ref = ForestLBM(cfg)
+    digests, counts, marks = [], [], []
+    for t in range(FC.C1CUT_PERIODS):
+        ref.step(FC.C1CUT_EVERY)
+        ref.sync()
+        m, _ = ref.criterion_marks()
+        marks.append(np.asarray(m, np.int8))
+        ref.adapt(m)
+        digests.append(FC.oracle_digest(ref.mesh))
+        counts.append(ref.mesh.counts())
+        print("c1cut period %d counts %s" % (t, counts[-1]), flush=True)
+    mesh = ref.mesh
+    ids = FC.sample_blocks(mesh.level, mesh.status, mesh.child0, mesh.nbr, mesh.lmax, mesh.nc,
+                           FC.C1CUT_SAMPLE_SEED)
+    np.savez_compressed(os.path.join(HERE, "c1cut_run.npz"), digests=np.array(digests),
+                        counts=np.array(counts, np.int64), marks=np.array(marks), ids=ids,
+                        f=ref.f[ids])
+
+
 def c1():
     cfg = FC.c1_config()
     ref = ForestLBM(cfg)
@@ -60,6 +84,6 @@ def c1():
 
 
 if __name__ == "__main__":
-    which = sys.argv[1:] or ["c0", "c1"]
+    which = sys.argv[1:] or ["c0", "c1", "c1cut"]
     for w in which:
-        {"c0": c0, "c1": c1}[w]()
+        {"c0": c0, "c1": c1, "c1cut": c1cut}[w]()

@@ -335,9 +335,29 @@ def test_mass_audit_matches_oracle():
 
 
 # ------------------------------------------------ cylinder, distance rule, force
-def test_cylinder_distance_rule_force_end_to_end():
-    cfg = W.channel_cylinder(q=19, nx=48, ny=24, nz=8, side=4, cx=16, cy=12, max_levels=3,
-                             max_blocks=72 * 30, refine_dist=0.15)
+def test_cavity_wall_distance_rule_end_to_end():
+    """Distance refinement towards the walls with freezing (REFINED_PERMANENT),
+    together with the vorticity criterion: tables bit-exact, fields 1e-12."""
+    cfg = W.cavity(dim=3, q=19, n=16, re=200.0, max_levels=3, max_blocks=64 * 40,
+                   refine_dist=0.1, refine_dist_freeze=1)
+    ref, gpu = run_pair(cfg, "f64", 60, 20)
+    compare_tables(gpu, ref.mesh)
+    assert np.any(ref.mesh.status == 4)
+    ref.sync()
+    gpu.rho_u()
+    ids = ref.mesh.active_ids()
+    assert rel_l2(gpu.populations()[ids], ref.f[ids]) <= 1e-12
+    gpu.close()
+
+
+@pytest.mark.parametrize("span_periodic", [False, True])
+def test_cylinder_distance_rule_force_end_to_end(span_periodic):
+    """Prism, outlet, distance refinement with freezing and the drag; with a
+    periodic one-block span (the quasi-2D case) as well."""
+    cfg = W.channel_cylinder(q=19, nx=48, ny=24, nz=4 if span_periodic else 8, side=4, cx=16,
+                             cy=13 if span_periodic else 12, max_levels=3,
+                             max_blocks=72 * (80 if span_periodic else 30), refine_dist=0.15,
+                             span_periodic=span_periodic)
     ref, gpu = run_pair(cfg, "f64", 60, 20)
     compare_tables(gpu, ref.mesh)
     assert np.any(ref.mesh.status == 4)             # frozen blocks around prism and outlet
@@ -435,3 +455,36 @@ def test_shifted_16bit_storage_within_rounding_bound(storage, unit_roundoff):
     assert err32 < err / 10
     gpu.close()
     gpu32.close()
+
+
+# ---------------------------------------------------- checkpoint / resume
+def test_checkpoint_restore_resumes_bit_exactly():
+    """A checkpoint image restored into a fresh instance (graphs off: the same
+    kernels launched one by one) continues exactly as the original: tables and
+    populations bit-identical after more steps and an adaptation."""
+    cfg = W.cavity(dim=3, q=19, n=16, re=400.0, max_levels=3, max_blocks=64 * 20)
+    a = new_gpu(cfg, "f32")
+    for _ in range(2):
+        a.step(20)
+        a.adapt()
+    img = a.checkpoint()
+    from paper_2308_08085_gb300 import AmrLBM
+    b = AmrLBM(cfg, storage="f32", use_graphs=False)
+    b.restore(img)
+    for sim in (a, b):
+        sim.step(15)
+        sim.adapt()
+        sim.step(5)
+    ca, cb = a.counts(), b.counts()
+    ca.pop("launches")                      # kernels launched by each instance differ
+    cb.pop("launches")
+    assert ca == cb
+    assert np.array_equal(a.nbr(), b.nbr())
+    assert a.id_sets() == b.id_sets() and a.gaps() == b.gaps()
+    assert np.array_equal(a.populations(), b.populations())
+    c = new_gpu(W.cavity(dim=3, q=19, n=16, max_levels=2, max_blocks=64 * 20), "f32")
+    from paper_2308_08085_gb300.amr import AmrError
+    with pytest.raises(AmrError):
+        c.restore(img)                      # other level count: refused
+    for sim in (a, b, c):
+        sim.close()

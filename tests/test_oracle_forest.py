@@ -671,3 +671,34 @@ def test_root_numbering_is_a_relabelling(dim):
     assert runs[0].keys() == runs[1].keys() and len(runs[0]) > 0
     for k in runs[0]:
         assert np.array_equal(runs[0][k], runs[1][k]), k
+
+
+def test_wall_distance_rule_matches_brute_force():
+    """Wall faces as distance targets: a leaf is within d_spec / 2^L of a wall
+    exactly when the nearest of its sampled points is (brute force over the
+    block's boundary points and the wall planes)."""
+    cfg = W.cavity(dim=3, q=19, n=16, max_levels=3, max_blocks=64 * 20, refine_dist=0.1,
+                   refine_dist_freeze=1)
+    lbm = ForestLBM(cfg)
+    lbm.mesh.adapt(np.ones(lbm.mesh.cap, np.int8))
+    checked = within = 0
+    n = cfg["nx"]
+    for b in lbm.mesh.active_ids():
+        L = int(lbm.mesh.level[b])
+        w = lbm.mesh.width(L)
+        X = lbm.mesh.X[b]
+        thr = 0.1 * n / 2 ** L
+        g = np.linspace(0.0, 1.0, 9)
+        pts = X + w * np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+        d = np.min(np.concatenate([pts, n - pts], axis=1))   # every face is a wall
+        if abs(d - thr) < 1e-9:
+            continue
+        assert lbm.within_refine_distance(b) == (d < thr), b
+        checked += 1
+        within += d < thr
+    assert checked > 100 and 0 < within < checked
+    # the criterion freezes the blocks it refines by distance
+    marks, _ = lbm.criterion_marks()
+    leaves = [b for b in lbm.mesh.active_ids() if lbm.mesh.status[b] == UNREFINED]
+    assert any(marks[b] == 2 for b in leaves)
+    assert all(marks[b] in (1, 2) for b in leaves if lbm.within_refine_distance(b))

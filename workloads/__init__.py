@@ -22,7 +22,7 @@ solid             None or (x0, x1, y0, y1): a square prism spanning z, in
                   root-cell units; a cell is solid when its centre lies inside
 length_x          physical domain length along x (dx_0 = length_x / nx)
 refine_dist       distance refinement: physical distance d_spec (0 = off)
-refine_dist_targets  bit 0 the solid prism, bit 1 the outlet faces
+refine_dist_targets  bit 0 the solid prism, bit 1 the outlet faces, bit 2 the wall faces
 refine_dist_freeze   1: blocks refined by distance are never coarsened
 """
 import numpy as np
@@ -51,7 +51,8 @@ def finalize(cfg):
 
 
 def cavity(dim=2, q=None, n=64, re=100.0, u_lid=0.05, max_levels=3,
-           crit_start=-2, crit_inc=1, max_blocks=None, ny=None, nz=None):
+           crit_start=-2, crit_inc=1, max_blocks=None, ny=None, nz=None,
+           refine_dist=0.0, refine_dist_freeze=0):
     """Lid-driven cavity (Section 5.2): all walls no-slip, the top wall (y+ in
     2D, z+ in 3D) moves along +x with speed u_lid.  nu0 = u_lid * n / Re in
     root-lattice units (characteristic length = cavity side)."""
@@ -65,7 +66,9 @@ def cavity(dim=2, q=None, n=64, re=100.0, u_lid=0.05, max_levels=3,
                nu0=u_lid * n / re, faces=faces, crit_start=crit_start,
                crit_inc=crit_inc,
                max_blocks=max_blocks or nroot * 6 + 64,
-               solid=None, length_x=1.0)
+               solid=None, length_x=1.0, refine_dist=refine_dist,
+               refine_dist_targets=4 if refine_dist > 0 else 0,
+               refine_dist_freeze=refine_dist_freeze)
     return finalize(cfg)
 
 
@@ -86,15 +89,18 @@ def periodic_box(dim=2, q=None, n=32, nu0=0.05, max_levels=1, max_blocks=None,
 
 def channel_cylinder(q=27, nx=256, ny=64, nz=64, side=8, cx=64, cy=32,
                      u0=0.05, re=100.0, max_levels=5, max_blocks=None,
-                     crit_start=-3, crit_inc=1, refine_dist=0.15):
+                     crit_start=-3, crit_inc=1, refine_dist=0.15, span_periodic=False):
     """3D channel past a square prism (Section 5.3 in 3D): uniform inlet at
     x- and far field on the y/z faces (moving-wall bounce-back with
     u = (u0, 0, 0)), anti-bounce-back outlet at x+.  nu0 = u0 * side / Re.
     Blocks within refine_dist / 2^L of the prism or the outlet are refined and
-    frozen (the paper's 0.15 / 2^L rule, channel length 1)."""
+    frozen (the paper's 0.15 / 2^L rule, channel length 1).  span_periodic:
+    periodic z faces (a quasi-2D flow when nz is one block)."""
     faces = [("moving", (u0, 0.0, 0.0)), ("outlet", (0.0, 0.0, 0.0)),
              ("moving", (u0, 0.0, 0.0)), ("moving", (u0, 0.0, 0.0)),
              ("moving", (u0, 0.0, 0.0)), ("moving", (u0, 0.0, 0.0))]
+    if span_periodic:
+        faces[4] = faces[5] = ("periodic", (0.0, 0.0, 0.0))
     h = side / 2.0
     nroot = (nx // 4) * (ny // 4) * (nz // 4)
     cfg = dict(dim=3, q=q, nx=nx, ny=ny, nz=nz, max_levels=max_levels,
@@ -192,7 +198,7 @@ def config_c1(n=64, re=1000.0, max_blocks=None):
     up to 3 extra levels (L_max = 4), adapt every 50 coarse steps."""
     nroot = (n // 4) ** 3
     return cavity(dim=3, q=19, n=n, re=re, max_levels=4,
-                  max_blocks=max_blocks or nroot * 80)
+                  max_blocks=max_blocks or nroot * 128)
 
 
 def config_uniform_bar(n=256):
