@@ -280,6 +280,15 @@ int amr_mass_audit_noalloc(int dim, int q, int storage, int64_t n_blocks,
 /* Release host-side state (the arena stays owned by the caller). */
 int amr_free(amr_t* a);
 
+/* Failure-detection check of the bounded waits: one CTA waits, with the wait
+ * function of the bulk-copy staged kernels and a limit of `limit_cycles` SM
+ * cycles (1 .. 2^32), on an mbarrier that nothing arrives at.  Returns
+ * AMR_E_TIMEOUT when the wait gave up and reported it (the expected result),
+ * AMR_OK if the barrier completed, AMR_E_INVAL / AMR_E_CUDA on errors.
+ * Synchronous on `stream`; no GPU fault or hang is involved.  The paper has
+ * no counterpart. */
+int amr_check_bounded_wait(long long limit_cycles, void* stream);
+
 /* ---------------------------------------------------- checkpoint / resume
  * The paper keeps all state on the device and has no checkpoint; this is a
  * service of the library.  A checkpoint is a host byte image of the whole

@@ -96,6 +96,8 @@ def load_library(path=LIB_PATH):
     lib.amr_profile_read.restype = i32
     lib.amr_free.argtypes = [vp]
     lib.amr_free.restype = i32
+    lib.amr_check_bounded_wait.argtypes = [ctypes.c_longlong, vp]
+    lib.amr_check_bounded_wait.restype = i32
     lib.amr_checkpoint_bytes.argtypes = [vp]
     lib.amr_checkpoint_bytes.restype = i64
     lib.amr_checkpoint.argtypes = [vp, vp, sz]

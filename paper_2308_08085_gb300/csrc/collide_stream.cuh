@@ -350,13 +350,18 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait for the phase of `parity` to complete: false after ~2^31 cycles
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// bounded wait for the phase of `parity` to complete: false once `limit`
+// cycles (default 2^31, about a second) have passed
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long limit = 1ll << 31) {
   if (mbar_test(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_test(bar, parity))
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
+}
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
                                           uint32_t bar) {
@@ -492,6 +497,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 2 : 4))
     }
     __syncthreads();
   }
+  if (threadIdx.x == 0)
+    for (int st = 0; st < STAGES; ++st) mbar_inval(smem_addr(bars + st));
 }
 
 }  // namespace amr

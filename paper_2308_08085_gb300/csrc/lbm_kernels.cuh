@@ -898,21 +898,23 @@ struct Launch {
       if (done) return;
     }
     // one-pass kernel: 1: 512 threads, table in shared memory; 4: 256 threads,
-    // shared; 5: 256 threads, table read through L1; 6 and 0 (auto, the fastest
-    // on the 256^3 forest): 512 threads, table through L1; 7: as 6 with 512
-    // more resident threads per SM (tighter register budget)
+    // shared; 5: 256 threads, table read through L1; 6: 512 threads, table
+    // through L1 (the fastest on the D3Q19 FP32 256^3 forest); 7: as 6 with 512
+    // more resident threads per SM (tighter register budget); 0 (auto): 7 for
+    // D3Q27 with 16-bit storage (63 -> 40 registers, measured faster), else 6
     const int v = prm.variant;
+    const bool dense = v == 7 || (v == 0 && Q == 27 && sizeof(T) == 2);
     if (sol) {
       if (v == 1) one_pass<true, 512, true>(s, list, n, fin, fout, nbr, sm, prm);
       else if (v == 4) one_pass<true, 256, true>(s, list, n, fin, fout, nbr, sm, prm);
       else if (v == 5) one_pass<true, 256, false>(s, list, n, fin, fout, nbr, sm, prm);
-      else if (v == 7) one_pass<true, 512, false, true>(s, list, n, fin, fout, nbr, sm, prm);
+      else if (dense) one_pass<true, 512, false, true>(s, list, n, fin, fout, nbr, sm, prm);
       else one_pass<true, 512, false>(s, list, n, fin, fout, nbr, sm, prm);
     } else {
       if (v == 1) one_pass<false, 512, true>(s, list, n, fin, fout, nbr, sm, prm);
       else if (v == 4) one_pass<false, 256, true>(s, list, n, fin, fout, nbr, sm, prm);
       else if (v == 5) one_pass<false, 256, false>(s, list, n, fin, fout, nbr, sm, prm);
-      else if (v == 7) one_pass<false, 512, false, true>(s, list, n, fin, fout, nbr, sm, prm);
+      else if (dense) one_pass<false, 512, false, true>(s, list, n, fin, fout, nbr, sm, prm);
       else one_pass<false, 512, false>(s, list, n, fin, fout, nbr, sm, prm);
     }
   }
