@@ -381,9 +381,10 @@ int amr_propose_marks(amr_t* a, const void* params_half, float threshold, int wi
  * amr_batch_refresh: rebuild the item lists after any member was adapted.
  * amr_batch_step: advance every member by n coarse steps (asynchronous);
  *   AMR_E_INVAL if a member was stepped outside the batch since.
- * amr_batch_autotune: time the collide-stream kernel with 8 and 4 blocks per
- *   CTA (512 / 256 threads) on `trial_steps` coarse steps each (the members
- *   advance), keep the faster, return it in *variant_out (6 or 4).
+ * amr_batch_autotune: time the collide-stream kernel with 512, 256, 128 and
+ *   64 threads per CTA (M_L = 8, 4, 2, 1 blocks per CTA in 3D; 32 .. 4 in 2D)
+ *   on `trial_steps` coarse steps each (the members advance), keep the
+ *   fastest, return its CTA size in *variant_out.
  * amr_batch_launches: kernels launched by the batch so far.
  * Errors: AMR_E_INVAL, AMR_E_ARENA, AMR_E_CUDA. */
 typedef struct amr_batch_t amr_batch_t;

@@ -245,8 +245,17 @@ class AmrLBM:
             raise AmrError(int(n), "amr_fields")
         return int(n)
 
+    # mesh tables above this size are exported to device memory and copied
+    # from there (the library stages host exports of tables through 32 MiB)
+    TABLE_STAGING_BYTES = 32 << 20
+
     def fields_host(self, what, dtype):
         n = self.field_bytes(what)
+        if n > self.TABLE_STAGING_BYTES and what not in (AMR_F, AMR_RHO_U, AMR_FEATURES):
+            import torch
+            tdt = {np.dtype(np.int32): torch.int32, np.dtype(np.float64): torch.float64,
+                   np.dtype(np.uint8): torch.uint8, np.dtype(np.int64): torch.int64}[np.dtype(dtype)]
+            return self.fields_device(what, tdt).cpu().numpy()
         out = np.empty(n // np.dtype(dtype).itemsize, dtype=dtype)
         rc = self.lib.amr_fields(self.h, what, out.ctypes.data_as(ctypes.c_void_p), n, 0)
         if rc < 0:

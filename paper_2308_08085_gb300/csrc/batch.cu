@@ -29,7 +29,7 @@ struct Batch {
           n_ids[BATCH_MAX_LEVELS] = {};
   int64_t list_cap = 0;
   unsigned cur = 0;
-  int variant = 6;
+  int variant = 512;   // threads per CTA of the batched collide-stream
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graph_valid = false;
   int64_t launches = 0, graph_launches[2] = {0, 0};
@@ -289,7 +289,9 @@ int amr_batch_step(amr_batch_t* h, int n_coarse_steps) {
 int amr_batch_autotune(amr_batch_t* h, int trial_steps, int* chosen) {
   Batch* b = reinterpret_cast<Batch*>(h);
   if (!b || trial_steps < 1) return AMR_E_INVAL;
-  static const int candidates[] = {6, 4};   // 512- and 256-thread CTAs (M_L = 8 / 4 blocks)
+  // CTA sizes of the batched collide-stream: 512 / 256 / 128 / 64 threads,
+  // i.e. M_L = 8 / 4 / 2 / 1 blocks of 64 cells per CTA in 3D
+  static const int candidates[] = {512, 256, 128, 64};
   cudaEvent_t e0, e1;
   AMR_CUDA(cudaEventCreate(&e0));
   AMR_CUDA(cudaEventCreate(&e1));

@@ -1019,12 +1019,25 @@ struct Launch {
   static void collide_stream_batch(cudaStream_t s, const uint32_t* items, int n,
                                    const InstDesc* descs, int level, int which_in, int variant) {
     if (n <= 0) return;
-    if (variant == 4 || variant == 5)
-      k_collide_stream_batch<D, Q, T, 256><<<grid_for(n, 256 / M), 256, 0, s>>>(
-          items, n, descs, level, which_in);
-    else
-      k_collide_stream_batch<D, Q, T, 512><<<grid_for(n, 512 / M), 512, 0, s>>>(
-          items, n, descs, level, which_in);
+    // variant = threads per CTA: 64 / 128 / 256 / 512, i.e. M_L = 64/M .. 512/M
+    // blocks per CTA (anything else: 512)
+    switch (variant) {
+      case 64:
+        k_collide_stream_batch<D, Q, T, 64><<<grid_for(n, 64 / M), 64, 0, s>>>(items, n, descs,
+                                                                              level, which_in);
+        break;
+      case 128:
+        k_collide_stream_batch<D, Q, T, 128><<<grid_for(n, 128 / M), 128, 0, s>>>(
+            items, n, descs, level, which_in);
+        break;
+      case 256:
+        k_collide_stream_batch<D, Q, T, 256><<<grid_for(n, 256 / M), 256, 0, s>>>(
+            items, n, descs, level, which_in);
+        break;
+      default:
+        k_collide_stream_batch<D, Q, T, 512><<<grid_for(n, 512 / M), 512, 0, s>>>(
+            items, n, descs, level, which_in);
+    }
   }
   static void interp_batch(cudaStream_t s, const uint32_t* items, int n, const InstDesc* descs,
                            int level, int which_par, int which_ch) {

@@ -201,6 +201,24 @@ def config_c1(n=64, re=1000.0, max_blocks=None):
                   max_blocks=max_blocks or nroot * 128)
 
 
+def batched_cavities(n=64, seed=0):
+    """Configurations of n independent 3D cavities (D3Q19) with seeded uneven
+    root grids (32^3 .. 64^3 cells), depths (0 .. 3 extra levels) and Reynolds
+    numbers (uniform in [100, 3200]); capacities 1, 9, 24, 48 blocks per root
+    for 0, 1, 2, 3 extra levels."""
+    g = rng(seed)
+    sizes = g.choice([32, 40, 48, 56, 64], size=n)
+    extra = g.integers(0, 4, size=n)
+    res = g.uniform(100.0, 3200.0, size=n)
+    out = []
+    for i in range(n):
+        root = (int(sizes[i]) // 4) ** 3
+        cap = root * {0: 1, 1: 9, 2: 24, 3: 48}[int(extra[i])]
+        out.append(cavity(dim=3, q=19, n=int(sizes[i]), re=float(res[i]),
+                          max_levels=1 + int(extra[i]), max_blocks=cap))
+    return out
+
+
 def config_uniform_bar(n=256):
     """Single-level D3Q19 periodic block forest of n^3 cells (roofline bar)."""
     return periodic_box(dim=3, q=19, n=n, nu0=0.01, max_levels=1,
