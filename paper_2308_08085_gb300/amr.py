@@ -393,6 +393,7 @@ class AmrLBM:
         if self.h:
             self.lib.amr_free(self.h)
             self.h = ctypes.c_void_p()
+        self.arena = None             # the device arena goes back to torch's allocator
 
     def __del__(self):
         try:
