@@ -40,7 +40,7 @@ PAPER_A100_MLUPS = 1753.0     # paper, 3D LDC D3Q19 FP32 64^3 L_max 4 on A100 (c
 # 256^3 forest (profiles/collide_stream_bar256_d3q19_f32.md), and the hash of
 # the kernel source it was measured on.  A changed source reports null.
 NCU_TRAFFIC_PER_UPDATE = 154.5     # bytes (dram read + write) per cell update
-NCU_SOURCE_SHA = "64edcd9758ace808"
+NCU_SOURCE_SHA = "4bc47af402e8d63c"
 
 
 def kernel_source_sha():

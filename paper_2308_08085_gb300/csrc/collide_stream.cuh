@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, D
   constexpr int BPC = THREADS / M;
   __shared__ int32_t s_nb[BPC][NCODE];
   __shared__ uint64_t s_sm[SOLID ? BPC : 1][SOLID ? NCODE : 1];
+  __shared__ int s_near[SOLID ? BPC : 1];   // a neighbour (or the block) has solid cells
   __shared__ uint16_t s_tab[TAB_SMEM ? Q * M : 1];
 
   const int slot = threadIdx.x / M;
@@ -172,6 +173,10 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, D
   const int first = blockIdx.x * BPC;
   if constexpr (TAB_SMEM)
     for (int t = threadIdx.x; t < Q * M; t += THREADS) s_tab[t] = g_stream_table<D, Q>.e[t];
+  if constexpr (SOLID) {
+    if (threadIdx.x < BPC) s_near[threadIdx.x] = 0;
+    __syncthreads();
+  }
   for (int t = threadIdx.x; t < BPC * NCODE; t += THREADS) {
     const int s = t / NCODE, code = t - s * NCODE;
     const int k = geo_to_k<D>(code);
@@ -179,7 +184,11 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, D
     int v = NONE;
     if (bi < n) v = __ldg(nbr + (size_t)__ldg(list + bi) * NBR_STRIDE + k);
     s_nb[s][code] = v;
-    if constexpr (SOLID) s_sm[s][code] = (v >= 0) ? __ldg(solidmask + v) : 0ull;
+    if constexpr (SOLID) {
+      const uint64_t sm = (v >= 0) ? __ldg(solidmask + v) : 0ull;
+      s_sm[s][code] = sm;
+      if (sm) s_near[s] = 1;
+    }
   }
   __syncthreads();
   if (first + slot >= n) return;
@@ -193,13 +202,15 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, D
   static_for<0, Q>([&](auto P) {
     f[P] = S::template load<D, Q, P>(fin[(size_t)P * stride + own]);
   });
-  if constexpr (TAB_SMEM)
-    collide_push<D, Q, T, SOLID, true>(f, l, b, s_tab, s_nb[slot], SOLID ? s_sm[slot] : nullptr,
-                                       fout, prm.stride, prm.omega, prm.faces);
+  const uint16_t* tab = TAB_SMEM ? s_tab : g_stream_table<D, Q>.e;
+  // blocks with no solid cell around them take the push without solid tests
+  // (a branch uniform over the block's two warps)
+  if (SOLID && s_near[SOLID ? slot : 0])
+    collide_push<D, Q, T, SOLID, TAB_SMEM>(f, l, b, tab, s_nb[slot], SOLID ? s_sm[slot] : nullptr,
+                                           fout, prm.stride, prm.omega, prm.faces);
   else
-    collide_push<D, Q, T, SOLID, false>(f, l, b, g_stream_table<D, Q>.e, s_nb[slot],
-                                        SOLID ? s_sm[slot] : nullptr, fout, prm.stride,
-                                        prm.omega, prm.faces);
+    collide_push<D, Q, T, false, TAB_SMEM>(f, l, b, tab, s_nb[slot], nullptr, fout, prm.stride,
+                                           prm.omega, prm.faces);
 }
 
 // ================================== pipelined persistent collide + stream
