@@ -34,6 +34,9 @@ sys.path.insert(0, ROOT)
 
 PERIOD = 50
 HBM_FALLBACK_GBS = 6800.0
+CAVITY_WORKLOAD = ("3D lid-driven cavity D3Q19 BGK FP32, 64^3 root cells in 4^3 blocks, lid "
+                   "0.05, Re 1000, L_max 4 (vorticity criterion N_start -2, N_inc 1), "
+                   "adaptation every 50 coarse steps")
 PAPER_A100_MLUPS = 1753.0     # paper, 3D LDC D3Q19 FP32 64^3 L_max 4 on A100 (context)
 
 # ncu DRAM traffic of k_collide_stream<3,19,float> per cell update on the
@@ -315,9 +318,7 @@ def run_ours(args):
             "vs_baseline": round(value / PAPER_A100_MLUPS, 3),
             "dtype": "f32", "data": "synthetic",
             "config": {
-                "workload": "3D lid-driven cavity D3Q19 BGK FP32, 64^3 root cells in 4^3 "
-                            "blocks, lid 0.05, Re 1000, L_max 4 (vorticity criterion "
-                            "N_start -2, N_inc 1), adaptation every 50 coarse steps",
+                "workload": CAVITY_WORKLOAD,
                 "step": "50 coarse steps (recursive level step) + 1 adaptation",
                 "parallelism": "replicas" if world > 1 else "single GPU",
                 "l2": "flushed between timed steps (256 MiB write, untimed)",
@@ -868,8 +869,9 @@ def run_reference(args):
             "ms_per_step": round(dt * 1e3 / max(1, args.steps), 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "3D lid-driven cavity D3Q19, Re 1000, L_max 4, "
-                                   "vorticity criterion (oracle sample on a 16^3 root grid)"},
+            "config": {"workload": CAVITY_WORKLOAD,
+                       "sample": "each step a bounded sample of the workload: the same cavity "
+                                 "on a 16^3 root grid, run by the oracle"},
             "cpu_baseline": {"value": round(value, 4), "unit": "MLUP/s",
                              "cores": 1, "kind": "oracle",
                              "sample": desc},
