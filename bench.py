@@ -293,12 +293,16 @@ def run_ours(args):
     # achieved algorithmic bandwidth (interpolation: 2^D parent cells per child
     # with ghost cells read + ghost cells written; averaging: interface fine
     # cells read + one parent cell per 2^D written)
-    t_prof = sum(v["ms"] for v in prof.values()) or 1.0
+    step_kinds = {k: v for k, v in prof.items() if not k.startswith("adapt_")}
+    t_prof = sum(v["ms"] for v in step_kinds.values()) or 1.0
     share = {k: {"ms": round(v["ms"], 4), "share": round(v["ms"] / t_prof, 4),
                  "launches": v["launches"],
                  "gbs": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None,
                  "frac": round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / peak, 4) if v["ms"] > 0 else None}
-             for k, v in prof.items()}
+             for k, v in step_kinds.items()}
+    # phases of the timed adaptations (device time between phase events)
+    adapt_phases = {k[len("adapt_"):]: round(v["ms"] / max(1, v["launches"]), 4)
+                    for k, v in prof.items() if k.startswith("adapt_") and v["launches"]}
 
     # single-level periodic 256^3 D3Q19 FP32 forest: the stencil's roofline bar
     bar = None
@@ -336,6 +340,7 @@ def run_ours(args):
                 "adapt_share": round(1 - t_solver / t_total, 4),
                 "capacity_errors": int(capacity_errors),
                 "kernels_sampled": share,
+                "adapt_phase_ms_per_adaptation": adapt_phases,
                 "baseline": "paper A100 mean MLUPS 1753 (D3Q19 FP32 64^3, L_max 4): context",
                 "uniform_bar": bar,
             },
@@ -610,6 +615,50 @@ def run_strouhal(args):
     return {"workload": "quasi-2D channel past a square prism, D3Q19, 256x64 root cells, "
                         "span one block (periodic), side 8, Re 100, L_max %d" % args.st_levels,
             "coarse_steps": args.st_steps, "spinup": args.st_spinup, "results": out}
+
+
+# ------------------------------------------------ adaptation cost sweep (E4)
+def run_adapt_sweep(args):
+    """Adaptation time against the number of inserted blocks (the paper's
+    insertion sweep): a periodic 3D D3Q19 FP32 forest of 128^3 root cells
+    (32,768 root blocks); seeded refine marks on a fraction of the roots,
+    adapt, then coarsen them all back; device time per phase from the profile
+    events and host wall time of the call."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2308_08085_gb300 import AmrLBM
+    torch.cuda.set_device(0)
+    n = 128
+    roots = (n // 4) ** 3
+    cfg = W.periodic_box(dim=3, q=19, n=n, nu0=0.01, max_levels=2, max_blocks=roots * 9)
+    rows = []
+    warm = AmrLBM(W.periodic_box(dim=3, q=19, n=16, nu0=0.01, max_levels=2, max_blocks=64 * 9),
+                  storage="f32")
+    warm.adapt(torch.ones(warm.cap, dtype=torch.int8, device="cuda"))
+    warm.close()
+    for frac in (0.003, 0.03, 0.1, 0.3, 1.0):
+        sim = AmrLBM(cfg, storage="f32")
+        sim.profile(1)
+        m = (W.rng(7).random(sim.cap) < frac).astype(np.int8)
+        m[roots:] = 0
+        out = {}
+        for kind, marks in (("refine", m), ("coarsen", -m)):
+            sim.profile_read(reset=True)
+            rc, st = sim.adapt(torch.from_numpy(marks).cuda())
+            prof = sim.profile_read(reset=True)
+            phases = {k[len("adapt_"):]: round(v["ms"], 4) for k, v in prof.items()
+                      if k.startswith("adapt_")}
+            out[kind] = {"blocks_changed": int(st["n_refined" if kind == "refine" else
+                                                  "n_coarsened"]) * 8,
+                         "host_ms": round(st["ms_total"], 3),
+                         "device_ms": round(sum(phases.values()), 3), "phases_ms": phases}
+        rows.append(out)
+        sim.close()
+        torch.cuda.empty_cache()
+    return {"workload": "periodic 3D D3Q19 FP32 forest, 128^3 root cells (32,768 root blocks), "
+                        "seeded refinement of a fraction of the roots, then coarsening back",
+            "rows": rows}
 
 
 # -------------------------------------------------------- batched workload
@@ -894,7 +943,8 @@ def main():
     ap.add_argument("--variant", type=int, default=0,
                     help="collide-stream kernel: 0 auto, 1 one-pass, 2/3 pipelined stages")
     ap.add_argument("--workload", default="cavity",
-                    choices=["cavity", "cylinder", "batched", "learned", "compare", "strouhal"])
+                    choices=["cavity", "cylinder", "batched", "learned", "compare", "strouhal",
+                             "adapt"])
     ap.add_argument("--st-steps", type=int, default=16000)
     ap.add_argument("--st-spinup", type=int, default=8000)
     ap.add_argument("--st-levels", type=int, default=3)
@@ -928,6 +978,9 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.workload == "cylinder":
         print(json.dumps(run_cylinder(args)))
+        return
+    if args.workload == "adapt":
+        print(json.dumps(run_adapt_sweep(args)))
         return
     if args.workload == "strouhal":
         print(json.dumps(run_strouhal(args)))

@@ -233,7 +233,10 @@ int amr_set_fields(amr_t* a, int what, const void* src, size_t src_bytes,
  * captured inside the coarse-step graphs; each amr_profile_read adds one
  * sample, the launches of the most recently replayed coarse step.
  * amr_profile_read synchronises, fills up to `max` entries (collide_stream,
- * interp, average) and returns how many kernel classes exist; reset != 0
+ * interp, average, then the phases of amr_adapt: adapt_sync, adapt_criterion,
+ * adapt_marks, adapt_alloc, adapt_idsets, adapt_relink, adapt_children,
+ * adapt_lists, timed between events at their boundaries) and returns how many
+ * classes exist; reset != 0
  * clears the sums.  Bytes are algorithmic, N_p bytes per stored population:
  * collide-stream 2 Q N_p per cell update (Section 4.2, read and write once);
  * interp Q N_p per ghost cell written plus 2^D Q N_p per child block with

@@ -334,8 +334,8 @@ class AmrLBM:
         self._check(self.lib.amr_profile(self.h, int(mode)), "amr_profile")
 
     def profile_read(self, reset=True):
-        arr = (AmrKernelProfile * 8)()
-        n = self.lib.amr_profile_read(self.h, arr, 8, 1 if reset else 0)
+        arr = (AmrKernelProfile * 16)()
+        n = self.lib.amr_profile_read(self.h, arr, 16, 1 if reset else 0)
         if n < 0:
             raise AmrError(n, "amr_profile_read")
         return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms,

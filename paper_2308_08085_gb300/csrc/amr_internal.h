@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/amr.h"
@@ -88,7 +89,9 @@ struct Instance {
   std::vector<ProfileSlot> gprof[2];
   std::vector<cudaEvent_t> event_pool;
   struct Acc { int64_t launches = 0; double ms = 0, bytes = 0, cells = 0; };
-  Acc acc[8];
+  Acc acc[16];
+  // adaptation phase boundaries of the current amr_adapt call (profiling on)
+  std::vector<std::pair<int, cudaEvent_t>> phase_marks;
 
   // interpolation mode bit of LbmOps::interp for this configuration
   int interp_bits() const { return cfg.interp == AMR_INTERP_CUBIC ? 2 : 0; }
@@ -102,7 +105,19 @@ struct Instance {
 // dcount slot of the device wait-timeout flag (StepParams::wait_flag)
 constexpr int kWaitFlagSlot = 16;
 
-enum ProfileKind { PK_COLLIDE = 0, PK_INTERP = 1, PK_AVERAGE = 2, PK_COUNT = 3 };
+enum ProfileKind {
+  PK_COLLIDE = 0, PK_INTERP = 1, PK_AVERAGE = 2,
+  // phases of an adaptation (the paper's Pre and S1-S8 grouped by what runs
+  // here): synchronisation, criterion, marks with 2:1 enforcement, ID
+  // allocation and gap pushes, ID sets, relinking, new children, level lists
+  PK_ADAPT_SYNC = 3, PK_ADAPT_CRITERION = 4, PK_ADAPT_MARKS = 5, PK_ADAPT_ALLOC = 6,
+  PK_ADAPT_IDSETS = 7, PK_ADAPT_RELINK = 8, PK_ADAPT_CHILDREN = 9, PK_ADAPT_LISTS = 10,
+  PK_COUNT = 11
+};
+
+// Start adaptation phase `kind` (a PK_ADAPT_* value; -1 closes the last one):
+// records an event on the stream when profiling is on, else does nothing.
+void adapt_phase(Instance* a, int kind);
 
 // mesh.cu
 int mesh_init_root(Instance* a);

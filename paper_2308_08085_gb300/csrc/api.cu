@@ -175,7 +175,10 @@ struct CheckpointHeader {
 static const char kCheckpointTag[8] = {'A', 'M', 'R', 'C', 'K', 'P', 'T', '1'};
 
 // ------------------------------------------------------------ profiling
-static const char* kPkNames[PK_COUNT] = {"collide_stream", "interp", "average"};
+static const char* kPkNames[PK_COUNT] = {
+    "collide_stream", "interp",       "average",       "adapt_sync",
+    "adapt_criterion", "adapt_marks", "adapt_alloc",   "adapt_idsets",
+    "adapt_relink",   "adapt_children", "adapt_lists"};
 
 static cudaEvent_t take_event(Instance* a) {
   if (!a->event_pool.empty()) {
@@ -186,6 +189,30 @@ static cudaEvent_t take_event(Instance* a) {
   cudaEvent_t e;
   cudaEventCreate(&e);
   return e;
+}
+
+void adapt_phase(Instance* a, int kind) {
+  if (a->profiling == 0) return;
+  cudaEvent_t e = take_event(a);
+  cudaEventRecord(e, a->stream);
+  a->phase_marks.emplace_back(kind, e);
+}
+
+// Durations between consecutive phase marks of the finished adaptation.
+static void harvest_phases(Instance* a) {
+  if (a->phase_marks.empty()) return;
+  cudaStreamSynchronize(a->stream);
+  for (size_t i = 0; i + 1 < a->phase_marks.size(); ++i) {
+    const int kind = a->phase_marks[i].first;
+    float ms = 0.f;
+    if (kind >= 0 && cudaEventElapsedTime(&ms, a->phase_marks[i].second,
+                                          a->phase_marks[i + 1].second) == cudaSuccess) {
+      a->acc[kind].launches += 1;
+      a->acc[kind].ms += ms;
+    }
+  }
+  for (auto& pm : a->phase_marks) a->event_pool.push_back(pm.second);
+  a->phase_marks.clear();
 }
 
 struct ProfScope {
@@ -665,7 +692,9 @@ int amr_adapt(amr_t* h, const int8_t* dev_marks, amr_adapt_stats* out) {
   if (!a) return AMR_E_INVAL;
   const auto t0 = std::chrono::steady_clock::now();
   amr_adapt_stats st{};
+  adapt_phase(a, PK_ADAPT_SYNC);
   level_sync(a);
+  adapt_phase(a, PK_ADAPT_CRITERION);
   if (dev_marks) {
     AMR_CUDA(cudaMemcpyAsync(a->marks, dev_marks, a->cap, cudaMemcpyDeviceToDevice, a->stream));
   } else {
@@ -673,10 +702,13 @@ int amr_adapt(amr_t* h, const int8_t* dev_marks, amr_adapt_stats* out) {
     if (crc != AMR_OK) return crc;
   }
   AMR_CUDA(cudaGetLastError());
+  adapt_phase(a, PK_ADAPT_MARKS);
   int rc = mesh_adapt(a, dev_marks != nullptr, &st);
+  adapt_phase(a, -1);
   if (rc != AMR_OK) return rc;
   destroy_graphs(a);
   AMR_CUDA(cudaStreamSynchronize(a->stream));
+  harvest_phases(a);
   if (int wrc = take_wait_flag(a)) return wrc;
   int64_t nb = 0;
   for (int L = 0; L < a->lmax; ++L) nb += a->n_ids[L];

@@ -706,6 +706,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
   std::vector<int64_t> nRL(a->lmax, 0), offR(a->lmax + 1, 0);
   std::vector<int64_t> nCL(a->lmax, 0);
 
+  adapt_phase(a, PK_ADAPT_ALLOC);
   // allocation (reads the gap stack top before any push)
   AMR_CUDA(cudaMemsetAsync(a->dcount + 8, 0, sizeof(int32_t), s));
   if (nR > 0) {
@@ -743,6 +744,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     a->launches += 1;
     AMR_CUDA(cudaGetLastError());
   }
+  adapt_phase(a, PK_ADAPT_IDSETS);
   // R grouped by level into C's storage (C is no longer needed)
   for (int L = 0; L < a->lmax; ++L) {
     AMR_TRY(compact(a, nR, PLevelEq{R, a->level, L}, VList{R}, C + offR[L], &nRL[L]));
@@ -764,6 +766,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
       AMR_CUDA(cudaMemcpyAsync(ids, W, sizeof(int32_t) * (kept + nadd), cudaMemcpyDeviceToDevice, s));
     a->n_ids[L] = kept + nadd;
   }
+  adapt_phase(a, PK_ADAPT_RELINK);
   k_branch_leaf<<<blocks_for(cap), 256, 0, s>>>(cap, a->status, a->child0, NC);
   a->launches += 1;
   AMR_CUDA(cudaGetLastError());
@@ -775,6 +778,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     a->launches += 1;
     AMR_CUDA(cudaGetLastError());
   }
+  adapt_phase(a, PK_ADAPT_CHILDREN);
   // solid bits of the new children, then every cell of them from the parents
   for (int L = 0; L + 1 < a->lmax; ++L) {
     if (nRL[L] == 0) continue;
@@ -801,6 +805,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     set_error("gap stack lost its group structure");
     return AMR_E_INVAL;
   }
+  adapt_phase(a, PK_ADAPT_LISTS);
   return mesh_refresh_lists(a);
 }
 
