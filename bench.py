@@ -617,6 +617,57 @@ def run_strouhal(args):
             "coarse_steps": args.st_steps, "spinup": args.st_spinup, "results": out}
 
 
+# --------------------------------------- the paper's MLUPS table on this GPU
+PAPER_A100_TABLE = {  # mean MLUPS on an A100 (FP32, FP64), lid-driven cavities, L_max 4
+    "D2Q9 128^2": (495.0, 452.0), "D3Q19 64^3": (1753.0, 1219.0),
+    "D3Q27 64^3": (1089.0, 786.0)}
+
+
+def run_table(args):
+    """The paper's MLUPS table for lid-driven cavities (D2Q9 at 128^2 root
+    cells, D3Q19 and D3Q27 at 64^3, L_max 4, Re 1000, the vorticity criterion
+    every 50 coarse steps) in FP32 and FP64, with the benchmark's protocol:
+    --warmup periods of 50 coarse steps + adaptation, then --steps timed
+    periods; the paper's A100 means are given as context."""
+    import torch
+    import workloads as W
+    from paper_2308_08085_gb300 import AmrLBM
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for name, dim, q, n in (("D2Q9 128^2", 2, 9, 128), ("D3Q19 64^3", 3, 19, 64),
+                            ("D3Q27 64^3", 3, 27, 64)):
+        for k, storage in enumerate(("f32", "f64")):
+            roots = (n // 4) ** dim
+            cfg = W.cavity(dim=dim, q=q, n=n, re=1000.0, max_levels=4, max_blocks=roots * 128)
+            sim = AmrLBM(cfg, storage=storage)
+            for _ in range(args.warmup):
+                sim.step(PERIOD)
+                sim.adapt()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            upd, t_all, t_solve = 0.0, 0.0, 0.0
+            for _ in range(args.steps):
+                upd += PERIOD * sim.updates_per_coarse_step()
+                e0.record(stream)
+                sim.step(PERIOD)
+                e1.record(stream)
+                sim.adapt()
+                e2.record(stream)
+                torch.cuda.synchronize()
+                t_all += e0.elapsed_time(e2) / 1e3
+                t_solve += e0.elapsed_time(e1) / 1e3
+            rows.append({"case": name, "storage": storage,
+                         "mlups": round(upd / t_all / 1e6, 1),
+                         "mlups_excl_adapt": round(upd / t_solve / 1e6, 1),
+                         "blocks_per_level": sim.counts()["n_ids"],
+                         "paper_a100_mlups": PAPER_A100_TABLE[name][k],
+                         "ratio_to_a100": round(upd / t_all / 1e6 / PAPER_A100_TABLE[name][k], 1)})
+            sim.close()
+            torch.cuda.empty_cache()
+    return {"workload": "lid-driven cavities, Re 1000, L_max 4, criterion every 50 coarse steps",
+            "warmup_periods": args.warmup, "timed_periods": args.steps, "rows": rows}
+
+
 # ------------------------------------------------ adaptation cost sweep (E4)
 def run_adapt_sweep(args):
     """Adaptation time against the number of inserted blocks (the paper's
@@ -944,7 +995,7 @@ def main():
                     help="collide-stream kernel: 0 auto, 1 one-pass, 2/3 pipelined stages")
     ap.add_argument("--workload", default="cavity",
                     choices=["cavity", "cylinder", "batched", "learned", "compare", "strouhal",
-                             "adapt"])
+                             "adapt", "table"])
     ap.add_argument("--st-steps", type=int, default=16000)
     ap.add_argument("--st-spinup", type=int, default=8000)
     ap.add_argument("--st-levels", type=int, default=3)
@@ -978,6 +1029,9 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.workload == "cylinder":
         print(json.dumps(run_cylinder(args)))
+        return
+    if args.workload == "table":
+        print(json.dumps(run_table(args)))
         return
     if args.workload == "adapt":
         print(json.dumps(run_adapt_sweep(args)))

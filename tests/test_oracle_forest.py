@@ -702,3 +702,48 @@ def test_wall_distance_rule_matches_brute_force():
     leaves = [b for b in lbm.mesh.active_ids() if lbm.mesh.status[b] == UNREFINED]
     assert any(marks[b] == 2 for b in leaves)
     assert all(marks[b] in (1, 2) for b in leaves if lbm.within_refine_distance(b))
+
+
+@pytest.mark.parametrize("interp", ["linear", "cubic"])
+def test_pressure_continuous_across_interfaces(interp):
+    """Section 5.3's observation that the pressure is continuous across
+    coarse-fine interfaces: a pressure-driven channel (anti-bounce-back inlet
+    and outlet at rho 1 +- 0.001, no-slip walls) with a refined band in the
+    middle, run to steady state.  Along the centre line the density falls
+    linearly; at both interfaces the step between the last coarse and the
+    first fine cell deviates from that line by under 10 % of the drop over one
+    coarse cell."""
+    cfg = W.cavity(dim=2, q=9, n=32, ny=16, max_levels=2, max_blocks=32 + 8 * 4)
+    cfg["faces"] = [("outlet", (0.0, 0.0, 0.0), 1.001), ("outlet", (0.0, 0.0, 0.0), 0.999),
+                    ("noslip", (0.0, 0.0, 0.0)), ("noslip", (0.0, 0.0, 0.0))]
+    cfg["nu0"] = 1.0 / 6.0
+    cfg["interp"] = interp
+    lbm = ForestLBM(cfg)
+    m = np.zeros(lbm.mesh.cap, np.int8)
+    for b in range(lbm.mesh.n_root):
+        if lbm.mesh.X[b][0] in (12.0, 16.0):
+            m[b] = 1
+    lbm.adapt(m)
+    assert lbm.mesh.counts() == [32, 32]
+    lbm.step(3000)
+    lbm.sync()
+    xs, rs = [], []
+    for b in lbm.mesh.active_ids():
+        if lbm.mesh.status[b] != UNREFINED:
+            continue
+        c = lbm.cell_centres(b)
+        rho, _ = moments(lbm.vs, lbm.f[b])
+        sel = np.abs(c[:, 1] - 8.0) < 0.6
+        xs += list(c[sel, 0])
+        rs += list(rho[sel])
+    xs, rs = np.array(xs), np.array(rs)
+    mid = (xs > 4) & (xs < 28)
+    slope, icpt = np.linalg.lstsq(np.stack([xs[mid], np.ones(mid.sum())], 1), rs[mid],
+                                  rcond=None)[0]
+    assert slope < 0
+    dev = (rs - (slope * xs + icpt)) / abs(slope)       # in coarse cells of pressure drop
+    assert np.abs(dev[mid]).max() < 0.25
+    for last_coarse, first_fine in ((11.5, 12.25), (20.5, 19.75)):
+        a = dev[np.isclose(xs, last_coarse)].mean()
+        b = dev[np.isclose(xs, first_fine)].mean()
+        assert abs(a - b) < 0.1, (interp, last_coarse, a, b)
