@@ -175,6 +175,19 @@ def dist_setup():
     return world, rank, local
 
 
+def combine_ranks(dist, seconds, units, device):
+    """Whole-job figures over the ranks of a replica run: the slowest rank's
+    time and the units (cell updates) all ranks processed."""
+    if dist is None:
+        return seconds, units
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -241,14 +254,7 @@ def run_ours(args):
     sim.profile(0)
     end_counts = sim.counts()
 
-    t_max = t_total
-    upd_all = updates
-    if dist is not None:
-        t = torch.tensor([t_total, float(updates)], dtype=torch.float64, device=dev)
-        tm = t.clone()
-        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
-        t_max, upd_all = float(tm[0]), float(tm[1])
+    t_max, upd_all = combine_ranks(dist, t_total, updates, dev)
 
     # end to end through the C ABI: result fields to pinned host memory
     nbytes = sim.field_bytes(0)
@@ -265,11 +271,7 @@ def run_ours(args):
         assert rc == nbytes
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([t_e2e, float(e2e_updates)], dtype=torch.float64, device=dev)
-        dist.all_reduce(t[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        t_e2e, e2e_updates = float(t[0]), float(t[1])
+    t_e2e, e2e_updates = combine_ranks(dist, t_e2e, e2e_updates, dev)
 
     # roofline of the fused collide-stream kernel
     cs = prof.get("collide_stream", {})
