@@ -100,8 +100,11 @@ typedef struct {
                               centre is strictly inside is solid               */
   amr_face faces[6];       /* x-, x+, y-, y+, z-, z+ (first 4 used in 2D)      */
   int32_t use_graphs;      /* 1: replay the coarse step as a CUDA graph         */
-  int32_t kernel_variant;  /* collide-stream kernel: 0 (default) / 6 one-pass,
-                              512-thread CTAs, push table read through L1;
+  int32_t kernel_variant;  /* collide-stream kernel: 6 one-pass, 512-thread
+                              CTAs, push table read through L1; 0 (default):
+                              6, with 128-thread CTAs for launches of fewer
+                              cells than two waves and the 7 budget for D3Q27
+                              with 16-bit storage;
                               1: 512 threads, table in shared memory; 4: 256
                               threads, shared; 5: 256 threads, L1; 2 / 3: 2- /
                               3-stage cp.async pipeline in a persistent grid;

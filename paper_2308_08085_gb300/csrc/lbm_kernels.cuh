@@ -825,10 +825,13 @@ struct Launch {
     return 0;
   }
 
+  static inline int sm_count = 152;
+
   static int setup() {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+    sm_count = sms;
     if (setup_one<false, 2>(sms) || setup_one<true, 2>(sms) || setup_one<false, 3>(sms) ||
         setup_one<true, 3>(sms))
       return -1;
@@ -904,6 +907,18 @@ struct Launch {
     // D3Q27 with 16-bit storage (63 -> 40 registers, measured faster), else 6
     const int v = prm.variant;
     const bool dense = v == 7 || (v == 0 && Q == 27 && sizeof(T) == 2);
+    // auto: a launch of fewer cells than two waves of 512-thread CTAs runs in
+    // 128-thread CTAs, which spread its blocks over more SMs
+    if (v == 0 && (int64_t)n * M < (int64_t)512 * 6 * sm_count) {
+      if (sol) {
+        if (dense) one_pass<true, 128, false, true>(s, list, n, fin, fout, nbr, sm, prm);
+        else one_pass<true, 128, false>(s, list, n, fin, fout, nbr, sm, prm);
+      } else {
+        if (dense) one_pass<false, 128, false, true>(s, list, n, fin, fout, nbr, sm, prm);
+        else one_pass<false, 128, false>(s, list, n, fin, fout, nbr, sm, prm);
+      }
+      return;
+    }
     if (sol) {
       if (v == 1) one_pass<true, 512, true>(s, list, n, fin, fout, nbr, sm, prm);
       else if (v == 4) one_pass<true, 256, true>(s, list, n, fin, fout, nbr, sm, prm);
