@@ -1,0 +1,61 @@
+"""Host-side helpers of the benchmark: the sinusoid fit of the Strouhal
+workload and the centreline sampling of the FP32/FP64 comparison, checked on
+synthetic signals and on an oracle forest (no GPU)."""
+import os
+import sys
+
+import numpy as np
+
+import workloads as W
+from oracle.lattice import equilibrium
+from oracle.solver import ForestLBM
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def test_fit_sinusoid_recovers_frequency_amplitude_and_mean():
+    t = np.arange(8000, 16000, 16.0)
+    for period, amp, mean in ((1067.0, 0.31, -0.004), (640.0, 1.2, 0.5)):
+        g = np.random.default_rng(3)
+        y = amp * np.sin(2 * np.pi * t / period + 0.7) + mean + 0.01 * g.standard_normal(len(t))
+        f, a, m = bench.fit_sinusoid(t, y)
+        assert abs(f * period - 1.0) < 2e-3
+        assert abs(a - amp) < 0.01 * amp + 0.005
+        assert abs(m - mean) < 0.005
+
+
+class _Forest:
+    """The attributes of AmrLBM that the centreline sampling reads, served
+    from an oracle forest."""
+
+    def __init__(self, lbm):
+        self.lbm, self.cfg = lbm, lbm.cfg
+
+    def rho_u(self):
+        return self.lbm.macroscopic()
+
+    def blocks(self):
+        return dict(level=self.lbm.mesh.level, status=self.lbm.mesh.status)
+
+    def coords(self):
+        return self.lbm.mesh.X
+
+
+def test_centreline_profiles_sample_the_leaf_cells():
+    cfg = W.cavity(dim=3, q=19, n=16, max_levels=2, max_blocks=64 * 10)
+    lbm = ForestLBM(cfg)
+    m = np.zeros(cfg["max_blocks"], np.int8)
+    m[[5, 6, 9, 10, 21, 22, 25, 26]] = 1
+    lbm.adapt(m)
+    for b in lbm.mesh.active_ids():
+        x = lbm.cell_centres(b)
+        u = np.stack([0.01 * x[:, 2], 0.0 * x[:, 0], 0.02 * x[:, 0]], 1)
+        lbm.f[b] = equilibrium(lbm.vs, np.ones(len(x)), u)
+    vx, vz = bench.centreline_profiles(_Forest(lbm), 32)
+    s = (np.arange(32) + 0.5) * 16 / 32
+    # each sample is the value at the centre of the leaf cell that holds it:
+    # within half a cell of the sample point (half a root cell at most)
+    assert np.all(np.abs(vx - 0.01 * s) <= 0.01 * 0.5 + 1e-12)
+    assert np.all(np.abs(vz - 0.02 * s) <= 0.02 * 0.5 + 1e-12)
+    assert np.all(np.diff(vx) >= -1e-12) and np.all(np.diff(vz) >= -1e-12)
