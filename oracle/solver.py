@@ -455,9 +455,10 @@ class ForestLBM:
     def mea_force(self, level=None):
         """Momentum-exchange force on the solid (Section 5.3):
         F = 2 dx^(dim-1) sum over fluid leaf cells x_b and links p with x_b + c_p
-        solid of f*_p c_p, dx the physical cell size of the level.  Parity
-        unpinned in 3D (no printed value); computed from the current state
-        (post-collision values recomputed here)."""
+        solid of f*_p c_p, dx the physical cell size of the level; computed from
+        the current state (post-collision values recomputed here).  No 3D value
+        is printed; pinned by the momentum balance of one periodic update (the
+        fluid loses F / dx^(dim-1) in lattice units)."""
         mesh, vs = self.mesh, self.vs
         F = np.zeros(self.dim)
         blocks = [b for L in range(mesh.lmax) for b in mesh.active_list(L)

@@ -10,7 +10,8 @@
 * a static two-level Couette flow stays linear (pins the rescaling factor);
 * Taylor-Green decay on a static two-level periodic forest;
 * the vorticity criterion on a linear shear (closed form);
-* the MLUPS update count against a brute-force leaf count.
+* the MLUPS update count against a brute-force leaf count;
+* the momentum-exchange force against the fluid's momentum balance.
 """
 import itertools
 
@@ -747,3 +748,51 @@ def test_pressure_continuous_across_interfaces(interp):
         a = dev[np.isclose(xs, last_coarse)].mean()
         b = dev[np.isclose(xs, first_fine)].mean()
         assert abs(a - b) < 0.1, (interp, last_coarse, a, b)
+
+
+# ---------------------------------------------------- momentum exchange
+def _fluid_momentum(lbm, blocks):
+    return sum((lbm.f[b][~lbm.solid[b]] @ lbm.vs.cf).sum(0) for b in blocks)
+
+
+MEA_CASES = [
+    ("2d_q9", lambda: W.periodic_box(dim=2, q=9, n=16, ny=16), 0),
+    ("3d_q27", lambda: W.periodic_box(dim=3, q=27, n=16, ny=16, nz=8), 0),
+    ("3d_q19_level1", lambda: W.periodic_box(dim=3, q=19, n=16, ny=16, nz=4,
+                                             max_levels=2, max_blocks=64 * 9), 1),
+]
+
+
+@pytest.mark.parametrize("name,mk,level", MEA_CASES, ids=[c[0] for c in MEA_CASES])
+def test_momentum_exchange_balances_fluid_momentum(name, mk, level):
+    """Halfway bounce-back returns every post-collision population that meets
+    the solid with the opposite velocity, while collision and streaming between
+    fluid cells conserve momentum.  Over one update of a fully periodic level
+    the fluid therefore loses exactly the momentum 2 sum f*_p c_p that the
+    momentum exchange of Section 5.3 assigns to the solid: in lattice units of
+    that level F / dx_L^(dim-1) = P(t) - P(t+1).  Pins the factor 2, the sign,
+    the use of post-collision values, the link directions and dx_L."""
+    cfg = mk()
+    cfg["solid"] = (6.0, 10.0, 5.0, 11.0)
+    lbm = ForestLBM(cfg)
+    if level:
+        m = np.zeros(lbm.mesh.cap, np.int8)
+        m[:lbm.mesh.n_root] = 1
+        lbm.adapt(m)
+        assert lbm.mesh.counts()[level] == lbm.mesh.n_root * lbm.mesh.nc
+    blocks = lbm.mesh.active_list(level)
+    assert all(lbm.mesh.level[b] == level for b in blocks)
+    for i, b in enumerate(blocks):
+        rho, u = W.random_macro(100 + i, lbm.m, lbm.dim)
+        f = equilibrium(lbm.vs, rho, u) + W.random_noise(5000 + i, (lbm.m, lbm.vs.q))
+        f[lbm.solid[b]] = lbm.rest
+        lbm.f[b] = f
+    assert lbm.solid[blocks].any() and not lbm.solid[blocks].all()
+    force = lbm.mea_force()
+    p0 = _fluid_momentum(lbm, blocks)
+    lbm.collide_stream(level)
+    p1 = _fluid_momentum(lbm, blocks)
+    dx = cfg["length_x"] / (cfg["nx"] * 2.0 ** level)
+    lattice = force / dx ** (lbm.dim - 1)
+    assert np.abs(lattice).max() > 1e-2
+    np.testing.assert_allclose(lattice, p0 - p1, rtol=1e-10, atol=1e-11)
