@@ -11,8 +11,11 @@
 * Taylor-Green decay on a static two-level periodic forest;
 * the vorticity criterion on a linear shear (closed form);
 * the MLUPS update count against a brute-force leaf count;
-* the momentum-exchange force against the fluid's momentum balance.
+* the momentum-exchange force against the fluid's momentum balance;
+* every mark pattern on tiny forests (2x2 roots in 2D, 2x1x1 in 3D) over two
+  calls: decisions from geometry alone, gap-stack group heads, invariants.
 """
+import copy
 import itertools
 
 import numpy as np
@@ -20,7 +23,8 @@ import pytest
 
 import workloads as W
 from oracle.forest import (BLOCK_EDGE, GHOST, INACTIVE, INTERFACE, INTERIOR, NONE,
-                           REFINED, REFINED_ANY, UNREFINED, Forest, local_coords)
+                           REFINED, REFINED_ANY, REFINED_PERMANENT, UNREFINED, Forest,
+                           local_coords)
 from oracle.lattice import CS2, equilibrium, moments
 from oracle.solver import ForestLBM
 from oracle.uniform import UniformLBM
@@ -796,3 +800,117 @@ def test_momentum_exchange_balances_fluid_momentum(name, mk, level):
     lattice = force / dx ** (lbm.dim - 1)
     assert np.abs(lattice).max() > 1e-2
     np.testing.assert_allclose(lattice, p0 - p1, rtol=1e-10, atol=1e-11)
+
+
+# ------------------------------------ exhaustive mark patterns, tiny forests
+def _expected_decisions(mesh, geo, marks):
+    """Refine and coarsen sets of one adaptation call, decided from geometry
+    alone: a leaf below L_max - 1 marked +1 refines when every one of its
+    same-level neighbour positions holds a block (walls count as present); a
+    block marked -1 whose children are all leaves coarsens unless one of its
+    children has, in some direction including itself, a same-level block that
+    has children or refines in this call."""
+    act = mesh.active_ids()
+    refine = sorted(b for b in act if marks[b] > 0 and mesh.child0[b] == NONE
+                    and mesh.level[b] < mesh.lmax - 1 and NONE not in geo[b])
+    rset = set(refine)
+    coarsen = []
+    for p in sorted(act):
+        c0 = mesh.child0[p]
+        if marks[p] >= 0 or c0 < 0 or mesh.status[p] == REFINED_PERMANENT:
+            continue
+        kids = [c0 + c for c in range(mesh.nc)]
+        if any(mesh.child0[c] >= 0 for c in kids):
+            continue
+        busy = any(n != "wall" and n != NONE and (mesh.child0[n] >= 0 or n in rset)
+                   for c in kids for n in geo[c])
+        if not busy:
+            coarsen.append(p)
+    return refine, coarsen
+
+
+def _mesh_key(mesh):
+    return tuple(sorted((int(mesh.level[b]), tuple(mesh.X[b]), int(mesh.status[b]))
+                        for b in mesh.active_ids()))
+
+
+def _check_call(mesh, marks, seen, classes):
+    geo = {b: geometric_nbr(mesh, b) for b in mesh.active_ids()}
+    refine, coarsen = _expected_decisions(mesh, geo, marks)
+    gap_before = list(mesh.gap)
+    child0_before = mesh.child0.copy()
+    res = mesh.adapt(marks)
+    assert not res["capacity_error"]
+    assert (res["n_refined"], res["n_coarsened"]) == (len(refine), len(coarsen))
+    for i, p in enumerate(refine):
+        assert mesh.status[p] in REFINED_ANY
+        assert mesh.child0[p] == gap_before[-1 - i * mesh.nc]
+    for p in coarsen:
+        assert mesh.status[p] == UNREFINED and mesh.child0[p] == NONE
+    for b in np.flatnonzero(marks):
+        if b not in refine and b not in coarsen:
+            assert mesh.child0[b] == child0_before[b]
+    brute_force_check(mesh)
+    key = _mesh_key(mesh)
+    if key in seen:
+        return
+    seen.add(key)
+    for b in mesh.active_ids():
+        g = geometric_nbr(mesh, b)
+        for k, n in enumerate(g):
+            assert mesh.nbr[b, k] <= -2 if n == "wall" else mesh.nbr[b, k] == n
+        # a cell's class looks at most one block width away, so the block's
+        # neighbour occupancy decides it: rasterise once per occupancy
+        occ = tuple("wall" if n == "wall" else n != NONE for n in g)
+        if occ not in classes:
+            classes[occ] = brute_force_classes(mesh, b)
+        assert np.array_equal(mesh.cell_classes(b), classes[occ])
+
+
+def _effective_patterns(mesh):
+    """Every mark pattern that can change the mesh: leaves 0 / +1, blocks with
+    children 0 / -1."""
+    act = sorted(mesh.active_ids())
+    opts = [(0, 1) if mesh.child0[b] == NONE else (0, -1) for b in act]
+    for combo in itertools.product(*opts):
+        m = np.zeros(mesh.cap, np.int8)
+        m[act] = combo
+        yield m
+
+
+EXHAUSTIVE = [
+    ("2d_2x2", lambda: W.cavity(dim=2, n=8, max_levels=3, max_blocks=4 + 4 * 12),
+     [(), (0,), (1,), (2,), (3,)]),
+    ("3d_2x1x1", lambda: W.cavity(dim=3, n=8, ny=4, nz=4, max_levels=3,
+                                  max_blocks=2 + 8 * 12), [(), (0,)]),
+]
+
+
+@pytest.mark.parametrize("name,mk,starts", EXHAUSTIVE, ids=[e[0] for e in EXHAUSTIVE])
+def test_exhaustive_mark_patterns(name, mk, starts):
+    """Every mark pattern (-1 / 0 / +1) on the roots, then every pattern that
+    can change the mesh on the forests with the listed roots refined: the
+    refine / coarsen decisions equal the geometric rule, the group heads follow
+    the gap stack, and the invariants hold after every call."""
+    cfg = mk()
+    n_root = Forest(cfg).n_root
+    seen, classes = set(), {}
+    for pat in itertools.product((-1, 0, 1), repeat=n_root):
+        mesh = Forest(cfg)
+        m = np.zeros(mesh.cap, np.int8)
+        m[:n_root] = pat
+        _check_call(mesh, m, seen, classes)
+        refined = tuple(b for b in range(n_root) if mesh.child0[b] >= 0)
+        assert refined == tuple(b for b in range(n_root) if pat[b] == 1)
+    n_calls = 0
+    for refined in starts:
+        start = Forest(cfg)
+        m = np.zeros(start.cap, np.int8)
+        m[list(refined)] = 1
+        start.adapt(m)
+        for m2 in _effective_patterns(start):
+            _check_call(copy.deepcopy(start), m2, seen, classes)
+            n_calls += 1
+    nc = Forest(cfg).nc
+    assert n_calls == sum(2 ** (n_root + len(r) * nc) for r in starts)
+    assert len(seen) > 10
