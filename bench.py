@@ -694,6 +694,85 @@ def run_table(args):
             "warmup_periods": args.warmup, "timed_periods": args.steps, "rows": rows}
 
 
+# ------------------------------------------- cell vs. block arrangement (E6)
+# block / cell time ratios of the paper's single-level comparison (A100), by
+# arrangement, for D2Q9 2048^2, D3Q19 192^3, D3Q27 192^3: context only
+PAPER_E6_RATIO = {"calculated": (1.73, 1.39, 1.47), "retrieved": (1.58, 1.25, 1.34),
+                  "morton": (1.58, 1.12, 1.15), "shuffled": (0.39, 0.44, 0.33)}
+
+
+def run_e6(args):
+    """Cell- against block-based arrangement on one level (the paper's
+    comparison, Section 5): periodic D2Q9 2048^2, D3Q19 192^3 and D3Q27 192^3
+    grids, FP32, from rest.  Cell-based: one element per cell with x-fastest
+    IDs and computed neighbours ('calculated'), the same IDs with neighbours
+    from a table ('retrieved'), Morton IDs, or shuffled IDs (table).
+    Block-based: the single-level block forest with its root blocks numbered
+    lexicographically (it always reads neighbours from its table: it serves
+    both structured rows), along the Morton curve, or shuffled.  Time per step
+    from CUDA events over --e6-steps launches after 5 warm-up steps; the
+    working sets exceed L2."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2308_08085_gb300 import AmrLBM, Cells
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = measured_peaks()
+    nsteps = args.e6_steps
+    rows = []
+
+    def timed(step_fn):
+        step_fn(5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        step_fn(nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / nsteps
+
+    for ci, (name, dim, q, shape) in enumerate((("D2Q9 2048^2", 2, 9, [2048, 2048]),
+                                                ("D3Q19 192^3", 3, 19, [192] * 3),
+                                                ("D3Q27 192^3", 3, 27, [192] * 3))):
+        n = int(np.prod(shape))
+        nu0 = 0.01
+        cell_t = {}
+        for arr in W.CELL_ARRANGEMENTS:
+            sim = Cells(dim, q, shape, nu0, W.cell_ids(shape, arr, seed=0))
+            sim.set_rest()
+            cell_t[arr] = timed(sim.step)
+            del sim
+            torch.cuda.empty_cache()
+        block_t = {}
+        for order in ("lexicographic", "morton", "shuffled"):
+            cfg = W.periodic_box(dim=dim, q=q, n=shape[0], nu0=nu0, max_levels=1,
+                                 max_blocks=n // 4 ** dim)
+            if order == "morton":
+                cfg["root_ids"] = W.morton_root_ids(cfg)
+            elif order == "shuffled":
+                cfg["root_ids"] = W.shuffled_root_ids(cfg, 0)
+            sim = AmrLBM(cfg, storage="f32")
+            block_t[order] = timed(sim.step)
+            sim.close()
+            torch.cuda.empty_cache()
+        block_of = {"calculated": "lexicographic", "retrieved": "lexicographic",
+                    "morton": "morton", "shuffled": "shuffled"}
+        alg = 2 * q * 4 * n
+        for arr in W.CELL_ARRANGEMENTS:
+            tc, tb = cell_t[arr], block_t[block_of[arr]]
+            rows.append({"case": name, "arrangement": arr,
+                         "cell_us": round(tc * 1e6, 1), "block_us": round(tb * 1e6, 1),
+                         "ratio_block_over_cell": round(tb / tc, 3),
+                         "paper_ratio_a100": PAPER_E6_RATIO[arr][ci],
+                         "cell_frac": round(alg / tc / 1e9 / peak, 4),
+                         "block_frac": round(alg / tb / 1e9 / peak, 4),
+                         "block_numbering": block_of[arr]})
+    return {"workload": "cell- vs block-based arrangement, one level, periodic, FP32, from rest",
+            "steps": nsteps, "peak_gbs": peak, "peak_source": peak_kind,
+            "bytes_per_update": "2 Q 4 (neighbour tables not counted)", "rows": rows}
+
+
 # ------------------------------------------------ adaptation cost sweep (E4)
 def run_adapt_sweep(args):
     """Adaptation time against the number of inserted blocks (the paper's
@@ -1023,7 +1102,8 @@ def main():
                     help="collide-stream kernel: 0 auto, 1 one-pass, 2/3 pipelined stages")
     ap.add_argument("--workload", default="cavity",
                     choices=["cavity", "cylinder", "batched", "learned", "compare", "strouhal",
-                             "adapt", "table"])
+                             "adapt", "table", "e6"])
+    ap.add_argument("--e6-steps", type=int, default=200)
     ap.add_argument("--st-steps", type=int, default=16000)
     ap.add_argument("--st-spinup", type=int, default=8000)
     ap.add_argument("--st-levels", type=int, default=3)
@@ -1060,6 +1140,9 @@ def main():
         return
     if args.workload == "table":
         print(json.dumps(run_table(args)))
+        return
+    if args.workload == "e6":
+        print(json.dumps(run_e6(args)))
         return
     if args.workload == "adapt":
         print(json.dumps(run_adapt_sweep(args)))

@@ -403,6 +403,49 @@ int amr_batch_autotune(amr_batch_t* b, int trial_steps, int* variant_out);
 int64_t amr_batch_launches(amr_batch_t* b);
 int amr_batch_free(amr_batch_t* b);
 
+/* ------------------------------------------------ cell-based uniform solver
+ * The cell arrangement of the paper's comparison of cell- and block-based
+ * grids on a single level (Section 5, "Cell vs. Block Arrangement"): a
+ * uniform grid of nx x ny (x nz) cells, periodic in every axis, in which
+ * every cell is its own element.  One kernel launch per time step: BGK
+ * collision with tau = 3 nu0 + 1/2 (FP32 arithmetic) and push streaming of
+ * each post-collision population f*_p to the element one link c_p
+ * downstream.  Populations: two caller-owned device buffers f_a, f_b of
+ * q * n FP32 values, [q][n] by element ID (n = nx ny, or nx ny nz in 3D).
+ *
+ * Element IDs are a permutation of the cell positions (x-fastest position
+ * i = x + nx (y + ny z)): id_of_pos[i] is the ID of the cell at position i.
+ * Connectivity:
+ *   AMR_CELLS_CALCULATED  IDs are the positions themselves; a thread derives
+ *                         the downstream IDs from its own ID (no table).
+ *   AMR_CELLS_RETRIEVED   downstream IDs are read from table[p * n + id]
+ *                         (device, int32, q * n entries, caller-owned), as
+ *                         filled by amr_cells_table for the same grid.
+ *
+ * amr_cells_table (host only, no GPU): fills the caller's host array
+ *   table[q * n] with table[p * n + id_of_pos[i]] = id_of_pos[j], j the
+ *   position one link c_p downstream of position i (periodic).  id_of_pos
+ *   (host, n entries) may be NULL for the x-fastest numbering.  AMR_E_INVAL
+ *   when id_of_pos is not a permutation of 0 .. n-1 (nothing written beyond
+ *   what was checked), for an unsupported velocity set, an empty grid, or
+ *   n >= 2^31.
+ * amr_cells_step: n_steps steps on `stream` (asynchronous); step k reads
+ *   f_a and writes f_b when k is even, the reverse when k is odd, so the
+ *   result of an odd count is in f_b.  AMR_E_INVAL for a null or aliased
+ *   buffer, a missing table with AMR_CELLS_RETRIEVED, n_steps < 0 or
+ *   nu0 <= 0; AMR_E_CUDA when a launch fails.  A table that amr_cells_table
+ *   did not fill for this grid is undefined behaviour.
+ * amr_cells_rest: writes the rest equilibrium (rho = 1, u = 0: f_p = w_p)
+ *   into the device buffer f of q * n FP32 values (asynchronous on `stream`);
+ *   AMR_E_INVAL for a null buffer or a grid amr_cells_table rejects. */
+#define AMR_CELLS_CALCULATED 0
+#define AMR_CELLS_RETRIEVED 1
+int amr_cells_table(int dim, int q, int nx, int ny, int nz, const int32_t* id_of_pos,
+                    int32_t* table);
+int amr_cells_step(int dim, int q, int nx, int ny, int nz, int connectivity, double nu0,
+                   const int32_t* table, float* f_a, float* f_b, int n_steps, void* stream);
+int amr_cells_rest(int dim, int q, int nx, int ny, int nz, float* f, void* stream);
+
 const char* amr_strerror(int code);
 const char* amr_last_error(void);
 

@@ -23,6 +23,8 @@ FACE = {"noslip": 0, "moving": 1, "outlet": 2, "periodic": 3}
 AMR_RHO_U, AMR_F, AMR_BLOCKS, AMR_COORDS, AMR_NBR, AMR_NBR_CHILD, AMR_IDSETS, AMR_GAPS, \
     AMR_MASKS, AMR_COUNTS, AMR_MASS, AMR_FORCE, AMR_FEATURES = range(13)
 MLP_INPUTS, MLP_HIDDEN = 27, 64
+# connectivity of the cell-based uniform solver
+AMR_CELLS_CALCULATED, AMR_CELLS_RETRIEVED = 0, 1
 
 EXPORTED = ["amr_arena_bytes", "amr_init", "amr_step", "amr_adapt", "amr_fields",
             "amr_set_fields", "amr_profile", "amr_profile_read", "amr_free", "amr_strerror",
@@ -142,6 +144,13 @@ def load_library(path=LIB_PATH):
     lib.amr_batch_launches.restype = i64
     lib.amr_batch_free.argtypes = [vp]
     lib.amr_batch_free.restype = i32
+    lib.amr_cells_table.argtypes = [i32, i32, i32, i32, i32, vp, vp]
+    lib.amr_cells_table.restype = i32
+    lib.amr_cells_step.argtypes = [i32, i32, i32, i32, i32, i32, ctypes.c_double, vp, vp, vp,
+                                   i32, vp]
+    lib.amr_cells_step.restype = i32
+    lib.amr_cells_rest.argtypes = [i32, i32, i32, i32, i32, vp, vp]
+    lib.amr_cells_rest.restype = i32
     _lib = lib
     return lib
 
@@ -514,3 +523,88 @@ class Mlp:
         if rc != AMR_OK:
             raise AmrError(rc, "amr_mlp_infer")
         return prob
+
+
+def cells_table(dim, q, shape, id_of_pos=None):
+    """Neighbour table int32 [q][n] of the cell-based solver, filled by the
+    library on the host: entry [p][id of position i] is the ID of the
+    position one link c_p downstream of i (periodic).  id_of_pos: element ID
+    of each x-fastest position (None: the positions themselves)."""
+    lib = load_library()
+    shape = list(shape) + [1] * (3 - len(shape))
+    n = int(np.prod(shape))
+    table = np.empty(q * n, np.int32)
+    ids = None
+    if id_of_pos is not None:
+        ids = np.ascontiguousarray(id_of_pos, dtype=np.int32)
+        if ids.size != n:
+            raise AmrError(AMR_E_INVAL, "cells_table: id_of_pos has %d entries, not %d" % (ids.size, n))
+    rc = lib.amr_cells_table(dim, q, shape[0], shape[1], shape[2],
+                             None if ids is None else ids.ctypes.data_as(ctypes.c_void_p),
+                             table.ctypes.data_as(ctypes.c_void_p))
+    if rc != AMR_OK:
+        raise AmrError(rc, "amr_cells_table")
+    return table.reshape(q, n)
+
+
+class Cells:
+    """Cell-based uniform periodic solver (the cell arrangement of the
+    comparison of cell- and block-based grids): FP32 populations [q][n] by
+    element ID in two device buffers, and for the retrieved connectivity the
+    neighbour table on the device.  id_of_pos None selects the computed
+    connectivity with x-fastest IDs; otherwise neighbours are read from the
+    table built for those IDs."""
+
+    def __init__(self, dim, q, shape, nu0, id_of_pos=None, stream=None, device=None):
+        import torch
+        self.lib = load_library()
+        self.dim, self.q = dim, q
+        self.shape = list(shape)
+        self.dims = self.shape + [1] * (3 - len(self.shape))
+        self.n = int(np.prod(self.shape))
+        self.nu0 = float(nu0)
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.ids = None if id_of_pos is None else np.ascontiguousarray(id_of_pos, dtype=np.int32)
+        self.connectivity = AMR_CELLS_CALCULATED if self.ids is None else AMR_CELLS_RETRIEVED
+        self.table = None
+        if self.ids is not None:
+            self.table = torch.from_numpy(cells_table(dim, q, self.shape, self.ids)).to(dev)
+        self.buf = [torch.empty(q * self.n, dtype=torch.float32, device=dev) for _ in range(2)]
+        self.cur = 0
+
+    def set_rest(self):
+        """Rest equilibrium (rho = 1, u = 0) in every cell."""
+        rc = self.lib.amr_cells_rest(self.dim, self.q, self.dims[0], self.dims[1], self.dims[2],
+                                     ctypes.c_void_p(self.buf[self.cur].data_ptr()),
+                                     ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_cells_rest")
+
+    def set_f(self, f_pos):
+        """Load populations given per x-fastest position, array [n, q]."""
+        import torch
+        f_pos = np.asarray(f_pos, np.float32).reshape(self.n, self.q)
+        f_id = np.empty((self.q, self.n), np.float32)
+        if self.ids is None:
+            f_id[:] = f_pos.T
+        else:
+            f_id[:, self.ids] = f_pos.T
+        self.buf[self.cur].copy_(torch.from_numpy(f_id.reshape(-1)))
+
+    def f(self):
+        """Populations per x-fastest position, array [n, q] (synchronises)."""
+        f_id = self.buf[self.cur].cpu().numpy().reshape(self.q, self.n)
+        return (f_id if self.ids is None else f_id[:, self.ids]).T.copy()
+
+    def step(self, n=1):
+        a, b = self.buf[self.cur], self.buf[1 - self.cur]
+        rc = self.lib.amr_cells_step(
+            self.dim, self.q, self.dims[0], self.dims[1], self.dims[2], self.connectivity,
+            self.nu0, None if self.table is None else ctypes.c_void_p(self.table.data_ptr()),
+            ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), int(n),
+            ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_cells_step")
+        self.cur ^= int(n) & 1

@@ -74,3 +74,59 @@ def test_init_rejects_small_arena_without_gpu(lib):
     h = ctypes.c_void_p()
     rc = lib.amr_init(ctypes.byref(c), ctypes.c_void_p(256), 1024, None, ctypes.byref(h))
     assert rc == AMR_E_ARENA and not h.value
+
+
+# ------------------------------------------------ cell-based uniform solver
+def brute_force_cell_table(vs, shape, ids):
+    """table[p][id of position i] = id of the position one link c_p downstream
+    of i, periodic, by direct coordinate arithmetic."""
+    import numpy as np
+    pos = W.grid_positions(shape)
+    n = len(pos)
+    ids = np.arange(n) if ids is None else ids
+    stride = [1, shape[0], shape[0] * shape[1]]
+    out = np.full((vs.q, n), -1, np.int64)
+    for p in range(vs.q):
+        tgt = (pos + vs.c[p][:len(shape)]) % np.array(shape)
+        j = sum(tgt[:, a] * stride[a] for a in range(len(shape)))
+        out[p, ids] = ids[j]
+    return out
+
+
+@pytest.mark.parametrize("dim,q,shape", [(2, 9, [6, 5]), (3, 19, [4, 3, 5]), (3, 27, [3, 4, 2])])
+@pytest.mark.parametrize("arrangement", W.CELL_ARRANGEMENTS)
+def test_cells_table_matches_geometry(lib, dim, q, shape, arrangement):
+    import numpy as np
+    from oracle.lattice import VelocitySet
+    from paper_2308_08085_gb300.amr import cells_table
+    ids = W.cell_ids(shape, arrangement, seed=3)
+    got = cells_table(dim, q, shape, ids)
+    want = brute_force_cell_table(VelocitySet(dim, q), shape, ids)
+    assert np.array_equal(got, want)
+    # every row is a permutation (push streaming writes each slot once)
+    assert all(np.array_equal(np.sort(r), np.arange(got.shape[1])) for r in got)
+
+
+def test_cells_rejects_bad_input_without_gpu(lib):
+    import numpy as np
+    from paper_2308_08085_gb300.amr import AMR_E_INVAL
+    n = 4 * 4
+    table = np.empty(9 * n, np.int32)
+    dup = np.arange(n, dtype=np.int32)
+    dup[3] = 2
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    assert lib.amr_cells_table(2, 9, 4, 4, 1, vp(dup), vp(table)) == AMR_E_INVAL
+    assert b"permutation" in lib.amr_last_error()
+    out_of_range = np.arange(n, dtype=np.int32)
+    out_of_range[0] = n
+    assert lib.amr_cells_table(2, 9, 4, 4, 1, vp(out_of_range), vp(table)) == AMR_E_INVAL
+    assert lib.amr_cells_table(3, 15, 4, 4, 4, None, vp(table)) == AMR_E_INVAL
+    assert lib.amr_cells_table(2, 9, 0, 4, 1, None, vp(table)) == AMR_E_INVAL
+    buf = ctypes.c_void_p(4096)     # never dereferenced: every call below is rejected first
+    assert lib.amr_cells_step(2, 9, 4, 4, 1, 7, 0.1, None, buf, ctypes.c_void_p(8192), 1,
+                              None) == AMR_E_INVAL
+    assert lib.amr_cells_step(2, 9, 4, 4, 1, 0, 0.1, None, buf, buf, 1, None) == AMR_E_INVAL
+    assert lib.amr_cells_step(2, 9, 4, 4, 1, 1, 0.1, None, buf, ctypes.c_void_p(8192), 1,
+                              None) == AMR_E_INVAL
+    assert lib.amr_cells_step(2, 9, 4, 4, 1, 0, 0.0, None, buf, ctypes.c_void_p(8192), 1,
+                              None) == AMR_E_INVAL

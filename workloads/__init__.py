@@ -154,22 +154,27 @@ def slab_marks(level, status, corner_z, lvl, width, centre, half, p_extra, seed)
     return m
 
 
-def root_positions(cfg):
-    """Integer positions (bx, by[, bz]) of the root blocks in x-fastest order."""
-    d = cfg["dim"]
-    n = [cfg["nx"] // 4, cfg["ny"] // 4] + ([cfg["nz"] // 4] if d == 3 else [])
-    idx = np.arange(int(np.prod(n)))
-    pos = [idx % n[0], (idx // n[0]) % n[1]]
-    if d == 3:
-        pos.append(idx // (n[0] * n[1]))
+def grid_positions(shape):
+    """Integer positions of the points of a grid of `shape` (2 or 3 extents)
+    in x-fastest order, one row per point."""
+    idx = np.arange(int(np.prod(shape)))
+    pos = [idx % shape[0], (idx // shape[0]) % shape[1]]
+    if len(shape) == 3:
+        pos.append(idx // (shape[0] * shape[1]))
     return np.stack(pos, axis=1)
 
 
-def morton_root_ids(cfg):
-    """root_ids numbering the root blocks along the Morton (Z-order) curve:
-    the ID of the root at x-fastest position i is its rank in bit-interleaved
-    order of (bx, by[, bz])."""
-    pos = root_positions(cfg)
+def root_positions(cfg):
+    """Integer positions (bx, by[, bz]) of the root blocks in x-fastest order."""
+    d = cfg["dim"]
+    return grid_positions([cfg["nx"] // 4, cfg["ny"] // 4] + ([cfg["nz"] // 4] if d == 3 else []))
+
+
+def morton_ids(shape):
+    """IDs numbering the points of a grid (x-fastest positions) along the
+    Morton (Z-order) curve: the ID of the point at position i is its rank in
+    bit-interleaved order of its coordinates."""
+    pos = grid_positions(shape)
     key = np.zeros(len(pos), np.int64)
     for bit in range(21):
         for ax in range(pos.shape[1]):
@@ -179,10 +184,37 @@ def morton_root_ids(cfg):
     return ids
 
 
+def morton_root_ids(cfg):
+    """root_ids numbering the root blocks along the Morton (Z-order) curve."""
+    d = cfg["dim"]
+    return morton_ids([cfg["nx"] // 4, cfg["ny"] // 4] + ([cfg["nz"] // 4] if d == 3 else []))
+
+
 def shuffled_root_ids(cfg, seed):
     """root_ids of a seeded random numbering of the root blocks."""
     n = len(root_positions(cfg))
     return rng(seed).permutation(n).astype(np.int32)
+
+
+CELL_ARRANGEMENTS = ("calculated", "retrieved", "morton", "shuffled")
+
+
+def cell_ids(shape, arrangement, seed=0):
+    """Element IDs of the cells of a uniform grid (x-fastest positions) for
+    the cell-based arrangements of the cell-versus-block comparison: None for
+    the x-fastest numbering with computed neighbours ('calculated'), the
+    identity ('retrieved': the same numbering, neighbours from a table), the
+    Morton numbering, or a seeded shuffle."""
+    n = int(np.prod(shape))
+    if arrangement == "calculated":
+        return None
+    if arrangement == "retrieved":
+        return np.arange(n, dtype=np.int32)
+    if arrangement == "morton":
+        return morton_ids(shape)
+    if arrangement == "shuffled":
+        return rng(seed).permutation(n).astype(np.int32)
+    raise ValueError(arrangement)
 
 
 # ------------------------------------------------------- named configurations
