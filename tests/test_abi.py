@@ -130,3 +130,24 @@ def test_cells_rejects_bad_input_without_gpu(lib):
                               None) == AMR_E_INVAL
     assert lib.amr_cells_step(2, 9, 4, 4, 1, 0, 0.0, None, buf, ctypes.c_void_p(8192), 1,
                               None) == AMR_E_INVAL
+
+
+def test_root_ids_and_interp_validated_on_host(lib):
+    import numpy as np
+    from paper_2308_08085_gb300.amr import AMR_E_INVAL, make_config
+    cfg = W.cavity(dim=2, n=16)
+    for bad in ([0, 1, 2, 2] + list(range(4, 16)), [16] + list(range(1, 16)),
+                [-1] + list(range(1, 16))):
+        cfg["root_ids"] = np.array(bad, np.int32)
+        c = make_config(cfg)
+        assert lib.amr_arena_bytes(ctypes.byref(c)) == 0
+        assert b"permutation" in lib.amr_last_error()
+        h = ctypes.c_void_p()
+        assert lib.amr_init(ctypes.byref(c), ctypes.c_void_p(256), 1 << 40, None,
+                            ctypes.byref(h)) == AMR_E_INVAL and not h.value
+    cfg["root_ids"] = W.shuffled_root_ids(cfg, 1)
+    assert lib.amr_arena_bytes(ctypes.byref(make_config(cfg))) > 0
+    c = make_config(W.cavity(dim=3, q=19, n=16))
+    for interp, ok in ((0, True), (3, True), (1, False), (2, False), (-1, False)):
+        c.interp = interp
+        assert (lib.amr_arena_bytes(ctypes.byref(c)) > 0) == ok, interp
