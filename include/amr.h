@@ -425,10 +425,9 @@ int amr_batch_free(amr_batch_t* b);
  * amr_cells_table (host only, no GPU): fills the caller's host array
  *   table[q * n] with table[p * n + id_of_pos[i]] = id_of_pos[j], j the
  *   position one link c_p downstream of position i (periodic).  id_of_pos
- *   (host, n entries) may be NULL for the x-fastest numbering.  AMR_E_INVAL
- *   when id_of_pos is not a permutation of 0 .. n-1 (nothing written beyond
- *   what was checked), for an unsupported velocity set, an empty grid, or
- *   n >= 2^31.
+ *   (host, n entries) may be NULL for the x-fastest numbering.  AMR_E_INVAL,
+ *   with nothing written, when id_of_pos is not a permutation of 0 .. n-1,
+ *   for an unsupported velocity set, an empty grid, or n >= 2^31.
  * amr_cells_step: n_steps steps on `stream` (asynchronous); step k reads
  *   f_a and writes f_b when k is even, the reverse when k is odd, so the
  *   result of an odd count is in f_b.  AMR_E_INVAL for a null or aliased
