@@ -59,3 +59,12 @@ def test_centreline_profiles_sample_the_leaf_cells():
     assert np.all(np.abs(vx - 0.01 * s) <= 0.01 * 0.5 + 1e-12)
     assert np.all(np.abs(vz - 0.02 * s) <= 0.02 * 0.5 + 1e-12)
     assert np.all(np.diff(vx) >= -1e-12) and np.all(np.diff(vz) >= -1e-12)
+
+
+def test_ncu_traffic_figure_matches_the_kernel_source():
+    """The DRAM traffic per update that the bench line reports was captured by
+    ncu on the kernel source with this hash; after a change to the kernel the
+    figure is stale (the bench then reports null) until it is captured again."""
+    assert bench.kernel_source_sha() == bench.NCU_SOURCE_SHA, (
+        "collide-stream source changed: capture its DRAM traffic again and update "
+        "NCU_TRAFFIC_PER_UPDATE / NCU_SOURCE_SHA")
