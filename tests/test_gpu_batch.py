@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from cellwise import assert_cells, oracle_classes
 from oracle.lattice import equilibrium
 from oracle.solver import ForestLBM
 
@@ -113,6 +114,7 @@ def test_batch_member_matches_oracle_and_autotune():
     got = members[1].populations()[ids]
     err = np.linalg.norm(got - ref.f[ids]) / np.linalg.norm(ref.f[ids])
     assert err <= 1e-12, err
+    assert_cells(got, ref.f[ids], oracle_classes(ref.mesh, ids), ref.vs.w, "f64")
     assert batch.launches() > 0
     batch.close()
 

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from cellwise import CELL_TOL
 from oracle.lattice import VelocitySet, bgk_collide, equilibrium, tau_level
 from oracle.uniform import UniformLBM
 
@@ -72,6 +73,9 @@ def test_cells_match_uniform_oracle(dim, q, shape, arrangement):
         want = to_positions(ref.f)
         err = rel_l2(got, want)
         assert err < TOL_F32, (arrangement, done, err)
+        # worst cell (a uniform periodic grid has interior cells only)
+        cell = np.max(np.abs(got - want) / np.maximum(np.abs(want), vs.w[None, :]))
+        assert cell <= CELL_TOL["f32"], (arrangement, done, cell)
 
 
 def test_cells_full_size_arrangements_agree_and_sampled_cells():

@@ -28,6 +28,7 @@ import pytest
 
 import fullsize_cases as FC
 import workloads as W
+from cellwise import assert_cells
 from oracle.lattice import VelocitySet, equilibrium, velocities
 
 torch = pytest.importorskip("torch")
@@ -42,13 +43,18 @@ def _lib():
     b.build()
 
 
-def per_level_errors(gpu, ids, want, lmax):
+def per_level_errors(gpu, ids, want, lmax, storage):
     """Relative L2 per level over the cells of the sampled blocks that carry
     the method's result (covered cells of refined blocks are left over), and
-    the same split into leaves and refined blocks for the message."""
+    the same split into leaves and refined blocks for the message.  The worst
+    cell of each class (ghost, interface, interior) is held to the per-cell
+    bar as well."""
     blk = gpu.blocks()
-    valid = FC.valid_cells(ids, blk["status"], blk["child0"], gpu.masks(), gpu.dim)
+    masks = gpu.masks()
+    valid = FC.valid_cells(ids, blk["status"], blk["child0"], masks, gpu.dim)
     got = gpu.populations()[ids]
+    vs = VelocitySet(gpu.dim, gpu.q)
+    assert_cells(got, want, masks[ids], vs.w, storage, valid=valid, what="sampled blocks")
     levels = blk["level"][ids]
     leaf = blk["status"][ids] == 1
     with_leaves = set(blk["level"][blk["status"] == 1].tolist())
@@ -78,7 +84,7 @@ def test_cavity2d_full_run_matches_oracle(golden_dir):
         gpu.adapt()
         assert gpu.counts()["n_ids"] == want["counts"][t].tolist(), t
         assert FC.gpu_digest(gpu) == str(want["digests"][t]), "mesh tables differ after adaptation %d" % t
-    err, detail = per_level_errors(gpu, want["ids"], want["f"], cfg["max_levels"])
+    err, detail = per_level_errors(gpu, want["ids"], want["f"], cfg["max_levels"], "f64")
     assert max(err.values()) <= 1e-12, detail
     gpu.close()
 
@@ -101,7 +107,7 @@ def test_cavity3d_full_size_step_matches_oracle(golden_dir):
     gpu.set_populations(f)
     del f
     gpu.step(1)
-    err, detail = per_level_errors(gpu, want["ids"], want["f"], cfg["max_levels"])
+    err, detail = per_level_errors(gpu, want["ids"], want["f"], cfg["max_levels"], "f32")
     assert max(err.values()) <= 1e-5, detail
     gpu.close()
 
@@ -116,7 +122,7 @@ def test_cavity3d_cut_run_matches_oracle(golden_dir):
         gpu.adapt()
         assert gpu.counts()["n_ids"] == want["counts"][t].tolist(), t
         assert FC.gpu_digest(gpu) == str(want["digests"][t]), "mesh tables differ after adaptation %d" % t
-    err, detail = per_level_errors(gpu, want["ids"], want["f"], cfg["max_levels"])
+    err, detail = per_level_errors(gpu, want["ids"], want["f"], cfg["max_levels"], "f64")
     assert max(err.values()) <= 1e-12, detail
     gpu.close()
     gpu = AmrLBM(cfg, storage="f32")
@@ -124,7 +130,7 @@ def test_cavity3d_cut_run_matches_oracle(golden_dir):
         gpu.step(FC.C1CUT_EVERY)
         gpu.adapt(torch.from_numpy(np.ascontiguousarray(want["marks"][t])).cuda())
         assert FC.gpu_digest(gpu) == str(want["digests"][t]), t
-    err, detail = per_level_errors(gpu, want["ids"], want["f"], cfg["max_levels"])
+    err, detail = per_level_errors(gpu, want["ids"], want["f"], cfg["max_levels"], "f32")
     assert max(err.values()) <= 1e-5, detail
     gpu.close()
 

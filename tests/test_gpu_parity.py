@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from cellwise import assert_cells, oracle_classes
 from oracle.forest import Forest
 from oracle.lattice import equilibrium
 from oracle.solver import ForestLBM
@@ -50,6 +51,15 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def check_fields(got, ref, ids, storage, what=""):
+    """Relative L2 over all compared cells within TOL, and the worst cell of
+    each class (ghost, interface, interior) within the per-cell bar."""
+    want = ref.f[ids]
+    err = rel_l2(got, want)
+    assert err <= TOL[storage], (what, storage, err)
+    assert_cells(got, want, oracle_classes(ref.mesh, ids), ref.vs.w, storage, what=what)
+
+
 def marks_tensor(m):
     return torch.from_numpy(np.ascontiguousarray(m, dtype=np.int8)).cuda()
 
@@ -84,9 +94,7 @@ def test_single_level_collide_stream(name, mk, storages, variant):
             ref.step(1)
             gpu.step(1)
         ids = ref.mesh.active_ids()
-        got = gpu.populations()[ids]
-        err = rel_l2(got, ref.f[ids])
-        assert err <= TOL[storage], (storage, err)
+        check_fields(gpu.populations()[ids], ref, ids, storage, name)
         gpu.close()
 
 
@@ -221,8 +229,7 @@ def test_three_level_step_2d(storage):
     ref2.sync()
     gpu.rho_u()                      # runs the level synchronisation
     ids = ref2.mesh.active_ids()
-    err = rel_l2(gpu.populations()[ids], ref2.f[ids])
-    assert err <= TOL[storage], err
+    check_fields(gpu.populations()[ids], ref2, ids, storage)
     gpu.close()
 
 
@@ -251,8 +258,7 @@ def two_level_case(cfg, storage, variant=0):
     ref.sync()
     gpu.rho_u()
     ids = ref.mesh.active_ids()
-    err = rel_l2(gpu.populations()[ids], ref.f[ids])
-    assert err <= TOL[storage], err
+    check_fields(gpu.populations()[ids], ref, ids, storage)
     gpu.close()
 
 
@@ -280,7 +286,7 @@ def test_cavity2d_criterion_end_to_end_f64():
     ids = ref.mesh.active_ids()
     rho_r, u_r = ref.macroscopic()
     assert rel_l2(u_g[ids], u_r[ids]) <= 1e-12
-    assert rel_l2(gpu.populations()[ids], ref.f[ids]) <= 1e-12
+    check_fields(gpu.populations()[ids], ref, ids, "f64")
     gpu.close()
 
 
@@ -292,7 +298,7 @@ def test_cavity3d_criterion_end_to_end_f64():
     ref.sync()
     gpu.rho_u()
     ids = ref.mesh.active_ids()
-    assert rel_l2(gpu.populations()[ids], ref.f[ids]) <= 1e-12
+    check_fields(gpu.populations()[ids], ref, ids, "f64")
     gpu.close()
 
 
@@ -308,7 +314,7 @@ def test_shuffled_roots_criterion_end_to_end_f64():
     ref.sync()
     gpu.rho_u()
     ids = ref.mesh.active_ids()
-    assert rel_l2(gpu.populations()[ids], ref.f[ids]) <= 1e-12
+    check_fields(gpu.populations()[ids], ref, ids, "f64")
     gpu.close()
 
 
@@ -348,7 +354,7 @@ def test_cavity_wall_distance_rule_end_to_end():
     ref.sync()
     gpu.rho_u()
     ids = ref.mesh.active_ids()
-    assert rel_l2(gpu.populations()[ids], ref.f[ids]) <= 1e-12
+    check_fields(gpu.populations()[ids], ref, ids, "f64")
     gpu.close()
 
 
@@ -366,7 +372,7 @@ def test_cylinder_distance_rule_force_end_to_end(span_periodic):
     ref.sync()
     gpu.rho_u()
     ids = ref.mesh.active_ids()
-    assert rel_l2(gpu.populations()[ids], ref.f[ids]) <= 1e-12
+    check_fields(gpu.populations()[ids], ref, ids, "f64")
     f_ref = ref.mea_force()
     f_gpu = gpu.force()
     assert abs(f_ref[0]) > 0
@@ -399,7 +405,7 @@ def test_cubic_criterion_end_to_end_2d_f64():
     ref.sync()
     gpu.rho_u()
     ids = ref.mesh.active_ids()
-    assert rel_l2(gpu.populations()[ids], ref.f[ids]) <= 1e-12
+    check_fields(gpu.populations()[ids], ref, ids, "f64")
     gpu.close()
 
 
@@ -412,7 +418,7 @@ def test_cubic_cylinder_end_to_end_f64():
     ref.sync()
     gpu.rho_u()
     ids = ref.mesh.active_ids()
-    assert rel_l2(gpu.populations()[ids], ref.f[ids]) <= 1e-12
+    check_fields(gpu.populations()[ids], ref, ids, "f64")
     f_ref, f_gpu = ref.mea_force(), gpu.force()
     assert np.max(np.abs(f_gpu - f_ref)) <= 1e-11 * np.max(np.abs(f_ref))
     gpu.close()
