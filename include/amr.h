@@ -27,6 +27,17 @@
  *   sentinels  AMR_NONE (-1): no same-level neighbour / no children;
  *              AMR_WALL(face) = -2 - face: the neighbour position leaves the
  *              domain through wall `face` (x-, x+, y-, y+, z-, z+ = 0..5).
+ *
+ * Stored populations.  The paper's state is the post-streaming
+ * (pre-collision) populations f_p(x) of every cell (Section 4.1).  The arena
+ * holds, for every cell y and direction p, the value that streams out of y
+ * along c_p: the post-collision f*_p(y) of the last step (the step is pulled:
+ * f_p(x) = f*_p(x - c_p)).  Where x - c_p is not a fluid cell of x's level (a
+ * coarse-fine interface, a wall, a solid cell) f_p(x) is kept in x's own slot
+ * of the opposite direction, with the link's boundary rule already applied.
+ * amr_fields(AMR_F / AMR_RHO_U / AMR_MASS) and amr_set_fields(AMR_F) convert:
+ * they read and write the paper's f_p(x); only the raw arena (checkpoints,
+ * amr_mass_audit_noalloc's inputs) is in the stored form.
  */
 #ifndef AMR_H
 #define AMR_H
@@ -100,16 +111,13 @@ typedef struct {
                               centre is strictly inside is solid               */
   amr_face faces[6];       /* x-, x+, y-, y+, z-, z+ (first 4 used in 2D)      */
   int32_t use_graphs;      /* 1: replay the coarse step as a CUDA graph         */
-  int32_t kernel_variant;  /* collide-stream kernel: 6 one-pass, 512-thread
-                              CTAs, push table read through L1; 0 (default):
-                              6, with 128-thread CTAs for launches of fewer
-                              cells than two waves and the 7 budget for D3Q27
-                              with 16-bit storage;
-                              1: 512 threads, table in shared memory; 4: 256
-                              threads, shared; 5: 256 threads, L1; 2 / 3: 2- /
-                              3-stage cp.async pipeline in a persistent grid;
-                              7: as 6 with 512 more resident threads per SM
-                              (tighter register budget)                        */
+  int32_t kernel_variant;  /* collide-stream kernel (fused BGK + pull
+                              streaming): 1 / 2 / 3 / 4: 512 / 256 / 128 /
+                              64 threads per CTA (8 / 4 / 2 / 1 blocks in 3D);
+                              5: 128 threads with 512 more resident threads
+                              per SM (tighter register budget); 0 (default):
+                              64 threads, with the tighter budget for D3Q27
+                              with 16-bit storage                              */
   double refine_dist;      /* distance refinement (Section 4.4): a leaf on level
                               L within refine_dist / 2^L (physical units) of a
                               target is marked for refinement; 0 = off        */
@@ -257,13 +265,19 @@ int amr_profile_read(amr_t* a, amr_kernel_profile* out, int max, int reset);
  * library's layout but no amr_t instance and no arena.
  *
  * Inputs (device pointers, owned by the caller): the two population buffers
- * f_a, f_b of `n_blocks` blocks in the AMR_F storage layout of `storage`
- * ([Q][n_blocks][4^dim], stored values; 16-bit storages hold f - w_p), a
- * per-level buffer choice `cur` (bit L set: blocks of level L are read from
- * f_b), and int32 level[n_blocks] / status[n_blocks] (AMR_BLOCKS rows 0 and
- * 1).  Output: out_dev[0 .. dim] (device, caller-owned) = the sum over leaf
- * blocks (status AMR_ST_UNREFINED) of rho V and rho u V, V = 2^(-dim level).
- * Asynchronous on `stream`.
+ * f_a, f_b of `n_blocks` blocks in this library's storage layout of
+ * `storage` ([Q][n_blocks][4^dim] stored values -- the outgoing
+ * post-collision populations, see "Stored populations" above; 16-bit
+ * storages hold value - w_p), a per-level buffer choice `cur` (bit L set:
+ * blocks of level L are read from f_b), int32 level[n_blocks] /
+ * status[n_blocks] (AMR_BLOCKS rows 0 and 1), the neighbour table
+ * nbr[n_blocks][32] (int32, 32 per block, the first 3^dim in the AMR_NBR
+ * order, the layout of the arena's table) and the solid-cell bits
+ * solidmask[n_blocks] (uint64, bit l = cell l; null when there are no solid
+ * cells).  Output: out_dev[0 .. dim] (device, caller-owned) = the sum over
+ * leaf blocks (status AMR_ST_UNREFINED) of rho V and rho u V,
+ * V = 2^(-dim level), rho and u the moments of the cell's pre-collision
+ * populations.  Asynchronous on `stream`.
  *
  * Scratch: a file-scope device array of AMR_NOALLOC_MAX_PARTIALS rows of 4
  * doubles (512 KiB), held by every GPU that loads the library until the
@@ -276,11 +290,13 @@ int amr_profile_read(amr_t* a, amr_kernel_profile* out, int max, int reset);
  * each call writes every row it reads, so nothing needs clearing, but calls
  * that overlap on the GPU (different streams, or different host threads)
  * race on it.  Calls no cudaMalloc, cudaFree or allocating library routine.
- * Errors: AMR_E_INVAL, AMR_E_CUDA. */
+ * Errors: AMR_E_INVAL, AMR_E_CUDA (also when a CUDA error from earlier work
+ * is already pending on the calling thread: it is left for its owner). */
 #define AMR_NOALLOC_MAX_PARTIALS 16384
 int amr_mass_audit_noalloc(int dim, int q, int storage, int64_t n_blocks,
                            const void* f_a, const void* f_b, uint32_t cur,
                            const int32_t* level, const int32_t* status,
+                           const int32_t* nbr, const uint64_t* solidmask,
                            double* out_dev, void* stream);
 
 /* Release host-side state (the arena stays owned by the caller). */

@@ -127,7 +127,7 @@ def load_library(path=LIB_PATH):
     lib.amr_propose_marks.argtypes = [vp, vp, ctypes.c_float, i32, vp]
     lib.amr_propose_marks.restype = i32
     lib.amr_mass_audit_noalloc.argtypes = [i32, i32, i32, i64, vp, vp, ctypes.c_uint32, vp, vp,
-                                           vp, vp]
+                                           vp, vp, vp, vp]
     lib.amr_mass_audit_noalloc.restype = i32
     pp = ctypes.POINTER(vp)
     lib.amr_batch_arena_bytes.argtypes = [pp, i32]

@@ -93,6 +93,8 @@ struct Instance {
   // adaptation phase boundaries of the current amr_adapt call (profiling on)
   std::vector<std::pair<int, cudaEvent_t>> phase_marks;
 
+  // solid-cell bits for the kernels (null: no solid cells in this instance)
+  const uint64_t* sm() const { return solid ? solidmask : nullptr; }
   // interpolation mode bit of LbmOps::interp for this configuration
   int interp_bits() const { return cfg.interp == AMR_INTERP_CUBIC ? 2 : 0; }
   size_t f_bytes() const { return (size_t)cap * M * q * elem; }

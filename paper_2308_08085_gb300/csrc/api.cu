@@ -281,7 +281,9 @@ static int drain_profile(Instance* a) {
 static double ratio_cf(const Instance* a, int L) { return a->tau[L + 1] / (2.0 * a->tau[L]); }
 static double ratio_fc(const Instance* a, int L) { return 2.0 * a->tau[L] / a->tau[L + 1]; }
 
-static void collide_stream_level(Instance* a, int L) {
+// ghost_in: the first substep of level L > 0, whose ghost cells read the
+// values the level step's interpolation left in their own output slots
+static void collide_stream_level(Instance* a, int L, bool ghost_in) {
   const int64_t n = a->n_active[L];
   // the parity flips even without active blocks: graph replay and batches
   // rely on level 0 flipping once and deeper levels an even number of times
@@ -294,13 +296,19 @@ static void collide_stream_level(Instance* a, int L) {
   {
     ProfScope ps(a, PK_COLLIDE, (double)n * a->M * 2.0 * a->q * a->elem, (double)n * a->M);
     a->ops->collide_stream(a->stream, a->active + (size_t)L * a->cap, (int)n, a->fbuf(L, 0),
-                           a->fbuf(L, 1), a->nbr, a->solidmask, prm, a->solid);
+                           a->fbuf(L, 1), a->nbr, a->sm(), prm, a->solid,
+                           ghost_in ? a->cellmask : nullptr);
     a->launches += 1;
   }
   a->cur ^= 1u << L;
 }
 
-static void advance(Instance* a, int L) {
+// Recursive level step (Section 4.1): interpolate into level L+1, collide and
+// stream level L, advance level L+1 twice, average level L+1 into level L.
+// The interpolation writes the ghost cells' values at time t into their own
+// slots of level L+1's output buffer; the first of the two substeps of level
+// L+1 (`first`) reads them there.
+static void advance(Instance* a, int L, bool first) {
   const bool fine = L + 1 < a->lmax && a->n_ids[L + 1] > 0;
   const int64_t np = a->n_parents[L];
   if (fine && np > 0) {
@@ -310,14 +318,14 @@ static void advance(Instance* a, int L) {
     ProfScope ps(a, PK_INTERP,
                  ((double)a->n_ghost_children[L] * a->nc + cells) * a->q * a->elem, cells);
     a->ops->interp(a->stream, a->parents + (size_t)L * a->cap, (int)np, a->fbuf(L, 0),
-                   a->fbuf(L + 1, 0), a->stride(), a->child0, a->cellmask, a->solidmask,
-                   ratio_cf(a, L), a->interp_bits(), a->solid);
+                   a->fbuf(L + 1, 1), a->stride(), a->child0, a->cellmask, a->nbr, a->sm(),
+                   nullptr, nullptr, ratio_cf(a, L), 4 | a->interp_bits(), a->solid);
     a->launches += 1;
   }
-  collide_stream_level(a, L);
+  collide_stream_level(a, L, first && L > 0 && a->n_parents[L - 1] > 0);
   if (fine) {
-    advance(a, L + 1);
-    advance(a, L + 1);
+    advance(a, L + 1, true);
+    advance(a, L + 1, false);
     if (np > 0) {
       // algorithmic bytes: interface fine cells (read) and their parent
       // cells, one per 2^D children (written)
@@ -330,11 +338,11 @@ static void advance(Instance* a, int L) {
       if (a->interp_bits())
         a->ops->average(a->stream, a->parents + (size_t)L * a->cap, (int)np, true,
                         a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0, a->parent,
-                        a->cellmask, a->status, a->solidmask, ratio_fc(a, L), 1, a->solid);
+                        a->cellmask, a->status, a->nbr, a->sm(), ratio_fc(a, L), 1, a->solid);
       else
         a->ops->average(a->stream, a->bnd + (size_t)(L + 1) * a->cap, (int)a->n_bnd[L + 1],
                         false, a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0,
-                        a->parent, a->cellmask, a->status, a->solidmask, ratio_fc(a, L), 0,
+                        a->parent, a->cellmask, a->status, a->nbr, a->sm(), ratio_fc(a, L), 0,
                         a->solid);
       a->launches += 1;
     }
@@ -374,7 +382,7 @@ static int build_graphs(Handle* h) {
       h->capturing = true;
       h->capture_parity = parity;
       const int64_t before = h->launches;
-      advance(h, 0);
+      advance(h, 0, false);
       h->graph_launches[parity] = h->launches - before;
       h->launches = before;
       h->capturing = false;
@@ -404,14 +412,15 @@ static void level_sync(Instance* a) {
     if (a->n_ids[L + 1] == 0) continue;
     a->ops->average(a->stream, a->idset + (size_t)L * a->cap, (int)a->n_ids[L], true,
                     a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0, a->parent,
-                    a->cellmask, a->status, a->solidmask, ratio_fc(a, L), 1, a->solid);
+                    a->cellmask, a->status, a->nbr, a->sm(), ratio_fc(a, L), 1, a->solid);
     a->launches += 1;
   }
   for (int L = 0; L + 1 < a->lmax; ++L) {
     if (a->n_parents[L] == 0) continue;
     a->ops->interp(a->stream, a->parents + (size_t)L * a->cap, (int)a->n_parents[L],
                    a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0, a->cellmask,
-                   a->solidmask, ratio_cf(a, L), a->interp_bits(), a->solid);
+                   a->nbr, a->sm(), nullptr, nullptr, ratio_cf(a, L), a->interp_bits(),
+                   a->solid);
     a->launches += 1;
   }
 }
@@ -423,7 +432,7 @@ static int criterion_into_marks(Instance* a) {
     if (a->n_ids[L] == 0) continue;
     const double inv_dx = a->cfg.nx * std::ldexp(1.0, L) / a->cfg.length_x;
     a->ops->criterion(a->stream, a->idset + (size_t)L * a->cap, (int)a->n_ids[L],
-                      a->fbuf(L, 0), a->stride(), a->status, L, a->lmax, inv_dx,
+                      a->fbuf(L, 0), a->stride(), a->nbr, a->sm(), a->status, L, a->lmax, inv_dx,
                       a->cfg.crit_start, a->cfg.crit_inc, a->marks, a->w2);
     a->launches += 1;
   }
@@ -442,7 +451,7 @@ static int features_all(Instance* a) {
     if (a->n_ids[L] == 0) continue;
     const double inv_dx = a->cfg.nx * std::ldexp(1.0, L) / a->cfg.length_x;
     a->ops->features(a->stream, a->idset + (size_t)L * a->cap, (int)a->n_ids[L], a->fbuf(L, 0),
-                     a->stride(), L, a->lmax, inv_dx, a->features);
+                     a->stride(), a->nbr, a->sm(), L, a->lmax, inv_dx, a->features);
     a->launches += 1;
   }
   AMR_CUDA(cudaGetLastError());
@@ -679,7 +688,7 @@ int amr_step(amr_t* h, int n) {
       a->last_parity = parity;
       a->cur ^= 1u;   // levels >= 1 flip an even number of times per coarse step
     } else {
-      advance(a, 0);
+      advance(a, 0, false);
     }
     a->coarse_steps += 1;
   }
@@ -769,7 +778,7 @@ int64_t amr_fields(amr_t* h, int what, void* dst, size_t dst_bytes, int dst_on_d
     double* out_dev = a->red + 8000;
     if (what == AMR_MASS) {
       const int g = a->ops->mass_partial(s, cap, a->f[0], a->f[1], a->cur, a->level, a->status,
-                                         a->red);
+                                         a->nbr, a->sm(), a->red);
       k_sum_partials<<<1, 256, 0, s>>>(g, 4, a->red, out_dev);
     } else {
       AMR_CUDA(cudaMemsetAsync(out_dev + 4, 0, 3 * 8, s));
@@ -823,9 +832,11 @@ int64_t amr_fields(amr_t* h, int what, void* dst, size_t dst_bytes, int dst_on_d
   if (what == AMR_RHO_U) level_sync(a);
   if (dst_on_device) {
     if (what == AMR_RHO_U) {
-      a->ops->export_rho_u(s, cap, 0, cap, a->f[0], a->f[1], a->cur, a->level, (double*)dst);
+      a->ops->export_rho_u(s, cap, 0, cap, a->f[0], a->f[1], a->cur, a->level, a->nbr, a->sm(),
+                           (double*)dst);
     } else if (what == AMR_F) {
-      a->ops->export_f(s, cap, 0, cap, a->f[0], a->f[1], a->cur, a->level, (double*)dst);
+      a->ops->export_f(s, cap, 0, cap, a->f[0], a->f[1], a->cur, a->level, a->nbr, a->sm(),
+                       (double*)dst);
     } else {
       int rc = mesh_export(a, what, dst);
       if (rc != AMR_OK) return rc;
@@ -841,11 +852,12 @@ int64_t amr_fields(amr_t* h, int what, void* dst, size_t dst_bytes, int dst_on_d
       const int64_t nb = std::min(chunk, cap - b0);
       double* st = (double*)a->staging;
       if (what == AMR_RHO_U) {
-        a->ops->export_rho_u(s, cap, b0, nb, a->f[0], a->f[1], a->cur, a->level, st);
+        a->ops->export_rho_u(s, cap, b0, nb, a->f[0], a->f[1], a->cur, a->level, a->nbr, a->sm(),
+                             st);
         AMR_CUDA(cudaMemcpyAsync((char*)dst + b0 * per_block, st, nb * per_block,
                                  cudaMemcpyDeviceToHost, s));
       } else {
-        a->ops->export_f(s, cap, b0, nb, a->f[0], a->f[1], a->cur, a->level, st);
+        a->ops->export_f(s, cap, b0, nb, a->f[0], a->f[1], a->cur, a->level, a->nbr, a->sm(), st);
         AMR_CUDA(cudaMemcpy2DAsync((char*)dst + b0 * M * 8, (size_t)cap * M * 8, st,
                                    (size_t)nb * M * 8, (size_t)nb * M * 8, Q,
                                    cudaMemcpyDeviceToHost, s));
@@ -897,7 +909,8 @@ int amr_set_fields(amr_t* h, int what, const void* src, size_t src_bytes, int sr
   }
   cudaStream_t s = a->stream;
   if (src_on_device) {
-    a->ops->import_f(s, cap, 0, cap, a->f[0], a->f[1], a->cur, a->level, (const double*)src);
+    a->ops->import_f(s, cap, 0, cap, a->f[0], a->f[1], a->cur, a->level, a->nbr, a->sm(),
+                     (const double*)src);
   } else {
     const int64_t per_block = (int64_t)M * Q * 8;
     const int64_t chunk = std::max<int64_t>(1, (int64_t)STAGING_BYTES / per_block);
@@ -907,7 +920,7 @@ int amr_set_fields(amr_t* h, int what, const void* src, size_t src_bytes, int sr
       AMR_CUDA(cudaMemcpy2DAsync(st, (size_t)nb * M * 8, (const char*)src + b0 * M * 8,
                                  (size_t)cap * M * 8, (size_t)nb * M * 8, Q,
                                  cudaMemcpyHostToDevice, s));
-      a->ops->import_f(s, cap, b0, nb, a->f[0], a->f[1], a->cur, a->level, st);
+      a->ops->import_f(s, cap, b0, nb, a->f[0], a->f[1], a->cur, a->level, a->nbr, a->sm(), st);
       AMR_CUDA(cudaGetLastError());
       AMR_CUDA(cudaStreamSynchronize(s));
     }

@@ -1,10 +1,33 @@
-// Fused collide + stream of one level (Sections 4.2, 4.3): the push-target
-// tables, the per-cell BGK collision and push, and the kernel variants that
-// drive it (one-pass, cp.async pipelined, bulk-copy staged).  Included by
-// lbm_kernels.cuh.
+// Fused collide + stream of one level (Sections 4.2, 4.3) in pull form, and
+// the link tables and the gather / scatter of a cell's populations that every
+// other kernel uses to read or write the state.  Included by lbm_kernels.cuh.
 //
-// Population layout (every storage type): f[p * stride + b * M + l], stride =
+// Population layout (every storage type): g[p * stride + b * M + l], stride =
 // capacity * M, M = 4^D cells per block, l = i + 4 j + 16 k.
+//
+// What is stored.  The paper stores the post-streaming (pre-collision)
+// populations f(x, t) of every cell.  This library stores, for every cell y
+// and direction p, the value that will stream out of y along c_p: the
+// post-collision f*_p(y) of the last step.  The pre-collision state is
+// therefore spread over the neighbours and is read by a gather:
+//
+//   f_p(x) = g_p(x - c_p)        when x - c_p is a fluid cell of the same level
+//          = g_pbar(x)           otherwise (no same-level block there -- the
+//                                coarse-fine interface --, a wall, or a solid
+//                                cell), pbar the opposite of p.
+//
+// In the second case the slot g_pbar(x) holds the value that bounced back
+// into x: the step that wrote it applied the boundary rule of the link (the
+// moving-wall term or the anti-bounce-back outlet value, Section 2), so the
+// gather needs no boundary arithmetic.  Writing a pre-collision value f_p(x)
+// (interpolation, averaging, imports) is the scatter into the same slot.
+// Each slot is the source of exactly one (cell, direction) pair, so gathers
+// and scatters of different cells never collide, and the whole method
+// (interpolation, averaging, criterion, exports) sees exactly the state of
+// the paper's formulation.  The fused step reads its Q values through the
+// gather (loads shifted across block edges, served by L1/L2) and writes all
+// Q post-collision values of a cell to its own slots: every store is a whole
+// row of the block, and no store crosses a block edge.
 #pragma once
 #include "lattice.cuh"
 #include "lbm_ops.h"
@@ -16,7 +39,7 @@ namespace amr {
 constexpr int ST_UNREFINED = 1;
 constexpr int ST_REFINED = 2;
 constexpr int CLS_INTERIOR = 0, CLS_INTERFACE = 1, CLS_GHOST = 2;
-constexpr int FACE_OUTLET = 2;
+constexpr int FACE_NOSLIP = 0, FACE_OUTLET = 2;
 
 // geometric neighbour code (sx+1) + 3 (sy+1) [+ 9 (sz+1)] -> neighbour index k
 struct GeoTable {
@@ -40,110 +63,197 @@ __device__ __forceinline__ int geo_to_k(int code) {
   return D == 2 ? c_geo2.k_of_code[code] : c_geo3.k_of_code[code];
 }
 
-
-// Push targets of the fused collide-stream: for direction p and cell l the
-// entry packs the geometric code of the block that holds x + c_p (5 bits)
-// and the cell index inside it (6 bits): e = code | (cell << 5).
+// Link tables: for direction p and cell l, the block that holds the cell
+// x + s c_p (s = +1: the target of the link leaving x, s = -1: the source of
+// the link arriving at x) and the cell index inside it, packed as
+// e = blk | (cell << 5).  blk is the geometric code of the neighbour block
+// (0 .. 3^D - 1, centre = the block itself) or, in the _K tables, its index
+// k in the block's neighbour row (0 = the block itself).
 template <int D, int Q>
-struct StreamTable {
+struct LinkTable {
   uint16_t e[Q * Block<D>::M];
 };
-template <int D, int Q, bool BY_K = false>
-constexpr StreamTable<D, Q> make_stream_table() {
-  StreamTable<D, Q> t{};
+template <int D, int Q, int SIGN, bool BY_K>
+constexpr LinkTable<D, Q> make_link_table() {
+  LinkTable<D, Q> t{};
   constexpr int M = Block<D>::M;
   for (int p = 0; p < Q; ++p)
     for (int l = 0; l < M; ++l) {
-      const int ti = Block<D>::ci(l) + VS<D, Q>::cx[p];
-      const int tj = Block<D>::cj(l) + VS<D, Q>::cy[p];
-      const int tk = Block<D>::ck(l) + VS<D, Q>::cz[p];
+      const int ti = Block<D>::ci(l) + SIGN * VS<D, Q>::cx[p];
+      const int tj = Block<D>::cj(l) + SIGN * VS<D, Q>::cy[p];
+      const int tk = Block<D>::ck(l) + SIGN * VS<D, Q>::cz[p];
       const int sx = ti < 0 ? -1 : (ti > 3 ? 1 : 0);
       const int sy = tj < 0 ? -1 : (tj > 3 ? 1 : 0);
       const int sz = tk < 0 ? -1 : (tk > 3 ? 1 : 0);
-      const int code = BY_K ? Nbr<D>::dir_of(sx, sy, sz)
-                            : (sx + 1) + 3 * (sy + 1) + (D == 3 ? 9 * (sz + 1) : 0);
+      const int blk = BY_K ? Nbr<D>::dir_of(sx, sy, sz)
+                           : (sx + 1) + 3 * (sy + 1) + (D == 3 ? 9 * (sz + 1) : 0);
       const int cell = (ti & 3) + 4 * (tj & 3) + (D == 3 ? 16 * (tk & 3) : 0);
-      t.e[p * M + l] = (uint16_t)(code | (cell << 5));
+      t.e[p * M + l] = (uint16_t)(blk | (cell << 5));
     }
   return t;
 }
 template <int D, int Q>
-__device__ const StreamTable<D, Q> g_stream_table = make_stream_table<D, Q>();
-// the same targets with the neighbour index k of the block's nbr row in place
-// of the geometric code (for kernels that use the raw row)
+__device__ const LinkTable<D, Q> g_src_geo = make_link_table<D, Q, -1, false>();
 template <int D, int Q>
-__device__ const StreamTable<D, Q> g_stream_table_k = make_stream_table<D, Q, true>();
+__device__ const LinkTable<D, Q> g_tgt_geo = make_link_table<D, Q, +1, false>();
+template <int D, int Q>
+__device__ const LinkTable<D, Q> g_src_k = make_link_table<D, Q, -1, true>();
+template <int D, int Q>
+__device__ const LinkTable<D, Q> g_tgt_k = make_link_table<D, Q, +1, true>();
 
-// One BGK collision + push of a cell whose populations are f[]: the common
-// body of both collide-stream kernels.  `tab` is the stream table, in shared
-// memory when TAB_SMEM, else the global copy read through the read-only
-// path; `nb` the neighbour block IDs of the cell's block in geometric order.
-template <int D, int Q, class T, bool SOLID, bool TAB_SMEM>
-__device__ __forceinline__ void collide_push(typename Store<T>::R (&f)[Q], int l, int b,
-                                             const uint16_t* __restrict__ tab,
-                                             const int32_t* __restrict__ nb,
-                                             const uint64_t* __restrict__ sm_nb,
-                                             T* __restrict__ fout, size_t stride, double omega,
-                                             const FaceParams& faces) {
-  using V = VS<D, Q>;
+template <int D, int Q, int P>
+__device__ __forceinline__ int link_entry(const LinkTable<D, Q>& t, int l) {
+  return __ldg(&t.e[P * Block<D>::M + l]);
+}
+
+// --------------------------------------------------------- gather / scatter
+// Pre-collision populations of cell l of block b (see the file comment).
+// `row` is the block's neighbour row (neighbour-index order), in global or
+// shared memory.  A solid cell holds its own (rest) values.  With
+// SOLID, `solidmask` (one bit per cell) may still be null: no solid cells.
+template <int D, int Q, class T, bool SOLID>
+__device__ __forceinline__ void gather_cell(typename Store<T>::R (&f)[Q],
+                                            const T* __restrict__ g, size_t stride, int b, int l,
+                                            const int32_t* __restrict__ row,
+                                            const uint64_t* __restrict__ solidmask) {
   using S = Store<T>;
-  using R = typename S::R;
   constexpr int M = Block<D>::M;
-  R rho, ux, uy, uz;
-  moments<D, Q>(f, rho, ux, uy, uz);
-  const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
-  const R om = R(omega);
-  const int own = b * M + l;
+  const size_t own = (size_t)b * M + l;
+  const bool has_sm = SOLID && solidmask != nullptr;
+  const bool solid_cell = has_sm && ((__ldg(solidmask + b) >> l) & 1ull);
   static_for<0, Q>([&](auto P) {
     constexpr int p = P;
-    constexpr int cx = V::cx[p], cy = V::cy[p], cz = V::cz[p];
-    constexpr int pb = V::opp[p];
-    const R fs = f[p] + om * (feq<D, Q, p>(rho, ux, uy, uz, usq15) - f[p]);
-    T* __restrict__ outp = fout + (size_t)p * stride;
+    constexpr int pb = VS<D, Q>::opp[p];
     if constexpr (p == 0) {
-      outp[own] = S::template save<D, Q, 0>(fs);
+      f[0] = S::template load<D, Q, 0>(g[own]);
     } else {
-      int e;
-      if constexpr (TAB_SMEM) e = tab[p * M + l];
-      else e = __ldg(tab + p * M + l);
-      const int code = e & 31, tl = e >> 5;
-      const int tgt = nb[code];
-      bool bounce = tgt < 0;
-      if constexpr (SOLID) bounce = bounce || ((sm_nb[code] >> tl) & 1ull);
-      if (!bounce) {
-        outp[tgt * M + tl] = S::template save<D, Q, p>(fs);
+      const int e = link_entry<D, Q, p>(g_src_k<D, Q>, l);
+      const int k = e & 31, sl = e >> 5;
+      const int src = k == 0 ? b : row[k];
+      bool back = src < 0;
+      if (has_sm && !back) back = (__ldg(solidmask + src) >> sl) & 1ull;
+      if (solid_cell) f[p] = S::template load<D, Q, p>(g[(size_t)p * stride + own]);
+      else if (back) f[p] = S::template load<D, Q, p>(g[(size_t)pb * stride + own]);
+      else f[p] = S::template load<D, Q, p>(g[(size_t)p * stride + (size_t)src * M + sl]);
+    }
+  });
+}
+
+// Opposite directions as a device table (for loops over runtime p).
+template <int D, int Q>
+struct OppTable {
+  int8_t o[Q];
+};
+template <int D, int Q>
+constexpr OppTable<D, Q> make_opp() {
+  OppTable<D, Q> t{};
+  for (int p = 0; p < Q; ++p) t.o[p] = (int8_t)VS<D, Q>::opp[p];
+  return t;
+}
+template <int D, int Q>
+__device__ const OppTable<D, Q> g_opp = make_opp<D, Q>();
+
+// The element of g that holds the pre-collision f_p of cell l of block b
+// (the scatter rule of scatter_cell for one runtime direction p).
+template <int D, int Q>
+__device__ __forceinline__ size_t src_slot(int p, int b, int l, size_t stride,
+                                           const int32_t* row,
+                                           const uint64_t* __restrict__ solidmask) {
+  constexpr int M = Block<D>::M;
+  if (p == 0) return (size_t)b * M + l;
+  const int e = __ldg(&g_src_k<D, Q>.e[p * M + l]);
+  const int k = e & 31, sl = e >> 5;
+  const int src = k == 0 ? b : row[k];
+  bool back = src < 0;
+  if (solidmask && !back) back = (__ldg(solidmask + src) >> sl) & 1ull;
+  if (solidmask && ((__ldg(solidmask + b) >> l) & 1ull)) return (size_t)p * stride + (size_t)b * M + l;
+  return back ? (size_t)g_opp<D, Q>.o[p] * stride + (size_t)b * M + l
+              : (size_t)p * stride + (size_t)src * M + sl;
+}
+
+// Store pre-collision populations f of cell l of block b so that gather_cell
+// returns them.  MOVE (new blocks of an adaptation): where the source cell
+// x - c_p lies in a block that existed before (is_new(block) false), its slot
+// still holds the value that bounced back into that old cell, which now has
+// to come from this cell: it is moved to this cell's opposite slot first.
+template <int D, int Q, class T, bool SOLID, bool MOVE = false, class IsNew = int>
+__device__ __forceinline__ void scatter_cell(const typename Store<T>::R (&f)[Q],
+                                             T* __restrict__ g, size_t stride, int b, int l,
+                                             const int32_t* __restrict__ row,
+                                             const uint64_t* __restrict__ solidmask,
+                                             IsNew is_new = 0) {
+  using S = Store<T>;
+  constexpr int M = Block<D>::M;
+  const size_t own = (size_t)b * M + l;
+  const bool has_sm = SOLID && solidmask != nullptr;
+  const bool solid_cell = has_sm && ((__ldg(solidmask + b) >> l) & 1ull);
+  static_for<0, Q>([&](auto P) {
+    constexpr int p = P;
+    constexpr int pb = VS<D, Q>::opp[p];
+    if constexpr (p == 0) {
+      g[own] = S::template save<D, Q, 0>(f[0]);
+    } else {
+      const int e = link_entry<D, Q, p>(g_src_k<D, Q>, l);
+      const int k = e & 31, sl = e >> 5;
+      const int src = k == 0 ? b : row[k];
+      bool back = src < 0;
+      if (has_sm && !back) back = (__ldg(solidmask + src) >> sl) & 1ull;
+      if (solid_cell) {
+        g[(size_t)p * stride + own] = S::template save<D, Q, p>(f[p]);
+      } else if (back) {
+        g[(size_t)pb * stride + own] = S::template save<D, Q, p>(f[p]);
       } else {
-        R v = fs;   // NONE (interface) or solid: halfway bounce-back
-        if (tgt <= -2) {
-          const int face = -2 - tgt;
-          if (faces.kind[face] == FACE_OUTLET) {
-            R cu = R(0);
-            if constexpr (cx != 0) cu += cx > 0 ? ux : -ux;
-            if constexpr (cy != 0) cu += cy > 0 ? uy : -uy;
-            if constexpr (cz != 0) cu += cz > 0 ? uz : -uz;
-            constexpr double wp = V::w[p];
-            v = -fs + R(2.0 * wp * faces.rho_w[face]) * (R(1) + R(4.5) * cu * cu - usq15);
-          } else {
-            v = fs + R(faces.bb[face][p]);
-          }
+        T* slot = g + (size_t)p * stride + (size_t)src * M + sl;
+        if constexpr (MOVE) {
+          if (k != 0 && !is_new(src)) g[(size_t)pb * stride + own] = *slot;
         }
-        fout[(size_t)pb * stride + own] = S::template save<D, Q, pb>(v);
+        *slot = S::template save<D, Q, p>(f[p]);
       }
     }
   });
 }
 
-// ===================================================== fused collide + stream
-// One thread per cell, 256 threads = 256/M blocks per CTA.  Each cell loads its
-// Q populations (coalesced planes), relaxes them with BGK (Section 4.3) and
-// pushes f*_p to x + c_p in the other buffer (Section 4.2).  Neighbour block
-// IDs are staged in shared memory in geometric order.  A push that leaves the
-// level (NONE), hits a wall, or hits a solid cell lands in the cell's own
-// opposite slot: halfway bounce-back, the moving-wall term, or the
-// anti-bounce-back outlet value (Section 2 boundary equations).
-// resident warps per SM targeted by the one-pass kernel: 48 for FP32 math
-// with Q <= 19 (40 registers), fewer for the larger register footprints
-// (+ 512 threads per SM with DENSE: a tighter register budget that may spill)
+// ------------------------------------------------------------ BGK collision
+template <int D, int Q, class R>
+__device__ __forceinline__ void bgk(R (&f)[Q], R om, R& ux, R& uy, R& uz, R& usq15) {
+  R rho;
+  moments<D, Q>(f, rho, ux, uy, uz);
+  usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+  static_for<0, Q>([&](auto P) {
+    f[P] = f[P] + om * (feq<D, Q, P>(rho, ux, uy, uz, usq15) - f[P]);
+  });
+}
+
+// Value stored in the own slot p of a cell whose link p leaves through wall
+// face `face` (Section 2 boundary equations): the moving-wall bounce-back
+// f* + bb, or the anti-bounce-back outlet value with the cell's velocity.
+template <int D, int Q, int P, class R>
+__device__ __forceinline__ R wall_value(R fs, int face, R ux, R uy, R uz, R usq15,
+                                        const FaceParams& faces) {
+  using V = VS<D, Q>;
+  constexpr int cx = V::cx[P], cy = V::cy[P], cz = V::cz[P];
+  if (faces.kind[face] == FACE_OUTLET) {
+    R cu = R(0);
+    if constexpr (cx != 0) cu += cx > 0 ? ux : -ux;
+    if constexpr (cy != 0) cu += cy > 0 ? uy : -uy;
+    if constexpr (cz != 0) cu += cz > 0 ? uz : -uz;
+    constexpr double wp = V::w[P];
+    return -fs + R(2.0 * wp * faces.rho_w[face]) * (R(1) + R(4.5) * cu * cu - usq15);
+  }
+  return fs + R(faces.bb[face][P]);
+}
+
+// ================================================= fused collide + stream
+// One thread per cell, THREADS / M blocks per CTA (tree order).  The
+// neighbour rows of the CTA's blocks are staged in shared memory in
+// geometric order.  Blocks whose 3^D neighbourhood is complete and free of
+// solid cells take a branch-free path (every source is a same-level cell);
+// the others test each link: a source across a missing block, a wall or a
+// solid cell reads the cell's own opposite slot, and the links that leave
+// through a wall store the wall value.  Solid cells are not advanced.
+// resident threads per SM targeted: 1536 for FP32 math with Q <= 19 (40
+// registers), fewer for the larger register footprints (+512 with DENSE: a
+// tighter register budget)
 template <class T, int Q, int THREADS, bool DENSE = false>
 constexpr int one_pass_min_blocks() {
   const int threads_per_sm = (sizeof(typename Store<T>::R) == 4 ? (Q <= 19 ? 1536 : 1024)
@@ -152,364 +262,198 @@ constexpr int one_pass_min_blocks() {
   return threads_per_sm / THREADS > 0 ? threads_per_sm / THREADS : 1;
 }
 
-template <int D, int Q, class T, bool SOLID, int THREADS, bool TAB_SMEM, bool DENSE = false>
+constexpr int BF_OUTSIDE = 1;   // a neighbour block is missing or a wall
+constexpr int BF_WALL = 2;      // a neighbour is a moving wall or an outlet (a no-slip wall
+                                // bounces back with no added term, like a missing block)
+constexpr int BF_SOLID = 4;     // the block or a neighbour has solid cells
+constexpr int BF_OUTLET = 8;    // a neighbour is an outlet face
+
+// The step of one cell of a block whose neighbourhood has a missing block, a
+// wall or solid cells: every source is tested, and the links whose source
+// lies outside (bit p of `back`) are the links p-bar that leave the cell
+// through a wall, which store the wall value.  Kept out of line so that the
+// branch-free path of the other blocks keeps its registers.  OUTLET: a
+// neighbour is an outlet face (anti-bounce-back needs the cell's velocity).
+template <int D, int Q, class T, bool SOLID, bool OUTLET>
+__device__ __noinline__ void step_cell_checked(const T* __restrict__ gin, T* __restrict__ gout,
+                                               size_t stride, size_t own, int l,
+                                               const int32_t* nb, const uint64_t* sm, int flags,
+                                               double omega, const FaceParams& faces) {
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int M = Block<D>::M;
+  R f[Q];
+  uint32_t back = 0u;
+  static_for<0, Q>([&](auto P) {
+    constexpr int p = P;
+    constexpr int pb = VS<D, Q>::opp[p];
+    if constexpr (p == 0) {
+      f[0] = S::template load<D, Q, 0>(gin[own]);
+    } else {
+      const int e = link_entry<D, Q, p>(g_src_geo<D, Q>, l);
+      const int code = e & 31, sl = e >> 5;
+      const int src = nb[code];
+      bool out = src < 0;
+      if constexpr (SOLID) out = out || ((sm[code] >> sl) & 1ull);
+      back |= (uint32_t)out << p;
+      f[p] = out ? S::template load<D, Q, p>(gin[(size_t)pb * stride + own])
+                 : S::template load<D, Q, p>(gin[(size_t)p * stride + (size_t)src * M + sl]);
+    }
+  });
+  R ux, uy, uz, usq15;
+  bgk<D, Q>(f, R(omega), ux, uy, uz, usq15);
+  if (!(flags & BF_WALL)) back = 0u;
+  static_for<0, Q>([&](auto P) {
+    constexpr int p = P;
+    constexpr int pb = VS<D, Q>::opp[p];
+    R v = f[p];
+    if constexpr (p != 0) {
+      if ((back >> pb) & 1u) {   // the target of link p is outside
+        const int tgt = nb[link_entry<D, Q, p>(g_tgt_geo<D, Q>, l) & 31];
+        if (tgt <= -2) {
+          if constexpr (OUTLET) v = wall_value<D, Q, p>(v, -2 - tgt, ux, uy, uz, usq15, faces);
+          else v += R(faces.bb[-2 - tgt][p]);
+        }
+      }
+    }
+    gout[(size_t)p * stride + own] = S::template save<D, Q, p>(v);
+  });
+}
+
+// A ghost cell at the first substep of its level: the interpolation of the
+// level step left its pre-collision values in its own slots of the output
+// buffer (Section 4.1); they are read there instead of gathered, then the
+// cell collides and stores like step_cell_checked.
+template <int D, int Q, class T, bool OUTLET>
+__device__ __noinline__ void step_cell_ghost(T* __restrict__ gout, size_t stride, size_t own,
+                                             int l, const int32_t* nb, int flags, double omega,
+                                             const FaceParams& faces) {
+  using S = Store<T>;
+  using R = typename S::R;
+  R f[Q];
+  static_for<0, Q>([&](auto P) {
+    f[P] = S::template load<D, Q, P>(gout[(size_t)P * stride + own]);
+  });
+  R ux, uy, uz, usq15;
+  bgk<D, Q>(f, R(omega), ux, uy, uz, usq15);
+  // the store addresses equal the load addresses: recompute them instead of
+  // keeping Q 64-bit addresses live across the collision
+  asm volatile("" : "+l"(stride), "+l"(own));
+  static_for<0, Q>([&](auto P) {
+    constexpr int p = P;
+    R v = f[p];
+    if constexpr (p != 0) {
+      if (flags & BF_WALL) {
+        const int tgt = nb[link_entry<D, Q, p>(g_tgt_geo<D, Q>, l) & 31];
+        if (tgt <= -2) {
+          if constexpr (OUTLET) v = wall_value<D, Q, p>(v, -2 - tgt, ux, uy, uz, usq15, faces);
+          else v += R(faces.bb[-2 - tgt][p]);
+        }
+      }
+    }
+    gout[(size_t)p * stride + own] = S::template save<D, Q, p>(v);
+  });
+}
+
+// GHOST_IN (the first of the two substeps of a level below the coarsest):
+// the coarse-to-fine interpolation of the level step (Section 4.1) wrote the
+// pre-collision values of this level's ghost cells into their own slots of
+// the output buffer (a direct write, see LbmOps::interp); the ghost cells read
+// them there instead of gathering, and overwrite them with their
+// post-collision values.  `ghostmask` (= the cell-class table's ghost bits,
+// cellmask[2 b]) tells the ghost cells.
+template <int D, int Q, class T, bool SOLID, int THREADS, bool DENSE = false, bool GHOST_IN = false>
 __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, DENSE>()))
-    k_collide_stream(const int32_t* __restrict__ list, int n, const T* __restrict__ fin,
-                     T* __restrict__ fout, const int32_t* __restrict__ nbr,
-                     const uint64_t* __restrict__ solidmask, StepParams prm) {
+    k_collide_stream(const int32_t* __restrict__ list, int n, const T* __restrict__ gin,
+                     T* __restrict__ gout, const int32_t* __restrict__ nbr,
+                     const uint64_t* __restrict__ solidmask, StepParams prm,
+                     const uint64_t* __restrict__ ghostmask) {
   using S = Store<T>;
   using R = typename S::R;
   constexpr int M = Block<D>::M;
   constexpr int NCODE = D == 2 ? 9 : 27;
   constexpr int CENTER = D == 2 ? 4 : 13;
   constexpr int BPC = THREADS / M;
+  static_assert(THREADS % M == 0 && THREADS >= 32, "whole blocks per CTA");
   __shared__ int32_t s_nb[BPC][NCODE];
   __shared__ uint64_t s_sm[SOLID ? BPC : 1][SOLID ? NCODE : 1];
-  __shared__ int s_near[SOLID ? BPC : 1];   // a neighbour (or the block) has solid cells
-  __shared__ uint16_t s_tab[TAB_SMEM ? Q * M : 1];
+  __shared__ uint64_t s_gm[GHOST_IN ? BPC : 1];   // ghost cells of the block
 
   const int slot = threadIdx.x / M;
   const int l = threadIdx.x - slot * M;
   const int first = blockIdx.x * BPC;
-  if constexpr (TAB_SMEM)
-    for (int t = threadIdx.x; t < Q * M; t += THREADS) s_tab[t] = g_stream_table<D, Q>.e[t];
-  if constexpr (SOLID) {
-    if (threadIdx.x < BPC) s_near[threadIdx.x] = 0;
-    __syncthreads();
-  }
   for (int t = threadIdx.x; t < BPC * NCODE; t += THREADS) {
     const int s = t / NCODE, code = t - s * NCODE;
-    const int k = geo_to_k<D>(code);
     const int bi = first + s;
     int v = NONE;
-    if (bi < n) v = __ldg(nbr + (size_t)__ldg(list + bi) * NBR_STRIDE + k);
-    s_nb[s][code] = v;
-    if constexpr (SOLID) {
-      const uint64_t sm = (v >= 0) ? __ldg(solidmask + v) : 0ull;
-      s_sm[s][code] = sm;
-      if (sm) s_near[s] = 1;
+    if (bi < n) {
+      const int b = __ldg(list + bi);
+      v = __ldg(nbr + (size_t)b * NBR_STRIDE + geo_to_k<D>(code));
+      if (GHOST_IN && code == 0) s_gm[s] = __ldg(ghostmask + 2 * (size_t)b);
     }
+    s_nb[s][code] = v;
+    if constexpr (SOLID) s_sm[s][code] = (v >= 0) ? __ldg(solidmask + v) : 0ull;
   }
   __syncthreads();
+  // block flags from the neighbour codes: every warp reads all codes of its
+  // block (32 consecutive cells cover every residue mod 3^D) and votes
+  int flags;
+  {
+    const int code = l % NCODE;
+    const int v = s_nb[slot][code];
+    const unsigned lanes = M >= 32 ? 0xffffffffu : (((1u << M) - 1u) << ((threadIdx.x & 31) & ~(M - 1)));
+    const unsigned outside = __ballot_sync(0xffffffffu, v < 0) & lanes;
+    const unsigned wall =
+        __ballot_sync(0xffffffffu, v <= -2 && prm.faces.kind[-2 - v] != FACE_NOSLIP) & lanes;
+    const unsigned outlet =
+        __ballot_sync(0xffffffffu, v <= -2 && prm.faces.kind[-2 - v] == FACE_OUTLET) & lanes;
+    unsigned solid = 0u;
+    if constexpr (SOLID) solid = __ballot_sync(0xffffffffu, s_sm[slot][code] != 0ull) & lanes;
+    flags = (outside ? BF_OUTSIDE : 0) | (wall ? BF_WALL : 0) | (solid ? BF_SOLID : 0) |
+            (outlet ? BF_OUTLET : 0);
+  }
   if (first + slot >= n) return;
   const int b = s_nb[slot][CENTER];
   if constexpr (SOLID) {
     if ((s_sm[slot][CENTER] >> l) & 1ull) return;   // solid cells are not advanced
   }
   const size_t stride = prm.stride;
-  const int own = b * M + l;
-  R f[Q];
-  static_for<0, Q>([&](auto P) {
-    f[P] = S::template load<D, Q, P>(fin[(size_t)P * stride + own]);
-  });
-  const uint16_t* tab = TAB_SMEM ? s_tab : g_stream_table<D, Q>.e;
-  // blocks with no solid cell around them take the push without solid tests
-  // (a branch uniform over the block's two warps)
-  if (SOLID && s_near[SOLID ? slot : 0])
-    collide_push<D, Q, T, SOLID, TAB_SMEM>(f, l, b, tab, s_nb[slot], SOLID ? s_sm[slot] : nullptr,
-                                           fout, prm.stride, prm.omega, prm.faces);
-  else
-    collide_push<D, Q, T, false, TAB_SMEM>(f, l, b, tab, s_nb[slot], nullptr, fout, prm.stride,
-                                           prm.omega, prm.faces);
-}
-
-// ================================== pipelined persistent collide + stream
-// Same arithmetic as k_collide_stream.  Each CTA walks tiles of 256/M blocks
-// (stride gridDim.x) and double-buffers them in shared memory: while tile t
-// is collided and pushed from shared memory, the populations and neighbour
-// rows of its next tile stream in with 16-byte cp.async copies, so the
-// memory system always has loads in flight.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-template <int D, int Q, class T, int STAGES>
-struct PipeShape {
-  static constexpr int M = Block<D>::M;
-  static constexpr int TILE = 256 / M;
-  static constexpr int STAGE_ELEMS = TILE * Q * M;
-  static constexpr int PLANE_CHUNKS = M * (int)sizeof(T) / 16;
-  static constexpr size_t SMEM =
-      STAGES * ((size_t)STAGE_ELEMS * sizeof(T) + (size_t)TILE * NBR_STRIDE * 4);
-};
-
-template <int D, int Q, class T, bool SOLID, int STAGES>
-__global__ void __launch_bounds__(256, (sizeof(T) == 8 && Q == 27) ? 1 : 2)
-    k_collide_stream_pipe(const int32_t* __restrict__ list, int n, const T* __restrict__ fin,
-                          T* __restrict__ fout, const int32_t* __restrict__ nbr,
-                          const uint64_t* __restrict__ solidmask, StepParams prm) {
-  using V = VS<D, Q>;
-  using S = Store<T>;
-  using R = typename S::R;
-  using PS = PipeShape<D, Q, T, STAGES>;
-  constexpr int M = PS::M, TILE = PS::TILE;
-  constexpr int NCODE = D == 2 ? 9 : 27;
-  constexpr int CENTER = D == 2 ? 4 : 13;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sf = reinterpret_cast<T*>(smem_raw);                           // [STAGES][TILE][Q][M]
-  int32_t* srow = reinterpret_cast<int32_t*>(smem_raw + STAGES * (size_t)PS::STAGE_ELEMS * sizeof(T));
-  __shared__ int32_t s_nb[TILE][NCODE];
-  __shared__ uint64_t s_sm[SOLID ? TILE : 1][SOLID ? NCODE : 1];
-  __shared__ uint16_t s_tab[Q * M];
-  const size_t stride = prm.stride;
-  const int n_tiles = (n + TILE - 1) / TILE;
-  for (int t = threadIdx.x; t < Q * M; t += blockDim.x) s_tab[t] = g_stream_table<D, Q>.e[t];
-
-  auto issue = [&](int tile, int stage) {
-    constexpr int NCH = TILE * Q * PS::PLANE_CHUNKS;
-#pragma unroll 1
-    for (int c = threadIdx.x; c < NCH; c += blockDim.x) {
-      const int s = c / (Q * PS::PLANE_CHUNKS);
-      const int rem = c - s * Q * PS::PLANE_CHUNKS;
-      const int p = rem / PS::PLANE_CHUNKS;
-      const int ch = rem - p * PS::PLANE_CHUNKS;
-      const int bi = tile * TILE + s;
-      if (bi < n) {
-        const int b = __ldg(list + bi);
-        cp_async16(reinterpret_cast<char*>(sf + (size_t)stage * PS::STAGE_ELEMS + (s * Q + p) * M) + 16 * ch,
-                   reinterpret_cast<const char*>(fin + (size_t)p * stride + (size_t)b * M) + 16 * ch);
+  const size_t own = (size_t)b * M + l;
+  const int32_t* nb = s_nb[slot];
+  bool ghost_in = false;
+  if constexpr (GHOST_IN) ghost_in = (s_gm[slot] >> l) & 1ull;
+  if (flags == 0) {   // (a block with ghost cells has a missing neighbour: flags != 0)
+    R f[Q];
+    static_for<0, Q>([&](auto P) {
+      constexpr int p = P;
+      if constexpr (p == 0) {
+        f[0] = S::template load<D, Q, 0>(gin[own]);
+      } else {
+        const int e = link_entry<D, Q, p>(g_src_geo<D, Q>, l);
+        f[p] = S::template load<D, Q, p>(
+            gin[(size_t)p * stride + (size_t)nb[e & 31] * M + (e >> 5)]);
       }
-    }
-#pragma unroll 1
-    for (int c = threadIdx.x; c < TILE * (NBR_STRIDE / 4); c += blockDim.x) {
-      const int s = c / (NBR_STRIDE / 4), ch = c - s * (NBR_STRIDE / 4);
-      const int bi = tile * TILE + s;
-      if (bi < n)
-        cp_async16(srow + (stage * TILE + s) * NBR_STRIDE + 4 * ch,
-                   nbr + (size_t)__ldg(list + bi) * NBR_STRIDE + 4 * ch);
-    }
-  };
-
-  const int slot = threadIdx.x / M;
-  const int l = threadIdx.x - slot * M;
-  // prologue: the first STAGES-1 tiles of this CTA are requested up front
-#pragma unroll
-  for (int k = 0; k < STAGES - 1; ++k) {
-    const int t = blockIdx.x + k * gridDim.x;
-    if (t < n_tiles) issue(t, k);
-    cp_async_commit();
+    });
+    R ux, uy, uz, usq15;
+    bgk<D, Q>(f, R(prm.omega), ux, uy, uz, usq15);
+    static_for<0, Q>([&](auto P) {
+      gout[(size_t)P * stride + own] = S::template save<D, Q, P>(f[P]);
+    });
+  } else if (ghost_in) {
+    if (flags & BF_OUTLET)
+      step_cell_ghost<D, Q, T, true>(gout, stride, own, l, nb, flags, prm.omega, prm.faces);
+    else
+      step_cell_ghost<D, Q, T, false>(gout, stride, own, l, nb, flags, prm.omega, prm.faces);
+  } else {
+    if (flags & BF_OUTLET)
+      step_cell_checked<D, Q, T, SOLID, true>(gin, gout, stride, own, l, nb,
+                                              SOLID ? s_sm[slot] : nullptr, flags, prm.omega,
+                                              prm.faces);
+    else
+      step_cell_checked<D, Q, T, SOLID, false>(gin, gout, stride, own, l, nb,
+                                               SOLID ? s_sm[slot] : nullptr, flags, prm.omega,
+                                               prm.faces);
   }
-  int stage = 0;
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int ahead = tile + (STAGES - 1) * gridDim.x;
-    if (ahead < n_tiles) issue(ahead, (stage + STAGES - 1) % STAGES);
-    cp_async_commit();
-    cp_async_wait<STAGES - 1>();   // this tile's group has landed
-    __syncthreads();
-#pragma unroll 1
-    for (int t = threadIdx.x; t < TILE * NCODE; t += blockDim.x) {
-      const int s = t / NCODE, code = t - s * NCODE;
-      const int v = (tile * TILE + s < n) ? srow[(stage * TILE + s) * NBR_STRIDE + geo_to_k<D>(code)]
-                                          : NONE;
-      s_nb[s][code] = v;
-      if constexpr (SOLID) s_sm[s][code] = (v >= 0) ? __ldg(solidmask + v) : 0ull;
-    }
-    __syncthreads();
-    const bool active = tile * TILE + slot < n;
-    bool solid_cell = false;
-    if constexpr (SOLID) solid_cell = active && ((s_sm[slot][CENTER] >> l) & 1ull);
-    if (active && !solid_cell) {
-      const int b = s_nb[slot][CENTER];
-      const T* sblk = sf + (size_t)stage * PS::STAGE_ELEMS + slot * Q * M;
-      R f[Q];
-      static_for<0, Q>([&](auto P) { f[P] = S::template load<D, Q, P>(sblk[P * M + l]); });
-      collide_push<D, Q, T, SOLID, true>(f, l, b, s_tab, s_nb[slot],
-                                         SOLID ? s_sm[slot] : nullptr, fout, prm.stride,
-                                         prm.omega, prm.faces);
-    }
-    __syncthreads();
-    stage = (stage + 1) % STAGES;
-  }
-  cp_async_wait<0>();
-}
-
-// ============================ bulk-copy staged persistent collide + stream
-// Same arithmetic as k_collide_stream.  Each CTA walks tiles of THREADS/M
-// blocks (tile = blockIdx.x + k gridDim.x, one cell per thread).  Warp 0
-// stages a tile into shared memory with bulk asynchronous copies
-// (cp.async.bulk, completion counted in bytes on the stage's mbarrier): the Q
-// population planes of each block (M N_p contiguous bytes each) and its
-// 128-byte neighbour row.  STAGES tiles are in flight while the CTA collides
-// the current one out of shared memory and pushes it to global memory.  The
-// loads occupy no registers and no load instructions of the computing
-// threads.  Every wait on an mbarrier is bounded (about a second); a CTA
-// that gives up sets *wait_flag, waits (bounded) for its copies in flight
-// and returns.
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait for the phase of `parity` to complete: false once `limit`
-// cycles (default 2^31, about a second) have passed
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
-                                          long long limit = 1ll << 31) {
-  if (mbar_test(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_test(bar, parity))
-    if (clock64() - t0 > limit) return false;
-  return true;
-}
-__device__ __forceinline__ void mbar_inval(uint32_t bar) {
-  asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
-                                          uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-          dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-
-template <int D, int Q, class T, int THREADS>
-struct BulkTile {
-  static constexpr int M = Block<D>::M;
-  static constexpr int TB = THREADS / M;                       // blocks per tile
-  static constexpr int PLANE = M * (int)sizeof(T);             // bytes, multiple of 16
-  static constexpr int POPS = TB * Q * PLANE;                  // [TB][Q][M] values
-  static constexpr int ROW = NBR_STRIDE * 4;                   // one neighbour row
-  static constexpr int STAGE = POPS + TB * ROW;
-  static constexpr size_t smem(int stages) { return (size_t)stages * STAGE + 8 * (size_t)stages; }
-  static_assert(PLANE % 16 == 0 && ROW % 16 == 0, "bulk copies move multiples of 16 bytes");
-  static_assert(TB <= 32, "one lane of warp 0 per block of a tile");
-};
-
-template <int D, int Q, class T, int THREADS, int STAGES>
-__global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 2 : 4))
-    k_collide_stream_bulk(const int32_t* __restrict__ list, int n, const T* __restrict__ fin,
-                          T* __restrict__ fout, const int32_t* __restrict__ nbr,
-                          StepParams prm) {
-  using BT = BulkTile<D, Q, T, THREADS>;
-  using S = Store<T>;
-  using R = typename S::R;
-  constexpr int M = BT::M, TB = BT::TB;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + STAGES * (size_t)BT::STAGE);
-  __shared__ int s_contig[STAGES];   // 1: the stage was filled by one copy per plane
-  const int n_tiles = (n + TB - 1) / TB;
-  const int lane = threadIdx.x & 31;
-  const bool producer = threadIdx.x < 32;
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < STAGES; ++st) mbar_init(smem_addr(bars + st), 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-
-  // warp 0: request tile `tile` into stage `st`
-  auto issue = [&](int tile, int st) {
-    const int first = tile * TB;
-    const int nb = min(TB, n - first);
-    const uint32_t bar = smem_addr(bars + st);
-    unsigned char* base = smem_raw + (size_t)st * BT::STAGE;
-    const int my_b = lane < nb ? __ldg(list + first + lane) : 0;
-    const int b0 = __shfl_sync(0xffffffffu, my_b, 0);
-    // consecutive IDs (sibling groups, uniform forests): one copy per plane
-    const bool contig = __all_sync(0xffffffffu, lane >= nb || my_b == b0 + lane);
-    if (lane == 0) s_contig[st] = contig ? 1 : 0;   // published by the arrive below
-    fence_proxy_async_smem();   // earlier generic reads of this stage before the async writes
-    __syncwarp();
-    if (lane == 0) mbar_expect_tx(bar, (uint32_t)nb * (Q * BT::PLANE + BT::ROW));
-    __syncwarp();
-    if (contig) {
-      for (int p = lane; p <= Q; p += 32) {
-        if (p < Q)
-          bulk_load(smem_addr(base + (size_t)p * BT::PLANE * TB),
-                    fin + (size_t)p * prm.stride + (size_t)b0 * M, nb * BT::PLANE, bar);
-        else
-          bulk_load(smem_addr(base + BT::POPS), nbr + (size_t)b0 * NBR_STRIDE, nb * BT::ROW, bar);
-      }
-      return;
-    }
-#pragma unroll 1
-    for (int s = 0; s < nb; ++s) {
-      const int b = __shfl_sync(0xffffffffu, my_b, s);
-      for (int p = lane; p <= Q; p += 32) {
-        if (p < Q)
-          bulk_load(smem_addr(base + (size_t)(s * Q + p) * BT::PLANE),
-                    fin + (size_t)p * prm.stride + (size_t)b * M, BT::PLANE, bar);
-        else
-          bulk_load(smem_addr(base + BT::POPS + s * BT::ROW), nbr + (size_t)b * NBR_STRIDE,
-                    BT::ROW, bar);
-      }
-    }
-  };
-
-  int k_issued = 0;   // tiles of this CTA requested so far
-  if (producer)
-    for (; k_issued < STAGES && blockIdx.x + k_issued * (int)gridDim.x < n_tiles; ++k_issued)
-      issue(blockIdx.x + k_issued * gridDim.x, k_issued);
-  if (producer) k_issued = __shfl_sync(0xffffffffu, k_issued, 0);
-
-  const int slot = threadIdx.x / M;
-  const int l = threadIdx.x - slot * M;
-  int k = 0;
-  bool failed = false;
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
-    const int st = k % STAGES;
-    const uint32_t parity = (uint32_t)(k / STAGES) & 1u;
-    const bool ok = mbar_wait(smem_addr(bars + st), parity);
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    const unsigned char* base = smem_raw + (size_t)st * BT::STAGE;
-    if (tile * TB + slot < n) {
-      const int32_t* row = reinterpret_cast<const int32_t*>(base + BT::POPS + slot * BT::ROW);
-      // plane-major [Q][TB][M] after a contiguous copy, else block-major [TB][Q][M]
-      const bool contig = s_contig[st] != 0;
-      const T* sf = reinterpret_cast<const T*>(base) + (contig ? (size_t)slot * M : (size_t)slot * Q * M);
-      const int pstride = contig ? TB * M : M;
-      R f[Q];
-      static_for<0, Q>([&](auto P) { f[P] = S::template load<D, Q, P>(sf[P * pstride + l]); });
-      collide_push<D, Q, T, false, false>(f, l, row[0], g_stream_table_k<D, Q>.e, row, nullptr,
-                                          fout, prm.stride, prm.omega, prm.faces);
-    }
-    __syncthreads();   // stage st is free again
-    const int next = tile + STAGES * (int)gridDim.x;
-    if (producer && next < n_tiles) {
-      issue(next, st);
-      ++k_issued;
-    }
-  }
-  if (failed) {
-    // give up: report, then let the copies already requested land (bounded)
-    if (threadIdx.x == 0) {
-      atomicExch(prm.wait_flag, 1);
-      for (int j = k; j < k_issued; ++j)
-        (void)mbar_wait(smem_addr(bars + (j % STAGES)), (uint32_t)(j / STAGES) & 1u);
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0)
-    for (int st = 0; st < STAGES; ++st) mbar_inval(smem_addr(bars + st));
 }
 
 }  // namespace amr

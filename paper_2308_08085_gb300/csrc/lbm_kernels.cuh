@@ -1,9 +1,12 @@
 // Templated LBM kernels of the block forest.  Included once per velocity-set
 // translation unit, which instantiates them through AMR_LBM_OPS.
 //
-// Population layout (every storage type): f[p * stride + b * M + l], stride =
+// Population layout (every storage type): g[p * stride + b * M + l], stride =
 // capacity * M, M = 4^D cells per block, l = i + 4 j + 16 k.  Two buffers A/B
 // are used per level in ping-pong; a level's current buffer is bit L of `cur`.
+// The stored values are the outgoing post-collision populations; every kernel
+// reads a cell's pre-collision populations with gather_cell and writes them
+// with scatter_cell (collide_stream.cuh).
 #pragma once
 #include "collide_stream.cuh"
 
@@ -17,18 +20,24 @@ namespace amr {
 // each child c, fine cell (I,J,K) takes the multilinear interpolant of the
 // 2^D parent cells of quadrant c at local coordinates -1/4 + I/2.  Writes the
 // ghost cells of every child (mode_all = 0) or every cell (mode_all = 1).
-template <int D, int Q, class T>
+// Neighbour rows of the blocks a CTA works on, copied to shared memory
+// (the gathers and scatters read one entry per link).
+template <int D>
+__device__ __forceinline__ void stage_row(int32_t* dst, const int32_t* __restrict__ nbr, int b,
+                                          int t, int nt) {
+  constexpr int NK = Nbr<D>::K;
+  for (int k = t; k < NK; k += nt) dst[k] = b >= 0 ? __ldg(nbr + (size_t)b * NBR_STRIDE + k) : NONE;
+}
+
+template <int D, int Q, class T, bool SOLID>
 __device__ __forceinline__ void interp_stage(typename Store<T>::R (*sF)[Block<D>::M],
                                              const T* __restrict__ fpar, size_t stride, int P,
-                                             int l, double ratio) {
+                                             int l, double ratio, const int32_t* prow,
+                                             const uint64_t* __restrict__ solidmask) {
   using S = Store<T>;
   using R = typename S::R;
-  constexpr int M = Block<D>::M;
-  const size_t base = (size_t)P * M + l;
   R f[Q];
-  static_for<0, Q>([&](auto Pp) {
-    f[Pp] = S::template load<D, Q, Pp>(fpar[(size_t)Pp * stride + base]);
-  });
+  gather_cell<D, Q, T, SOLID>(f, fpar, stride, P, l, prow, solidmask);
   R rho, ux, uy, uz;
   moments<D, Q>(f, rho, ux, uy, uz);
   const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
@@ -39,15 +48,44 @@ __device__ __forceinline__ void interp_stage(typename Store<T>::R (*sF)[Block<D>
   });
 }
 
+// Store the interpolated populations v of cell l of child ch.  mode_all (new
+// children of an adaptation): values that old neighbours stored in the new
+// block's place are moved first (scatter_cell MOVE); a solid cell takes the
+// rest state.
+template <int D, int Q, class T, bool SOLID>
+__device__ __forceinline__ void store_child_cell(typename Store<T>::R (&v)[Q], T* __restrict__ fch,
+                                                 size_t stride, int ch, int l, const int32_t* row,
+                                                 const uint64_t* __restrict__ solidmask,
+                                                 const int32_t* __restrict__ parent,
+                                                 const int8_t* __restrict__ marks, int mode_all) {
+  using S = Store<T>;
+  using R = typename S::R;
+  if (mode_all & 4) {   // the level step: as they are, into the child's own slots
+    const size_t own = (size_t)ch * Block<D>::M + l;
+    static_for<0, Q>([&](auto Pp) { fch[(size_t)Pp * stride + own] = S::template save<D, Q, Pp>(v[Pp]); });
+    return;
+  }
+  if (mode_all & 1) {
+    auto is_new = [&](int blk) {
+      const int pp = __ldg(parent + blk);
+      return pp >= 0 && __ldg(marks + pp) > 0;
+    };
+    scatter_cell<D, Q, T, SOLID, true>(v, fch, stride, ch, l, row, solidmask, is_new);
+  } else {
+    scatter_cell<D, Q, T, SOLID>(v, fch, stride, ch, l, row, solidmask);
+  }
+}
+
 template <int D, int Q, class T, bool SOLID>
 __device__ __forceinline__ void interp_children(const typename Store<T>::R (*sF)[Block<D>::M],
                                                 int l, T* __restrict__ fch, size_t stride,
                                                 int c0, const uint64_t* __restrict__ cellmask,
+                                                const int32_t (*crow)[Nbr<D>::K],
                                                 const uint64_t* __restrict__ solidmask,
-                                                int mode_all) {
+                                                const int32_t* __restrict__ parent,
+                                                const int8_t* __restrict__ marks, int mode_all) {
   using S = Store<T>;
   using R = typename S::R;
-  constexpr int M = Block<D>::M;
   constexpr int NC = Block<D>::NC;
   const int i = Block<D>::ci(l), j = Block<D>::cj(l), k = Block<D>::ck(l);
   const R x = R(-0.25) + R(0.5) * R(i);
@@ -60,52 +98,66 @@ __device__ __forceinline__ void interp_children(const typename Store<T>::R (*sF)
     if (D == 3) wv *= (a & 4) ? z : R(1) - z;
     wgt[a] = wv;
   }
+#pragma unroll 1
   for (int c = 0; c < NC; ++c) {
     const int ch = c0 + c;
-    if (!mode_all) {
+    if (!(mode_all & 1)) {
       const uint64_t gm = __ldg(cellmask + 2 * (size_t)ch);   // ghost cells of the child
       if (gm == 0ull) continue;
       if (!((gm >> l) & 1ull)) continue;
     }
-    if constexpr (SOLID) {
-      if ((__ldg(solidmask + ch) >> l) & 1ull) continue;
+    R v[Q];
+    if (SOLID && solidmask && ((__ldg(solidmask + ch) >> l) & 1ull)) {
+      if (!(mode_all & 1)) continue;                 // solid cells keep the rest state
+      static_for<0, Q>([&](auto Pp) { v[Pp] = R(VS<D, Q>::w[Pp]); });
+    } else {
+      const int qx = c & 1, qy = (c >> 1) & 1, qz = (c >> 2) & 1;
+      int corner[NC];
+#pragma unroll
+      for (int a = 0; a < NC; ++a)
+        corner[a] = Block<D>::cell(2 * qx + (a & 1), 2 * qy + ((a >> 1) & 1),
+                                   2 * qz + ((a >> 2) & 1));
+      static_for<0, Q>([&](auto Pp) {
+        R acc = R(0);
+#pragma unroll
+        for (int a = 0; a < NC; ++a) acc += wgt[a] * sF[Pp][corner[a]];
+        v[Pp] = acc;
+      });
     }
-    const int qx = c & 1, qy = (c >> 1) & 1, qz = (c >> 2) & 1;
-    int corner[NC];
-#pragma unroll
-    for (int a = 0; a < NC; ++a)
-      corner[a] = Block<D>::cell(2 * qx + (a & 1), 2 * qy + ((a >> 1) & 1),
-                                 2 * qz + ((a >> 2) & 1));
-    const size_t base = (size_t)ch * M + l;
-    static_for<0, Q>([&](auto Pp) {
-      R v = R(0);
-#pragma unroll
-      for (int a = 0; a < NC; ++a) v += wgt[a] * sF[Pp][corner[a]];
-      fch[(size_t)Pp * stride + base] = S::template save<D, Q, Pp>(v);
-    });
+    store_child_cell<D, Q, T, SOLID>(v, fch, stride, ch, l, crow[c], solidmask, parent, marks,
+                                     mode_all);
   }
 }
 
 template <int D, int Q, class T, bool SOLID>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 8)
     k_interp(const int32_t* __restrict__ list, int n, const T* __restrict__ fpar,
              T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
-             const uint64_t* __restrict__ cellmask, const uint64_t* __restrict__ solidmask,
-             double ratio, int mode_all) {
+             const uint64_t* __restrict__ cellmask, const int32_t* __restrict__ nbr,
+             const uint64_t* __restrict__ solidmask, const int32_t* __restrict__ parent,
+             const int8_t* __restrict__ marks, double ratio, int mode_all) {
   using R = typename Store<T>::R;
   constexpr int M = Block<D>::M;
+  constexpr int NC = Block<D>::NC;
+  constexpr int NK = Nbr<D>::K;
   constexpr int BPC = 128 / M;
   __shared__ R sF[BPC][Q][M];
+  __shared__ int32_t s_row[BPC][1 + NC][NK];   // the parent's row, then its children's
   const int slot = threadIdx.x / M;
   const int l = threadIdx.x - slot * M;
   const int bi = blockIdx.x * BPC + slot;
   const bool valid = bi < n;
   const int P = valid ? list[bi] : 0;
-  if (valid) interp_stage<D, Q, T>(sF[slot], fpar, stride, P, l, ratio);
+  const int c0 = valid ? child0[P] : 0;
+  for (int r = 0; r <= NC; ++r)
+    stage_row<D>(s_row[slot][r], nbr, valid ? (r == 0 ? P : c0 + r - 1) : NONE, l, M);
+  __syncthreads();
+  if (valid) interp_stage<D, Q, T, SOLID>(sF[slot], fpar, stride, P, l, ratio, s_row[slot][0],
+                                          solidmask);
   __syncthreads();
   if (!valid) return;
-  interp_children<D, Q, T, SOLID>(sF[slot], l, fch, stride, child0[P], cellmask, solidmask,
-                                  mode_all);
+  interp_children<D, Q, T, SOLID>(sF[slot], l, fch, stride, c0, cellmask, s_row[slot] + 1,
+                                  solidmask, parent, marks, mode_all);
 }
 
 // ========================================== coarse-to-fine cubic interpolation
@@ -141,8 +193,9 @@ template <int D, int Q, class T, bool SOLID>
 __global__ void __launch_bounds__(64)
     k_interp_cubic(const int32_t* __restrict__ list, int n, const T* __restrict__ fpar,
                    T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
-                   const uint64_t* __restrict__ cellmask, const uint64_t* __restrict__ solidmask,
-                   double ratio, int mode_all) {
+                   const uint64_t* __restrict__ cellmask, const int32_t* __restrict__ nbr,
+                   const uint64_t* __restrict__ solidmask, const int32_t* __restrict__ parent,
+                   const int8_t* __restrict__ marks, double ratio, int mode_all) {
   using S = Store<T>;
   using R = typename S::R;
   constexpr int M = Block<D>::M;
@@ -156,17 +209,23 @@ __global__ void __launch_bounds__(64)
   const int l = threadIdx.x - slot * M;
   const int i = Block<D>::ci(l), j = Block<D>::cj(l), k = Block<D>::ck(l);
   if (threadIdx.x < 32) sw[threadIdx.x >> 2][threadIdx.x & 3] = R(c_cubic_w.w[threadIdx.x >> 2][threadIdx.x & 3]);
+  constexpr int NK = Nbr<D>::K;
+  __shared__ int32_t s_row[PPC][1 + NC][NK];   // the parent's row, then its children's
   const int bi = blockIdx.x * PPC + slot;
   const bool valid = bi < n;
   const int P = valid ? list[bi] : 0;
-  if (valid) interp_stage<D, Q, T>(sF[slot], fpar, stride, P, l, ratio);
   const int c0 = valid ? child0[P] : 0;
+  for (int r = 0; r <= NC; ++r)
+    stage_row<D>(s_row[slot][r], nbr, valid ? (r == 0 ? P : c0 + r - 1) : NONE, l, M);
+  __syncthreads();
+  if (valid) interp_stage<D, Q, T, SOLID>(sF[slot], fpar, stride, P, l, ratio, s_row[slot][0],
+                                          solidmask);
   __syncthreads();
   for (int c = 0; c < NC; ++c) {
     const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
     const int ch = c0 + c;
     uint64_t gm = 0ull;
-    if (valid) gm = mode_all ? ~0ull : __ldg(cellmask + 2 * (size_t)ch);
+    if (valid) gm = (mode_all & 1) ? ~0ull : __ldg(cellmask + 2 * (size_t)ch);
     const bool need = gm != 0ull;   // uniform over the parent's threads
     // pass 1: thread (i, j, k) -> sum_m w_i(m) F(m, j, k)
     if (need) {
@@ -196,26 +255,26 @@ __global__ void __launch_bounds__(64)
       __syncthreads();
     }
     // pass 3 (3D): thread (i, j, k) -> sum_l w_k(l) B(i, j, l); then the write
-    if (need) {
-      bool write = (gm >> l) & 1ull;
-      if constexpr (SOLID) write = write && !((__ldg(solidmask + ch) >> l) & 1ull);
-      if (write) {
-        const size_t base = (size_t)ch * M + l;
-        if constexpr (D == 3) {
-          const R w0 = sw[k + 4 * cz][0], w1 = sw[k + 4 * cz][1], w2 = sw[k + 4 * cz][2],
-                  w3 = sw[k + 4 * cz][3];
-          const int r = i + 4 * j;
-          static_for<0, Q>([&](auto Pp) {
-            const R* b = sB[slot][Pp];
-            const R v = w0 * b[r] + w1 * b[r + 16] + w2 * b[r + 32] + w3 * b[r + 48];
-            fch[(size_t)Pp * stride + base] = S::template save<D, Q, Pp>(v);
-          });
-        } else {
-          static_for<0, Q>([&](auto Pp) {
-            fch[(size_t)Pp * stride + base] = S::template save<D, Q, Pp>(out2[Pp]);
-          });
-        }
+    if (need && ((gm >> l) & 1ull)) {
+      R v[Q];
+      const bool solid_cell = SOLID && solidmask && ((__ldg(solidmask + ch) >> l) & 1ull);
+      if (solid_cell) {
+        static_for<0, Q>([&](auto Pp) { v[Pp] = R(VS<D, Q>::w[Pp]); });
+      } else if constexpr (D == 3) {
+        const R w0 = sw[k + 4 * cz][0], w1 = sw[k + 4 * cz][1], w2 = sw[k + 4 * cz][2],
+                w3 = sw[k + 4 * cz][3];
+        const int r = i + 4 * j;
+        static_for<0, Q>([&](auto Pp) {
+          const R* b = sB[slot][Pp];
+          v[Pp] = w0 * b[r] + w1 * b[r + 16] + w2 * b[r + 32] + w3 * b[r + 48];
+        });
+      } else {
+        static_for<0, Q>([&](auto Pp) { v[Pp] = out2[Pp]; });
       }
+      // solid cells: the rest state for new children, untouched otherwise
+      if (!solid_cell || (mode_all & 1))
+        store_child_cell<D, Q, T, SOLID>(v, fch, stride, ch, l, s_row[slot][1 + c], solidmask,
+                                         parent, marks, mode_all);
     }
     (void)cz;
     // 2D: pass 1 of the next child rewrites the x sums that pass 2 just read
@@ -224,93 +283,123 @@ __global__ void __launch_bounds__(64)
 }
 
 // ===================================================== fine-to-coarse averaging
-// Section 3.4.3.  One thread per parent cell over a child: a child covers
-// 2^D parent cells (g = gx + 2 gy [+ 4 gz]), each the mean of a 2^D group
-// of the child's fine cells, which share one class.  A group is taken when
-// its cells are interface cells (mode_sync = 0) or not ghosts
-// (mode_sync = 1); its fine cells are rescaled to the coarse level
-// (f_eq + (f - f_eq) r) and averaged.
+// Section 3.4.3.  A child covers 2^D parent cells (g = gx + 2 gy [+ 4 gz]),
+// each the mean of a 2^D group of the child's fine cells, which share one
+// class.  A group is taken when its cells are interface cells (mode_sync = 0)
+// or not ghosts (mode_sync = 1), and its parent cell is not solid.  One thread
+// per fine cell gathers it and rescales it to the coarse level
+// (f_eq + (f - f_eq) r) into shared memory; then one thread per taken group
+// sums its 2^D cells and scatters the mean into the parent cell.
+template <int D>
+__device__ __forceinline__ bool average_group_taken(const uint64_t* __restrict__ cellmask, int ch,
+                                                    int g, int mode_sync) {
+  const int f0 = Block<D>::cell(2 * (g & 1), 2 * ((g >> 1) & 1), 2 * ((g >> 2) & 1));
+  if (mode_sync) return !((__ldg(cellmask + 2 * (size_t)ch) >> f0) & 1ull);
+  return (__ldg(cellmask + 2 * (size_t)ch + 1) >> f0) & 1ull;
+}
+
 template <int D, int Q, class T, bool SOLID>
-__device__ __forceinline__ void average_cell(int P, int c, int g, T* __restrict__ fpar,
-                                             const T* __restrict__ fch, size_t stride, int c0,
-                                             const uint64_t* __restrict__ cellmask,
-                                             const uint64_t* __restrict__ solidmask,
-                                             double ratio, int mode_sync) {
+__device__ __forceinline__ void average_child(typename Store<T>::R (*sR)[Block<D>::M],
+                                              bool valid, int P, int c, int ch,
+                                              int l, T* __restrict__ fpar,
+                                              const T* __restrict__ fch, size_t stride,
+                                              const uint64_t* __restrict__ cellmask,
+                                              const int32_t* crow, const int32_t* prow,
+                                              const uint64_t* __restrict__ solidmask,
+                                              double ratio, int mode_sync) {
   using S = Store<T>;
   using R = typename S::R;
   constexpr int M = Block<D>::M;
   constexpr int NC = Block<D>::NC;
-  const int ch = c0 + c;
-  const int gx = g & 1, gy = (g >> 1) & 1, gz = (g >> 2) & 1;
-  const int f0 = Block<D>::cell(2 * gx, 2 * gy, 2 * gz);
-  if (!mode_sync && !((__ldg(cellmask + 2 * (size_t)ch + 1) >> f0) & 1ull)) return;
-  if (mode_sync && ((__ldg(cellmask + 2 * (size_t)ch) >> f0) & 1ull)) return;
-  const int pl = Block<D>::cell(2 * (c & 1) + gx, 2 * ((c >> 1) & 1) + gy,
-                                2 * ((c >> 2) & 1) + gz);
-  if constexpr (SOLID) {
-    if ((__ldg(solidmask + P) >> pl) & 1ull) return;
-  }
-  const R r = R(ratio);
-  R acc[Q];
-  static_for<0, Q>([&](auto Pp) { acc[Pp] = R(0); });
-#pragma unroll
-  for (int s = 0; s < NC; ++s) {
-    const int fl = f0 + Block<D>::cell(s & 1, (s >> 1) & 1, (s >> 2) & 1);
-    const size_t base = (size_t)ch * M + fl;
+  const int i = Block<D>::ci(l), j = Block<D>::cj(l), k = Block<D>::ck(l);
+  const int g = (i >> 1) + 2 * (j >> 1) + (D == 3 ? 4 * (k >> 1) : 0);
+  auto parent_cell = [&](int gg) {
+    return Block<D>::cell(2 * (c & 1) + (gg & 1), 2 * ((c >> 1) & 1) + ((gg >> 1) & 1),
+                          2 * ((c >> 2) & 1) + ((gg >> 2) & 1));
+  };
+  // group gg is taken: its class matches and its parent cell is not solid
+  auto taken = [&](int gg) {
+    return average_group_taken<D>(cellmask, ch, gg, mode_sync) &&
+           !(SOLID && solidmask && ((__ldg(solidmask + P) >> parent_cell(gg)) & 1ull));
+  };
+  if (valid && taken(g)) {
     R f[Q];
-    static_for<0, Q>([&](auto Pp) {
-      f[Pp] = S::template load<D, Q, Pp>(fch[(size_t)Pp * stride + base]);
-    });
+    gather_cell<D, Q, T, SOLID>(f, fch, stride, ch, l, crow, solidmask);
     R rho, ux, uy, uz;
     moments<D, Q>(f, rho, ux, uy, uz);
     const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+    const R r = R(ratio);
     static_for<0, Q>([&](auto Pp) {
       const R e = feq<D, Q, Pp>(rho, ux, uy, uz, usq15);
-      acc[Pp] += e + (f[Pp] - e) * r;
+      sR[Pp][l] = e + (f[Pp] - e) * r;
     });
   }
-  const size_t base = (size_t)P * M + pl;
-  const R inv = R(1) / R(NC);
-  static_for<0, Q>([&](auto Pp) {
-    fpar[(size_t)Pp * stride + base] = S::template save<D, Q, Pp>(acc[Pp] * inv);
-  });
+  __syncthreads();
+  // one thread per taken group: the mean of its 2^D rescaled cells,
+  // scattered into the parent cell
+  if (valid && l < NC && taken(l)) {
+    const int f0 = Block<D>::cell(2 * (l & 1), 2 * ((l >> 1) & 1), 2 * ((l >> 2) & 1));
+    R acc[Q];
+    const R inv = R(1) / R(NC);
+    static_for<0, Q>([&](auto Pp) {
+      R a = R(0);
+#pragma unroll
+      for (int s = 0; s < NC; ++s) a += sR[Pp][f0 + Block<D>::cell(s & 1, (s >> 1) & 1, (s >> 2) & 1)];
+      acc[Pp] = a * inv;
+    });
+    scatter_cell<D, Q, T, SOLID>(acc, fpar, stride, P, parent_cell(l), prow, solidmask);
+  }
 }
 
-// One thread per (child, parent cell): 128 threads = 128 / 2^D children.
-// by_parent: child item i is child i % N_c of list[i / N_c]; else child item
-// i is the block list[i] (a block with a NONE neighbour: the only blocks with
-// interface cells).
+// 128 threads = 128 / 4^D children.  by_parent: child item i is child i % N_c
+// of list[i / N_c] (skipped when the parent has no children, or, in
+// mode_sync, is not refined); else child item i is the block list[i] (a
+// block with a NONE neighbour: the only blocks with interface cells).
 template <int D, int Q, class T, bool SOLID>
 __global__ void __launch_bounds__(128)
     k_average(const int32_t* __restrict__ list, int64_t n_items, bool by_parent,
               T* __restrict__ fpar, const T* __restrict__ fch, size_t stride,
               const int32_t* __restrict__ child0, const int32_t* __restrict__ parent,
               const uint64_t* __restrict__ cellmask, const int32_t* __restrict__ status,
-              const uint64_t* __restrict__ solidmask, double ratio, int mode_sync) {
+              const int32_t* __restrict__ nbr, const uint64_t* __restrict__ solidmask,
+              double ratio, int mode_sync) {
+  using R = typename Store<T>::R;
+  constexpr int M = Block<D>::M;
   constexpr int NC = Block<D>::NC;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t item = t / NC;
-  const int g = (int)(t % NC);
-  if (item >= n_items) return;
-  int P, c, c0;
-  if (by_parent) {
-    P = list[item / NC];
-    c = (int)(item % NC);
-    c0 = child0[P];
-    if (c0 < 0 || (mode_sync && status[P] < ST_REFINED)) return;
-  } else {
-    const int ch = list[item];
-    P = parent[ch];
-    c0 = child0[P];
-    c = ch - c0;
+  constexpr int NK = Nbr<D>::K;
+  constexpr int CPC = 128 / M;
+  __shared__ R sR[CPC][Q][M];
+  __shared__ int32_t s_row[CPC][2][NK];   // the child's row and its parent's
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int64_t item = (int64_t)blockIdx.x * CPC + slot;
+  bool valid = item < n_items;
+  int P = 0, c = 0, ch = 0;
+  if (valid) {
+    if (by_parent) {
+      P = list[item / NC];
+      c = (int)(item % NC);
+      const int c0 = child0[P];
+      valid = c0 >= 0 && !(mode_sync && status[P] < ST_REFINED);
+      ch = c0 + c;
+    } else {
+      ch = list[item];
+      P = parent[ch];
+      c = ch - child0[P];
+    }
   }
-  average_cell<D, Q, T, SOLID>(P, c, g, fpar, fch, stride, c0, cellmask, solidmask, ratio,
-                               mode_sync);
+  stage_row<D>(s_row[slot][0], nbr, valid ? ch : NONE, l, M);
+  stage_row<D>(s_row[slot][1], nbr, valid ? P : NONE, l, M);
+  __syncthreads();
+  average_child<D, Q, T, SOLID>(sR[slot], valid, P, c, ch, l, fpar, fch, stride,
+                                cellmask, s_row[slot][0], s_row[slot][1], solidmask, ratio,
+                                mode_sync);
 }
 
 // ================================================ batched instances (lock-step)
 // Work items pack (instance, block) as inst << BATCH_SHIFT | block; each
 // instance's buffers, tables and per-level factors come from its descriptor.
+// The same pull step as k_collide_stream (no solid cells in a batch).
 template <int D, int Q, class T, int THREADS>
 __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS>()))
     k_collide_stream_batch(const uint32_t* __restrict__ items, int n,
@@ -340,64 +429,120 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS>()
     s_nb[s][code] = v;
   }
   __syncthreads();
+  int flags;
+  {
+    const int v = s_nb[slot][l % NCODE];
+    const unsigned lanes = M >= 32 ? 0xffffffffu : (((1u << M) - 1u) << ((threadIdx.x & 31) & ~(M - 1)));
+    const unsigned outside = __ballot_sync(0xffffffffu, v < 0) & lanes;
+    // (a slot past the end of the list has only NONE entries: no descriptor read)
+    const unsigned wall = __ballot_sync(
+        0xffffffffu, v <= -2 && descs[s_inst[slot]].faces.kind[-2 - v] != FACE_NOSLIP) & lanes;
+    const unsigned outlet = __ballot_sync(
+        0xffffffffu, v <= -2 && descs[s_inst[slot]].faces.kind[-2 - v] == FACE_OUTLET) & lanes;
+    flags = (outside ? BF_OUTSIDE : 0) | (wall ? BF_WALL : 0) | (outlet ? BF_OUTLET : 0);
+  }
   if (first + slot >= n) return;
   const InstDesc& d = descs[s_inst[slot]];
   const int b = s_nb[slot][CENTER];
-  const T* __restrict__ fin = (const T*)d.f[which_in];
-  T* __restrict__ fout = (T*)d.f[which_in ^ 1];
+  const T* __restrict__ gin = (const T*)d.f[which_in];
+  T* __restrict__ gout = (T*)d.f[which_in ^ 1];
   const size_t stride = d.stride;
-  const int own = b * M + l;
-  R f[Q];
-  static_for<0, Q>([&](auto P) {
-    f[P] = S::template load<D, Q, P>(fin[(size_t)P * stride + own]);
-  });
-  collide_push<D, Q, T, false, false>(f, l, b, g_stream_table<D, Q>.e, s_nb[slot], nullptr, fout,
-                                      stride, d.omega[level], d.faces);
+  const size_t own = (size_t)b * M + l;
+  const int32_t* nb = s_nb[slot];
+  if (flags == 0) {
+    R f[Q];
+    static_for<0, Q>([&](auto P) {
+      constexpr int p = P;
+      if constexpr (p == 0) {
+        f[0] = S::template load<D, Q, 0>(gin[own]);
+      } else {
+        const int e = link_entry<D, Q, p>(g_src_geo<D, Q>, l);
+        f[p] = S::template load<D, Q, p>(
+            gin[(size_t)p * stride + (size_t)nb[e & 31] * M + (e >> 5)]);
+      }
+    });
+    R ux, uy, uz, usq15;
+    bgk<D, Q>(f, R(d.omega[level]), ux, uy, uz, usq15);
+    static_for<0, Q>([&](auto P) {
+      gout[(size_t)P * stride + own] = S::template save<D, Q, P>(f[P]);
+    });
+  } else {
+    if (flags & BF_OUTLET)
+      step_cell_checked<D, Q, T, false, true>(gin, gout, stride, own, l, nb, nullptr, flags,
+                                              d.omega[level], d.faces);
+    else
+      step_cell_checked<D, Q, T, false, false>(gin, gout, stride, own, l, nb, nullptr, flags,
+                                               d.omega[level], d.faces);
+  }
 }
 
 template <int D, int Q, class T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 5)
     k_interp_batch(const uint32_t* __restrict__ items, int n, const InstDesc* __restrict__ descs,
                    int level, int which_par, int which_ch) {
   using R = typename Store<T>::R;
   constexpr int M = Block<D>::M;
+  constexpr int NC = Block<D>::NC;
+  constexpr int NK = Nbr<D>::K;
   constexpr int BPC = 128 / M;
   __shared__ R sF[BPC][Q][M];
+  __shared__ int32_t s_row[BPC][1 + NC][NK];
   const int slot = threadIdx.x / M;
   const int l = threadIdx.x - slot * M;
   const int bi = blockIdx.x * BPC + slot;
   const bool valid = bi < n;
-  int inst = 0, P = 0;
+  int inst = 0, P = 0, c0 = 0;
   if (valid) {
     const uint32_t it = __ldg(items + bi);
     inst = (int)(it >> BATCH_SHIFT);
     P = (int)(it & BATCH_MASK);
-    const InstDesc& d = descs[inst];
-    interp_stage<D, Q, T>(sF[slot], (const T*)d.f[which_par], d.stride, P, l, d.r_cf[level]);
+    c0 = descs[inst].child0[P];
   }
+  const InstDesc& d = descs[inst];
+  for (int r = 0; r <= NC; ++r)
+    stage_row<D>(s_row[slot][r], d.nbr, valid ? (r == 0 ? P : c0 + r - 1) : NONE, l, M);
+  __syncthreads();
+  if (valid)
+    interp_stage<D, Q, T, false>(sF[slot], (const T*)d.f[which_par], d.stride, P, l,
+                                 d.r_cf[level], s_row[slot][0], nullptr);
   __syncthreads();
   if (!valid) return;
-  const InstDesc& d = descs[inst];
-  interp_children<D, Q, T, false>(sF[slot], l, (T*)d.f[which_ch], d.stride, d.child0[P],
-                                  d.cellmask, nullptr, 0);
+  interp_children<D, Q, T, false>(sF[slot], l, (T*)d.f[which_ch], d.stride, c0, d.cellmask,
+                                  s_row[slot] + 1, nullptr, nullptr, nullptr, 0);
 }
 
 // items are parents; child item i is child i % N_c of items[i / N_c]; one
-// thread per (child, parent cell)
+// child per 4^D threads as in k_average
 template <int D, int Q, class T>
 __global__ void __launch_bounds__(128)
     k_average_batch(const uint32_t* __restrict__ items, int64_t n_items,
                     const InstDesc* __restrict__ descs, int level, int which_par, int which_ch) {
+  using R = typename Store<T>::R;
+  constexpr int M = Block<D>::M;
   constexpr int NC = Block<D>::NC;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t item = t / NC;
-  if (item >= n_items) return;
-  const uint32_t it = __ldg(items + item / NC);
-  const InstDesc& d = descs[it >> BATCH_SHIFT];
-  const int P = (int)(it & BATCH_MASK);
-  average_cell<D, Q, T, false>(P, (int)(item % NC), (int)(t % NC), (T*)d.f[which_par],
-                               (const T*)d.f[which_ch], d.stride, d.child0[P], d.cellmask,
-                               nullptr, d.r_fc[level], 0);
+  constexpr int NK = Nbr<D>::K;
+  constexpr int CPC = 128 / M;
+  __shared__ R sR[CPC][Q][M];
+  __shared__ int32_t s_row[CPC][2][NK];
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int64_t item = (int64_t)blockIdx.x * CPC + slot;
+  const bool valid = item < n_items;
+  int inst = 0, P = 0, c = 0, ch = 0;
+  if (valid) {
+    const uint32_t it = __ldg(items + item / NC);
+    inst = (int)(it >> BATCH_SHIFT);
+    P = (int)(it & BATCH_MASK);
+    c = (int)(item % NC);
+    ch = descs[inst].child0[P] + c;
+  }
+  const InstDesc& d = descs[inst];
+  stage_row<D>(s_row[slot][0], d.nbr, valid ? ch : NONE, l, M);
+  stage_row<D>(s_row[slot][1], d.nbr, valid ? P : NONE, l, M);
+  __syncthreads();
+  average_child<D, Q, T, false>(sR[slot], valid, P, c, ch, l, (T*)d.f[which_par],
+                                (const T*)d.f[which_ch], d.stride, d.cellmask, s_row[slot][0],
+                                s_row[slot][1], nullptr, d.r_fc[level], 0);
 }
 
 // ================================================================ criterion
@@ -408,6 +553,7 @@ __global__ void __launch_bounds__(128)
 template <int D, int Q, class T>
 __global__ void __launch_bounds__(128)
     k_criterion(const int32_t* __restrict__ list, int n, const T* __restrict__ f, size_t stride,
+                const int32_t* __restrict__ nbr, const uint64_t* __restrict__ solidmask,
                 const int32_t* __restrict__ status, int level, int lmax, double inv_dx,
                 int n_start, int n_inc, int8_t* __restrict__ marks, double* __restrict__ w2out) {
   using S = Store<T>;
@@ -424,9 +570,7 @@ __global__ void __launch_bounds__(128)
   if (valid) {
     b = list[bi];
     R fl[Q];
-    static_for<0, Q>([&](auto P) {
-      fl[P] = S::template load<D, Q, P>(f[(size_t)P * stride + (size_t)b * M + l]);
-    });
+    gather_cell<D, Q, T, true>(fl, f, stride, b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
     R rho, ux, uy, uz;
     moments<D, Q>(fl, rho, ux, uy, uz);
     su[slot][0][l] = ux;
@@ -496,6 +640,7 @@ __device__ __forceinline__ float squash(float x) { return copysignf(log1pf(fabsf
 template <int Q, class T>
 __global__ void __launch_bounds__(128)
     k_features(const int32_t* __restrict__ list, int n, const T* __restrict__ f, size_t stride,
+               const int32_t* __restrict__ nbr, const uint64_t* __restrict__ solidmask,
                int level, int lmax, double inv_dx, float* __restrict__ out) {
   using S = Store<T>;
   using R = typename S::R;
@@ -510,9 +655,7 @@ __global__ void __launch_bounds__(128)
   if (valid) {
     b = list[bi];
     R fl[Q];
-    static_for<0, Q>([&](auto P) {
-      fl[P] = S::template load<D, Q, P>(f[(size_t)P * stride + (size_t)b * M + l]);
-    });
+    gather_cell<D, Q, T, true>(fl, f, stride, b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
     R rho, ux, uy, uz;
     moments<D, Q>(fl, rho, ux, uy, uz);
     su[slot][0][l] = (float)ux;
@@ -596,50 +739,58 @@ __global__ void __launch_bounds__(128)
 template <int D, int Q, class T>
 __global__ void k_export_f(int64_t cap, int64_t b0, int64_t nb, const T* __restrict__ fa,
                            const T* __restrict__ fb, unsigned cur,
-                           const int32_t* __restrict__ level, double* __restrict__ out) {
+                           const int32_t* __restrict__ level, const int32_t* __restrict__ nbr,
+                           const uint64_t* __restrict__ solidmask, double* __restrict__ out) {
+  using R = typename Store<T>::R;
   constexpr int M = Block<D>::M;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nb * M) return;
   const int64_t b = b0 + g / M;
+  const int l = (int)(g % M);
   const int L = level[b];
+  if (L < 0) {
+    for (int p = 0; p < Q; ++p) out[(size_t)p * nb * M + g] = 0.0;
+    return;
+  }
   const size_t stride = (size_t)cap * M;
-  const size_t src = (size_t)b0 * M + g;
-  const T* f = (L >= 0 && ((cur >> L) & 1u)) ? fb : fa;
-  static_for<0, Q>([&](auto P) {
-    out[(size_t)P * nb * M + g] =
-        L >= 0 ? (double)Store<T>::template load<D, Q, P>(f[(size_t)P * stride + src]) : 0.0;
-  });
+  const T* f = ((cur >> L) & 1u) ? fb : fa;
+  R fl[Q];
+  gather_cell<D, Q, T, true>(fl, f, stride, (int)b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
+  static_for<0, Q>([&](auto P) { out[(size_t)P * nb * M + g] = (double)fl[P]; });
 }
 
 template <int D, int Q, class T>
 __global__ void k_import_f(int64_t cap, int64_t b0, int64_t nb, T* __restrict__ fa,
                            T* __restrict__ fb, unsigned cur, const int32_t* __restrict__ level,
+                           const int32_t* __restrict__ nbr, const uint64_t* __restrict__ solidmask,
                            const double* __restrict__ in) {
   using R = typename Store<T>::R;
   constexpr int M = Block<D>::M;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nb * M) return;
   const int64_t b = b0 + g / M;
+  const int l = (int)(g % M);
   const int L = level[b];
   if (L < 0) return;
   const size_t stride = (size_t)cap * M;
-  const size_t dst = (size_t)b0 * M + g;
   T* f = ((cur >> L) & 1u) ? fb : fa;
-  static_for<0, Q>([&](auto P) {
-    f[(size_t)P * stride + dst] =
-        Store<T>::template save<D, Q, P>((R)in[(size_t)P * nb * M + g]);
-  });
+  R v[Q];
+  static_for<0, Q>([&](auto P) { v[P] = (R)in[(size_t)P * nb * M + g]; });
+  scatter_cell<D, Q, T, true>(v, f, stride, (int)b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
 }
 
 template <int D, int Q, class T>
 __global__ void k_export_rho_u(int64_t cap, int64_t b0, int64_t nb, const T* __restrict__ fa,
                                const T* __restrict__ fb, unsigned cur,
-                               const int32_t* __restrict__ level, double* __restrict__ out) {
+                               const int32_t* __restrict__ level,
+                               const int32_t* __restrict__ nbr,
+                               const uint64_t* __restrict__ solidmask, double* __restrict__ out) {
   using R = typename Store<T>::R;
   constexpr int M = Block<D>::M;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nb * M) return;
   const int64_t b = b0 + g / M;
+  const int l = (int)(g % M);
   const int L = level[b];
   double* o = out + (size_t)g * (1 + D);
   if (L < 0) {
@@ -647,12 +798,9 @@ __global__ void k_export_rho_u(int64_t cap, int64_t b0, int64_t nb, const T* __r
     return;
   }
   const size_t stride = (size_t)cap * M;
-  const size_t src = (size_t)b0 * M + g;
   const T* f = ((cur >> L) & 1u) ? fb : fa;
   R fl[Q];
-  static_for<0, Q>([&](auto P) {
-    fl[P] = Store<T>::template load<D, Q, P>(f[(size_t)P * stride + src]);
-  });
+  gather_cell<D, Q, T, true>(fl, f, stride, (int)b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
   R rho, ux, uy, uz;
   moments<D, Q>(fl, rho, ux, uy, uz);
   o[0] = rho;
@@ -661,6 +809,7 @@ __global__ void k_export_rho_u(int64_t cap, int64_t b0, int64_t nb, const T* __r
   if (D == 3) o[3] = uz;
 }
 
+// The rest state (f = w_p in every slot; the gather of it is w_p everywhere).
 template <int D, int Q, class T>
 __global__ void k_init_rest(int64_t cap, T* __restrict__ f) {
   using R = typename Store<T>::R;
@@ -671,6 +820,44 @@ __global__ void k_init_rest(int64_t cap, T* __restrict__ f) {
   static_for<0, Q>([&](auto P) {
     constexpr double wp = VS<D, Q>::w[P];
     f[(size_t)P * stride + g] = Store<T>::template save<D, Q, P>(R(wp));
+  });
+}
+
+// Adaptation: for every cell x of a child about to be removed and every link
+// p whose target y = x + c_p lies in a same-level block that stays, the value
+// stored in x's slot p is y's pre-collision f_p; once the block is gone y
+// reads it from its own opposite slot, so it is moved there.  One thread per
+// (removed child, cell).
+template <int D, int Q, class T>
+__global__ void k_coarsen_fixup(const int32_t* __restrict__ list, int n,
+                                const int32_t* __restrict__ child0,
+                                const int32_t* __restrict__ parent,
+                                const int8_t* __restrict__ marks,
+                                const int32_t* __restrict__ nbr,
+                                const uint64_t* __restrict__ solidmask,
+                                const int32_t* __restrict__ level, T* __restrict__ fa,
+                                T* __restrict__ fb, unsigned cur, size_t stride) {
+  constexpr int M = Block<D>::M, NC = Block<D>::NC;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * NC * M) return;
+  const int l = (int)(t % M);
+  const int64_t it = t / M;
+  const int x = child0[list[it / NC]] + (int)(it % NC);
+  if (solidmask && ((solidmask[x] >> l) & 1ull)) return;
+  T* g = ((cur >> level[x]) & 1u) ? fb : fa;
+  const int32_t* row = nbr + (size_t)x * NBR_STRIDE;
+  static_for<1, Q>([&](auto P) {
+    constexpr int p = P;
+    constexpr int pb = VS<D, Q>::opp[p];
+    const int e = link_entry<D, Q, p>(g_tgt_k<D, Q>, l);
+    const int k = e & 31, tl = e >> 5;
+    if (k == 0) return;
+    const int y = row[k];
+    if (y < 0) return;
+    const int py = parent[y];
+    if (py >= 0 && marks[py] == -1) return;       // removed as well
+    if (solidmask && ((solidmask[y] >> tl) & 1ull)) return;
+    g[(size_t)pb * stride + (size_t)y * M + tl] = g[(size_t)p * stride + (size_t)x * M + l];
   });
 }
 
@@ -700,6 +887,7 @@ template <int D, int Q, class T>
 __global__ void __launch_bounds__(256)
     k_mass_partial(int64_t cap, const T* __restrict__ fa, const T* __restrict__ fb, unsigned cur,
                    const int32_t* __restrict__ level, const int32_t* __restrict__ status,
+                   const int32_t* __restrict__ nbr, const uint64_t* __restrict__ solidmask,
                    double* __restrict__ partial) {
   using R = typename Store<T>::R;
   constexpr int M = Block<D>::M;
@@ -711,9 +899,12 @@ __global__ void __launch_bounds__(256)
     if (status[b] != ST_UNREFINED) continue;
     const int L = level[b];
     const T* f = ((cur >> L) & 1u) ? fb : fa;
+    R fl[Q];
+    gather_cell<D, Q, T, true>(fl, f, stride, (int)b, (int)(g % M),
+                               nbr + (size_t)b * NBR_STRIDE, solidmask);
     double r = 0, jx = 0, jy = 0, jz = 0;
     static_for<0, Q>([&](auto P) {
-      const double v = (double)Store<T>::template load<D, Q, P>(f[(size_t)P * stride + g]);
+      const double v = (double)fl[P];
       constexpr int cx = VS<D, Q>::cx[P], cy = VS<D, Q>::cy[P], cz = VS<D, Q>::cz[P];
       r += v;
       jx += cx * v;
@@ -752,9 +943,7 @@ __global__ void __launch_bounds__(256)
     if (status[b] != ST_UNREFINED) continue;
     if ((solidmask[b] >> l) & 1ull) continue;
     R fl[Q];
-    static_for<0, Q>([&](auto P) {
-      fl[P] = S::template load<D, Q, P>(f[(size_t)P * stride + (size_t)b * M + l]);
-    });
+    gather_cell<D, Q, T, true>(fl, f, stride, b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
     R rho, ux, uy, uz;
     moments<D, Q>(fl, rho, ux, uy, uz);
     const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
@@ -788,43 +977,6 @@ inline int grid_for(int64_t n, int per) { return (int)((n + per - 1) / per); }
 template <int D, int Q, class T>
 struct Launch {
   static constexpr int M = Block<D>::M;
-  // persistent grid of the pipelined kernel: [solid][stages - 2]
-  static inline int pipe_grid[2][2] = {{0, 0}, {0, 0}};
-
-  template <bool SOLID, int STAGES>
-  static int setup_one(int sms) {
-    using PS = PipeShape<D, Q, T, STAGES>;
-    const void* fn = (const void*)k_collide_stream_pipe<D, Q, T, SOLID, STAGES>;
-    if (PS::SMEM > 227 * 1024) return 0;   // not launchable: leave grid 0
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PS::SMEM) !=
-        cudaSuccess)
-      return -1;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, PS::SMEM) != cudaSuccess)
-      return -1;
-    pipe_grid[SOLID ? 1 : 0][STAGES - 2] = per_sm > 0 ? per_sm * sms : 0;
-    return 0;
-  }
-
-  // persistent grids of the bulk-copy kernel: [threads 256/512][stages 2..4]
-  static inline int bulk_grid[2][3] = {{0, 0, 0}, {0, 0, 0}};
-
-  template <int THREADS, int STAGES>
-  static int setup_bulk(int sms) {
-    using BT = BulkTile<D, Q, T, THREADS>;
-    const size_t bytes = BT::smem(STAGES);
-    const void* fn = (const void*)k_collide_stream_bulk<D, Q, T, THREADS, STAGES>;
-    if (bytes > 227 * 1024) return 0;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-        cudaSuccess)
-      return -1;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, THREADS, bytes) != cudaSuccess)
-      return -1;
-    bulk_grid[THREADS == 512 ? 1 : 0][STAGES - 2] = per_sm > 0 ? per_sm * sms : 0;
-    return 0;
-  }
-
   static inline int sm_count = 152;
 
   static int setup() {
@@ -832,186 +984,132 @@ struct Launch {
     if (cudaGetDevice(&dev) != cudaSuccess) return -1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
     sm_count = sms;
-    if (setup_one<false, 2>(sms) || setup_one<true, 2>(sms) || setup_one<false, 3>(sms) ||
-        setup_one<true, 3>(sms))
-      return -1;
-    if (setup_bulk<512, 2>(sms) || setup_bulk<512, 3>(sms) || setup_bulk<512, 4>(sms) ||
-        setup_bulk<256, 2>(sms) || setup_bulk<256, 3>(sms) || setup_bulk<256, 4>(sms))
-      return -1;
     return 0;
   }
 
-  template <int THREADS, int STAGES>
-  static bool launch_bulk(cudaStream_t s, const int32_t* list, int n, const void* fin, void* fout,
-                          const int32_t* nbr, const StepParams& prm) {
-    using BT = BulkTile<D, Q, T, THREADS>;
-    const int g = bulk_grid[THREADS == 512 ? 1 : 0][STAGES - 2];
-    if (g <= 0) return false;
-    const int n_tiles = (n + BT::TB - 1) / BT::TB;
-    k_collide_stream_bulk<D, Q, T, THREADS, STAGES>
-        <<<std::min(n_tiles, g), THREADS, BT::smem(STAGES), s>>>(list, n, (const T*)fin,
-                                                                (T*)fout, nbr, prm);
-    return true;
+  template <bool SOLID, int THREADS, bool DENSE = false>
+  static void one_pass(cudaStream_t s, const int32_t* list, int n, const void* fin, void* fout,
+                       const int32_t* nbr, const uint64_t* sm, const StepParams& prm,
+                       const uint64_t* gm) {
+    if (gm)
+      k_collide_stream<D, Q, T, SOLID, THREADS, DENSE, true>
+          <<<grid_for(n, THREADS / M), THREADS, 0, s>>>(list, n, (const T*)fin, (T*)fout, nbr,
+                                                        sm, prm, gm);
+    else
+      k_collide_stream<D, Q, T, SOLID, THREADS, DENSE, false>
+          <<<grid_for(n, THREADS / M), THREADS, 0, s>>>(list, n, (const T*)fin, (T*)fout, nbr,
+                                                        sm, prm, nullptr);
   }
 
-  template <bool SOLID, int STAGES>
-  static void launch_pipe(cudaStream_t s, int grid, const int32_t* list, int n, const void* fin,
-                          void* fout, const int32_t* nbr, const uint64_t* sm,
-                          const StepParams& prm) {
-    k_collide_stream_pipe<D, Q, T, SOLID, STAGES>
-        <<<grid, 256, PipeShape<D, Q, T, STAGES>::SMEM, s>>>(list, n, (const T*)fin, (T*)fout,
-                                                            nbr, sm, prm);
+  template <bool SOLID>
+  static void collide_stream_t(cudaStream_t s, const int32_t* list, int n, const void* fin,
+                               void* fout, const int32_t* nbr, const uint64_t* sm,
+                               const StepParams& prm, const uint64_t* gm) {
+    // kernel_variant: 1 / 2 / 3 / 4: 512 / 256 / 128 / 64 threads per CTA
+    // (8 / 4 / 2 / 1 blocks of 4^3 cells); 5: 128 threads with 512 more
+    // resident threads per SM (tighter register budget); 0 (auto): 64
+    // threads (the fastest in the 3D cavity's AMR step, where the blocks of
+    // a CTA take different paths), with the tighter budget for D3Q27 with
+    // 16-bit storage
+    constexpr bool kDenseAuto = Q == 27 && sizeof(T) == 2;
+    switch (prm.variant) {
+      case 1: one_pass<SOLID, 512>(s, list, n, fin, fout, nbr, sm, prm, gm); break;
+      case 2: one_pass<SOLID, 256>(s, list, n, fin, fout, nbr, sm, prm, gm); break;
+      case 3: one_pass<SOLID, 128>(s, list, n, fin, fout, nbr, sm, prm, gm); break;
+      case 4: one_pass<SOLID, 64>(s, list, n, fin, fout, nbr, sm, prm, gm); break;
+      case 5: one_pass<SOLID, 128, true>(s, list, n, fin, fout, nbr, sm, prm, gm); break;
+      default: one_pass<SOLID, 64, kDenseAuto>(s, list, n, fin, fout, nbr, sm, prm, gm);
+    }
   }
 
   static void collide_stream(cudaStream_t s, const int32_t* list, int n, const void* fin,
                              void* fout, const int32_t* nbr, const uint64_t* sm,
-                             const StepParams& prm, bool solid) {
+                             const StepParams& prm, bool solid, const uint64_t* gm) {
     if (n <= 0) return;
-    const int tile = 256 / M;
-    const int n_tiles = (n + tile - 1) / tile;
-    const bool sol = solid && D == 3;
-    // variant 0 (auto): 2-stage pipeline for launches of at least two waves
-    const int stages = prm.variant == 3 ? 3 : 2;
-    const int pg = pipe_grid[sol ? 1 : 0][stages - 2];
-    const bool pipe = pg > 0 && (prm.variant == 2 || prm.variant == 3);
-    (void)n_tiles;
-    if (pipe) {
-      const int grid = std::min(n_tiles, pg);
-      if (sol) {
-        if (stages == 3) launch_pipe<true, 3>(s, grid, list, n, fin, fout, nbr, sm, prm);
-        else launch_pipe<true, 2>(s, grid, list, n, fin, fout, nbr, sm, prm);
-      } else {
-        if (stages == 3) launch_pipe<false, 3>(s, grid, list, n, fin, fout, nbr, sm, prm);
-        else launch_pipe<false, 2>(s, grid, list, n, fin, fout, nbr, sm, prm);
-      }
-      return;
-    }
-    // bulk-copy staged persistent kernel (no solid cells): 8 / 9 / 10: 512
-    // threads, 2 / 3 / 4 stages; 11 / 12 / 13: 256 threads, 2 / 3 / 4 stages
-    if (!sol && prm.variant >= 8 && prm.variant <= 13) {
-      bool done = false;
-      switch (prm.variant) {
-        case 8: done = launch_bulk<512, 2>(s, list, n, fin, fout, nbr, prm); break;
-        case 9: done = launch_bulk<512, 3>(s, list, n, fin, fout, nbr, prm); break;
-        case 10: done = launch_bulk<512, 4>(s, list, n, fin, fout, nbr, prm); break;
-        case 11: done = launch_bulk<256, 2>(s, list, n, fin, fout, nbr, prm); break;
-        case 12: done = launch_bulk<256, 3>(s, list, n, fin, fout, nbr, prm); break;
-        default: done = launch_bulk<256, 4>(s, list, n, fin, fout, nbr, prm); break;
-      }
-      if (done) return;
-    }
-    // one-pass kernel: 1: 512 threads, table in shared memory; 4: 256 threads,
-    // shared; 5: 256 threads, table read through L1; 6: 512 threads, table
-    // through L1 (the fastest on the D3Q19 FP32 256^3 forest); 7: as 6 with 512
-    // more resident threads per SM (tighter register budget); 0 (auto): 7 for
-    // D3Q27 with 16-bit storage (63 -> 40 registers, measured faster), else 6
-    const int v = prm.variant;
-    const bool dense = v == 7 || (v == 0 && Q == 27 && sizeof(T) == 2);
-    // auto: a launch of fewer cells than two waves of 512-thread CTAs runs in
-    // 128-thread CTAs, which spread its blocks over more SMs
-    if (v == 0 && (int64_t)n * M < (int64_t)512 * 6 * sm_count) {
-      if (sol) {
-        if (dense) one_pass<true, 128, false, true>(s, list, n, fin, fout, nbr, sm, prm);
-        else one_pass<true, 128, false>(s, list, n, fin, fout, nbr, sm, prm);
-      } else {
-        if (dense) one_pass<false, 128, false, true>(s, list, n, fin, fout, nbr, sm, prm);
-        else one_pass<false, 128, false>(s, list, n, fin, fout, nbr, sm, prm);
-      }
-      return;
-    }
-    if (sol) {
-      if (v == 1) one_pass<true, 512, true>(s, list, n, fin, fout, nbr, sm, prm);
-      else if (v == 4) one_pass<true, 256, true>(s, list, n, fin, fout, nbr, sm, prm);
-      else if (v == 5) one_pass<true, 256, false>(s, list, n, fin, fout, nbr, sm, prm);
-      else if (dense) one_pass<true, 512, false, true>(s, list, n, fin, fout, nbr, sm, prm);
-      else one_pass<true, 512, false>(s, list, n, fin, fout, nbr, sm, prm);
-    } else {
-      if (v == 1) one_pass<false, 512, true>(s, list, n, fin, fout, nbr, sm, prm);
-      else if (v == 4) one_pass<false, 256, true>(s, list, n, fin, fout, nbr, sm, prm);
-      else if (v == 5) one_pass<false, 256, false>(s, list, n, fin, fout, nbr, sm, prm);
-      else if (dense) one_pass<false, 512, false, true>(s, list, n, fin, fout, nbr, sm, prm);
-      else one_pass<false, 512, false>(s, list, n, fin, fout, nbr, sm, prm);
-    }
+    if (solid) collide_stream_t<true>(s, list, n, fin, fout, nbr, sm, prm, gm);
+    else collide_stream_t<false>(s, list, n, fin, fout, nbr, nullptr, prm, gm);
   }
 
-  template <bool SOLID, int THREADS, bool TAB_SMEM, bool DENSE = false>
-  static void one_pass(cudaStream_t s, const int32_t* list, int n, const void* fin, void* fout,
-                       const int32_t* nbr, const uint64_t* sm, const StepParams& prm) {
-    k_collide_stream<D, Q, T, SOLID, THREADS, TAB_SMEM, DENSE>
-        <<<grid_for(n, THREADS / M), THREADS, 0, s>>>(list, n, (const T*)fin, (T*)fout, nbr, sm,
-                                                      prm);
-  }
   static void interp(cudaStream_t s, const int32_t* list, int n, const void* fpar, void* fch,
-                     size_t stride, const int32_t* child0, const uint64_t* nm, const uint64_t* sm,
-                     double ratio, int mode_all, bool solid) {
+                     size_t stride, const int32_t* child0, const uint64_t* nm,
+                     const int32_t* nbr, const uint64_t* sm, const int32_t* parent,
+                     const int8_t* marks, double ratio, int mode_all, bool solid) {
     if (n <= 0) return;
-    // mode bit 0: every cell (new children), else ghost cells; bit 1: cubic
-    const int all = mode_all & 1;
+    // mode bit 0: every cell (new children), else ghost cells; bit 1: cubic;
+    // bit 2: direct writes into the children's own slots
+    const int all = mode_all & 5;
     if (mode_all & 2) {
       const int grid = grid_for(n, 64 / M);
-      if (solid && D == 3)
+      if (solid)
         k_interp_cubic<D, Q, T, true><<<grid, 64, 0, s>>>(list, n, (const T*)fpar, (T*)fch,
-                                                         stride, child0, nm, sm, ratio, all);
+                                                         stride, child0, nm, nbr, sm, parent,
+                                                         marks, ratio, all);
       else
         k_interp_cubic<D, Q, T, false><<<grid, 64, 0, s>>>(list, n, (const T*)fpar, (T*)fch,
-                                                          stride, child0, nm, sm, ratio, all);
+                                                          stride, child0, nm, nbr, nullptr,
+                                                          parent, marks, ratio, all);
       return;
     }
     const int grid = grid_for(n, 128 / M);
-    if (solid && D == 3)
+    if (solid)
       k_interp<D, Q, T, true><<<grid, 128, 0, s>>>(list, n, (const T*)fpar, (T*)fch, stride,
-                                                  child0, nm, sm, ratio, all);
+                                                  child0, nm, nbr, sm, parent, marks, ratio, all);
     else
       k_interp<D, Q, T, false><<<grid, 128, 0, s>>>(list, n, (const T*)fpar, (T*)fch, stride,
-                                                   child0, nm, sm, ratio, all);
+                                                   child0, nm, nbr, nullptr, parent, marks, ratio,
+                                                   all);
   }
   static void average(cudaStream_t s, const int32_t* list, int n, bool by_parent, void* fpar,
                       const void* fch, size_t stride, const int32_t* child0,
                       const int32_t* parent, const uint64_t* nm, const int32_t* status,
-                      const uint64_t* sm, double ratio, int mode_sync, bool solid) {
+                      const int32_t* nbr, const uint64_t* sm, double ratio, int mode_sync,
+                      bool solid) {
     if (n <= 0) return;
     const int64_t items = by_parent ? (int64_t)n * Block<D>::NC : (int64_t)n;
-    const int grid = (int)((items * Block<D>::NC + 127) / 128);
-    if (solid && D == 3)
+    const int grid = (int)((items + 128 / M - 1) / (128 / M));
+    if (solid)
       k_average<D, Q, T, true><<<grid, 128, 0, s>>>(list, items, by_parent, (T*)fpar,
                                                    (const T*)fch, stride, child0, parent, nm,
-                                                   status, sm, ratio, mode_sync);
+                                                   status, nbr, sm, ratio, mode_sync);
     else
       k_average<D, Q, T, false><<<grid, 128, 0, s>>>(list, items, by_parent, (T*)fpar,
                                                     (const T*)fch, stride, child0, parent, nm,
-                                                    status, sm, ratio, mode_sync);
+                                                    status, nbr, nullptr, ratio, mode_sync);
   }
   static void criterion(cudaStream_t s, const int32_t* list, int n, const void* f, size_t stride,
-                        const int32_t* status, int level, int lmax, double inv_dx, int ns, int ni,
-                        int8_t* marks, double* w2out) {
+                        const int32_t* nbr, const uint64_t* sm, const int32_t* status, int level,
+                        int lmax, double inv_dx, int ns, int ni, int8_t* marks, double* w2out) {
     if (n <= 0) return;
     k_criterion<D, Q, T><<<grid_for(n, 128 / M), 128, 0, s>>>(
-        list, n, (const T*)f, stride, status, level, lmax, inv_dx, ns, ni, marks, w2out);
+        list, n, (const T*)f, stride, nbr, sm, status, level, lmax, inv_dx, ns, ni, marks, w2out);
   }
   static void export_f(cudaStream_t s, int64_t cap, int64_t b0, int64_t nb, const void* fa,
-                       const void* fb, unsigned cur, const int32_t* level, double* out) {
-    k_export_f<D, Q, T><<<grid_for(nb * M, 256), 256, 0, s>>>(cap, b0, nb, (const T*)fa,
-                                                               (const T*)fb, cur, level, out);
+                       const void* fb, unsigned cur, const int32_t* level, const int32_t* nbr,
+                       const uint64_t* sm, double* out) {
+    k_export_f<D, Q, T><<<grid_for(nb * M, 256), 256, 0, s>>>(
+        cap, b0, nb, (const T*)fa, (const T*)fb, cur, level, nbr, sm, out);
   }
   static void import_f(cudaStream_t s, int64_t cap, int64_t b0, int64_t nb, void* fa, void* fb,
-                       unsigned cur, const int32_t* level, const double* in) {
+                       unsigned cur, const int32_t* level, const int32_t* nbr,
+                       const uint64_t* sm, const double* in) {
     k_import_f<D, Q, T><<<grid_for(nb * M, 256), 256, 0, s>>>(cap, b0, nb, (T*)fa, (T*)fb, cur,
-                                                               level, in);
+                                                               level, nbr, sm, in);
   }
   static void export_rho_u(cudaStream_t s, int64_t cap, int64_t b0, int64_t nb, const void* fa,
-                           const void* fb, unsigned cur, const int32_t* level, double* out) {
+                           const void* fb, unsigned cur, const int32_t* level,
+                           const int32_t* nbr, const uint64_t* sm, double* out) {
     k_export_rho_u<D, Q, T><<<grid_for(nb * M, 256), 256, 0, s>>>(
-        cap, b0, nb, (const T*)fa, (const T*)fb, cur, level, out);
+        cap, b0, nb, (const T*)fa, (const T*)fb, cur, level, nbr, sm, out);
   }
   static void init_rest(cudaStream_t s, int64_t cap, void* f) {
     k_init_rest<D, Q, T><<<grid_for(cap * M, 256), 256, 0, s>>>(cap, (T*)f);
   }
   static int mass_partial(cudaStream_t s, int64_t cap, const void* fa, const void* fb,
                           unsigned cur, const int32_t* level, const int32_t* status,
-                          double* partial) {
+                          const int32_t* nbr, const uint64_t* sm, double* partial) {
     const int grid = 152 * 4;
     k_mass_partial<D, Q, T><<<grid, 256, 0, s>>>(cap, (const T*)fa, (const T*)fb, cur, level,
-                                                 status, partial);
+                                                 status, nbr, sm, partial);
     return grid;
   }
   static int force_partial(cudaStream_t s, const int32_t* list, int n, const void* f,
@@ -1023,12 +1121,22 @@ struct Launch {
     return grid;
   }
   static void features(cudaStream_t s, const int32_t* list, int n, const void* f, size_t stride,
-                       int level, int lmax, double inv_dx, float* out) {
+                       const int32_t* nbr, const uint64_t* sm, int level, int lmax,
+                       double inv_dx, float* out) {
     if constexpr (D == 3) {
       if (n > 0)
-        k_features<Q, T><<<grid_for(n, 2), 128, 0, s>>>(list, n, (const T*)f, stride, level, lmax,
-                                                        inv_dx, out);
+        k_features<Q, T><<<grid_for(n, 2), 128, 0, s>>>(list, n, (const T*)f, stride, nbr, sm,
+                                                        level, lmax, inv_dx, out);
     }
+  }
+  static void coarsen_fixup(cudaStream_t s, const int32_t* list, int n, const int32_t* child0,
+                            const int32_t* parent, const int8_t* marks, const int32_t* nbr,
+                            const uint64_t* sm, const int32_t* level, void* fa, void* fb,
+                            unsigned cur, size_t stride) {
+    if (n <= 0) return;
+    const int64_t threads = (int64_t)n * Block<D>::NC * M;
+    k_coarsen_fixup<D, Q, T><<<(int)((threads + 255) / 256), 256, 0, s>>>(
+        list, n, child0, parent, marks, nbr, sm, level, (T*)fa, (T*)fb, cur, stride);
   }
 
   static void collide_stream_batch(cudaStream_t s, const uint32_t* items, int n,
@@ -1064,7 +1172,7 @@ struct Launch {
                             int level, int which_par, int which_ch) {
     if (n <= 0) return;
     const int64_t kids = (int64_t)n * Block<D>::NC;
-    k_average_batch<D, Q, T><<<(int)((kids * Block<D>::NC + 127) / 128), 128, 0, s>>>(
+    k_average_batch<D, Q, T><<<(int)((kids + 128 / M - 1) / (128 / M)), 128, 0, s>>>(
         items, kids, descs, level, which_par, which_ch);
   }
 
@@ -1072,7 +1180,8 @@ struct Launch {
     static const LbmOps o = {setup,         collide_stream, interp,   average,
                              criterion,     export_f,       import_f, export_rho_u,
                              init_rest,     mass_partial,   force_partial,
-                             collide_stream_batch, interp_batch, average_batch, features};
+                             collide_stream_batch, interp_batch, average_batch, features,
+                             coarsen_fixup};
     return &o;
   }
 };

@@ -40,45 +40,62 @@ struct StepParams {
   int32_t* wait_flag;   // device int set to 1 by a kernel whose bounded wait gave up
 };
 
+// Every kernel reads the populations of a cell through the gather and writes
+// them through the scatter of collide_stream.cuh, so the neighbour table
+// (`nbr`, NBR_STRIDE int32 per block) and the solid-cell bits (`solidmask`,
+// one uint64 per block, null when the instance has no solid cells) go with
+// every population buffer.
 struct LbmOps {
-  // one-time kernel attributes (dynamic shared memory, occupancy); call
-  // outside any stream capture
+  // one-time kernel attributes (SM count); call outside any stream capture
   int (*setup)();
-  // fused BGK collision + push streaming over `list` (active blocks of a level)
+  // fused BGK collision + pull streaming over `list` (active blocks of a level)
+  // (ghostmask: the first substep of a level below the coarsest -- its ghost
+  // cells read their interpolated pre-collision values from their own slots
+  // of fout, see interp mode bit 2; null otherwise)
   void (*collide_stream)(cudaStream_t, const int32_t* list, int n, const void* fin, void* fout,
                          const int32_t* nbr, const uint64_t* solidmask, const StepParams& prm,
-                         bool solid);
-  // coarse-to-fine linear interpolation: parents in `list`, into their children
-  // (mode bit 0: every cell of the children, else their ghost cells; bit 1:
-  // cubic instead of linear interpolation)
+                         bool solid, const uint64_t* ghostmask);
+  // coarse-to-fine interpolation: parents in `list`, into their children
+  // (mode bit 0: every cell of new children, else their ghost cells; bit 1:
+  // cubic instead of linear interpolation; bit 2, the level step: the ghost
+  // values are written as they are into the ghost cells' own slots of `fch`,
+  // the children's output buffer, for their next collide-stream to read,
+  // instead of being scattered into the stored form).  With bit 0, `parent`
+  // and `marks` (> 0: refined in this adaptation) tell new blocks from old.
   void (*interp)(cudaStream_t, const int32_t* list, int n, const void* fpar, void* fch,
                  size_t stride, const int32_t* child0, const uint64_t* cellmask,
-                 const uint64_t* solidmask, double ratio, int mode, bool solid);
+                 const int32_t* nbr, const uint64_t* solidmask, const int32_t* parent,
+                 const int8_t* marks, double ratio, int mode, bool solid);
   // fine-to-coarse averaging: by_parent -- `list` holds parents, all their
   // children are visited; else `list` holds children (boundary blocks of the
   // fine level) and parent[] leads to their parents.  mode 0: parent cells
   // over interface children, 1: over every non-ghost child (refined parents)
   void (*average)(cudaStream_t, const int32_t* list, int n, bool by_parent, void* fpar,
                   const void* fch, size_t stride, const int32_t* child0, const int32_t* parent,
-                  const uint64_t* cellmask, const int32_t* status, const uint64_t* solidmask,
-                  double ratio, int mode_sync, bool solid);
+                  const uint64_t* cellmask, const int32_t* status, const int32_t* nbr,
+                  const uint64_t* solidmask, double ratio, int mode_sync, bool solid);
   // vorticity criterion marks (+1/-1/0) and block max |w|^2
   void (*criterion)(cudaStream_t, const int32_t* list, int n, const void* f, size_t stride,
-                    const int32_t* status, int level, int lmax, double inv_dx, int n_start,
-                    int n_inc, int8_t* marks, double* w2out);
+                    const int32_t* nbr, const uint64_t* solidmask, const int32_t* status,
+                    int level, int lmax, double inv_dx, int n_start, int n_inc, int8_t* marks,
+                    double* w2out);
   // exports / imports of the blocks b0 .. b0+nb-1; the buffer of block b is
   // bufs[(cur >> level[b]) & 1].  AMR_F layout [Q][nb][M], AMR_RHO_U [nb][M][1+D]
   void (*export_f)(cudaStream_t, int64_t cap, int64_t b0, int64_t nb, const void* fa,
-                   const void* fb, unsigned cur, const int32_t* level, double* out);
+                   const void* fb, unsigned cur, const int32_t* level, const int32_t* nbr,
+                   const uint64_t* solidmask, double* out);
   void (*import_f)(cudaStream_t, int64_t cap, int64_t b0, int64_t nb, void* fa, void* fb,
-                   unsigned cur, const int32_t* level, const double* in);
+                   unsigned cur, const int32_t* level, const int32_t* nbr,
+                   const uint64_t* solidmask, const double* in);
   void (*export_rho_u)(cudaStream_t, int64_t cap, int64_t b0, int64_t nb, const void* fa,
-                       const void* fb, unsigned cur, const int32_t* level, double* out);
+                       const void* fb, unsigned cur, const int32_t* level, const int32_t* nbr,
+                       const uint64_t* solidmask, double* out);
   void (*init_rest)(cudaStream_t, int64_t cap, void* f);
   // FP64 audit: per-CTA partial sums of rho V and rho u V over leaf cells into
   // `partial` [grid][4]; returns the grid size used
   int (*mass_partial)(cudaStream_t, int64_t cap, const void* fa, const void* fb, unsigned cur,
-                      const int32_t* level, const int32_t* status, double* partial);
+                      const int32_t* level, const int32_t* status, const int32_t* nbr,
+                      const uint64_t* solidmask, double* partial);
   // momentum-exchange force (Section 5.3) partial sums [grid][3] over the
   // leaves in `list` (one level, buffer f); returns the grid size used
   int (*force_partial)(cudaStream_t, const int32_t* list, int n, const void* f, size_t stride,
@@ -94,7 +111,15 @@ struct LbmOps {
                         int level, int which_par, int which_ch);
   // 27 block summaries of the learned refinement proposal (3D only)
   void (*features)(cudaStream_t, const int32_t* list, int n, const void* f, size_t stride,
-                   int level, int lmax, double inv_dx, float* out);
+                   const int32_t* nbr, const uint64_t* solidmask, int level, int lmax,
+                   double inv_dx, float* out);
+  // adaptation, before the children of the coarsen-marked blocks in `list`
+  // are removed: a same-level neighbour that stays takes back, into its own
+  // slots, the values that were stored in the removed blocks for it
+  void (*coarsen_fixup)(cudaStream_t, const int32_t* list, int n, const int32_t* child0,
+                        const int32_t* parent, const int8_t* marks, const int32_t* nbr,
+                        const uint64_t* solidmask, const int32_t* level, void* fa, void* fb,
+                        unsigned cur, size_t stride);
 };
 
 const LbmOps* lbm_ops_d2q9(int storage);

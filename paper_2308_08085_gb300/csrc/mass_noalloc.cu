@@ -13,7 +13,7 @@
 #include <string>
 
 #include "../../include/amr.h"
-#include "lattice.cuh"
+#include "collide_stream.cuh"
 
 namespace amr {
 
@@ -54,11 +54,16 @@ int scratch_for_current_device(double** out) {
   return AMR_OK;
 }
 
+// The pre-collision populations of a cell are read with the library's gather
+// (its stored values are the outgoing post-collision populations), which needs
+// the neighbour rows and the solid-cell bits.
 template <int D, int Q, class T>
 __global__ void __launch_bounds__(kThreads)
     k_mass_static(int64_t n_blocks, const T* __restrict__ fa, const T* __restrict__ fb,
                   unsigned cur, const int32_t* __restrict__ level,
-                  const int32_t* __restrict__ status, double* __restrict__ partials) {
+                  const int32_t* __restrict__ status, const int32_t* __restrict__ nbr,
+                  const uint64_t* __restrict__ solidmask, double* __restrict__ partials) {
+  using R = typename Store<T>::R;
   constexpr int M = Block<D>::M;
   const size_t stride = (size_t)n_blocks * M;
   const int64_t first = (int64_t)blockIdx.x * kBlocksPerCta * M;
@@ -69,10 +74,13 @@ __global__ void __launch_bounds__(kThreads)
     if (status[b] != 1) continue;   // leaves only
     const int L = level[b];
     const T* f = ((cur >> L) & 1u) ? fb : fa;
+    R fl[Q];
+    gather_cell<D, Q, T, true>(fl, f, stride, (int)b, (int)(g % M), nbr + (size_t)b * NBR_STRIDE,
+                               solidmask);
     double r = 0, jx = 0, jy = 0, jz = 0;
     static_for<0, Q>([&](auto P) {
       constexpr int cx = VS<D, Q>::cx[P], cy = VS<D, Q>::cy[P], cz = VS<D, Q>::cz[P];
-      const double v = (double)Store<T>::template load<D, Q, P>(f[(size_t)P * stride + g]);
+      const double v = (double)fl[P];
       r += v;
       jx += cx * v;
       jy += cy * v;
@@ -117,11 +125,19 @@ __global__ void k_mass_static_sum(int n, int nv, const double* __restrict__ part
   }
 }
 
+struct Args {
+  int64_t n_blocks;
+  const void *fa, *fb;
+  unsigned cur;
+  const int32_t *level, *status, *nbr;
+  const uint64_t* solidmask;
+};
+
 template <int D, int Q, class T>
-void launch(int grid, cudaStream_t s, int64_t n_blocks, const void* fa, const void* fb,
-            unsigned cur, const int32_t* level, const int32_t* status, double* scratch) {
-  k_mass_static<D, Q, T><<<grid, kThreads, 0, s>>>(n_blocks, (const T*)fa, (const T*)fb, cur,
-                                                   level, status, scratch);
+void launch(int grid, cudaStream_t s, const Args& a, double* scratch) {
+  k_mass_static<D, Q, T><<<grid, kThreads, 0, s>>>(a.n_blocks, (const T*)a.fa, (const T*)a.fb,
+                                                   a.cur, a.level, a.status, a.nbr, a.solidmask,
+                                                   scratch);
 }
 
 }  // namespace
@@ -130,14 +146,22 @@ void launch(int grid, cudaStream_t s, int64_t n_blocks, const void* fa, const vo
 extern "C" int amr_mass_audit_noalloc(int dim, int q, int storage, int64_t n_blocks,
                                       const void* f_a, const void* f_b, uint32_t cur,
                                       const int32_t* level, const int32_t* status,
+                                      const int32_t* nbr, const uint64_t* solidmask,
                                       double* out_dev, void* stream) {
   using namespace amr;
+  // an error left pending by earlier work on this thread is not this call's
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess) {
+    set_error(std::string("amr_mass_audit_noalloc: CUDA error pending before the audit: ") +
+              cudaGetErrorString(pending));
+    return AMR_E_CUDA;
+  }
   const bool ok_set = (dim == 2 && q == 9) || (dim == 3 && (q == 19 || q == 27));
   if (!ok_set || storage < AMR_F64 || storage > AMR_F32_F16 || (dim == 2 && storage > AMR_F32)) {
     set_error("amr_mass_audit_noalloc: unsupported velocity set / storage");
     return AMR_E_INVAL;
   }
-  if (n_blocks <= 0 || !f_a || !f_b || !level || !status || !out_dev) {
+  if (n_blocks <= 0 || !f_a || !f_b || !level || !status || !nbr || !out_dev) {
     set_error("amr_mass_audit_noalloc: null pointer or empty input");
     return AMR_E_INVAL;
   }
@@ -153,24 +177,30 @@ extern "C" int amr_mass_audit_noalloc(int dim, int q, int storage, int64_t n_blo
   if (rc != AMR_OK) return rc;
   const int grid = (int)grid64;
   cudaStream_t s = (cudaStream_t)stream;
+  const Args args{n_blocks, f_a, f_b, cur, level, status, nbr, solidmask};
   if (dim == 2) {
-    if (storage == AMR_F64) launch<2, 9, double>(grid, s, n_blocks, f_a, f_b, cur, level, status, scratch);
-    else launch<2, 9, float>(grid, s, n_blocks, f_a, f_b, cur, level, status, scratch);
+    if (storage == AMR_F64) launch<2, 9, double>(grid, s, args, scratch);
+    else launch<2, 9, float>(grid, s, args, scratch);
   } else if (q == 19) {
-    if (storage == AMR_F64) launch<3, 19, double>(grid, s, n_blocks, f_a, f_b, cur, level, status, scratch);
-    else if (storage == AMR_F32) launch<3, 19, float>(grid, s, n_blocks, f_a, f_b, cur, level, status, scratch);
-    else if (storage == AMR_F32_BF16) launch<3, 19, __nv_bfloat16>(grid, s, n_blocks, f_a, f_b, cur, level, status, scratch);
-    else launch<3, 19, __half>(grid, s, n_blocks, f_a, f_b, cur, level, status, scratch);
+    if (storage == AMR_F64) launch<3, 19, double>(grid, s, args, scratch);
+    else if (storage == AMR_F32) launch<3, 19, float>(grid, s, args, scratch);
+    else if (storage == AMR_F32_BF16) launch<3, 19, __nv_bfloat16>(grid, s, args, scratch);
+    else launch<3, 19, __half>(grid, s, args, scratch);
   } else {
-    if (storage == AMR_F64) launch<3, 27, double>(grid, s, n_blocks, f_a, f_b, cur, level, status, scratch);
-    else if (storage == AMR_F32) launch<3, 27, float>(grid, s, n_blocks, f_a, f_b, cur, level, status, scratch);
-    else if (storage == AMR_F32_BF16) launch<3, 27, __nv_bfloat16>(grid, s, n_blocks, f_a, f_b, cur, level, status, scratch);
-    else launch<3, 27, __half>(grid, s, n_blocks, f_a, f_b, cur, level, status, scratch);
+    if (storage == AMR_F64) launch<3, 27, double>(grid, s, args, scratch);
+    else if (storage == AMR_F32) launch<3, 27, float>(grid, s, args, scratch);
+    else if (storage == AMR_F32_BF16) launch<3, 27, __nv_bfloat16>(grid, s, args, scratch);
+    else launch<3, 27, __half>(grid, s, args, scratch);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("amr_mass_audit_noalloc: partial-sum launch: ") + cudaGetErrorString(e));
+    return AMR_E_CUDA;
   }
   k_mass_static_sum<<<1, kThreads, 0, s>>>(grid, 1 + dim, scratch, out_dev);
-  const cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) {
-    set_error(std::string("amr_mass_audit_noalloc: launch: ") + cudaGetErrorString(e));
+    set_error(std::string("amr_mass_audit_noalloc: final-sum launch: ") + cudaGetErrorString(e));
     return AMR_E_CUDA;
   }
   return AMR_OK;

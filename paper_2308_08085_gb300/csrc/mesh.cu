@@ -730,6 +730,11 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     off += nCL[L] * NC;
   }
   if (nC > 0) {
+    // values stored in the removed children for their staying neighbours go
+    // back to those neighbours (the neighbour rows still hold the old links)
+    a->ops->coarsen_fixup(s, C, (int)nC, a->child0, a->parent, a->marks, a->nbr, a->sm(),
+                          a->level, a->f[0], a->f[1], a->cur, a->stride());
+    a->launches += 1;
     k_remove_children<D><<<blocks_for(nC * NC), 256, 0, s>>>(C, (int)nC, a->child0, a->status,
                                                               a->level, a->parent, a->nbr,
                                                               a->nonemask, a->cellmask);
@@ -794,7 +799,8 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     AMR_CUDA(cudaGetLastError());
     const double ratio = a->tau[L + 1] / (2.0 * a->tau[L]);
     a->ops->interp(s, C + offR[L], (int)nRL[L], a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(),
-                   a->child0, a->cellmask, a->solidmask, ratio, 1 | a->interp_bits(), a->solid);
+                   a->child0, a->cellmask, a->nbr, a->sm(), a->parent, a->marks, ratio,
+                   1 | a->interp_bits(), a->solid);
     a->launches += 1;
     AMR_CUDA(cudaGetLastError());
   }

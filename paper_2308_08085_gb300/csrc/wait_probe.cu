@@ -1,10 +1,10 @@
-// Check of the bounded mbarrier wait used by the bulk-copy staged kernels: a
-// single CTA waits on a barrier that nothing arrives at, with the same wait
-// function and a caller-chosen limit; the wait must give up and report it.
-// This exercises failure detection without any GPU fault or hang.
+// Check of the bounded mbarrier wait of mbarrier.cuh: a single CTA waits on
+// a barrier that nothing arrives at, with the library's wait function and a
+// caller-chosen limit; the wait must give up and report it.  This exercises
+// failure detection without any GPU fault or hang.
 #include "../../include/amr.h"
 #include "amr_internal.h"
-#include "collide_stream.cuh"
+#include "mbarrier.cuh"
 
 namespace amr {
 
