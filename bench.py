@@ -40,10 +40,10 @@ CAVITY_WORKLOAD = ("3D lid-driven cavity D3Q19 BGK FP32, 64^3 root cells in 4^3 
 PAPER_A100_MLUPS = 1753.0     # paper, 3D LDC D3Q19 FP32 64^3 L_max 4 on A100 (context)
 
 # ncu DRAM traffic of k_collide_stream<3,19,float> per cell update on the
-# 256^3 forest (profiles/collide_stream_bar256_d3q19_f32.md), and the hash of
-# the kernel source it was measured on.  A changed source reports null.
-NCU_TRAFFIC_PER_UPDATE = 154.5     # bytes (dram read + write) per cell update
-NCU_SOURCE_SHA = "4bc47af402e8d63c"
+# single-level 256^3 D3Q19 FP32 forest, and the hash of the kernel source it
+# was measured on.  A changed source reports null.
+NCU_TRAFFIC_PER_UPDATE = 155.4     # bytes (dram read + write) per cell update
+NCU_SOURCE_SHA = "0a3b8957d10afee6"
 
 
 def kernel_source_sha():
