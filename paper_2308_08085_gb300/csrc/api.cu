@@ -172,7 +172,7 @@ struct CheckpointHeader {
   int64_t n_gaps, coarse_steps;
   uint32_t cur, pad2_;
 };
-static const char kCheckpointTag[8] = {'A', 'M', 'R', 'C', 'K', 'P', 'T', '1'};
+static const char kCheckpointTag[8] = {'A', 'M', 'R', 'C', 'K', 'P', 'T', '2'};
 
 // ------------------------------------------------------------ profiling
 static const char* kPkNames[PK_COUNT] = {
@@ -282,8 +282,10 @@ static double ratio_cf(const Instance* a, int L) { return a->tau[L + 1] / (2.0 *
 static double ratio_fc(const Instance* a, int L) { return 2.0 * a->tau[L] / a->tau[L + 1]; }
 
 // ghost_in: the first substep of level L > 0, whose ghost cells read the
-// values the level step's interpolation left in their own output slots
-static void collide_stream_level(Instance* a, int L, bool ghost_in) {
+// values the level step's interpolation left in their own output slots.
+// xchg: level L's exchanging parents interpolate into their children's ghost
+// cells (linear interpolation).
+static void collide_stream_level(Instance* a, int L, bool ghost_in, const Exchange* xchg) {
   const int64_t n = a->n_active[L];
   // the parity flips even without active blocks: graph replay and batches
   // rely on level 0 flipping once and deeper levels an even number of times
@@ -293,11 +295,13 @@ static void collide_stream_level(Instance* a, int L, bool ghost_in) {
   }
   StepParams prm = a->prm;
   prm.omega = 1.0 / a->tau[L];
+  double bytes = (double)n * a->M * 2.0 * a->q * a->elem;
+  if (xchg) bytes += (double)a->n_ghost_cells[L] * a->q * a->elem;   // ghost cells written
   {
-    ProfScope ps(a, PK_COLLIDE, (double)n * a->M * 2.0 * a->q * a->elem, (double)n * a->M);
+    ProfScope ps(a, PK_COLLIDE, bytes, (double)n * a->M);
     a->ops->collide_stream(a->stream, a->active + (size_t)L * a->cap, (int)n, a->fbuf(L, 0),
                            a->fbuf(L, 1), a->nbr, a->sm(), prm, a->solid,
-                           ghost_in ? a->cellmask : nullptr);
+                           ghost_in ? a->cellmask : nullptr, xchg);
     a->launches += 1;
   }
   a->cur ^= 1u << L;
@@ -305,13 +309,16 @@ static void collide_stream_level(Instance* a, int L, bool ghost_in) {
 
 // Recursive level step (Section 4.1): interpolate into level L+1, collide and
 // stream level L, advance level L+1 twice, average level L+1 into level L.
-// The interpolation writes the ghost cells' values at time t into their own
-// slots of level L+1's output buffer; the first of the two substeps of level
-// L+1 (`first`) reads them there.
+// The interpolated ghost values go into their own slots of level L+1's output
+// buffer, where the first of its two substeps (`first`) reads them.  With
+// linear interpolation the interpolation is fused into level L's
+// collide-stream (Exchange: its exchanging parents gather their cells anyway);
+// cubic interpolation, which needs every cell of the parent, keeps its launch.
 static void advance(Instance* a, int L, bool first) {
   const bool fine = L + 1 < a->lmax && a->n_ids[L + 1] > 0;
   const int64_t np = a->n_parents[L];
-  if (fine && np > 0) {
+  const bool cubic = a->interp_bits() != 0;
+  if (fine && np > 0 && cubic) {
     // algorithmic bytes: the 2^D parent cells under each child with ghost
     // cells (read) and the ghost cells (written)
     const double cells = (double)a->n_ghost_cells[L];
@@ -322,7 +329,15 @@ static void advance(Instance* a, int L, bool first) {
                    nullptr, nullptr, ratio_cf(a, L), 4 | a->interp_bits(), a->solid);
     a->launches += 1;
   }
-  collide_stream_level(a, L, first && L > 0 && a->n_parents[L - 1] > 0);
+  Exchange ex{};
+  const bool xchg = fine && np > 0 && !cubic;
+  if (xchg) {
+    ex.fine_out = a->fbuf(L + 1, 1);
+    ex.child0 = a->child0;
+    ex.cellmask = a->cellmask;
+    ex.r_cf = ratio_cf(a, L);
+  }
+  collide_stream_level(a, L, first && L > 0 && a->n_parents[L - 1] > 0, xchg ? &ex : nullptr);
   if (fine) {
     advance(a, L + 1, true);
     advance(a, L + 1, false);
@@ -335,7 +350,7 @@ static void advance(Instance* a, int L, bool first) {
       // parent cells over interior children are averaged as well (mode 1:
       // every cell whose children are not ghosts), else only those over
       // interface children (mode 0)
-      if (a->interp_bits())
+      if (cubic)
         a->ops->average(a->stream, a->parents + (size_t)L * a->cap, (int)np, true,
                         a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0, a->parent,
                         a->cellmask, a->status, a->nbr, a->sm(), ratio_fc(a, L), 1, a->solid);

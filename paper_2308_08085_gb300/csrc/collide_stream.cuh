@@ -355,6 +355,107 @@ __device__ __noinline__ void step_cell_ghost(T* __restrict__ gout, size_t stride
   });
 }
 
+// An exchanging parent cell (see Exchange): the checked step of
+// step_cell_checked, with the cell's pre-collision values rescaled to the
+// fine level (f_eq + (f - f_eq) r_cf, Section 3.4.1) stored to rc[p * M + l]
+// for the interpolation into the children.
+template <int D, int Q, class T, bool SOLID, bool OUTLET>
+__device__ __noinline__ void step_cell_parent(const T* __restrict__ gin, T* __restrict__ gout,
+                                              size_t stride, size_t own, int l,
+                                              const int32_t* nb, const uint64_t* sm, int flags,
+                                              double omega, const FaceParams& faces, double r_cf,
+                                              typename Store<T>::R* rc) {
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int M = Block<D>::M;
+  R f[Q];
+  uint32_t back = 0u;
+  static_for<0, Q>([&](auto P) {
+    constexpr int p = P;
+    constexpr int pb = VS<D, Q>::opp[p];
+    if constexpr (p == 0) {
+      f[0] = S::template load<D, Q, 0>(gin[own]);
+    } else {
+      const int e = link_entry<D, Q, p>(g_src_geo<D, Q>, l);
+      const int code = e & 31, sl = e >> 5;
+      const int src = nb[code];
+      bool out = src < 0;
+      if constexpr (SOLID) out = out || ((sm[code] >> sl) & 1ull);
+      back |= (uint32_t)out << p;
+      f[p] = out ? S::template load<D, Q, p>(gin[(size_t)pb * stride + own])
+                 : S::template load<D, Q, p>(gin[(size_t)p * stride + (size_t)src * M + sl]);
+    }
+  });
+  R rho, ux, uy, uz;
+  moments<D, Q>(f, rho, ux, uy, uz);
+  const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+  const R om = R(omega), rcf = R(r_cf);
+  static_for<0, Q>([&](auto P) {
+    const R e = feq<D, Q, P>(rho, ux, uy, uz, usq15);
+    rc[P * M + l] = e + (f[P] - e) * rcf;
+    f[P] = f[P] + om * (e - f[P]);
+  });
+  if (!(flags & BF_WALL)) back = 0u;
+  static_for<0, Q>([&](auto P) {
+    constexpr int p = P;
+    constexpr int pb = VS<D, Q>::opp[p];
+    R v = f[p];
+    if constexpr (p != 0) {
+      if ((back >> pb) & 1u) {
+        const int tgt = nb[link_entry<D, Q, p>(g_tgt_geo<D, Q>, l) & 31];
+        if (tgt <= -2) {
+          if constexpr (OUTLET) v = wall_value<D, Q, p>(v, -2 - tgt, ux, uy, uz, usq15, faces);
+          else v += R(faces.bb[-2 - tgt][p]);
+        }
+      }
+    }
+    gout[(size_t)p * stride + own] = S::template save<D, Q, p>(v);
+  });
+}
+
+// The ghost cells of the children of an exchanging parent: cell l of every
+// child c with ghost cells takes the multilinear interpolant of the 2^D
+// rescaled parent cells of quadrant c (child cell I at -1/4 + I/2 between the
+// parent cell centres; Section 3.4.1), written as it is into its own slots of
+// the fine output buffer.  Solid cells are skipped.
+template <int D, int Q, class T>
+__device__ __noinline__ void interp_out(const typename Store<T>::R* rc, int l, int c0,
+                                        const uint64_t* cgm, T* __restrict__ fout, size_t stride,
+                                        const uint64_t* __restrict__ solidmask) {
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int M = Block<D>::M;
+  constexpr int NC = Block<D>::NC;
+  const R x = R(-0.25) + R(0.5) * R(Block<D>::ci(l));
+  const R y = R(-0.25) + R(0.5) * R(Block<D>::cj(l));
+  const R z = R(-0.25) + R(0.5) * R(Block<D>::ck(l));
+  R wgt[NC];
+#pragma unroll
+  for (int a = 0; a < NC; ++a) {
+    R wv = ((a & 1) ? x : R(1) - x) * ((a & 2) ? y : R(1) - y);
+    if (D == 3) wv *= (a & 4) ? z : R(1) - z;
+    wgt[a] = wv;
+  }
+#pragma unroll 1
+  for (int c = 0; c < NC; ++c) {
+    if (!((cgm[2 * c] >> l) & 1ull)) continue;   // cgm[2 c]: ghost cells of child c
+    const int ch = c0 + c;
+    if (solidmask && ((__ldg(solidmask + ch) >> l) & 1ull)) continue;
+    const int qx = c & 1, qy = (c >> 1) & 1, qz = (c >> 2) & 1;
+    int corner[NC];
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+      corner[a] = Block<D>::cell(2 * qx + (a & 1), 2 * qy + ((a >> 1) & 1), 2 * qz + ((a >> 2) & 1));
+    const size_t own = (size_t)ch * M + l;
+    static_for<0, Q>([&](auto P) {
+      R acc = R(0);
+#pragma unroll
+      for (int a = 0; a < NC; ++a) acc += wgt[a] * rc[P * M + corner[a]];
+      fout[(size_t)P * stride + own] = S::template save<D, Q, P>(acc);
+    });
+  }
+}
+
 // GHOST_IN (the first of the two substeps of a level below the coarsest):
 // the coarse-to-fine interpolation of the level step (Section 4.1) wrote the
 // pre-collision values of this level's ghost cells into their own slots of
@@ -362,22 +463,30 @@ __device__ __noinline__ void step_cell_ghost(T* __restrict__ gout, size_t stride
 // them there instead of gathering, and overwrite them with their
 // post-collision values.  `ghostmask` (= the cell-class table's ghost bits,
 // cellmask[2 b]) tells the ghost cells.
-template <int D, int Q, class T, bool SOLID, int THREADS, bool DENSE = false, bool GHOST_IN = false>
+// XCHG: the level has exchanging parents; they run step_cell_parent and then,
+// after a barrier, interp_out (see Exchange): the coarse-to-fine interpolation
+// of the level step fused into the parent level's collide-stream.
+template <int D, int Q, class T, bool SOLID, int THREADS, bool DENSE = false, bool GHOST_IN = false,
+          bool XCHG = false>
 __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, DENSE>()))
     k_collide_stream(const int32_t* __restrict__ list, int n, const T* __restrict__ gin,
                      T* __restrict__ gout, const int32_t* __restrict__ nbr,
                      const uint64_t* __restrict__ solidmask, StepParams prm,
-                     const uint64_t* __restrict__ ghostmask) {
+                     const uint64_t* __restrict__ ghostmask, Exchange ex) {
   using S = Store<T>;
   using R = typename S::R;
   constexpr int M = Block<D>::M;
+  constexpr int NC = Block<D>::NC;
   constexpr int NCODE = D == 2 ? 9 : 27;
   constexpr int CENTER = D == 2 ? 4 : 13;
   constexpr int BPC = THREADS / M;
   static_assert(THREADS % M == 0 && THREADS >= 32, "whole blocks per CTA");
   __shared__ int32_t s_nb[BPC][NCODE];
   __shared__ uint64_t s_sm[SOLID ? BPC : 1][SOLID ? NCODE : 1];
-  __shared__ uint64_t s_gm[GHOST_IN ? BPC : 1];   // ghost cells of the block
+  __shared__ uint64_t s_gm[GHOST_IN ? BPC : 1];                 // ghost cells of the block
+  __shared__ int32_t s_c0[XCHG ? BPC : 1];                       // first child, or NONE
+  __shared__ uint64_t s_cm[XCHG ? BPC : 1][XCHG ? 2 * NC : 1];   // children's ghost, interface
+  __shared__ R s_rc[XCHG ? BPC : 1][XCHG ? Q * M : 1];           // rescaled parent cells
 
   const int slot = threadIdx.x / M;
   const int l = threadIdx.x - slot * M;
@@ -390,11 +499,20 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, D
       const int b = __ldg(list + bi);
       v = __ldg(nbr + (size_t)b * NBR_STRIDE + geo_to_k<D>(code));
       if (GHOST_IN && code == 0) s_gm[s] = __ldg(ghostmask + 2 * (size_t)b);
+      if (XCHG && code == 0) s_c0[s] = __ldg(ex.child0 + b);
+    } else if (XCHG && code == 0) {
+      s_c0[s] = NONE;
     }
     s_nb[s][code] = v;
     if constexpr (SOLID) s_sm[s][code] = (v >= 0) ? __ldg(solidmask + v) : 0ull;
   }
   __syncthreads();
+  int c0 = NONE;
+  if constexpr (XCHG) {
+    c0 = s_c0[slot];
+    if (c0 >= 0 && l < 2 * NC) s_cm[slot][l] = __ldg(ex.cellmask + 2 * (size_t)c0 + l);
+    __syncthreads();
+  }
   // block flags from the neighbour codes: every warp reads all codes of its
   // block (32 consecutive cells cover every residue mod 3^D) and votes
   int flags;
@@ -412,47 +530,67 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, D
     flags = (outside ? BF_OUTSIDE : 0) | (wall ? BF_WALL : 0) | (solid ? BF_SOLID : 0) |
             (outlet ? BF_OUTLET : 0);
   }
-  if (first + slot >= n) return;
+  const bool active = first + slot < n;
+  bool solid_cell = false;
+  if constexpr (SOLID) solid_cell = (s_sm[slot][CENTER] >> l) & 1ull;   // not advanced
   const int b = s_nb[slot][CENTER];
-  if constexpr (SOLID) {
-    if ((s_sm[slot][CENTER] >> l) & 1ull) return;   // solid cells are not advanced
-  }
   const size_t stride = prm.stride;
   const size_t own = (size_t)b * M + l;
   const int32_t* nb = s_nb[slot];
-  bool ghost_in = false;
-  if constexpr (GHOST_IN) ghost_in = (s_gm[slot] >> l) & 1ull;
-  if (flags == 0) {   // (a block with ghost cells has a missing neighbour: flags != 0)
-    R f[Q];
-    static_for<0, Q>([&](auto P) {
-      constexpr int p = P;
-      if constexpr (p == 0) {
-        f[0] = S::template load<D, Q, 0>(gin[own]);
-      } else {
-        const int e = link_entry<D, Q, p>(g_src_geo<D, Q>, l);
-        f[p] = S::template load<D, Q, p>(
-            gin[(size_t)p * stride + (size_t)nb[e & 31] * M + (e >> 5)]);
-      }
-    });
-    R ux, uy, uz, usq15;
-    bgk<D, Q>(f, R(prm.omega), ux, uy, uz, usq15);
-    static_for<0, Q>([&](auto P) {
-      gout[(size_t)P * stride + own] = S::template save<D, Q, P>(f[P]);
-    });
-  } else if (ghost_in) {
-    if (flags & BF_OUTLET)
-      step_cell_ghost<D, Q, T, true>(gout, stride, own, l, nb, flags, prm.omega, prm.faces);
-    else
-      step_cell_ghost<D, Q, T, false>(gout, stride, own, l, nb, flags, prm.omega, prm.faces);
-  } else {
-    if (flags & BF_OUTLET)
-      step_cell_checked<D, Q, T, SOLID, true>(gin, gout, stride, own, l, nb,
+  if (XCHG && active && c0 >= 0) {
+    // an exchanging parent (a refined block has every same-level neighbour,
+    // so it never holds ghost cells)
+    if (solid_cell) {
+      static_for<0, Q>([&](auto P) { s_rc[slot][P * M + l] = R(VS<D, Q>::w[P]); });
+    } else if (flags & BF_OUTLET) {
+      step_cell_parent<D, Q, T, SOLID, true>(gin, gout, stride, own, l, nb,
+                                             SOLID ? s_sm[slot] : nullptr, flags, prm.omega,
+                                             prm.faces, ex.r_cf, s_rc[slot]);
+    } else {
+      step_cell_parent<D, Q, T, SOLID, false>(gin, gout, stride, own, l, nb,
                                               SOLID ? s_sm[slot] : nullptr, flags, prm.omega,
-                                              prm.faces);
-    else
-      step_cell_checked<D, Q, T, SOLID, false>(gin, gout, stride, own, l, nb,
-                                               SOLID ? s_sm[slot] : nullptr, flags, prm.omega,
-                                               prm.faces);
+                                              prm.faces, ex.r_cf, s_rc[slot]);
+    }
+  } else if (active && !solid_cell) {
+    bool ghost_in = false;
+    if constexpr (GHOST_IN) ghost_in = (s_gm[slot] >> l) & 1ull;
+    if (flags == 0) {   // (a block with ghost cells has a missing neighbour: flags != 0)
+      R f[Q];
+      static_for<0, Q>([&](auto P) {
+        constexpr int p = P;
+        if constexpr (p == 0) {
+          f[0] = S::template load<D, Q, 0>(gin[own]);
+        } else {
+          const int e = link_entry<D, Q, p>(g_src_geo<D, Q>, l);
+          f[p] = S::template load<D, Q, p>(
+              gin[(size_t)p * stride + (size_t)nb[e & 31] * M + (e >> 5)]);
+        }
+      });
+      R ux, uy, uz, usq15;
+      bgk<D, Q>(f, R(prm.omega), ux, uy, uz, usq15);
+      static_for<0, Q>([&](auto P) {
+        gout[(size_t)P * stride + own] = S::template save<D, Q, P>(f[P]);
+      });
+    } else if (ghost_in) {
+      if (flags & BF_OUTLET)
+        step_cell_ghost<D, Q, T, true>(gout, stride, own, l, nb, flags, prm.omega, prm.faces);
+      else
+        step_cell_ghost<D, Q, T, false>(gout, stride, own, l, nb, flags, prm.omega, prm.faces);
+    } else {
+      if (flags & BF_OUTLET)
+        step_cell_checked<D, Q, T, SOLID, true>(gin, gout, stride, own, l, nb,
+                                                SOLID ? s_sm[slot] : nullptr, flags, prm.omega,
+                                                prm.faces);
+      else
+        step_cell_checked<D, Q, T, SOLID, false>(gin, gout, stride, own, l, nb,
+                                                 SOLID ? s_sm[slot] : nullptr, flags, prm.omega,
+                                                 prm.faces);
+    }
+  }
+  if constexpr (XCHG) {
+    __syncthreads();
+    if (active && c0 >= 0)
+      interp_out<D, Q, T>(s_rc[slot], l, c0, s_cm[slot], (T*)ex.fine_out, stride, solidmask);
   }
 }
 

@@ -990,44 +990,59 @@ struct Launch {
   template <bool SOLID, int THREADS, bool DENSE = false>
   static void one_pass(cudaStream_t s, const int32_t* list, int n, const void* fin, void* fout,
                        const int32_t* nbr, const uint64_t* sm, const StepParams& prm,
-                       const uint64_t* gm) {
-    if (gm)
-      k_collide_stream<D, Q, T, SOLID, THREADS, DENSE, true>
-          <<<grid_for(n, THREADS / M), THREADS, 0, s>>>(list, n, (const T*)fin, (T*)fout, nbr,
-                                                        sm, prm, gm);
+                       const uint64_t* gm, const Exchange* xchg) {
+    const int grid = grid_for(n, THREADS / M);
+    const T* in = (const T*)fin;
+    T* out = (T*)fout;
+    Exchange ex{};
+    if (xchg) ex = *xchg;
+    if (gm && xchg)
+      k_collide_stream<D, Q, T, SOLID, THREADS, DENSE, true, true>
+          <<<grid, THREADS, 0, s>>>(list, n, in, out, nbr, sm, prm, gm, ex);
+    else if (gm)
+      k_collide_stream<D, Q, T, SOLID, THREADS, DENSE, true, false>
+          <<<grid, THREADS, 0, s>>>(list, n, in, out, nbr, sm, prm, gm, ex);
+    else if (xchg)
+      k_collide_stream<D, Q, T, SOLID, THREADS, DENSE, false, true>
+          <<<grid, THREADS, 0, s>>>(list, n, in, out, nbr, sm, prm, nullptr, ex);
     else
-      k_collide_stream<D, Q, T, SOLID, THREADS, DENSE, false>
-          <<<grid_for(n, THREADS / M), THREADS, 0, s>>>(list, n, (const T*)fin, (T*)fout, nbr,
-                                                        sm, prm, nullptr);
+      k_collide_stream<D, Q, T, SOLID, THREADS, DENSE, false, false>
+          <<<grid, THREADS, 0, s>>>(list, n, in, out, nbr, sm, prm, nullptr, ex);
   }
 
   template <bool SOLID>
   static void collide_stream_t(cudaStream_t s, const int32_t* list, int n, const void* fin,
                                void* fout, const int32_t* nbr, const uint64_t* sm,
-                               const StepParams& prm, const uint64_t* gm) {
+                               const StepParams& prm, const uint64_t* gm, const Exchange* x) {
     // kernel_variant: 1 / 2 / 3 / 4: 512 / 256 / 128 / 64 threads per CTA
     // (8 / 4 / 2 / 1 blocks of 4^3 cells); 5: 128 threads with 512 more
     // resident threads per SM (tighter register budget); 0 (auto): 64
     // threads (the fastest in the 3D cavity's AMR step, where the blocks of
     // a CTA take different paths), with the tighter budget for D3Q27 with
-    // 16-bit storage
+    // 16-bit storage.  Launches with exchanging parents always run 64
+    // threads per CTA, so that a parent's barrier holds no other block.
     constexpr bool kDenseAuto = Q == 27 && sizeof(T) == 2;
+    if (x) {
+      one_pass<SOLID, 64, kDenseAuto>(s, list, n, fin, fout, nbr, sm, prm, gm, x);
+      return;
+    }
     switch (prm.variant) {
-      case 1: one_pass<SOLID, 512>(s, list, n, fin, fout, nbr, sm, prm, gm); break;
-      case 2: one_pass<SOLID, 256>(s, list, n, fin, fout, nbr, sm, prm, gm); break;
-      case 3: one_pass<SOLID, 128>(s, list, n, fin, fout, nbr, sm, prm, gm); break;
-      case 4: one_pass<SOLID, 64>(s, list, n, fin, fout, nbr, sm, prm, gm); break;
-      case 5: one_pass<SOLID, 128, true>(s, list, n, fin, fout, nbr, sm, prm, gm); break;
-      default: one_pass<SOLID, 64, kDenseAuto>(s, list, n, fin, fout, nbr, sm, prm, gm);
+      case 1: one_pass<SOLID, 512>(s, list, n, fin, fout, nbr, sm, prm, gm, nullptr); break;
+      case 2: one_pass<SOLID, 256>(s, list, n, fin, fout, nbr, sm, prm, gm, nullptr); break;
+      case 3: one_pass<SOLID, 128>(s, list, n, fin, fout, nbr, sm, prm, gm, nullptr); break;
+      case 4: one_pass<SOLID, 64>(s, list, n, fin, fout, nbr, sm, prm, gm, nullptr); break;
+      case 5: one_pass<SOLID, 128, true>(s, list, n, fin, fout, nbr, sm, prm, gm, nullptr); break;
+      default: one_pass<SOLID, 64, kDenseAuto>(s, list, n, fin, fout, nbr, sm, prm, gm, nullptr);
     }
   }
 
   static void collide_stream(cudaStream_t s, const int32_t* list, int n, const void* fin,
                              void* fout, const int32_t* nbr, const uint64_t* sm,
-                             const StepParams& prm, bool solid, const uint64_t* gm) {
+                             const StepParams& prm, bool solid, const uint64_t* gm,
+                             const Exchange* x) {
     if (n <= 0) return;
-    if (solid) collide_stream_t<true>(s, list, n, fin, fout, nbr, sm, prm, gm);
-    else collide_stream_t<false>(s, list, n, fin, fout, nbr, nullptr, prm, gm);
+    if (solid) collide_stream_t<true>(s, list, n, fin, fout, nbr, sm, prm, gm, x);
+    else collide_stream_t<false>(s, list, n, fin, fout, nbr, nullptr, prm, gm, x);
   }
 
   static void interp(cudaStream_t s, const int32_t* list, int n, const void* fpar, void* fch,

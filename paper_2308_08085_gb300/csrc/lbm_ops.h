@@ -32,6 +32,19 @@ struct InstDesc {
   FaceParams faces;
 };
 
+// The coarse-to-fine interpolation of the level step (Section 4.1) fused
+// into the collide-stream of a level's exchanging parent blocks: every parent
+// cell's pre-collision value, rescaled to the fine level, goes to shared
+// memory, and the ghost cells of its children are interpolated (Section
+// 3.4.1) into their own slots of the fine output buffer, where their first
+// substep reads them.
+struct Exchange {
+  void* fine_out;              // the fine level's output buffer
+  const int32_t* child0;
+  const uint64_t* cellmask;    // [2 b]: ghost cells, [2 b + 1]: interface cells
+  double r_cf;                 // coarse -> fine rescale, tau_F / (2 tau_C)
+};
+
 struct StepParams {
   size_t stride;        // elements between population planes (capacity * M)
   double omega;         // 1 / tau_L
@@ -52,9 +65,11 @@ struct LbmOps {
   // (ghostmask: the first substep of a level below the coarsest -- its ghost
   // cells read their interpolated pre-collision values from their own slots
   // of fout, see interp mode bit 2; null otherwise)
+  // xchg: null, or the exchange with the next finer level fused into the
+  // parent blocks of this level (linear interpolation only)
   void (*collide_stream)(cudaStream_t, const int32_t* list, int n, const void* fin, void* fout,
                          const int32_t* nbr, const uint64_t* solidmask, const StepParams& prm,
-                         bool solid, const uint64_t* ghostmask);
+                         bool solid, const uint64_t* ghostmask, const Exchange* xchg);
   // coarse-to-fine interpolation: parents in `list`, into their children
   // (mode bit 0: every cell of new children, else their ghost cells; bit 1:
   // cubic instead of linear interpolation; bit 2, the level step: the ghost
