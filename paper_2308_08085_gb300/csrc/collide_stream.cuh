@@ -274,21 +274,27 @@ constexpr int BF_OUTLET = 8;    // a neighbour is an outlet face
 // through a wall, which store the wall value.  Kept out of line so that the
 // branch-free path of the other blocks keeps its registers.  OUTLET: a
 // neighbour is an outlet face (anti-bounce-back needs the cell's velocity).
-template <int D, int Q, class T, bool SOLID, bool OUTLET>
+template <int D, int Q, class T, bool SOLID, bool OUTLET, bool GHOST = false>
 __device__ __noinline__ void step_cell_checked(const T* __restrict__ gin, T* __restrict__ gout,
                                                size_t stride, size_t own, int l,
                                                const int32_t* nb, const uint64_t* sm, int flags,
-                                               double omega, const FaceParams& faces) {
+                                               double omega, const FaceParams& faces,
+                                               bool ghost_in) {
   using S = Store<T>;
   using R = typename S::R;
   constexpr int M = Block<D>::M;
   R f[Q];
   uint32_t back = 0u;
+  // ghost_in: a ghost cell at the first substep of its level reads the values
+  // the interpolation left in its own slots of the output buffer (the same
+  // loads with another address, so that the cells of a warp do not diverge)
+  if constexpr (!GHOST) ghost_in = false;
+  const T* gsrc = ghost_in ? (const T*)gout : gin;
   static_for<0, Q>([&](auto P) {
     constexpr int p = P;
     constexpr int pb = VS<D, Q>::opp[p];
     if constexpr (p == 0) {
-      f[0] = S::template load<D, Q, 0>(gin[own]);
+      f[0] = S::template load<D, Q, 0>(gsrc[own]);
     } else {
       const int e = link_entry<D, Q, p>(g_src_geo<D, Q>, l);
       const int code = e & 31, sl = e >> 5;
@@ -296,8 +302,10 @@ __device__ __noinline__ void step_cell_checked(const T* __restrict__ gin, T* __r
       bool out = src < 0;
       if constexpr (SOLID) out = out || ((sm[code] >> sl) & 1ull);
       back |= (uint32_t)out << p;
-      f[p] = out ? S::template load<D, Q, p>(gin[(size_t)pb * stride + own])
-                 : S::template load<D, Q, p>(gin[(size_t)p * stride + (size_t)src * M + sl]);
+      const size_t at = ghost_in ? (size_t)p * stride + own
+                                 : (out ? (size_t)pb * stride + own
+                                        : (size_t)p * stride + (size_t)src * M + sl);
+      f[p] = S::template load<D, Q, p>(gsrc[at]);
     }
   });
   R ux, uy, uz, usq15;
@@ -309,41 +317,6 @@ __device__ __noinline__ void step_cell_checked(const T* __restrict__ gin, T* __r
     R v = f[p];
     if constexpr (p != 0) {
       if ((back >> pb) & 1u) {   // the target of link p is outside
-        const int tgt = nb[link_entry<D, Q, p>(g_tgt_geo<D, Q>, l) & 31];
-        if (tgt <= -2) {
-          if constexpr (OUTLET) v = wall_value<D, Q, p>(v, -2 - tgt, ux, uy, uz, usq15, faces);
-          else v += R(faces.bb[-2 - tgt][p]);
-        }
-      }
-    }
-    gout[(size_t)p * stride + own] = S::template save<D, Q, p>(v);
-  });
-}
-
-// A ghost cell at the first substep of its level: the interpolation of the
-// level step left its pre-collision values in its own slots of the output
-// buffer (Section 4.1); they are read there instead of gathered, then the
-// cell collides and stores like step_cell_checked.
-template <int D, int Q, class T, bool OUTLET>
-__device__ __noinline__ void step_cell_ghost(T* __restrict__ gout, size_t stride, size_t own,
-                                             int l, const int32_t* nb, int flags, double omega,
-                                             const FaceParams& faces) {
-  using S = Store<T>;
-  using R = typename S::R;
-  R f[Q];
-  static_for<0, Q>([&](auto P) {
-    f[P] = S::template load<D, Q, P>(gout[(size_t)P * stride + own]);
-  });
-  R ux, uy, uz, usq15;
-  bgk<D, Q>(f, R(omega), ux, uy, uz, usq15);
-  // the store addresses equal the load addresses: recompute them instead of
-  // keeping Q 64-bit addresses live across the collision
-  asm volatile("" : "+l"(stride), "+l"(own));
-  static_for<0, Q>([&](auto P) {
-    constexpr int p = P;
-    R v = f[p];
-    if constexpr (p != 0) {
-      if (flags & BF_WALL) {
         const int tgt = nb[link_entry<D, Q, p>(g_tgt_geo<D, Q>, l) & 31];
         if (tgt <= -2) {
           if constexpr (OUTLET) v = wall_value<D, Q, p>(v, -2 - tgt, ux, uy, uz, usq15, faces);
@@ -571,20 +544,15 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, D
       static_for<0, Q>([&](auto P) {
         gout[(size_t)P * stride + own] = S::template save<D, Q, P>(f[P]);
       });
-    } else if (ghost_in) {
-      if (flags & BF_OUTLET)
-        step_cell_ghost<D, Q, T, true>(gout, stride, own, l, nb, flags, prm.omega, prm.faces);
-      else
-        step_cell_ghost<D, Q, T, false>(gout, stride, own, l, nb, flags, prm.omega, prm.faces);
     } else {
       if (flags & BF_OUTLET)
-        step_cell_checked<D, Q, T, SOLID, true>(gin, gout, stride, own, l, nb,
-                                                SOLID ? s_sm[slot] : nullptr, flags, prm.omega,
-                                                prm.faces);
+        step_cell_checked<D, Q, T, SOLID, true, GHOST_IN>(gin, gout, stride, own, l, nb,
+                                                          SOLID ? s_sm[slot] : nullptr, flags,
+                                                          prm.omega, prm.faces, ghost_in);
       else
-        step_cell_checked<D, Q, T, SOLID, false>(gin, gout, stride, own, l, nb,
-                                                 SOLID ? s_sm[slot] : nullptr, flags, prm.omega,
-                                                 prm.faces);
+        step_cell_checked<D, Q, T, SOLID, false, GHOST_IN>(gin, gout, stride, own, l, nb,
+                                                           SOLID ? s_sm[slot] : nullptr, flags,
+                                                           prm.omega, prm.faces, ghost_in);
     }
   }
   if constexpr (XCHG) {

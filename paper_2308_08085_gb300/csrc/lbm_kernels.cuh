@@ -469,10 +469,10 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS>()
   } else {
     if (flags & BF_OUTLET)
       step_cell_checked<D, Q, T, false, true>(gin, gout, stride, own, l, nb, nullptr, flags,
-                                              d.omega[level], d.faces);
+                                              d.omega[level], d.faces, false);
     else
       step_cell_checked<D, Q, T, false, false>(gin, gout, stride, own, l, nb, nullptr, flags,
-                                               d.omega[level], d.faces);
+                                               d.omega[level], d.faces, false);
   }
 }
 
