@@ -226,6 +226,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     step_updates = []
     active_updates = 0
+    torch.cuda.nvtx.range_push("timed")            # ncu --nvtx --nvtx-include "timed/"
     for k in range(args.steps):
         flush.fill_(k & 0xFF)                      # untimed: evict L2 between steps
         step_updates.append(PERIOD * sim.updates_per_coarse_step())
@@ -242,6 +243,7 @@ def run_ours(args):
         e2.record(stream)
         sim.profile_read(reset=False)              # one graph-captured coarse-step sample
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     launches = sim.counts()["launches"] - launches0     # this library's kernels only
     t_total = sum(e0.elapsed_time(e2) for e0, _, e2 in ev) / 1e3
