@@ -110,13 +110,37 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------- the oracle leg
+def cpu_info():
+    """Host core count and CPU model (the oracle runs on these cores)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": os.uname().machine}
+
+
 class OracleSample:
     """The CPU oracle, as it stands, on a bounded sample of the workload: the
-    same cavity (D3Q19, Re 1000, L_max 4, vorticity criterion) on a 16^3-cell
-    root grid, spun up with adaptation every 10 coarse steps (untimed); then
-    whole coarse steps are timed until a budget of seconds has passed."""
+    cavity of the benchmark cut to 32^3 root cells (D3Q19, the same Re 1000,
+    L_max 4, vorticity criterion every 50 coarse steps; the oracle cut of the
+    parity tests), spun up for 50 coarse steps and one adaptation (untimed);
+    then whole coarse steps are timed until a budget of seconds has passed."""
 
-    def __init__(self, n=16, spin_periods=3, spin_every=10):
+    def __init__(self, n=32, spin_periods=1, spin_every=50):
         import workloads as W
         from oracle.solver import ForestLBM
         self.n, self.spin = n, (spin_periods, spin_every)
@@ -134,37 +158,104 @@ class OracleSample:
             steps += 1
         return self.ups * steps, time.perf_counter() - t0, steps
 
-    def describe(self, steps):
-        return ("oracle ForestLBM (numpy, FP64, one thread) on the same cavity at a %d^3 "
-                "root grid after %d coarse steps with adaptation every %d; %d timed coarse "
-                "steps of %d leaf updates each; blocks per level %s" %
-                (self.n, self.spin[0] * self.spin[1], self.spin[1], steps, self.ups,
-                 self.sim.mesh.counts()))
+    def describe(self):
+        return ("oracle ForestLBM (numpy, FP64) on the benchmark cavity cut to %d^3 root "
+                "cells (Re 1000, L_max 4) after %d coarse steps and one adaptation; "
+                "coarse steps of %d leaf updates each, blocks per level %s"
+                % (self.n, self.spin[0] * self.spin[1], self.ups, self.sim.mesh.counts()))
 
 
-def oracle_sample(budget_s=20.0):
-    s = OracleSample()
-    upd, dt, steps = s.run(budget_s)
-    return upd / dt / 1e6, s.describe(steps), dt, upd
+FULL_RUNS = {
+    # name: (config factory, coarse steps, criterion every)
+    "c0": (lambda W: W.config_c0(), 2000, 100),
+    "c1cut": (lambda W: W.config_c1(n=32, max_blocks=(32 // 4) ** 3 * 80), 150, 50),
+}
+
+
+def oracle_full_run(name):
+    """The oracle's complete run of one of FULL_RUNS: coarse steps with the
+    criterion-driven adaptation every `every` steps, all of it timed."""
+    import workloads as W
+    from oracle.solver import ForestLBM
+    mk, steps, every = FULL_RUNS[name]
+    sim = ForestLBM(mk(W))
+    upd = 0
+    t0 = time.perf_counter()
+    for _ in range(steps // every):
+        upd += every * sim.updates_per_coarse_step()
+        sim.step(every)
+        sim.adapt()
+    return upd, time.perf_counter() - t0, sim.mesh.counts()
 
 
 def cpu_worker(args):
-    mlups, desc, dt, upd = oracle_sample(args.cpu_budget)
-    print(json.dumps({"mlups": mlups, "desc": desc, "seconds": dt, "updates": upd}))
+    """One process of the oracle leg: `--cpu-steps` steps of `--cpu-budget`
+    seconds each, after the spin-up; prints the per-step updates and times.
+    With `--cpu-run`, the complete run of FULL_RUNS[name] instead."""
+    if args.cpu_run:
+        u, t, counts = oracle_full_run(args.cpu_run)
+        print(json.dumps({"steps": [[u, t, 1]], "desc": "blocks per level at the end %s"
+                          % (counts,)}))
+        return
+    s = OracleSample()
+    steps = []
+    for _ in range(max(1, args.cpu_steps)):
+        u, t, n = s.run(args.cpu_budget)
+        steps.append([u, t, n])
+    print(json.dumps({"steps": steps, "desc": s.describe()}))
+
+
+def oracle_processes(procs, budget, n_steps, timeout, run=None):
+    """Run `procs` oracle workers at once (fresh interpreters, one thread
+    each); returns their JSON results.  The workers are independent replicas
+    of the sample: the oracle is a plain single-threaded program."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--cpu-budget",
+           str(budget), "--cpu-steps", str(n_steps)] + (["--cpu-run", run] if run else [])
+    ps = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                           env=env) for _ in range(procs)]
+    res = []
+    for p in ps:
+        try:
+            out, _ = p.communicate(timeout=timeout)
+        except subprocess.TimeoutExpired:
+            p.kill()
+            out = ""
+        line = [l for l in out.splitlines() if l.startswith("{")]
+        if p.returncode == 0 and line:
+            res.append(json.loads(line[-1]))
+    return res
+
+
+def aggregate(res, first_step=0):
+    """MLUPS of concurrent workers: all their updates over the longest
+    worker's time, counting steps from `first_step` on."""
+    upd = sum(sum(s[0] for s in r["steps"][first_step:]) for r in res)
+    sec = max(sum(s[1] for s in r["steps"][first_step:]) for r in res)
+    return upd / sec / 1e6, upd, sec
 
 
 def run_cpu_baseline(budget):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
-               MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker",
-                        "--cpu-budget", str(budget)], capture_output=True, text=True, env=env,
-                       timeout=budget * 20 + 300)
-    line = [l for l in r.stdout.splitlines() if l.startswith("{")]
-    if r.returncode != 0 or not line:
+    """The oracle leg of the default run: one worker (one core), then one
+    worker per host core at once, `budget` seconds each."""
+    info = cpu_info()
+    one = oracle_processes(1, budget, 1, budget * 20 + 300)
+    if not one:
         return None
-    d = json.loads(line[-1])
-    return {"value": d["mlups"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": d["desc"], "seconds": d["seconds"]}
+    v1, u1, s1 = aggregate(one)
+    n = max(1, info["nproc"] or 1)
+    alln = oracle_processes(n, budget, 1, budget * 20 + 600)
+    out = {"value": round(v1, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+           "sample": one[0]["desc"] + "; timed %.1f s" % s1, "seconds": round(s1, 2),
+           "cpu_model": info["model"], "nproc": info["nproc"], "machine": info["machine"]}
+    if len(alln) == n:
+        vn, un, sn = aggregate(alln)
+        out["all_cores"] = {"value": round(vn, 4), "unit": "MLUPS", "cores": n,
+                            "processes": n, "seconds": round(sn, 2),
+                            "note": "one oracle process per core at once, each the sample "
+                                    "above; all their updates over the longest time"}
+    return out
 
 
 # ---------------------------------------------------------------- our arm
@@ -255,6 +346,7 @@ def run_ours(args):
     prof = sim.profile_read(reset=True)
     sim.profile(0)
     end_counts = sim.counts()
+    leaf_updates_end = sim.updates_per_coarse_step()   # the mesh of the last timed step
 
     t_max, upd_all = combine_ranks(dist, t_total, updates, dev)
 
@@ -279,6 +371,7 @@ def run_ours(args):
     # samples of the instantaneous MLUPS of single coarse steps, each timed
     # alone (solver only; the mesh adapts every PERIOD coarse steps, untimed)
     inst = []
+    section51_start = sim.counts()["coarse_steps"]
     if args.paper_samples > 0:
         ev1 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.paper_samples)]
@@ -352,16 +445,20 @@ def run_ours(args):
                 "coarse_step_at_start": start_counts["coarse_steps"],
                 "blocks_per_level_start": start_counts["n_ids"],
                 "blocks_per_level_end": end_counts["n_ids"],
-                "leaf_updates_per_coarse_step_end": sim.updates_per_coarse_step(),
+                "leaf_updates_per_coarse_step_end": leaf_updates_end,
                 "solver_mlups_excl_adapt": round(updates / t_solver / 1e6, 2),
                 "window_mlups": [round(w, 1) for w in win],
                 "median_window_mlups": round(float(sorted(win)[len(win) // 2]), 1) if win else None,
                 "active_cell_mlups": round(active_updates / t_total / 1e6, 2),
-                "paper_mean_mlups": round(float(np.mean(inst)), 1) if inst else None,
-                "paper_mean_samples": len(inst),
-                "paper_mean_note": "mean of the instantaneous MLUPS of single coarse steps "
-                                   "(CUDA events around each), solver only, as Section 5.1 "
-                                   "averages its last 1024 samples",
+                "section51_mean": {
+                    "mlups": round(float(np.mean(inst)), 1) if inst else None,
+                    "samples": len(inst),
+                    "coarse_step_at_start": section51_start,
+                    "note": "context, not the headline: the mean of the instantaneous MLUPS "
+                            "of single coarse steps (CUDA events around each, solver only, "
+                            "no L2 flush), as Section 5.1 averages its last 1024 samples; "
+                            "measured after the timed and end-to-end steps, on the mesh of "
+                            "that later time"},
                 "mlups_count": "leaf-cell updates, sum_L 2^L (N_L - N_(L+1)/N_c) M (Section 5.1); "
                                "active_cell_mlups also counts the refined blocks advanced at the "
                                "coarse-fine interface",
@@ -376,8 +473,11 @@ def run_ours(args):
             "e2e": {"value": round(e2e_updates / t_e2e / 1e6, 2), "unit": "MLUP/s",
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": nbytes,
                     "note": "amr_step + amr_adapt + amr_fields(AMR_RHO_U) to pinned host "
-                            "memory every step; the workload's input is its configuration "
-                            "(the initial state is the rest equilibrium built by amr_init)"},
+                            "memory every step",
+                    "h2d_reason": "no per-step input: a lid-driven cavity started from rest "
+                                  "is defined by its configuration (amr_init builds the rest "
+                                  "state on the device); each step's result (rho and u of "
+                                  "every block, d2h_bytes_per_step) is read back to the host"},
             "gpu_launches": int(launches),
             "clocks": clk,
         }
@@ -1057,20 +1157,69 @@ def run_learned(args):
 
 
 # ----------------------------------------------------------- reference arm
+def run_oracle_timing(args):
+    """The oracle's complete runs of the 2D cavity (C0: D2Q9 FP64, 64^2 root
+    cells, 2000 coarse steps, criterion every 100) and of the benchmark
+    cavity cut to 32^3 root cells (150 coarse steps, criterion every 50), on
+    one core and on every core at once (one complete run per core), next to
+    the GPU running the same inputs (FP64 for C0; FP32 and FP64 for the cut)
+    through the library, adaptations included in every time."""
+    import torch
+    import workloads as W
+    from paper_2308_08085_gb300 import AmrLBM
+    info = cpu_info()
+    n = max(1, info["nproc"] or 1)
+    out = {"workload": "oracle timing", "cpu": info, "runs": {}}
+    gpu_storages = {"c0": ["f64"], "c1cut": ["f32", "f64"]}
+    for name, (mk, steps, every) in FULL_RUNS.items():
+        row = {"coarse_steps": steps, "criterion_every": every}
+        one = oracle_processes(1, 0, 1, 7200, run=name)
+        if one:
+            v, u, t = aggregate(one)
+            row["oracle_one_core"] = {"mlups": round(v, 4), "seconds": round(t, 2),
+                                      "updates": u, "mesh_end": one[0]["desc"]}
+        alln = oracle_processes(n, 0, 1, 14400, run=name)
+        if len(alln) == n:
+            v, u, t = aggregate(alln)
+            row["oracle_all_cores"] = {"mlups": round(v, 4), "seconds": round(t, 2),
+                                       "processes": n}
+        for st in gpu_storages[name]:
+            cfg = mk(W)
+            sim = AmrLBM(cfg, storage=st)
+            torch.cuda.synchronize()
+            upd = 0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps // every):
+                upd += every * sim.updates_per_coarse_step()
+                sim.step(every)
+                sim.adapt()
+            e1.record()
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            row["gpu_" + st] = {"mlups": round(upd / sec / 1e6, 1), "seconds": round(sec, 4)}
+            sim.close()
+        out["runs"][name] = row
+    return out
+
+
 def run_reference(args):
+    """The oracle as it stands on the host cores (one process per core, each
+    the bounded sample of OracleSample), `--warmup` + `--steps` steps of about
+    120 s / (warmup + steps) each; a step's value is all processes' updates
+    over the longest process time."""
     world, rank, local = dist_setup()
     if rank != 0:
         return None
+    info = cpu_info()
+    n = max(1, info["nproc"] or 1)
     per_step = max(1.0, 120.0 / max(1, args.steps + args.warmup))
-    sample = OracleSample()
-    upd = dt = 0.0
-    steps = 0
-    for i in range(args.warmup + args.steps):
-        u, t, s = sample.run(per_step)
-        if i >= args.warmup:
-            upd, dt, steps = upd + u, dt + t, steps + s
-    value = upd / dt / 1e6
-    desc = sample.describe(steps)
+    res = oracle_processes(n, per_step, args.warmup + args.steps,
+                           per_step * (args.warmup + args.steps) * 20 + 600)
+    if len(res) != n:
+        return {"impl": "reference", "unavailable": "oracle worker processes failed"}
+    value, upd, dt = aggregate(res, args.warmup)
+    desc = res[0]["desc"]
     return {"impl": "reference", "metric": "MLUPS", "value": round(value, 4),
             "unit": "MLUP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt * 1e3 / max(1, args.steps), 3),
@@ -1078,10 +1227,10 @@ def run_reference(args):
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": CAVITY_WORKLOAD,
                        "sample": "each step a bounded sample of the workload: the same cavity "
-                                 "on a 16^3 root grid, run by the oracle"},
-            "cpu_baseline": {"value": round(value, 4), "unit": "MLUP/s",
-                             "cores": 1, "kind": "oracle",
-                             "sample": desc},
+                                 "cut to 32^3 root cells, run by the oracle in one process "
+                                 "per host core"},
+            "cpu_baseline": {"value": round(value, 4), "unit": "MLUP/s", "cores": n,
+                             "kind": "oracle", "sample": desc, "cpu_model": info["model"]},
             "e2e": {"value": round(value, 4), "unit": "MLUP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -1100,11 +1249,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-bar", action="store_true")
     ap.add_argument("--cpu-worker", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--cpu-run", default=None, choices=["c0", "c1cut"])
     ap.add_argument("--variant", type=int, default=0,
                     help="collide-stream kernel: 0 auto, 1 one-pass, 2/3 pipelined stages")
     ap.add_argument("--workload", default="cavity",
                     choices=["cavity", "cylinder", "batched", "learned", "compare", "strouhal",
-                             "adapt", "table", "e6"])
+                             "adapt", "table", "e6", "oracle"])
     ap.add_argument("--e6-steps", type=int, default=200)
     ap.add_argument("--st-steps", type=int, default=16000)
     ap.add_argument("--st-spinup", type=int, default=8000)
@@ -1139,6 +1290,9 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.workload == "cylinder":
         print(json.dumps(run_cylinder(args)))
+        return
+    if args.workload == "oracle":
+        print(json.dumps(run_oracle_timing(args)))
         return
     if args.workload == "table":
         print(json.dumps(run_table(args)))

@@ -68,3 +68,24 @@ def test_ncu_traffic_figure_matches_the_kernel_source():
     assert bench.kernel_source_sha() == bench.NCU_SOURCE_SHA, (
         "collide-stream source changed: capture its DRAM traffic again and update "
         "NCU_TRAFFIC_PER_UPDATE / NCU_SOURCE_SHA")
+
+
+def test_oracle_aggregate_and_cpu_info():
+    """All-core oracle figure: every worker's updates over the longest
+    worker's time, from the first counted step on."""
+    res = [{"steps": [[10.0, 1.0, 1], [20.0, 2.0, 2]]},
+           {"steps": [[30.0, 3.0, 3], [40.0, 4.0, 4]]}]
+    v, u, s = bench.aggregate(res)
+    assert u == 100.0 and s == 7.0 and abs(v - 100.0 / 7.0 / 1e6) < 1e-18
+    v, u, s = bench.aggregate(res, first_step=1)
+    assert u == 60.0 and s == 4.0
+    info = bench.cpu_info()
+    assert info["nproc"] == os.cpu_count() and info["machine"]
+
+
+def test_oracle_sample_spins_up_and_times_whole_coarse_steps():
+    s = bench.OracleSample(n=16)
+    assert s.ups == s.sim.updates_per_coarse_step() > 0
+    u, t, n = s.run(0.0)                 # at least one coarse step
+    assert n == 1 and u == s.ups and t > 0
+    assert "16^3" in s.describe()
