@@ -713,14 +713,21 @@ def run_strouhal(args):
     side, u0, nx = 8.0, 0.05, 256
     out = {}
     for interp in args.st_interp.split(","):
-        cfg = W.channel_cylinder(q=19, nx=nx, ny=64, nz=4, side=side, cx=64, cy=33,
-                                 max_levels=args.st_levels, crit_start=100, crit_inc=1,
-                                 max_blocks=1024 * 40, span_periodic=True)
+        if args.st_dim == 2:
+            # the paper's 2D case: a 32 D x 32 D domain (256^2 root cells, D = 8),
+            # the prism 10 D downstream, one cell above the centre line
+            cfg = W.channel_cylinder(dim=2, nx=nx, ny=nx, side=side, cx=80, cy=129,
+                                     max_levels=args.st_levels, crit_start=100, crit_inc=1,
+                                     max_blocks=4096 * 40)
+        else:
+            cfg = W.channel_cylinder(q=19, nx=nx, ny=64, nz=4, side=side, cx=64, cy=33,
+                                     max_levels=args.st_levels, crit_start=100, crit_inc=1,
+                                     max_blocks=1024 * 40, span_periodic=True)
         cfg["interp"] = interp
-        sim = AmrLBM(cfg, storage="f32")
+        sim = AmrLBM(cfg, storage="f64" if args.st_dim == 2 else "f32")
         for _ in range(args.st_levels):
             sim.adapt()
-        area = (side / nx) * (cfg["nz"] / nx)
+        area = (side / nx) * ((cfg["nz"] / nx) if args.st_dim == 3 else 1.0)
         t, cl, cd = [], [], []
         n = 0
         t0 = time.perf_counter()
@@ -740,8 +747,13 @@ def run_strouhal(args):
                        "blocks_per_level": sim.counts()["n_ids"],
                        "wall_s": round(wall, 1)}
         sim.close()
-    return {"workload": "quasi-2D channel past a square prism, D3Q19, 256x64 root cells, "
-                        "span one block (periodic), side 8, Re 100, L_max %d" % args.st_levels,
+    if args.st_dim == 2:
+        name = ("2D flow past a square cylinder (Section 5.3), D2Q9 FP64, 256^2 root cells "
+                "(32 D x 32 D), D = 8, prism 10 D downstream, Re 100, L_max %d" % args.st_levels)
+    else:
+        name = ("quasi-2D channel past a square prism, D3Q19, 256x64 root cells, span one block "
+                "(periodic), side 8, Re 100, L_max %d" % args.st_levels)
+    return {"workload": name,
             "coarse_steps": args.st_steps, "spinup": args.st_spinup, "results": out}
 
 
@@ -1260,6 +1272,8 @@ def main():
     ap.add_argument("--st-steps", type=int, default=16000)
     ap.add_argument("--st-spinup", type=int, default=8000)
     ap.add_argument("--st-levels", type=int, default=3)
+    ap.add_argument("--st-dim", type=int, default=3, choices=[2, 3],
+                    help="2: the paper's 2D D2Q9 case; 3: quasi-2D D3Q19 span")
     ap.add_argument("--st-interp", default="linear,cubic")
     ap.add_argument("--cmp-steps", type=int, default=10000,
                     help="coarse steps of the FP32 / FP64 cavity comparison")

@@ -102,7 +102,8 @@ typedef struct {
   int32_t max_levels;      /* L_max, 1 .. AMR_MAX_LEVELS                       */
   int32_t crit_start;      /* N_start of the vorticity criterion (Alg. 3)      */
   int32_t crit_inc;        /* N_inc of the vorticity criterion (Alg. 3)        */
-  int32_t has_solid;       /* 1: square prism spanning z (see solid[])          */
+  int32_t has_solid;       /* 1: square prism (a square in 2D, spanning z in 3D;
+                              see solid[])                                     */
   int64_t max_blocks;      /* block capacity; (max_blocks - n_root) must be a
                               multiple of 2^dim                                 */
   double nu0;              /* viscosity, root-lattice units                     */

@@ -84,7 +84,6 @@ static int validate(const amr_config* c, std::string* why) {
       if (k < AMR_FACE_NOSLIP || k > AMR_FACE_PERIODIC) { *why = "bad face kind"; return AMR_E_INVAL; }
     }
   }
-  if (c->has_solid && c->dim != 3) { *why = "solid prism is 3D only"; return AMR_E_INVAL; }
   const int64_t n_root = (int64_t)(n[0] / 4) * (n[1] / 4) * (c->dim == 3 ? n[2] / 4 : 1);
   const int nc = c->dim == 2 ? 4 : 8;
   if (c->max_blocks < n_root || (c->max_blocks - n_root) % nc) {

@@ -379,6 +379,28 @@ def test_cylinder_distance_rule_force_end_to_end(span_periodic):
     gpu.close()
 
 
+def test_cylinder_2d_distance_rule_force_end_to_end():
+    """The paper's 2D flow past a square cylinder (Section 5.3) in small: D2Q9
+    with a solid square, inlet and far field by moving-wall bounce-back, the
+    anti-bounce-back outlet, distance refinement with freezing and the
+    vorticity criterion; tables bit-exact, fields within 1e-12, the
+    momentum-exchange force within 1e-11 of the oracle."""
+    cfg = W.channel_cylinder(dim=2, nx=96, ny=48, side=4, cx=24, cy=25, max_levels=3,
+                             max_blocks=288 * 40, refine_dist=0.05, crit_start=-1)
+    ref, gpu = run_pair(cfg, "f64", 80, 20)
+    assert ref.mesh.counts()[2] > 0
+    compare_tables(gpu, ref.mesh)
+    assert np.any(ref.mesh.status == 4)
+    ref.sync()
+    gpu.rho_u()
+    ids = ref.mesh.active_ids()
+    check_fields(gpu.populations()[ids], ref, ids, "f64")
+    f_ref, f_gpu = ref.mea_force(), gpu.force()
+    assert len(f_ref) == 2 and abs(f_ref[0]) > 0 and f_gpu[2] == 0.0
+    assert np.max(np.abs(f_gpu[:2] - f_ref)) <= 1e-11 * np.max(np.abs(f_ref))
+    gpu.close()
+
+
 # ------------------------------------------------- cubic interpolation
 def cubic(cfg):
     cfg = dict(cfg)

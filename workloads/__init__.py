@@ -89,21 +89,28 @@ def periodic_box(dim=2, q=None, n=32, nu0=0.05, max_levels=1, max_blocks=None,
 
 def channel_cylinder(q=27, nx=256, ny=64, nz=64, side=8, cx=64, cy=32,
                      u0=0.05, re=100.0, max_levels=5, max_blocks=None,
-                     crit_start=-3, crit_inc=1, refine_dist=0.15, span_periodic=False):
-    """3D channel past a square prism (Section 5.3 in 3D): uniform inlet at
-    x- and far field on the y/z faces (moving-wall bounce-back with
+                     crit_start=-3, crit_inc=1, refine_dist=0.15, span_periodic=False,
+                     dim=3):
+    """Channel past a square prism (Section 5.3): uniform inlet at x- and far
+    field on the other side faces (moving-wall bounce-back with
     u = (u0, 0, 0)), anti-bounce-back outlet at x+.  nu0 = u0 * side / Re.
     Blocks within refine_dist / 2^L of the prism or the outlet are refined and
-    frozen (the paper's 0.15 / 2^L rule, channel length 1).  span_periodic:
-    periodic z faces (a quasi-2D flow when nz is one block)."""
+    frozen (the paper's 0.15 / 2^L rule, channel length 1).  dim = 2: the
+    paper's 2D case (D2Q9 unless q is given; nz is ignored); dim = 3 spans the
+    prism along z, span_periodic: periodic z faces (a quasi-2D flow when nz is
+    one block)."""
     faces = [("moving", (u0, 0.0, 0.0)), ("outlet", (0.0, 0.0, 0.0)),
              ("moving", (u0, 0.0, 0.0)), ("moving", (u0, 0.0, 0.0)),
              ("moving", (u0, 0.0, 0.0)), ("moving", (u0, 0.0, 0.0))]
     if span_periodic:
         faces[4] = faces[5] = ("periodic", (0.0, 0.0, 0.0))
+    if dim == 2:
+        faces = faces[:4]
+        q = 9
+        nz = 4
     h = side / 2.0
-    nroot = (nx // 4) * (ny // 4) * (nz // 4)
-    cfg = dict(dim=3, q=q, nx=nx, ny=ny, nz=nz, max_levels=max_levels,
+    nroot = (nx // 4) * (ny // 4) * ((nz // 4) if dim == 3 else 1)
+    cfg = dict(dim=dim, q=q, nx=nx, ny=ny, nz=nz, max_levels=max_levels,
                nu0=u0 * side / re, faces=faces, crit_start=crit_start,
                crit_inc=crit_inc, max_blocks=max_blocks or nroot * 8 + 64,
                solid=(cx - h, cx + h, cy - h, cy + h), length_x=1.0,
