@@ -43,7 +43,7 @@ PAPER_A100_MLUPS = 1753.0     # paper, 3D LDC D3Q19 FP32 64^3 L_max 4 on A100 (c
 # single-level 256^3 D3Q19 FP32 forest, and the hash of the kernel source it
 # was measured on.  A changed source reports null.
 NCU_TRAFFIC_PER_UPDATE = 155.5     # bytes (dram read + write) per cell update
-NCU_SOURCE_SHA = "94699f3bc65d8cec"
+NCU_SOURCE_SHA = "8f5809b955f23e47"
 
 
 def kernel_source_sha():
@@ -935,18 +935,25 @@ def run_adapt_sweep(args):
 def run_batched(args):
     """64 independent 3D cavities (D3Q19 FP32) with seeded uneven sizes (32^3 to
     64^3 root cells), depths (0 to 3 extra levels) and Reynolds numbers
-    (uniform in [100, 3200]), advanced in lock-step by one batched launch
-    sequence replayed as a CUDA graph, the collide-stream CTA size picked by the
-    autotuner; compared with the same instances advanced one by one."""
+    (uniform in [100, 3200]).  Members that are BGK-unstable after the warm-up
+    (tau_0 close to 1/2 on the coarsest grids) are taken out before anything
+    is timed and listed.  The autotuner times the graph form (one launch per
+    level operation, CUDA graph) and the persistent form (one launch per call,
+    M_L x threads); the best of each form is timed over the same periods with
+    the per-member adaptations between them, and compared with the same
+    members advanced one by one.  Per-member relative L2 of rho and u after
+    one period, batched against the same members advanced one by one from the
+    same state (plain FP32 runs), on every 8th member."""
     import numpy as np
     import torch
     import workloads as W
-    from paper_2308_08085_gb300 import AmrBatch, AmrLBM
+    from paper_2308_08085_gb300 import AMR_RHO_U, AmrBatch, AmrLBM
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     n = args.batch_n
-    members = [AmrLBM(cfg, storage="f32") for cfg in W.batched_cavities(n, seed=0)]
+    cfgs = W.batched_cavities(n, seed=0)
+    members = [AmrLBM(cfg, storage="f32") for cfg in cfgs]
     batch = AmrBatch(members)
     cap_err = 0
     for _ in range(args.warmup):
@@ -954,8 +961,26 @@ def run_batched(args):
         for m in members:
             cap_err += m.adapt()[0] != 0
         batch.refresh()
-    # CTA size tuned on the refined meshes; it advances the members
-    variant = batch.autotune(trial_steps=2)
+
+    def stable(m):
+        try:
+            return bool(np.all(np.isfinite(m.mass())))
+        except Exception:
+            return False
+
+    keep = [i for i, m in enumerate(members) if stable(m)]
+    excluded = [{"member": i, "n": cfgs[i]["nx"],
+                 "re": round(0.05 * cfgs[i]["nx"] / cfgs[i]["nu0"], 1),
+                 "tau0": round(3.0 * cfgs[i]["nu0"] + 0.5, 5)} for i in range(n) if i not in keep]
+    if len(keep) < n:
+        batch.close()
+        for i in range(n):
+            if i not in keep:
+                members[i].close()
+        members = [members[i] for i in keep]
+        batch = AmrBatch(members)
+    # both forms tuned on the refined meshes; it advances the members
+    chosen, times = batch.autotune(trial_steps=2)
     for m in members:
         cap_err += m.adapt()[0] != 0
     batch.refresh()
@@ -964,26 +989,39 @@ def run_batched(args):
     def ups():
         return sum(m.updates_per_coarse_step() for m in members)
 
+    best = {}
+    for (form, t, ml), ms in times.items():
+        if form not in best or ms < best[form][1]:
+            best[form] = ((form, t, ml), ms)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_b = t_adapt = 0.0
-    upd_b = 0
-    l0 = batch.launches()
-    for _ in range(args.steps):
-        upd_b += PERIOD * ups()
-        e0.record(stream)
-        batch.step(PERIOD)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_b += e0.elapsed_time(e1) / 1e3
-        h0 = time.perf_counter()
-        for m in members:
-            cap_err += m.adapt()[0] != 0
-        batch.refresh()
-        torch.cuda.synchronize()
-        t_adapt += time.perf_counter() - h0
-    launches_b = batch.launches() - l0
+    timed = {}
+    for form in ("graph", "persistent"):
+        (f, t, ml), _ = best[form]
+        batch.configure(f, t, ml)
+        tb = ta = 0.0
+        upd = 0
+        l0 = batch.launches()
+        for _ in range(args.steps):
+            upd += PERIOD * ups()
+            e0.record(stream)
+            batch.step(PERIOD)
+            e1.record(stream)
+            batch.sync()
+            tb += e0.elapsed_time(e1) / 1e3
+            h0 = time.perf_counter()
+            for m in members:
+                cap_err += m.adapt()[0] != 0
+            batch.refresh()
+            torch.cuda.synchronize()
+            ta += time.perf_counter() - h0
+        timed[form] = {"threads_per_cta": t, "blocks_per_tile": ml,
+                       "mlups_step": round(upd / tb / 1e6, 1),
+                       "mlups_with_adapt": round(upd / (tb + ta) / 1e6, 1),
+                       "launches_per_period": (batch.launches() - l0) / args.steps}
     for m in members:                          # build each member's own graphs (untimed)
         m.step(1)
+    for m in members:
+        m.step(1)                              # back to the batch's buffer parity
     torch.cuda.synchronize()
     t_s = 0.0
     upd_s = 0
@@ -997,24 +1035,43 @@ def run_batched(args):
         torch.cuda.synchronize()
         t_s += e0.elapsed_time(e1) / 1e3
     launches_s = sum(m.launches() for m in members) - l1
-    unstable = 0
-    for m in members:
-        try:
-            m.mass()
-        except Exception:
-            unstable += 1
+    seq = round(upd_s / t_s / 1e6, 1)
+    # per-member L2, batched (chosen form) against one by one from one state
+    batch.configure(chosen["form"], chosen["threads"], chosen["tile_blocks"])
+    sample = list(range(0, len(members), 8))
+    images = {i: members[i].checkpoint() for i in sample}
+    batch.step(PERIOD)
+    batch.sync()
+    got = {i: members[i].fields_device(AMR_RHO_U, torch.float64) for i in sample}
+    l2 = []
+    for i in sample:
+        members[i].restore(images[i])
+        members[i].step(PERIOD)
+        want = members[i].fields_device(AMR_RHO_U, torch.float64)
+        l2.append(float(torch.linalg.norm(got[i] - want) / torch.linalg.norm(want)))
+        del want
+    unstable_end = sum(0 if stable(m) else 1 for m in members)
     blocks = [sum(m.counts()["n_ids"]) for m in members]
+    win = "persistent" if timed["persistent"]["mlups_step"] > timed["graph"]["mlups_step"] \
+        else "graph"
     out = {"workload": "%d 3D lid-driven cavities D3Q19 FP32, root 32^3..64^3, 0..3 extra "
                        "levels, Re uniform in [100, 3200] (seed 0), lid 0.05" % n,
-           "autotuned_threads_per_cta": variant, "autotuned_blocks_per_cta": variant // 64,
+           "members_timed": len(members),
+           "excluded_unstable_after_warmup": excluded,
+           "autotuned": chosen,
+           "autotune_ms_per_coarse_step": {"%s/%d threads/M_L %d" % k: round(v, 3)
+                                           for k, v in sorted(times.items())},
            "blocks_min_max_total": [min(blocks), max(blocks), sum(blocks)],
-           "batched_mlups_step": round(upd_b / t_b / 1e6, 1),
-           "batched_mlups_with_adapt": round(upd_b / (t_b + t_adapt) / 1e6, 1),
-           "sequential_mlups_step": round(upd_s / t_s / 1e6, 1),
-           "speedup_step": round((upd_b / t_b) / (upd_s / t_s), 3),
-           "launches_per_period_batched": launches_b / args.steps,
+           "graph_form": timed["graph"], "persistent_form": timed["persistent"],
+           "sequential_mlups_step": seq,
            "launches_per_period_sequential": launches_s / args.steps,
-           "capacity_errors": int(cap_err), "unstable_instances": unstable,
+           "faster_form": win,
+           "persistent_over_graph": round(timed["persistent"]["mlups_step"] /
+                                          timed["graph"]["mlups_step"], 3),
+           "speedup_step_over_sequential": round(timed[win]["mlups_step"] / seq, 3),
+           "per_member_rel_l2_rho_u_vs_individual_fp32":
+               {"members": sample, "max": max(l2), "median": float(np.median(l2))},
+           "capacity_errors": int(cap_err), "unstable_at_end": unstable_end,
            "periods_timed": args.steps, "coarse_steps_per_period": PERIOD}
     batch.close()
     for m in members:
@@ -1028,15 +1085,17 @@ def run_learned(args):
     FP32, distance + vorticity criterion).  Training pairs: block summaries at
     t and the plain criterion's refine flag at t + 20 coarse steps, from seeded
     runs (seed s sets Re = 100 (0.8 + 0.05 s)); seeds 1-6 train, 7-8 test.
-    Evaluation from one spun-up state: plain criterion every 50 coarse steps
-    against proposal + criterion every 200 (and criterion alone every 200).
-    Missed-refinement rate: of the leaves (below the finest level) that the
-    plain criterion flags 20 steps after an adaptation, on a copy that skipped
-    that adaptation, the fraction the adaptation did not refine."""
+    Evaluation from one spun-up state: the plain criterion every 50, 100 and
+    200 coarse steps, and proposal + criterion every 200.  Measures of late
+    refinement (see evaluate): the time-averaged under-refined leaf fraction,
+    and the missed rate at t + 20 on a shadow copy, both over leaves the
+    adaptation could refine.  With --learn-fp64-ref: the relative L2 of u on
+    two wake lines at the end of each mode against an FP64 run of the plain
+    criterion every 50 steps from the same spun-up state."""
     import numpy as np
     import torch
     import workloads as W
-    from paper_2308_08085_gb300 import AmrLBM, Mlp
+    from paper_2308_08085_gb300 import AMR_BLOCKS, AMR_NBR, AMR_RHO_U, AmrLBM, Mlp
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
@@ -1046,12 +1105,13 @@ def run_learned(args):
     def cfg_for(seed):
         return W.channel_cylinder(q=27, nx=nx, ny=int(64 * sc), nz=int(64 * sc), side=8 * sc,
                                   cx=64 * sc, cy=32 * sc, re=100.0 * (0.8 + 0.05 * seed),
-                                  max_levels=args.cyl_levels, max_blocks=args.cyl_cap)
+                                  max_levels=args.cyl_levels, max_blocks=args.cyl_cap,
+                                  crit_start=args.learn_crit_start)
 
     cap_errors = {"spin": 0}
 
-    def spun_up(seed):
-        sim = AmrLBM(cfg_for(seed), storage="f32")
+    def spun_up(seed, storage="f32"):
+        sim = AmrLBM(cfg_for(seed), storage=storage)
         for _ in range(args.learn_spin):
             sim.step(50)
             cap_errors["spin"] += sim.adapt()[0] != 0
@@ -1099,18 +1159,36 @@ def run_learned(args):
             "accuracy": float((pr.float() == yte).float().mean())}
 
     # ---- evaluation from one spun-up state (deterministic: equal histories).
-    # A shadow copy skips each adaptation for 20 steps; the plain criterion's
-    # flags there (leaves below the finest level) are the blocks that needed
-    # refinement 20 steps ahead; a flag is missed when the main run's
-    # adaptation did not refine that block.  The shadow then applies the same
-    # marks, so both meshes stay identical.
+    # Two measures of refinement that came too late:
+    # * under-refinement: every `sample_every` coarse steps the plain
+    #   criterion is evaluated on the running mesh without adapting; the
+    #   fraction of leaves it would refine that the mesh could refine (leaf
+    #   below the finest level with every same-level neighbour present: the
+    #   eligibility rule of the adaptation) is averaged over the run;
+    # * missed at t + 20: a shadow copy skips each adaptation for 20 coarse
+    #   steps; of the eligible leaves the plain criterion flags there, the
+    #   fraction that the adaptation at t did not refine (windows whose
+    #   adaptation hit the capacity are left out and counted).  The shadow
+    #   then applies the same marks, so both meshes stay identical.
     lmax = args.cyl_levels
+    every = args.learn_sample_every
 
-    def evaluate(mode):
-        main, shadow = spun_up(9), spun_up(9)
+    def eligible_flagged(sim):
+        marks = sim.criterion_marks()
+        blk = sim.fields_device(AMR_BLOCKS, torch.int32).reshape(4, sim.cap)
+        nbr = sim.fields_device(AMR_NBR, torch.int32).reshape(sim.cap, -1)
+        leaf = blk[1] == 1
+        elig = leaf & (blk[0] < lmax - 1) & ~(nbr == -1).any(1)
+        del nbr
+        return (marks > 0) & elig, leaf
+
+    def evaluate(mode, period, shadow_on):
+        main = spun_up(9)
+        shadow = spun_up(9) if shadow_on else None
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        period = 50 if mode == "plain" else 200
-        ups_sum, t_ms, flagged, missed, adapts, cap_err = 0.0, 0.0, 0, 0, 0, 0
+        ups_sum, t_ms, adapts, cap_err = 0.0, 0.0, 0, 0
+        flagged = missed = skipped = 0
+        under = []
         steps = 0
 
         def timed(fn):
@@ -1132,40 +1210,105 @@ def run_learned(args):
             cap_err += rc != 0
             adapts += 1
             ups = main.updates_per_coarse_step()
-            t_ms += timed(lambda: main.step(20))[1]
-            shadow.step(20)
-            blk = shadow.blocks()
-            want = ((shadow.criterion_marks() > 0).cpu().numpy() & (blk["status"] == 1)
-                    & (blk["level"] < lmax - 1))
-            still_leaf = main.blocks()["status"] == 1
-            flagged += int(want.sum())
-            missed += int((want & still_leaf).sum())
-            shadow.adapt(marks)
-            t_ms += timed(lambda: main.step(period - 20))[1]
-            shadow.step(period - 20)
+            done = 0
+            while done < period:
+                k = min(every, period - done)
+                t_ms += timed(lambda: main.step(k))[1]
+                done += k
+                f, leaf = eligible_flagged(main)
+                under.append(float(f.sum()) / max(1.0, float(leaf.sum())))
+                if shadow is not None and done == 20:
+                    shadow.step(20)
+                    want, _ = eligible_flagged(shadow)
+                    if rc == 0:
+                        still = main.fields_device(AMR_BLOCKS, torch.int32).reshape(4, main.cap)[1] == 1
+                        flagged += int(want.sum())
+                        missed += int((want & still).sum())
+                    else:
+                        skipped += 1
+                    shadow.adapt(marks)
+                    shadow.step(period - 20)
             ups_sum += ups * period
             steps += period
-        out = {"mlups_incl_adapt": round(ups_sum / (t_ms / 1e3) / 1e6, 1),
+        if ref_lines is not None:
+            got = wake_lines(main)
+            out_l2 = float(np.linalg.norm(got - ref_lines) / np.linalg.norm(ref_lines))
+        out = {"period": period, "mlups_incl_adapt": round(ups_sum / (t_ms / 1e3) / 1e6, 1),
                "adaptations": adapts, "coarse_steps": steps,
-               "needed_at_t_plus_20": flagged,
-               "missed_refinement_rate": round(missed / max(1, flagged), 4),
-               "capacity_errors": cap_err,
-               "blocks_end": main.counts()["n_ids"]}
+               "under_refined_leaf_fraction": round(float(np.mean(under)), 5),
+               "capacity_errors": cap_err, "blocks_end": main.counts()["n_ids"]}
+        if ref_lines is not None:
+            out["rel_l2_wake_lines_vs_fp64_plain_every_50"] = round(out_l2, 6)
+        if shadow is not None:
+            out["missed_at_t_plus_20"] = {"eligible_flagged": flagged, "missed": missed,
+                                          "rate": round(missed / max(1, flagged), 4),
+                                          "windows_left_out_capacity": skipped}
+            shadow.close()
         main.close()
-        shadow.close()
         torch.cuda.empty_cache()
         return out
 
-    ev = {m: evaluate(m) for m in ("plain", "learned", "criterion_every_200")}
+    def wake_lines(sim):
+        """u_x, u_y (lattice units of the root grid) on the wake centreline
+        (y = prism centre, z = mid-span, from the prism's rear face to the
+        outlet) and on the cross line two side lengths behind the prism, 128
+        points each, from the leaf cell that holds each point."""
+        side, cx, cy = 8 * sc, 64 * sc, 32 * sc
+        ny, nz = int(64 * sc), int(64 * sc)
+        s = (np.arange(128) + 0.5) / 128
+        pts = np.concatenate([
+            np.stack([cx + side / 2 + s * (nx - cx - side / 2), np.full(128, cy),
+                      np.full(128, nz / 2)], 1),
+            np.stack([np.full(128, cx + 2 * side), s * ny, np.full(128, nz / 2)], 1)])
+        blk = sim.blocks()
+        X = sim.coords()
+        leaves = np.nonzero(blk["status"] == 1)[0]
+        w = 4.0 / 2.0 ** blk["level"][leaves]
+        lo, hi = X[leaves], X[leaves] + w[:, None]
+        idx = np.empty(len(pts), np.int64)
+        for i, pnt in enumerate(pts):
+            k = np.nonzero(np.all((lo <= pnt) & (pnt < hi), axis=1))[0][0]
+            b = leaves[k]
+            cell = np.floor((pnt - X[b]) / (w[k] / 4.0)).astype(int)
+            idx[i] = b * 64 + cell[0] + 4 * cell[1] + 16 * cell[2]
+        ru = sim.fields_device(AMR_RHO_U, torch.float64).view(-1, 4)
+        u = ru[torch.from_numpy(idx).to(dev)][:, 1:3].cpu().numpy()
+        del ru
+        return u.reshape(-1)
+
+    ref_lines = None
+    fp64_ref = None
+    if args.learn_fp64_ref:
+        ref = spun_up(9, "f64")
+        for _ in range(args.learn_eval_steps // 50):
+            ref.adapt()
+            ref.step(50)
+        ref_lines = wake_lines(ref)
+        fp64_ref = {"blocks_end": ref.counts()["n_ids"]}
+        ref.close()
+        torch.cuda.empty_cache()
+
+    shadow_on = not args.learn_no_shadow
+    ev = {"plain_every_50": evaluate("plain", 50, shadow_on),
+          "plain_every_100": evaluate("plain", 100, shadow_on),
+          "plain_every_200": evaluate("plain", 200, shadow_on),
+          "learned_every_200": evaluate("learned", 200, shadow_on)}
+    fr = [ev["plain_every_%d" % p]["under_refined_leaf_fraction"] for p in (50, 100, 200)]
     return {"workload": "learned refinement proposal, channel past a square prism D3Q27 FP32, "
-                        "%dx%dx%d root, L_max %d" % (nx, int(64 * sc), int(64 * sc),
-                                                     args.cyl_levels),
+                        "%dx%dx%d root, L_max %d, criterion N_start %d" % (
+                            nx, int(64 * sc), int(64 * sc), args.cyl_levels,
+                            args.learn_crit_start),
             "pairs_train": int(xtr.shape[0]), "pairs_test": test["pairs"],
             "pos_weight": round(pw, 2), "epochs": args.learn_epochs,
             "loss_first_last": [round(losses[0], 4), round(losses[-1], 4)],
             "train_seconds": round(t_train, 3), "threshold": args.learn_threshold,
-            "test": test, "capacity_errors_spin_up": int(cap_errors["spin"]),
-            "evaluation": ev}
+            "test": test, "capacity": args.cyl_cap,
+            "capacity_errors_spin_up": int(cap_errors["spin"]),
+            "under_refinement_monotone_in_period": bool(fr[0] <= fr[1] <= fr[2]),
+            "sample_every": every, "fp64_reference": fp64_ref, "evaluation": ev,
+            "learned_speedup_over_plain_every_50": round(
+                ev["learned_every_200"]["mlups_incl_adapt"] /
+                ev["plain_every_50"]["mlups_incl_adapt"], 3)}
 
 
 # ----------------------------------------------------------- reference arm
@@ -1283,6 +1426,10 @@ def main():
     ap.add_argument("--learn-epochs", type=int, default=12)
     ap.add_argument("--learn-threshold", type=float, default=0.5)
     ap.add_argument("--learn-eval-steps", type=int, default=800)
+    ap.add_argument("--learn-sample-every", type=int, default=10)
+    ap.add_argument("--learn-crit-start", type=int, default=-3)
+    ap.add_argument("--learn-no-shadow", action="store_true")
+    ap.add_argument("--learn-fp64-ref", action="store_true")
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--cyl-nx", type=int, default=256)
     ap.add_argument("--cyl-levels", type=int, default=5)

@@ -303,15 +303,6 @@ int amr_mass_audit_noalloc(int dim, int q, int storage, int64_t n_blocks,
 /* Release host-side state (the arena stays owned by the caller). */
 int amr_free(amr_t* a);
 
-/* Failure-detection check of the bounded waits: one CTA waits, with the wait
- * function of the bulk-copy staged kernels and a limit of `limit_cycles` SM
- * cycles (1 .. 2^32), on an mbarrier that nothing arrives at.  Returns
- * AMR_E_TIMEOUT when the wait gave up and reported it (the expected result),
- * AMR_OK if the barrier completed, AMR_E_INVAL / AMR_E_CUDA on errors.
- * Synchronous on `stream`; no GPU fault or hang is involved.  The paper has
- * no counterpart. */
-int amr_check_bounded_wait(long long limit_cycles, void* stream);
-
 /* ---------------------------------------------------- checkpoint / resume
  * The paper keeps all state on the device and has no checkpoint; this is a
  * service of the library.  A checkpoint is a host byte image of the whole
@@ -390,33 +381,88 @@ int amr_propose_marks(amr_t* a, const void* params_half, float threshold, int wi
 
 /* ---------------------------------------------------------- batched instances
  * Many independent instances (same velocity set and storage, no solid) are
- * advanced in lock-step: each level operation of the recursive level step
- * (Section 4.1) is one launch over an instance-major list of
- * (instance, block) items, and the batched coarse step is replayed as a CUDA
- * graph.  The paper runs one forest per GPU; batching is this library's
- * extension.  Members keep their own arenas; the batch arena holds the
- * instance descriptors and the per-level item lists.
+ * advanced together.  The recursive level step (Section 4.1) has the same
+ * shape for every member, so a batch runs it in one of two forms:
+ *
+ * AMR_BATCH_GRAPH       each level operation is one launch over an
+ *                       instance-major list of (instance, block) items, and
+ *                       the batched coarse step is replayed as a CUDA graph.
+ * AMR_BATCH_PERSISTENT  one launch advances every member by n coarse steps.
+ *                       The level step is unrolled into a list of phases
+ *                       (interpolation into level L+1, collide-stream of
+ *                       level L, averaging of level L+1 into L); a phase's
+ *                       items are cut into tiles of one member each, and the
+ *                       CTAs take tiles in (step, phase, member, tile) order
+ *                       from one device queue.  Before it runs, a tile waits
+ *                       until its member has finished the member's previous
+ *                       phase; members advance independently, with no
+ *                       grid-wide barrier.  Every wait is bounded (about one
+ *                       second of clock64 cycles): when one gives up, the
+ *                       launch stops, every member's wait flag is raised, and
+ *                       amr_batch_sync returns AMR_E_TIMEOUT.
+ *
+ * The paper runs one forest per GPU; batching is this library's extension.
+ * Members keep their own arenas; the batch arena holds the instance
+ * descriptors, the per-level item lists and the persistent form's phase
+ * tables and counters.  Results of the two forms agree to rounding (the
+ * kernels are compiled separately).
  *
  * amr_batch_arena_bytes: device bytes for a batch of these instances.
  * amr_batch_create: members must have equal buffer parities (equally many
  *   coarse steps since amr_init, modulo 2) and capacities below 2^25 blocks;
- *   at most 127 members.  `stream` as in amr_init.
+ *   at most 127 members.  `stream` as in amr_init.  Starts in the graph form
+ *   with 512 threads per CTA.
  * amr_batch_refresh: rebuild the item lists after any member was adapted.
  * amr_batch_step: advance every member by n coarse steps (asynchronous);
- *   AMR_E_INVAL if a member was stepped outside the batch since.
- * amr_batch_autotune: time the collide-stream kernel with 512, 256, 128 and
- *   64 threads per CTA (M_L = 8, 4, 2, 1 blocks per CTA in 3D; 32 .. 4 in 2D)
- *   on `trial_steps` coarse steps each (the members advance), keep the
- *   fastest, return its CTA size in *variant_out.
+ *   AMR_E_INVAL if a member was stepped outside the batch since.  After a
+ *   timeout the persistent form does nothing until amr_batch_sync has
+ *   reported it; the members' populations are then part-way through a step.
+ * amr_batch_configure: select the form and its tile shape.  Graph form:
+ *   threads per CTA of the batched collide-stream 64, 128, 256 or 512 (the
+ *   CTA takes threads / 4^D blocks); tile_blocks and ctas are ignored.
+ *   Persistent form: threads 64, 128 or 256 per CTA, tile_blocks M_L = 1..8
+ *   blocks per collide-stream tile (an interpolation or averaging tile holds
+ *   threads / 4^D parents or children), ctas = CTAs launched (0: as many as
+ *   stay resident together; the queue needs no co-residency).
+ * amr_batch_get_config: the current form; in the graph form tile_blocks is
+ *   threads / 4^D and ctas is 0.
+ * amr_batch_autotune: time `trial_steps` coarse steps of each candidate
+ *   (forms: bit 0 the graph form with 512, 256, 128, 64 threads; bit 1 the
+ *   persistent form with M_L = 1, 2, 4, 8 x threads 64, 128, 256, resident
+ *   CTAs), keep the fastest and write it to *chosen (may be NULL).  ms_out
+ *   (NULL, or 16 floats) receives milliseconds per coarse step in that
+ *   candidate order, -1 for a candidate not timed.  The members advance.
+ *   Synchronous.
+ * amr_batch_sync: wait for the batch's stream; AMR_E_TIMEOUT (once) if a
+ *   bounded wait of the persistent form gave up since the last call.
+ * amr_batch_check_timeout: a check of the failure path of the persistent
+ *   form that needs no GPU fault: one launch in which no tile's wait can be
+ *   satisfied, with waits of `limit_cycles` clock64 cycles (0 < limit <=
+ *   2^32).  Returns AMR_E_TIMEOUT when the waits gave up and the launch
+ *   ended (the expected result).  The members are left part-way through a
+ *   step: use it on a batch whose results are not needed.  Synchronous.
  * amr_batch_launches: kernels launched by the batch so far.
- * Errors: AMR_E_INVAL, AMR_E_ARENA, AMR_E_CUDA. */
+ * Errors: AMR_E_INVAL, AMR_E_ARENA, AMR_E_CUDA, AMR_E_TIMEOUT. */
+#define AMR_BATCH_GRAPH 0
+#define AMR_BATCH_PERSISTENT 1
 typedef struct amr_batch_t amr_batch_t;
+typedef struct {
+  int32_t mode;         /* AMR_BATCH_GRAPH or AMR_BATCH_PERSISTENT */
+  int32_t threads;      /* threads per CTA                          */
+  int32_t tile_blocks;  /* M_L: blocks per collide-stream tile      */
+  int32_t ctas;         /* persistent form: CTAs launched (0: all resident) */
+} amr_batch_config_t;
 size_t amr_batch_arena_bytes(amr_t* const* instances, int n);
 int amr_batch_create(amr_t* const* instances, int n, void* dev_arena, size_t arena_bytes,
                      void* stream, amr_batch_t** out);
 int amr_batch_refresh(amr_batch_t* b);
 int amr_batch_step(amr_batch_t* b, int n_coarse_steps);
-int amr_batch_autotune(amr_batch_t* b, int trial_steps, int* variant_out);
+int amr_batch_configure(amr_batch_t* b, const amr_batch_config_t* cfg);
+int amr_batch_get_config(amr_batch_t* b, amr_batch_config_t* out);
+int amr_batch_autotune(amr_batch_t* b, int trial_steps, int forms, amr_batch_config_t* chosen,
+                       float* ms_out);
+int amr_batch_sync(amr_batch_t* b);
+int amr_batch_check_timeout(amr_batch_t* b, long long limit_cycles);
 int64_t amr_batch_launches(amr_batch_t* b);
 int amr_batch_free(amr_batch_t* b);
 

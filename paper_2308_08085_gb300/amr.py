@@ -98,8 +98,6 @@ def load_library(path=LIB_PATH):
     lib.amr_profile_read.restype = i32
     lib.amr_free.argtypes = [vp]
     lib.amr_free.restype = i32
-    lib.amr_check_bounded_wait.argtypes = [ctypes.c_longlong, vp]
-    lib.amr_check_bounded_wait.restype = i32
     lib.amr_checkpoint_bytes.argtypes = [vp]
     lib.amr_checkpoint_bytes.restype = i64
     lib.amr_checkpoint.argtypes = [vp, vp, sz]
@@ -138,8 +136,17 @@ def load_library(path=LIB_PATH):
     lib.amr_batch_refresh.restype = i32
     lib.amr_batch_step.argtypes = [vp, i32]
     lib.amr_batch_step.restype = i32
-    lib.amr_batch_autotune.argtypes = [vp, i32, ctypes.POINTER(i32)]
+    cfgp = ctypes.POINTER(AmrBatchConfig)
+    lib.amr_batch_configure.argtypes = [vp, cfgp]
+    lib.amr_batch_configure.restype = i32
+    lib.amr_batch_get_config.argtypes = [vp, cfgp]
+    lib.amr_batch_get_config.restype = i32
+    lib.amr_batch_autotune.argtypes = [vp, i32, i32, cfgp, ctypes.POINTER(ctypes.c_float)]
     lib.amr_batch_autotune.restype = i32
+    lib.amr_batch_sync.argtypes = [vp]
+    lib.amr_batch_sync.restype = i32
+    lib.amr_batch_check_timeout.argtypes = [vp, ctypes.c_longlong]
+    lib.amr_batch_check_timeout.restype = i32
     lib.amr_batch_launches.argtypes = [vp]
     lib.amr_batch_launches.restype = i64
     lib.amr_batch_free.argtypes = [vp]
@@ -411,8 +418,24 @@ class AmrLBM:
             pass
 
 
+AMR_BATCH_GRAPH, AMR_BATCH_PERSISTENT = 0, 1
+# candidate order of amr_batch_autotune's ms_out
+BATCH_CANDIDATES = ([("graph", t, t // 64) for t in (512, 256, 128, 64)] +
+                    [("persistent", t, m) for m in (1, 2, 4, 8) for t in (64, 128, 256)])
+
+
+class AmrBatchConfig(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("tile_blocks", ctypes.c_int32), ("ctas", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"form": "persistent" if self.mode == AMR_BATCH_PERSISTENT else "graph",
+                "threads": self.threads, "tile_blocks": self.tile_blocks, "ctas": self.ctas}
+
+
 class AmrBatch:
-    """Lock-step batch of AmrLBM instances (same velocity set and storage)."""
+    """Batch of AmrLBM instances (same velocity set and storage) advanced
+    together, in the graph form or the persistent form (amr_batch_configure)."""
 
     def __init__(self, members, stream=None):
         import torch
@@ -445,12 +468,40 @@ class AmrBatch:
         if rc != AMR_OK:
             raise AmrError(rc, "amr_batch_step")
 
-    def autotune(self, trial_steps=2):
-        v = ctypes.c_int(0)
-        rc = self.lib.amr_batch_autotune(self.h, int(trial_steps), ctypes.byref(v))
+    def configure(self, form="graph", threads=512, tile_blocks=0, ctas=0):
+        mode = AMR_BATCH_PERSISTENT if form == "persistent" else AMR_BATCH_GRAPH
+        cfg = AmrBatchConfig(mode, int(threads), int(tile_blocks), int(ctas))
+        rc = self.lib.amr_batch_configure(self.h, ctypes.byref(cfg))
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_batch_configure")
+
+    def config(self):
+        cfg = AmrBatchConfig()
+        rc = self.lib.amr_batch_get_config(self.h, ctypes.byref(cfg))
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_batch_get_config")
+        return cfg.as_dict()
+
+    def autotune(self, trial_steps=2, forms=("graph", "persistent")):
+        """Times every candidate; returns (chosen config, {candidate: ms per
+        coarse step}).  The members advance."""
+        bits = (1 if "graph" in forms else 0) | (2 if "persistent" in forms else 0)
+        cfg = AmrBatchConfig()
+        ms = (ctypes.c_float * len(BATCH_CANDIDATES))()
+        rc = self.lib.amr_batch_autotune(self.h, int(trial_steps), bits, ctypes.byref(cfg), ms)
         if rc != AMR_OK:
             raise AmrError(rc, "amr_batch_autotune")
-        return v.value
+        times = {c: float(v) for c, v in zip(BATCH_CANDIDATES, ms) if v >= 0}
+        return cfg.as_dict(), times
+
+    def sync(self):
+        rc = self.lib.amr_batch_sync(self.h)
+        if rc != AMR_OK:
+            raise AmrError(rc, "amr_batch_sync")
+
+    def check_timeout(self, limit_cycles):
+        """Return code of amr_batch_check_timeout (AMR_E_TIMEOUT expected)."""
+        return int(self.lib.amr_batch_check_timeout(self.h, int(limit_cycles)))
 
     def launches(self):
         return int(self.lib.amr_batch_launches(self.h))

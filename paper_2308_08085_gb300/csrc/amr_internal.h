@@ -48,6 +48,8 @@ struct Instance {
   // in space are advanced close together in time whatever their IDs
   int32_t* order = nullptr;
   int32_t* bnd = nullptr;          // [lmax][cap]: blocks with a NONE neighbour, tree order
+  int32_t* agrp = nullptr;         // [cap * N_c]: averaging groups (block << 3 | group) of
+                                   // the boundary blocks, level L at agrp_off[L]
   int32_t* gap = nullptr;          // [cap]
   int8_t* marks = nullptr;         // [cap]
   double* w2 = nullptr;            // [cap] criterion block maxima
@@ -60,7 +62,8 @@ struct Instance {
   // host mirror of the mesh sizes and time-stepping state
   int64_t n_ids[AMR_MAX_LEVELS] = {}, n_active[AMR_MAX_LEVELS] = {},
           n_parents[AMR_MAX_LEVELS] = {}, n_leaves[AMR_MAX_LEVELS] = {},
-          n_bnd[AMR_MAX_LEVELS] = {};
+          n_bnd[AMR_MAX_LEVELS] = {}, n_agrp[AMR_MAX_LEVELS] = {},
+          agrp_off[AMR_MAX_LEVELS] = {};
   // per level L: over the children of level L's exchanging parents, the
   // children holding ghost cells, their ghost cells and their interface cells
   // (the algorithmic work of interpolation into and averaging from level L+1)

@@ -140,6 +140,7 @@ static Layout layout_for(const amr_config* c) {
       (size_t)cap * 4,                         // 26 proposal probabilities
       (size_t)lmax * cap * 4,                  // 27 tree order of each level
       (size_t)lmax * cap * 4,                  // 28 blocks with a NONE neighbour, per level
+      (size_t)cap * (c->dim == 2 ? 4 : 8) * 4, // 29 averaging groups, packed by level
   };
   size_t off = 0;
   int i = 0;
@@ -167,11 +168,12 @@ struct CheckpointHeader {
   uint64_t arena_used;
   int64_t n_ids[AMR_MAX_LEVELS], n_active[AMR_MAX_LEVELS], n_parents[AMR_MAX_LEVELS],
       n_leaves[AMR_MAX_LEVELS], n_bnd[AMR_MAX_LEVELS], n_ghost_children[AMR_MAX_LEVELS],
-      n_ghost_cells[AMR_MAX_LEVELS], n_iface_cells[AMR_MAX_LEVELS];
+      n_ghost_cells[AMR_MAX_LEVELS], n_iface_cells[AMR_MAX_LEVELS], n_agrp[AMR_MAX_LEVELS],
+      agrp_off[AMR_MAX_LEVELS];
   int64_t n_gaps, coarse_steps;
   uint32_t cur, pad2_;
 };
-static const char kCheckpointTag[8] = {'A', 'M', 'R', 'C', 'K', 'P', 'T', '2'};
+static const char kCheckpointTag[8] = {'A', 'M', 'R', 'C', 'K', 'P', 'T', '3'};
 
 // ------------------------------------------------------------ profiling
 static const char* kPkNames[PK_COUNT] = {
@@ -348,16 +350,16 @@ static void advance(Instance* a, int L, bool first) {
       // cubic interpolation samples every cell of the parent, so with it the
       // parent cells over interior children are averaged as well (mode 1:
       // every cell whose children are not ghosts), else only those over
-      // interface children (mode 0)
+      // interface children: the groups of interface cells of the fine
+      // level's boundary blocks, listed at adaptation
       if (cubic)
         a->ops->average(a->stream, a->parents + (size_t)L * a->cap, (int)np, true,
                         a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0, a->parent,
                         a->cellmask, a->status, a->nbr, a->sm(), ratio_fc(a, L), 1, a->solid);
       else
-        a->ops->average(a->stream, a->bnd + (size_t)(L + 1) * a->cap, (int)a->n_bnd[L + 1],
-                        false, a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0,
-                        a->parent, a->cellmask, a->status, a->nbr, a->sm(), ratio_fc(a, L), 0,
-                        a->solid);
+        a->ops->average_groups(a->stream, a->agrp + a->agrp_off[L + 1], (int)a->n_agrp[L + 1],
+                               a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0,
+                               a->parent, a->nbr, a->sm(), ratio_fc(a, L), a->solid);
       a->launches += 1;
     }
   }
@@ -512,7 +514,7 @@ static int take_wait_flag(Instance* a) {
   AMR_CUDA(cudaStreamSynchronize(a->stream));
   if (v == 0) return AMR_OK;
   AMR_CUDA(cudaMemsetAsync(a->dcount + kWaitFlagSlot, 0, sizeof(int32_t), a->stream));
-  set_error("a bounded wait for staged populations timed out in the collide-stream kernel");
+  set_error("a bounded wait of the persistent batched kernel timed out");
   return AMR_E_TIMEOUT;
 }
 
@@ -614,6 +616,7 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
   a->prob = (float*)(base + L.off[i++]);
   a->order = (int32_t*)(base + L.off[i++]);
   a->bnd = (int32_t*)(base + L.off[i++]);
+  a->agrp = (int32_t*)(base + L.off[i++]);
 
   const double tau0 = 3.0 * cfg->nu0 + 0.5;
   for (int l = 0; l < a->lmax; ++l) a->tau[l] = 0.5 + std::ldexp(tau0 - 0.5, l);
@@ -1037,6 +1040,8 @@ int amr_checkpoint(amr_t* h, void* dst, size_t dst_bytes) {
     hd.n_parents[L] = a->n_parents[L];
     hd.n_leaves[L] = a->n_leaves[L];
     hd.n_bnd[L] = a->n_bnd[L];
+    hd.n_agrp[L] = a->n_agrp[L];
+    hd.agrp_off[L] = a->agrp_off[L];
     hd.n_ghost_children[L] = a->n_ghost_children[L];
     hd.n_ghost_cells[L] = a->n_ghost_cells[L];
     hd.n_iface_cells[L] = a->n_iface_cells[L];
@@ -1079,6 +1084,8 @@ int amr_restore(amr_t* h, const void* src, size_t src_bytes) {
     a->n_parents[L] = hd.n_parents[L];
     a->n_leaves[L] = hd.n_leaves[L];
     a->n_bnd[L] = hd.n_bnd[L];
+    a->n_agrp[L] = hd.n_agrp[L];
+    a->agrp_off[L] = hd.agrp_off[L];
     a->n_ghost_children[L] = hd.n_ghost_children[L];
     a->n_ghost_cells[L] = hd.n_ghost_cells[L];
     a->n_iface_cells[L] = hd.n_iface_cells[L];

@@ -1,10 +1,14 @@
-// Batched instances: many independent block forests advanced in lock-step by
-// one sequence of launches.  The recursive level step of Section 4.1 has the
-// same shape for every instance (an instance without level L+1 contributes no
-// work there), so each level operation becomes one launch over an
-// instance-major list of (instance, block) items.  The batched coarse step is
-// captured as a CUDA graph (one per parity of level 0); the collide-stream
-// variant is picked by timing the candidates on the batch itself.
+// Batched instances: many independent block forests advanced together.  The
+// recursive level step of Section 4.1 has the same shape for every instance
+// (an instance without level L+1 contributes no work there).  Two forms:
+//  * graph: each level operation is one launch over an instance-major list
+//    of (instance, block) items, and the batched coarse step is captured as
+//    a CUDA graph (one per parity of level 0);
+//  * persistent: one launch per call advances every member by n coarse steps
+//    through a work queue of (step, phase, member, tile) items with
+//    per-member dependency counters (PersistArgs in lbm_ops.h).
+// The form and its tile shape are picked by timing the candidates on the
+// batch itself.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,7 +37,24 @@ struct Batch {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graph_valid = false;
   int64_t launches = 0, graph_launches[2] = {0, 0};
+  // persistent form
+  int mode = AMR_BATCH_GRAPH;
+  int p_threads = 128, p_tile = 2, p_ctas_req = 0, p_ctas = 0;
+  long long wait_limit = 1ll << 31;
+  int n_phase_cap = 0, n_phase = 0, tiles_per_step = 0, max_member_tiles = 0;
+  bool plan_valid = false;
+  PersistPhase* d_phases = nullptr;    // device [2][n_phase_cap]
+  int32_t* d_tile_off = nullptr;       // device [n_phase_cap][n + 1]
+  int32_t* d_item_off = nullptr;
+  int32_t* d_dep = nullptr;            // device [n_phase_cap][n]
+  uint32_t* d_done = nullptr;          // device [n_phase_cap][n], then the queue head
+  unsigned long long* d_head = nullptr;
+  int32_t* d_abort = nullptr;
 };
+
+// phases of one coarse step: 2^(lmax+1) - 3 (interpolation, collide-stream
+// and averaging of every level visit of the recursion)
+static int phase_cap(int lmax) { return (1 << (lmax + 1)) - 3; }
 
 static size_t align256b(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -75,6 +96,7 @@ static int refresh(Batch* b) {
       }
     }
     d.faces = a->prm.faces;
+    d.wait_flag = a->prm.wait_flag;
   }
   AMR_CUDA(cudaMemcpyAsync(b->descs, h.data(), sizeof(InstDesc) * b->n, cudaMemcpyHostToDevice,
                            b->stream));
@@ -105,6 +127,7 @@ static int refresh(Batch* b) {
     g = nullptr;
   }
   b->graph_valid = false;
+  b->plan_valid = false;
   return AMR_OK;
 }
 
@@ -165,12 +188,170 @@ static int build_batch_graphs(Batch* b) {
   return AMR_OK;
 }
 
+// ------------------------------------------------------------ persistent form
+struct PhaseRec {
+  int op, level, which_in, which_ch;
+};
+
+// The phases of one coarse step in the order of advance_batch.
+static void plan_rec(const Batch* b, int L, unsigned& cur, std::vector<PhaseRec>& out) {
+  const bool fine = L + 1 < b->lmax && b->n_ids[L + 1] > 0;
+  const int64_t np = b->n_par[L];
+  const int wl = (int)((cur >> L) & 1u);
+  if (fine && np > 0) out.push_back({PH_INTERP, L, wl, (int)((cur >> (L + 1)) & 1u)});
+  if (b->n_act[L] > 0) out.push_back({PH_COLLIDE, L, wl, 0});
+  cur ^= 1u << L;
+  if (fine) {
+    plan_rec(b, L + 1, cur, out);
+    plan_rec(b, L + 1, cur, out);
+    if (np > 0)
+      out.push_back({PH_AVERAGE, L, (int)((cur >> L) & 1u), (int)((cur >> (L + 1)) & 1u)});
+  }
+}
+
+// Items of member a in a phase, and the tiles they make.
+static int64_t member_items(const Instance* a, const PhaseRec& r) {
+  if (r.level >= a->lmax) return 0;
+  return r.op == PH_COLLIDE ? a->n_active[r.level] : a->n_parents[r.level];
+}
+
+static int64_t member_tiles(const Batch* b, const Instance* a, const PhaseRec& r) {
+  const int64_t ni = member_items(a, r);
+  const int M = b->dim == 2 ? 16 : 64, NC = b->dim == 2 ? 4 : 8;
+  const int U = b->p_threads / M;
+  if (r.op == PH_COLLIDE) return (ni + b->p_tile - 1) / b->p_tile;
+  if (r.op == PH_INTERP) return (ni + U - 1) / U;
+  return (ni * NC + U - 1) / U;
+}
+
+static int build_plan(Batch* b) {
+  std::vector<PhaseRec> rec[2];
+  for (int parity = 0; parity < 2; ++parity) {
+    unsigned cur = (b->cur & ~1u) | (unsigned)parity;
+    plan_rec(b, 0, cur, rec[parity]);
+  }
+  const int n = b->n;
+  const int np = (int)rec[0].size();
+  if (np == 0 || np > b->n_phase_cap || rec[1].size() != rec[0].size()) {
+    set_error("persistent batch: unexpected phase list");
+    return AMR_E_INVAL;
+  }
+  std::vector<int32_t> toff((size_t)np * (n + 1)), ioff((size_t)np * (n + 1)), dep((size_t)np * n);
+  std::vector<PersistPhase> ph(2 * (size_t)np);
+  int64_t tile0 = 0, max_tiles = 0;
+  for (int k = 0; k < np; ++k) {
+    int64_t t = 0, it = 0;
+    for (int i = 0; i < n; ++i) {
+      toff[(size_t)k * (n + 1) + i] = (int32_t)t;
+      ioff[(size_t)k * (n + 1) + i] = (int32_t)it;
+      const int64_t ti = member_tiles(b, b->inst[i], rec[0][k]);
+      t += ti;
+      it += member_items(b->inst[i], rec[0][k]);
+      max_tiles = std::max(max_tiles, ti);
+    }
+    toff[(size_t)k * (n + 1) + n] = (int32_t)t;
+    ioff[(size_t)k * (n + 1) + n] = (int32_t)it;
+    for (int parity = 0; parity < 2; ++parity) {
+      const PhaseRec& r = rec[parity][k];
+      PersistPhase& p = ph[(size_t)parity * np + k];
+      p.op = r.op;
+      p.level = r.level;
+      p.which_in = r.which_in;
+      p.which_ch = r.which_ch;
+      p.tile0 = (int32_t)tile0;
+      p.n_tiles = (int32_t)t;
+      p.items = r.op == PH_COLLIDE ? b->act[r.level] : b->par[r.level];
+    }
+    tile0 += t;
+    if (tile0 >= (1ll << 30)) {
+      set_error("persistent batch: more than 2^30 tiles per coarse step");
+      return AMR_E_INVAL;
+    }
+  }
+  // dependencies: the member's previous phase with tiles, cyclically
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < np; ++k) {
+      int d = -1, wrap = 0;
+      for (int back = 1; back <= np; ++back) {
+        const int kk = k - back;
+        const int kc = kk < 0 ? kk + np : kk;
+        if (toff[(size_t)kc * (n + 1) + i + 1] > toff[(size_t)kc * (n + 1) + i]) {
+          d = kc;
+          wrap = kk < 0 ? 1 : 0;
+          break;
+        }
+      }
+      dep[(size_t)k * n + i] = d < 0 ? 1 : 2 * d + wrap;   // no tiles at all: never waits
+    }
+  cudaStream_t s = b->stream;
+  AMR_CUDA(cudaMemcpyAsync(b->d_phases, ph.data(), sizeof(PersistPhase) * ph.size(),
+                           cudaMemcpyHostToDevice, s));
+  AMR_CUDA(cudaMemcpyAsync(b->d_tile_off, toff.data(), 4 * toff.size(), cudaMemcpyHostToDevice, s));
+  AMR_CUDA(cudaMemcpyAsync(b->d_item_off, ioff.data(), 4 * ioff.size(), cudaMemcpyHostToDevice, s));
+  AMR_CUDA(cudaMemcpyAsync(b->d_dep, dep.data(), 4 * dep.size(), cudaMemcpyHostToDevice, s));
+  AMR_CUDA(cudaStreamSynchronize(s));   // the host vectors go out of scope
+  b->n_phase = np;
+  b->tiles_per_step = (int)tile0;
+  b->max_member_tiles = (int)max_tiles;
+  b->plan_valid = true;
+  return AMR_OK;
+}
+
+static int launch_persistent(Batch* b, int n, int stall, long long limit) {
+  if (!b->plan_valid) {
+    const int rc = build_plan(b);
+    if (rc != AMR_OK) return rc;
+  }
+  // counters stay below 2^30 within a launch
+  const int64_t per_launch = std::max<int64_t>(1, (1ll << 30) / std::max(1, b->tiles_per_step));
+  for (int done = 0; done < n;) {
+    const int chunk = (int)std::min<int64_t>(n - done, per_launch);
+    AMR_CUDA(cudaMemsetAsync(b->d_done, 0, align256b((size_t)b->n_phase_cap * b->n * 4) + 8,
+                             b->stream));
+    PersistArgs a{};
+    a.descs = b->descs;
+    a.phases = b->d_phases;
+    a.tile_off = b->d_tile_off;
+    a.item_off = b->d_item_off;
+    a.dep = b->d_dep;
+    a.done = b->d_done;
+    a.head = b->d_head;
+    a.abort = b->d_abort;
+    a.n_phase = b->n_phase;
+    a.n_inst = b->n;
+    a.tiles_per_step = b->tiles_per_step;
+    a.parity0 = (int)(b->cur & 1u);
+    a.n_steps = chunk;
+    a.tile_blocks = b->p_tile;
+    a.wait_limit = limit;
+    a.stall = stall;
+    const int64_t tiles = (int64_t)b->tiles_per_step * chunk;
+    const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(b->p_ctas, tiles));
+    b->ops->batch_persistent(b->stream, a, b->p_threads, ctas);
+    AMR_CUDA(cudaGetLastError());
+    b->launches += 1;
+    if (stall) return AMR_OK;
+    b->cur ^= (unsigned)(chunk & 1);
+    done += chunk;
+  }
+  return AMR_OK;
+}
+
 static int step_batch(Batch* b, int n) {
   for (Instance* a : b->inst)
     if (a->cur != b->cur) {
       set_error("batch members were stepped outside the batch (buffer parities differ)");
       return AMR_E_INVAL;
     }
+  if (b->mode == AMR_BATCH_PERSISTENT) {
+    const int rc = launch_persistent(b, n, 0, b->wait_limit);
+    if (rc != AMR_OK) return rc;
+    for (Instance* a : b->inst) {
+      a->cur = b->cur;
+      a->coarse_steps += n;
+    }
+    return AMR_OK;
+  }
   if (!b->graph_valid) {
     const int rc = build_batch_graphs(b);
     if (rc != AMR_OK) return rc;
@@ -199,7 +380,10 @@ size_t amr_batch_arena_bytes(amr_t* const* instances, int n) {
   if (!instances || n <= 0) return 0;
   const int64_t caps = sum_caps(instances, n);
   const int lmax = max_levels(instances, n);
-  return align256b(sizeof(InstDesc) * n) + 2 * (size_t)lmax * align256b((size_t)caps * 4);
+  const size_t npc = (size_t)phase_cap(lmax);
+  return align256b(sizeof(InstDesc) * n) + 2 * (size_t)lmax * align256b((size_t)caps * 4) +
+         align256b(2 * npc * sizeof(PersistPhase)) + 2 * align256b(npc * (n + 1) * 4) +
+         align256b(npc * n * 4) + align256b(npc * n * 4) + 256 + 256;
 }
 
 int amr_batch_create(amr_t* const* instances, int n, void* dev_arena, size_t arena_bytes,
@@ -259,6 +443,26 @@ int amr_batch_create(amr_t* const* instances, int n, void* dev_arena, size_t are
     b->par[L] = (uint32_t*)(base + off);
     off += align256b((size_t)b->list_cap * 4);
   }
+  b->n_phase_cap = phase_cap(b->lmax);
+  const size_t npc = (size_t)b->n_phase_cap;
+  b->d_phases = (PersistPhase*)(base + off);
+  off += align256b(2 * npc * sizeof(PersistPhase));
+  b->d_tile_off = (int32_t*)(base + off);
+  off += align256b(npc * (n + 1) * 4);
+  b->d_item_off = (int32_t*)(base + off);
+  off += align256b(npc * (n + 1) * 4);
+  b->d_dep = (int32_t*)(base + off);
+  off += align256b(npc * n * 4);
+  b->d_done = (uint32_t*)(base + off);                       // done, then the head
+  off += align256b(npc * n * 4);
+  b->d_head = (unsigned long long*)(base + off);
+  off += 256;
+  b->d_abort = (int32_t*)(base + off);
+  if (cudaMemsetAsync(b->d_abort, 0, sizeof(int32_t), b->stream) != cudaSuccess) {
+    delete b;
+    set_error("cannot clear the batch abort word");
+    return AMR_E_CUDA;
+  }
   if (cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete b;
     set_error("cannot create capture stream");
@@ -286,40 +490,139 @@ int amr_batch_step(amr_batch_t* h, int n_coarse_steps) {
   return step_batch(b, n_coarse_steps);
 }
 
-int amr_batch_autotune(amr_batch_t* h, int trial_steps, int* chosen) {
+int amr_batch_configure(amr_batch_t* h, const amr_batch_config_t* cfg) {
   Batch* b = reinterpret_cast<Batch*>(h);
-  if (!b || trial_steps < 1) return AMR_E_INVAL;
-  // CTA sizes of the batched collide-stream: 512 / 256 / 128 / 64 threads,
-  // i.e. M_L = 8 / 4 / 2 / 1 blocks of 64 cells per CTA in 3D
-  static const int candidates[] = {512, 256, 128, 64};
+  if (!b || !cfg) return AMR_E_INVAL;
+  if (cfg->mode == AMR_BATCH_GRAPH) {
+    if (cfg->threads != 64 && cfg->threads != 128 && cfg->threads != 256 && cfg->threads != 512) {
+      set_error("graph form: threads per CTA must be 64, 128, 256 or 512");
+      return AMR_E_INVAL;
+    }
+    b->mode = AMR_BATCH_GRAPH;
+    b->variant = cfg->threads;
+    b->graph_valid = false;
+    return AMR_OK;
+  }
+  if (cfg->mode != AMR_BATCH_PERSISTENT) {
+    set_error("unknown batch mode");
+    return AMR_E_INVAL;
+  }
+  if ((cfg->threads != 64 && cfg->threads != 128 && cfg->threads != 256) ||
+      cfg->tile_blocks < 1 || cfg->tile_blocks > PERSIST_MAX_TILE || cfg->ctas < 0) {
+    set_error("persistent form: threads 64, 128 or 256, tile_blocks 1..8, ctas >= 0");
+    return AMR_E_INVAL;
+  }
+  const int resident = b->ops->persistent_ctas(cfg->threads);
+  if (resident <= 0) {
+    cudaGetLastError();
+    set_error("persistent form: the kernel cannot be made resident with this CTA size");
+    return AMR_E_CUDA;
+  }
+  b->mode = AMR_BATCH_PERSISTENT;
+  b->p_threads = cfg->threads;
+  b->p_tile = cfg->tile_blocks;
+  b->p_ctas_req = cfg->ctas;
+  b->p_ctas = cfg->ctas > 0 ? cfg->ctas : resident;
+  b->plan_valid = false;
+  return AMR_OK;
+}
+
+int amr_batch_get_config(amr_batch_t* h, amr_batch_config_t* out) {
+  Batch* b = reinterpret_cast<Batch*>(h);
+  if (!b || !out) return AMR_E_INVAL;
+  out->mode = b->mode;
+  out->threads = b->mode == AMR_BATCH_GRAPH ? b->variant : b->p_threads;
+  out->tile_blocks = b->mode == AMR_BATCH_GRAPH ? b->variant / (b->dim == 2 ? 16 : 64)
+                                                : b->p_tile;
+  out->ctas = b->mode == AMR_BATCH_GRAPH ? 0 : b->p_ctas;
+  return AMR_OK;
+}
+
+int amr_batch_autotune(amr_batch_t* h, int trial_steps, int forms, amr_batch_config_t* chosen,
+                       float* ms_out) {
+  Batch* b = reinterpret_cast<Batch*>(h);
+  if (!b || trial_steps < 1 || forms < 1 || forms > 3) return AMR_E_INVAL;
+  // candidates in the order of ms_out: the graph form with 512 / 256 / 128 /
+  // 64 threads per CTA (M_L = 8 / 4 / 2 / 1 blocks per CTA in 3D), then the
+  // persistent form with M_L = 1, 2, 4, 8 blocks per tile x 64, 128, 256
+  // threads per CTA
+  std::vector<amr_batch_config_t> cand;
+  for (int t : {512, 256, 128, 64}) cand.push_back({AMR_BATCH_GRAPH, t, 0, 0});
+  for (int m : {1, 2, 4, 8})
+    for (int t : {64, 128, 256}) cand.push_back({AMR_BATCH_PERSISTENT, t, m, 0});
+  amr_batch_config_t keep{};
+  amr_batch_get_config(h, &keep);
   cudaEvent_t e0, e1;
   AMR_CUDA(cudaEventCreate(&e0));
   AMR_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_v = b->variant;
-  for (int v : candidates) {
-    b->variant = v;
-    b->graph_valid = false;
-    int rc = step_batch(b, 1);   // capture and warm
-    if (rc != AMR_OK) return rc;
-    AMR_CUDA(cudaEventRecord(e0, b->stream));
-    rc = step_batch(b, trial_steps);
-    if (rc != AMR_OK) return rc;
-    AMR_CUDA(cudaEventRecord(e1, b->stream));
-    AMR_CUDA(cudaEventSynchronize(e1));
+  amr_batch_config_t best_c = keep;
+  int rc = AMR_OK;
+  for (size_t c = 0; c < cand.size() && rc == AMR_OK; ++c) {
+    if (ms_out) ms_out[c] = -1.f;
+    const bool want = cand[c].mode == AMR_BATCH_GRAPH ? (forms & 1) : (forms & 2);
+    if (!want) continue;
+    rc = amr_batch_configure(h, &cand[c]);
+    if (rc != AMR_OK) break;
+    rc = step_batch(b, 1);   // capture or plan, and warm
+    if (rc != AMR_OK) break;
+    if (cudaEventRecord(e0, b->stream) != cudaSuccess) rc = AMR_E_CUDA;
+    if (rc == AMR_OK) rc = step_batch(b, trial_steps);
+    if (rc == AMR_OK && cudaEventRecord(e1, b->stream) != cudaSuccess) rc = AMR_E_CUDA;
+    if (rc == AMR_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = AMR_E_CUDA;
     float ms = 0.f;
-    AMR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (rc == AMR_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = AMR_E_CUDA;
+    if (rc != AMR_OK) break;
+    if (ms_out) ms_out[c] = ms / (float)trial_steps;
     if (ms < best) {
       best = ms;
-      best_v = v;
+      amr_batch_get_config(h, &best_c);
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->variant = best_v;
-  b->graph_valid = false;
-  if (chosen) *chosen = best_v;
+  if (rc != AMR_OK) {
+    if (rc == AMR_E_CUDA) set_error(std::string("batch autotune: ") + cudaGetErrorString(cudaGetLastError()));
+    return rc;
+  }
+  best_c.ctas = 0;
+  rc = amr_batch_configure(h, &best_c);
+  if (rc != AMR_OK) return rc;
+  if (chosen) amr_batch_get_config(h, chosen);
   return AMR_OK;
+}
+
+int amr_batch_sync(amr_batch_t* h) {
+  Batch* b = reinterpret_cast<Batch*>(h);
+  if (!b) return AMR_E_INVAL;
+  int32_t ab = 0;
+  AMR_CUDA(cudaMemcpyAsync(&ab, b->d_abort, sizeof(ab), cudaMemcpyDeviceToHost, b->stream));
+  AMR_CUDA(cudaStreamSynchronize(b->stream));
+  if (ab == 0) return AMR_OK;
+  AMR_CUDA(cudaMemsetAsync(b->d_abort, 0, sizeof(int32_t), b->stream));
+  for (Instance* a : b->inst)
+    AMR_CUDA(cudaMemsetAsync(a->prm.wait_flag, 0, sizeof(int32_t), b->stream));
+  AMR_CUDA(cudaStreamSynchronize(b->stream));
+  set_error("a bounded wait of the persistent batched kernel timed out");
+  return AMR_E_TIMEOUT;
+}
+
+int amr_batch_check_timeout(amr_batch_t* h, long long limit_cycles) {
+  Batch* b = reinterpret_cast<Batch*>(h);
+  if (!b) return AMR_E_INVAL;
+  if (limit_cycles <= 0 || limit_cycles > (1ll << 32)) {
+    set_error("limit_cycles must be in (0, 2^32]");
+    return AMR_E_INVAL;
+  }
+  if (b->mode != AMR_BATCH_PERSISTENT) {
+    set_error("amr_batch_check_timeout needs the persistent form");
+    return AMR_E_INVAL;
+  }
+  int rc = amr_batch_sync(h);   // report (and clear) anything earlier first
+  if (rc != AMR_OK) return rc;
+  rc = launch_persistent(b, 1, 1, limit_cycles);
+  if (rc != AMR_OK) return rc;
+  return amr_batch_sync(h);
 }
 
 int64_t amr_batch_launches(amr_batch_t* h) {

@@ -106,12 +106,21 @@ __device__ __forceinline__ int link_entry(const LinkTable<D, Q>& t, int l) {
   return __ldg(&t.e[P * Block<D>::M + l]);
 }
 
+// A population load.  COH: the value may have been stored by another CTA of
+// the same launch (the persistent batched kernel), so it is read from L2
+// (ld.global.cg), never through a path that may hold an older copy.
+template <bool COH, class T>
+__device__ __forceinline__ T ld_pop(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+
 // --------------------------------------------------------- gather / scatter
 // Pre-collision populations of cell l of block b (see the file comment).
 // `row` is the block's neighbour row (neighbour-index order), in global or
 // shared memory.  A solid cell holds its own (rest) values.  With
 // SOLID, `solidmask` (one bit per cell) may still be null: no solid cells.
-template <int D, int Q, class T, bool SOLID>
+template <int D, int Q, class T, bool SOLID, bool COH = false>
 __device__ __forceinline__ void gather_cell(typename Store<T>::R (&f)[Q],
                                             const T* __restrict__ g, size_t stride, int b, int l,
                                             const int32_t* __restrict__ row,
@@ -125,16 +134,17 @@ __device__ __forceinline__ void gather_cell(typename Store<T>::R (&f)[Q],
     constexpr int p = P;
     constexpr int pb = VS<D, Q>::opp[p];
     if constexpr (p == 0) {
-      f[0] = S::template load<D, Q, 0>(g[own]);
+      f[0] = S::template load<D, Q, 0>(ld_pop<COH>(g + own));
     } else {
       const int e = link_entry<D, Q, p>(g_src_k<D, Q>, l);
       const int k = e & 31, sl = e >> 5;
       const int src = k == 0 ? b : row[k];
       bool back = src < 0;
       if (has_sm && !back) back = (__ldg(solidmask + src) >> sl) & 1ull;
-      if (solid_cell) f[p] = S::template load<D, Q, p>(g[(size_t)p * stride + own]);
-      else if (back) f[p] = S::template load<D, Q, p>(g[(size_t)pb * stride + own]);
-      else f[p] = S::template load<D, Q, p>(g[(size_t)p * stride + (size_t)src * M + sl]);
+      const size_t at = solid_cell ? (size_t)p * stride + own
+                                   : (back ? (size_t)pb * stride + own
+                                           : (size_t)p * stride + (size_t)src * M + sl);
+      f[p] = S::template load<D, Q, p>(ld_pop<COH>(g + at));
     }
   });
 }
@@ -274,7 +284,7 @@ constexpr int BF_OUTLET = 8;    // a neighbour is an outlet face
 // through a wall, which store the wall value.  Kept out of line so that the
 // branch-free path of the other blocks keeps its registers.  OUTLET: a
 // neighbour is an outlet face (anti-bounce-back needs the cell's velocity).
-template <int D, int Q, class T, bool SOLID, bool OUTLET, bool GHOST = false>
+template <int D, int Q, class T, bool SOLID, bool OUTLET, bool GHOST = false, bool COH = false>
 __device__ __noinline__ void step_cell_checked(const T* __restrict__ gin, T* __restrict__ gout,
                                                size_t stride, size_t own, int l,
                                                const int32_t* nb, const uint64_t* sm, int flags,
@@ -294,7 +304,7 @@ __device__ __noinline__ void step_cell_checked(const T* __restrict__ gin, T* __r
     constexpr int p = P;
     constexpr int pb = VS<D, Q>::opp[p];
     if constexpr (p == 0) {
-      f[0] = S::template load<D, Q, 0>(gsrc[own]);
+      f[0] = S::template load<D, Q, 0>(ld_pop<COH>(gsrc + own));
     } else {
       const int e = link_entry<D, Q, p>(g_src_geo<D, Q>, l);
       const int code = e & 31, sl = e >> 5;
@@ -305,7 +315,7 @@ __device__ __noinline__ void step_cell_checked(const T* __restrict__ gin, T* __r
       const size_t at = ghost_in ? (size_t)p * stride + own
                                  : (out ? (size_t)pb * stride + own
                                         : (size_t)p * stride + (size_t)src * M + sl);
-      f[p] = S::template load<D, Q, p>(gsrc[at]);
+      f[p] = S::template load<D, Q, p>(ld_pop<COH>(gsrc + at));
     }
   });
   R ux, uy, uz, usq15;

@@ -29,7 +29,7 @@ __device__ __forceinline__ void stage_row(int32_t* dst, const int32_t* __restric
   for (int k = t; k < NK; k += nt) dst[k] = b >= 0 ? __ldg(nbr + (size_t)b * NBR_STRIDE + k) : NONE;
 }
 
-template <int D, int Q, class T, bool SOLID>
+template <int D, int Q, class T, bool SOLID, bool COH = false>
 __device__ __forceinline__ void interp_stage(typename Store<T>::R (*sF)[Block<D>::M],
                                              const T* __restrict__ fpar, size_t stride, int P,
                                              int l, double ratio, const int32_t* prow,
@@ -37,7 +37,7 @@ __device__ __forceinline__ void interp_stage(typename Store<T>::R (*sF)[Block<D>
   using S = Store<T>;
   using R = typename S::R;
   R f[Q];
-  gather_cell<D, Q, T, SOLID>(f, fpar, stride, P, l, prow, solidmask);
+  gather_cell<D, Q, T, SOLID, COH>(f, fpar, stride, P, l, prow, solidmask);
   R rho, ux, uy, uz;
   moments<D, Q>(f, rho, ux, uy, uz);
   const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
@@ -298,7 +298,7 @@ __device__ __forceinline__ bool average_group_taken(const uint64_t* __restrict__
   return (__ldg(cellmask + 2 * (size_t)ch + 1) >> f0) & 1ull;
 }
 
-template <int D, int Q, class T, bool SOLID>
+template <int D, int Q, class T, bool SOLID, bool COH = false>
 __device__ __forceinline__ void average_child(typename Store<T>::R (*sR)[Block<D>::M],
                                               bool valid, int P, int c, int ch,
                                               int l, T* __restrict__ fpar,
@@ -324,7 +324,7 @@ __device__ __forceinline__ void average_child(typename Store<T>::R (*sR)[Block<D
   };
   if (valid && taken(g)) {
     R f[Q];
-    gather_cell<D, Q, T, SOLID>(f, fch, stride, ch, l, crow, solidmask);
+    gather_cell<D, Q, T, SOLID, COH>(f, fch, stride, ch, l, crow, solidmask);
     R rho, ux, uy, uz;
     moments<D, Q>(f, rho, ux, uy, uz);
     const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
@@ -394,6 +394,83 @@ __global__ void __launch_bounds__(128)
   average_child<D, Q, T, SOLID>(sR[slot], valid, P, c, ch, l, fpar, fch, stride,
                                 cellmask, s_row[slot][0], s_row[slot][1], solidmask, ratio,
                                 mode_sync);
+}
+
+// The level step's averaging (mode 0) over a list of (child block, group)
+// items, the groups of 2^D interface cells of the fine level's boundary
+// blocks whose parent cell is fluid.  One lane per fine cell gathers and
+// rescales it (f_eq + (f - f_eq) r, Section 3.4.3); the 2^D lanes of a group
+// sum their values with a butterfly that halves the directions each lane
+// carries at every exchange (a reduce-scatter: afterwards each lane holds the
+// sums of ceil(Q / 2^D) directions), and each lane stores the means of its
+// directions into the parent cell's slots.  No shared memory, no barrier,
+// every lane busy.
+template <int D, int Q, class T, bool SOLID>
+__global__ void __launch_bounds__(128, 8)
+    k_average_groups(const int32_t* __restrict__ items, int n, T* __restrict__ fpar,
+                     const T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
+                     const int32_t* __restrict__ parent, const int32_t* __restrict__ nbr,
+                     const uint64_t* __restrict__ solidmask, double ratio) {
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int NC = Block<D>::NC;            // lanes of a group
+  constexpr int PER = (Q + NC - 1) / NC;      // directions a lane keeps
+  constexpr int QP = PER * NC;
+  const int s = threadIdx.x & (NC - 1);
+  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / NC;
+  const bool valid = item < n;                // the same for the lanes of a group
+  int ch = 0, g = 0, P = 0, c = 0;
+  if (valid) {
+    const int it = __ldg(items + item);
+    ch = it >> 3;
+    g = it & 7;
+    P = __ldg(parent + ch);
+    c = ch - __ldg(child0 + P);
+  }
+  const int l = Block<D>::cell(2 * (g & 1) + (s & 1), 2 * ((g >> 1) & 1) + ((s >> 1) & 1),
+                               2 * ((g >> 2) & 1) + ((s >> 2) & 1));
+  R v[QP];
+#pragma unroll
+  for (int p = 0; p < QP; ++p) v[p] = R(0);
+  if (valid) {
+    R f[Q];
+    gather_cell<D, Q, T, SOLID>(f, fch, stride, ch, l, nbr + (size_t)ch * NBR_STRIDE, solidmask);
+    R rho, ux, uy, uz;
+    moments<D, Q>(f, rho, ux, uy, uz);
+    const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+    const R r = R(ratio);
+    static_for<0, Q>([&](auto Pp) {
+      const R e = feq<D, Q, Pp>(rho, ux, uy, uz, usq15);
+      v[Pp] = e + (f[Pp] - e) * r;
+    });
+  }
+  // reduce-scatter over the group: at the exchange with lane s ^ m, the lane
+  // with bit m set keeps the upper half of its K directions, the other the
+  // lower half, each adding the partner's copy of the half it keeps
+  int base = 0;
+#pragma unroll
+  for (int m = NC / 2, K = QP; m >= 1; m >>= 1, K >>= 1) {
+    const bool hi = (s & m) != 0;
+    if (hi) base += K / 2;
+#pragma unroll
+    for (int i = 0; i < K / 2; ++i) {
+      const R send = hi ? v[i] : v[i + K / 2];
+      const R recv = __shfl_xor_sync(0xffffffffu, send, m);
+      v[i] = (hi ? v[i + K / 2] : v[i]) + recv;
+    }
+  }
+  if (!valid) return;
+  const int pc = Block<D>::cell(2 * (c & 1) + (g & 1), 2 * ((c >> 1) & 1) + ((g >> 1) & 1),
+                                2 * ((c >> 2) & 1) + ((g >> 2) & 1));
+  const int32_t* prow = nbr + (size_t)P * NBR_STRIDE;
+  const R inv = R(1) / R(NC);
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int p = base + j;
+    if (p < Q)
+      fpar[src_slot<D, Q>(p, P, pc, stride, prow, SOLID ? solidmask : nullptr)] =
+          save_rt<D, Q, T>(v[j] * inv, p);
+  }
 }
 
 // ================================================ batched instances (lock-step)
@@ -543,6 +620,255 @@ __global__ void __launch_bounds__(128)
   average_child<D, Q, T, false>(sR[slot], valid, P, c, ch, l, (T*)d.f[which_par],
                                 (const T*)d.f[which_ch], d.stride, d.cellmask, s_row[slot][0],
                                 s_row[slot][1], nullptr, d.r_fc[level], 0);
+}
+
+// ============================ batched instances: persistent form (PersistArgs)
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Wait until *cnt >= target.  False when *abort is raised, or when `limit`
+// clock64 cycles have passed (then this wait raises *abort itself).
+__device__ __forceinline__ bool persist_wait(const uint32_t* cnt, uint32_t target, int32_t* abort,
+                                             long long limit) {
+  const long long t0 = clock64();
+  for (;;) {
+    if (ld_acquire_u32(cnt) >= target) return true;
+    if (*(volatile int32_t*)abort) return false;
+    if (clock64() - t0 > limit) {
+      atomicExch(abort, 1);
+      return false;
+    }
+    __nanosleep(64);
+  }
+}
+
+// Collide-stream tile: `nblk` (<= PERSIST_MAX_TILE) active blocks of one
+// member, the cells spread over the CTA's threads.  The same pull step as
+// k_collide_stream_batch, with every population read from L2.
+template <int D, int Q, class T, int THREADS>
+__device__ __forceinline__ void persist_collide(const InstDesc& d, const uint32_t* items, int nblk,
+                                                int level, int which_in,
+                                                int32_t (*s_nb)[D == 2 ? 9 : 27],
+                                                int32_t* s_flags) {
+  using S = Store<T>;
+  using R = typename S::R;
+  constexpr int M = Block<D>::M;
+  constexpr int NCODE = D == 2 ? 9 : 27;
+  constexpr int CENTER = D == 2 ? 4 : 13;
+  for (int e = threadIdx.x; e < nblk * NCODE; e += THREADS) {
+    const int s = e / NCODE, code = e - s * NCODE;
+    const int b = (int)(__ldg(items + s) & BATCH_MASK);
+    s_nb[s][code] = __ldg(d.nbr + (size_t)b * NBR_STRIDE + geo_to_k<D>(code));
+  }
+  __syncthreads();
+  if (threadIdx.x < nblk) {
+    int flags = 0;
+    for (int code = 0; code < NCODE; ++code) {
+      const int v = s_nb[threadIdx.x][code];
+      if (v < 0) flags |= BF_OUTSIDE;
+      if (v <= -2 && d.faces.kind[-2 - v] != FACE_NOSLIP) flags |= BF_WALL;
+      if (v <= -2 && d.faces.kind[-2 - v] == FACE_OUTLET) flags |= BF_OUTLET;
+    }
+    s_flags[threadIdx.x] = flags;
+  }
+  __syncthreads();
+  const T* gin = (const T*)d.f[which_in];
+  T* gout = (T*)d.f[which_in ^ 1];
+  const size_t stride = d.stride;
+  const double omega = d.omega[level];
+  for (int c = threadIdx.x; c < nblk * M; c += THREADS) {
+    const int s = c / M, l = c - s * M;
+    const int32_t* nb = s_nb[s];
+    const size_t own = (size_t)nb[CENTER] * M + l;
+    const int flags = s_flags[s];
+    if (flags == 0) {
+      R f[Q];
+      static_for<0, Q>([&](auto P) {
+        constexpr int p = P;
+        if constexpr (p == 0) {
+          f[0] = S::template load<D, Q, 0>(__ldcg(gin + own));
+        } else {
+          const int e = link_entry<D, Q, p>(g_src_geo<D, Q>, l);
+          f[p] = S::template load<D, Q, p>(
+              __ldcg(gin + (size_t)p * stride + (size_t)nb[e & 31] * M + (e >> 5)));
+        }
+      });
+      R ux, uy, uz, usq15;
+      bgk<D, Q>(f, R(omega), ux, uy, uz, usq15);
+      static_for<0, Q>([&](auto P) {
+        gout[(size_t)P * stride + own] = S::template save<D, Q, P>(f[P]);
+      });
+    } else if (flags & BF_OUTLET) {
+      step_cell_checked<D, Q, T, false, true, false, true>(gin, gout, stride, own, l, nb, nullptr,
+                                                           flags, omega, d.faces, false);
+    } else {
+      step_cell_checked<D, Q, T, false, false, false, true>(gin, gout, stride, own, l, nb,
+                                                            nullptr, flags, omega, d.faces, false);
+    }
+  }
+}
+
+// Interpolation tile: THREADS / M parents of one member (as k_interp_batch).
+// Out of line, like the averaging tile, so that their register needs do not
+// weigh on the collide-stream tiles.
+template <int D, int Q, class T, int THREADS>
+__device__ __noinline__ void persist_interp(const InstDesc& d, const uint32_t* items, int ni,
+                                            int tile, int level, int win, int wch,
+                                            typename Store<T>::R (*sF)[Q][Block<D>::M],
+                                            int32_t (*s_rows)[1 + Block<D>::NC][Nbr<D>::K]) {
+  constexpr int M = Block<D>::M;
+  constexpr int NC = Block<D>::NC;
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int j = tile * (THREADS / M) + slot;
+  const bool valid = j < ni;
+  int P = 0, c0 = 0;
+  if (valid) {
+    P = (int)(__ldg(items + j) & BATCH_MASK);
+    c0 = __ldg(d.child0 + P);
+  }
+  for (int rr = 0; rr <= NC; ++rr)
+    stage_row<D>(s_rows[slot][rr], d.nbr, valid ? (rr == 0 ? P : c0 + rr - 1) : NONE, l, M);
+  __syncthreads();
+  if (valid)
+    interp_stage<D, Q, T, false, true>(sF[slot], (const T*)d.f[win], d.stride, P, l,
+                                       d.r_cf[level], s_rows[slot][0], nullptr);
+  __syncthreads();
+  if (valid)
+    interp_children<D, Q, T, false>(sF[slot], l, (T*)d.f[wch], d.stride, c0, d.cellmask,
+                                    s_rows[slot] + 1, nullptr, nullptr, nullptr, 0);
+}
+
+// Averaging tile: THREADS / M children of one member; child item j is child
+// j % N_c of parent item j / N_c (as k_average_batch).
+template <int D, int Q, class T, int THREADS>
+__device__ __noinline__ void persist_average(const InstDesc& d, const uint32_t* items, int ni,
+                                             int tile, int level, int win, int wch,
+                                             typename Store<T>::R (*sF)[Q][Block<D>::M],
+                                             int32_t (*s_rows)[1 + Block<D>::NC][Nbr<D>::K]) {
+  constexpr int M = Block<D>::M;
+  constexpr int NC = Block<D>::NC;
+  const int slot = threadIdx.x / M;
+  const int l = threadIdx.x - slot * M;
+  const int j = tile * (THREADS / M) + slot;
+  const bool valid = j < ni * NC;
+  int P = 0, c = 0, ch = 0;
+  if (valid) {
+    P = (int)(__ldg(items + j / NC) & BATCH_MASK);
+    c = j % NC;
+    ch = __ldg(d.child0 + P) + c;
+  }
+  stage_row<D>(s_rows[slot][0], d.nbr, valid ? ch : NONE, l, M);
+  stage_row<D>(s_rows[slot][1], d.nbr, valid ? P : NONE, l, M);
+  __syncthreads();
+  average_child<D, Q, T, false, true>(sF[slot], valid, P, c, ch, l, (T*)d.f[win],
+                                      (const T*)d.f[wch], d.stride, d.cellmask, s_rows[slot][0],
+                                      s_rows[slot][1], nullptr, d.r_fc[level], 0);
+}
+
+// The persistent kernel.  Dynamic shared memory: the rescaled populations of
+// the THREADS / M parents (interpolation) or children (averaging) of a tile,
+// then their neighbour rows.
+template <int D, int Q, class T, int THREADS>
+__global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS>()))
+    k_batch_persistent(PersistArgs a) {
+  using R = typename Store<T>::R;
+  constexpr int M = Block<D>::M;
+  constexpr int NC = Block<D>::NC;
+  constexpr int NK = Nbr<D>::K;
+  constexpr int U = THREADS / M;     // parents or children per interface tile
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  R (*sF)[Q][M] = reinterpret_cast<R (*)[Q][M]>(s_dyn);
+  int32_t (*s_rows)[1 + NC][NK] =
+      reinterpret_cast<int32_t (*)[1 + NC][NK]>(s_dyn + sizeof(R) * U * Q * M);
+  __shared__ int32_t s_nb[PERSIST_MAX_TILE][D == 2 ? 9 : 27];
+  __shared__ int32_t s_flags[PERSIST_MAX_TILE];
+  __shared__ long long s_take;
+  __shared__ int32_t s_go;
+  const long long total = (long long)a.tiles_per_step * a.n_steps;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      long long t = -1;
+      if (!*(volatile int32_t*)a.abort) {
+        const unsigned long long q = atomicAdd(a.head, 1ull);
+        if ((long long)q < total) t = (long long)q;
+      }
+      s_take = t;
+    }
+    __syncthreads();
+    const long long t = s_take;
+    if (t < 0) return;
+    const int step = (int)(t / a.tiles_per_step);
+    const int r = (int)(t - (long long)step * a.tiles_per_step);
+    const PersistPhase* list = a.phases + (size_t)((a.parity0 + step) & 1) * a.n_phase;
+    // the phase: the last one starting at or before tile r (every listed
+    // phase has tiles); the member: the last one whose tiles start at or
+    // before the phase-local tile
+    int lo = 0, hi = a.n_phase - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(&list[mid].tile0) <= r) lo = mid;
+      else hi = mid - 1;
+    }
+    const int k = lo;
+    const int tt = r - __ldg(&list[k].tile0);
+    const int32_t* toff = a.tile_off + (size_t)k * (a.n_inst + 1);
+    int ilo = 0, ihi = a.n_inst - 1;
+    while (ilo < ihi) {
+      const int mid = (ilo + ihi + 1) >> 1;
+      if (__ldg(toff + mid) <= tt) ilo = mid;
+      else ihi = mid - 1;
+    }
+    const int inst = ilo;
+    const int tile = tt - __ldg(toff + inst);
+    if (threadIdx.x == 0) {
+      int go = 1;
+      const int dep = __ldg(a.dep + (size_t)k * a.n_inst + inst);
+      const int dk = dep >> 1;
+      const long long need = (long long)step + 1 - (dep & 1);   // coarse steps of phase dk
+      if (need > 0) {
+        const int32_t* doff = a.tile_off + (size_t)dk * (a.n_inst + 1);
+        uint32_t target = (uint32_t)need * (uint32_t)(__ldg(doff + inst + 1) - __ldg(doff + inst));
+        if (a.stall) target += 1u << 30;
+        go = persist_wait(a.done + (size_t)dk * a.n_inst + inst, target, a.abort, a.wait_limit);
+        if (!go)
+          for (int i = 0; i < a.n_inst; ++i) atomicExch(a.descs[i].wait_flag, 1);
+      }
+      __threadfence();
+      s_go = go;
+    }
+    __syncthreads();
+    if (!s_go) return;
+    const InstDesc& d = a.descs[inst];
+    const int op = __ldg(&list[k].op), level = __ldg(&list[k].level);
+    const int win = __ldg(&list[k].which_in), wch = __ldg(&list[k].which_ch);
+    const int32_t i0 = __ldg(a.item_off + (size_t)k * (a.n_inst + 1) + inst);
+    const int32_t ni = __ldg(a.item_off + (size_t)k * (a.n_inst + 1) + inst + 1) - i0;
+    const uint32_t* items = list[k].items + i0;
+    if (op == PH_COLLIDE) {
+      const int first = tile * a.tile_blocks;
+      const int nblk = min(a.tile_blocks, ni - first);
+      persist_collide<D, Q, T, THREADS>(d, items + first, nblk, level, win, s_nb, s_flags);
+    } else if (op == PH_INTERP) {
+      persist_interp<D, Q, T, THREADS>(d, items, ni, tile, level, win, wch, sF, s_rows);
+    } else {
+      persist_average<D, Q, T, THREADS>(d, items, ni, tile, level, win, wch, sF, s_rows);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(a.done + (size_t)k * a.n_inst + inst, 1u);
+    }
+  }
+}
+
+template <int D, int Q, class T, int THREADS>
+constexpr size_t persist_smem_bytes() {
+  return sizeof(typename Store<T>::R) * THREADS * Q +
+         sizeof(int32_t) * (THREADS / Block<D>::M) * (1 + Block<D>::NC) * Nbr<D>::K;
 }
 
 // ================================================================ criterion
@@ -1191,11 +1517,61 @@ struct Launch {
         items, kids, descs, level, which_par, which_ch);
   }
 
+  static void average_groups(cudaStream_t s, const int32_t* items, int n, void* fpar,
+                             const void* fch, size_t stride, const int32_t* child0,
+                             const int32_t* parent, const int32_t* nbr, const uint64_t* sm,
+                             double ratio, bool solid) {
+    if (n <= 0) return;
+    const int grid = (int)(((int64_t)n * Block<D>::NC + 127) / 128);
+    if (solid)
+      k_average_groups<D, Q, T, true><<<grid, 128, 0, s>>>(items, n, (T*)fpar, (const T*)fch,
+                                                           stride, child0, parent, nbr, sm,
+                                                           ratio);
+    else
+      k_average_groups<D, Q, T, false><<<grid, 128, 0, s>>>(items, n, (T*)fpar, (const T*)fch,
+                                                            stride, child0, parent, nbr,
+                                                            nullptr, ratio);
+  }
+
+  template <int THREADS>
+  static int persistent_ctas_t() {
+    constexpr size_t smem = persist_smem_bytes<D, Q, T, THREADS>();
+    auto k = k_batch_persistent<D, Q, T, THREADS>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, THREADS, smem) != cudaSuccess)
+      return 0;
+    return per_sm * sm_count;
+  }
+  static int persistent_ctas(int threads) {
+    switch (threads) {
+      case 64: return persistent_ctas_t<64>();
+      case 128: return persistent_ctas_t<128>();
+      case 256: return persistent_ctas_t<256>();
+      default: return 0;
+    }
+  }
+  static void batch_persistent(cudaStream_t s, const PersistArgs& a, int threads, int ctas) {
+    switch (threads) {
+      case 64:
+        k_batch_persistent<D, Q, T, 64><<<ctas, 64, persist_smem_bytes<D, Q, T, 64>(), s>>>(a);
+        break;
+      case 128:
+        k_batch_persistent<D, Q, T, 128><<<ctas, 128, persist_smem_bytes<D, Q, T, 128>(), s>>>(a);
+        break;
+      default:
+        k_batch_persistent<D, Q, T, 256><<<ctas, 256, persist_smem_bytes<D, Q, T, 256>(), s>>>(a);
+    }
+  }
+
   static const LbmOps* ops() {
     static const LbmOps o = {setup,         collide_stream, interp,   average,
-                             criterion,     export_f,       import_f, export_rho_u,
+                             average_groups, criterion,     export_f,       import_f, export_rho_u,
                              init_rest,     mass_partial,   force_partial,
-                             collide_stream_batch, interp_batch, average_batch, features,
+                             collide_stream_batch, interp_batch, average_batch,
+                             persistent_ctas, batch_persistent, features,
                              coarsen_fixup};
     return &o;
   }

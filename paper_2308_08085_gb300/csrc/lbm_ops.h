@@ -30,6 +30,47 @@ struct InstDesc {
   double r_cf[BATCH_MAX_LEVELS];    // tau_{L+1} / (2 tau_L)
   double r_fc[BATCH_MAX_LEVELS];    // 2 tau_L / tau_{L+1}
   FaceParams faces;
+  int32_t* wait_flag;               // the member's device wait-timeout flag
+};
+
+// The persistent form of the batched level step: one launch advances every
+// member by n_steps coarse steps.  The recursive level step (Section 4.1) is
+// unrolled on the host into a list of phases (interpolation into level L+1,
+// collide-stream of level L, averaging of level L+1 into L), the same list
+// for every member; the items of a phase are cut into tiles of one member
+// each.  CTAs take tiles in queue order (step, phase, member, tile) from one
+// counter, and a tile first waits until its member has completed the
+// member's previous phase that has tiles: each member advances on its own,
+// with no grid-wide barrier.  A tile only waits for tiles taken before it and
+// a CTA holds one tile at a time, so the earliest unfinished tile can always
+// run whatever the number of resident CTAs.
+constexpr int PH_INTERP = 0;
+constexpr int PH_COLLIDE = 1;
+constexpr int PH_AVERAGE = 2;
+constexpr int PERSIST_MAX_TILE = 8;    // blocks per collide-stream tile (M_L)
+
+struct PersistPhase {
+  int32_t op, level;
+  int32_t which_in;       // buffer of level L (collide input; interpolation / averaging parent)
+  int32_t which_ch;       // buffer of level L + 1 (interpolation / averaging children)
+  int32_t tile0;          // first tile of the phase within a coarse step
+  int32_t n_tiles;
+  const uint32_t* items;  // the phase's instance-major item list (active blocks or parents)
+};
+
+struct PersistArgs {
+  const InstDesc* descs;
+  const PersistPhase* phases;   // [2][n_phase]: steps starting with cur bit 0 clear / set
+  const int32_t* tile_off;      // [n_phase][n_inst + 1]: first tile of each member
+  const int32_t* item_off;      // [n_phase][n_inst + 1]: first item of each member
+  const int32_t* dep;           // [n_phase][n_inst]: 2 k + wrap, the member's previous phase
+                                // with tiles (wrap: in the previous coarse step)
+  uint32_t* done;               // [n_phase][n_inst]: tiles completed, summed over the launch
+  unsigned long long* head;     // queue head
+  int32_t* abort;               // raised when a wait gave up; sticky until read by the host
+  int n_phase, n_inst, tiles_per_step, parity0, n_steps, tile_blocks;
+  long long wait_limit;         // clock64 cycles a tile may wait
+  int stall;                    // check of the timeout path: no wait can be satisfied
 };
 
 // The coarse-to-fine interpolation of the level step (Section 4.1) fused
@@ -89,6 +130,13 @@ struct LbmOps {
                   const void* fch, size_t stride, const int32_t* child0, const int32_t* parent,
                   const uint64_t* cellmask, const int32_t* status, const int32_t* nbr,
                   const uint64_t* solidmask, double ratio, int mode_sync, bool solid);
+  // the averaging of the level step over (block << 3 | group) items: the
+  // groups of 2^D interface cells of the fine level's boundary blocks, each
+  // into its parent cell (the work of average mode 0, listed in advance)
+  void (*average_groups)(cudaStream_t, const int32_t* items, int n, void* fpar, const void* fch,
+                         size_t stride, const int32_t* child0, const int32_t* parent,
+                         const int32_t* nbr, const uint64_t* solidmask, double ratio,
+                         bool solid);
   // vorticity criterion marks (+1/-1/0) and block max |w|^2
   void (*criterion)(cudaStream_t, const int32_t* list, int n, const void* f, size_t stride,
                     const int32_t* nbr, const uint64_t* solidmask, const int32_t* status,
@@ -124,6 +172,11 @@ struct LbmOps {
                        int level, int which_par, int which_ch);
   void (*average_batch)(cudaStream_t, const uint32_t* items, int n, const InstDesc* descs,
                         int level, int which_par, int which_ch);
+  // persistent form (PersistArgs): the number of CTAs of `threads` threads
+  // that stay resident together (0: unsupported CTA size), after setting the
+  // kernel's shared-memory attribute; call outside any stream capture
+  int (*persistent_ctas)(int threads);
+  void (*batch_persistent)(cudaStream_t, const PersistArgs& a, int threads, int ctas);
   // 27 block summaries of the learned refinement proposal (3D only)
   void (*features)(cudaStream_t, const int32_t* list, int n, const void* f, size_t stride,
                    const int32_t* nbr, const uint64_t* solidmask, int level, int lmax,

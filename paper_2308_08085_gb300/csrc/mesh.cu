@@ -122,6 +122,36 @@ struct PLeaf {
   const int32_t* status;
   __device__ bool operator()(int i) const { return status[list[i]] == ST_UNREFINED; }
 };
+// Averaging work of the level step (Section 3.4.3): group g of 2^D cells of
+// boundary block list[i / N_c] (the cells under one parent cell) when they
+// are interface cells and that parent cell is fluid
+template <int D>
+struct PAvgGroup {
+  const int32_t* list;
+  const uint64_t* cellmask;
+  const int32_t* parent;
+  const int32_t* child0;
+  const uint64_t* solidmask;
+  __device__ bool operator()(int i) const {
+    constexpr int NC = Block<D>::NC;
+    const int ch = list[i / NC], g = i % NC;
+    const int f0 = Block<D>::cell(2 * (g & 1), 2 * ((g >> 1) & 1), 2 * ((g >> 2) & 1));
+    if (!((cellmask[2 * (size_t)ch + 1] >> f0) & 1ull)) return false;
+    if (!solidmask) return true;
+    const int P = parent[ch], c = ch - child0[P];
+    const int pc = Block<D>::cell(2 * (c & 1) + (g & 1), 2 * ((c >> 1) & 1) + ((g >> 1) & 1),
+                                  2 * ((c >> 2) & 1) + ((g >> 2) & 1));
+    return !((solidmask[P] >> pc) & 1ull);
+  }
+};
+template <int D>
+struct VAvgGroup {   // block << 3 | group
+  const int32_t* list;
+  __device__ int32_t operator()(int i) const {
+    return (list[i / Block<D>::NC] << 3) | (i % Block<D>::NC);
+  }
+};
+
 // leaves, and refined blocks with a child that has a NONE neighbour
 struct PActive {
   const int32_t* list;
@@ -646,6 +676,23 @@ int mesh_refresh_lists(Instance* a) {
     AMR_TRY(compact(a, n, PLeaf{ord, a->status}, VIdent{}, nullptr, &a->n_leaves[L], 0, false));
     AMR_TRY(compact(a, n, PNoneNbr{ord, a->nonemask}, VList{ord}, a->bnd + (size_t)L * a->cap,
                     &a->n_bnd[L]));
+  }
+  // averaging groups of every level's boundary blocks, packed by level
+  int64_t off = 0;
+  for (int L = 0; L < a->lmax; ++L) {
+    a->agrp_off[L] = off;
+    a->n_agrp[L] = 0;
+    if (L == 0 || a->n_bnd[L] == 0) continue;
+    const int32_t* bl = a->bnd + (size_t)L * a->cap;
+    if (a->dim == 2)
+      AMR_TRY(compact(a, a->n_bnd[L] * 4,
+                      PAvgGroup<2>{bl, a->cellmask, a->parent, a->child0, a->sm()},
+                      VAvgGroup<2>{bl}, a->agrp + off, &a->n_agrp[L]));
+    else
+      AMR_TRY(compact(a, a->n_bnd[L] * 8,
+                      PAvgGroup<3>{bl, a->cellmask, a->parent, a->child0, a->sm()},
+                      VAvgGroup<3>{bl}, a->agrp + off, &a->n_agrp[L]));
+    off += a->n_agrp[L];
   }
   // exchange work per level, for the profile's algorithmic bytes
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(a->red);

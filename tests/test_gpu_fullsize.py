@@ -218,10 +218,10 @@ def test_cylinder_full_size_mesh_invariants_and_rest_prism():
 def test_batched_cavities_full_size_equal_individual_runs():
     """The 64 batched cavities of the benchmark at full size (their root grids,
     depths and capacities): after refining two block layers under the lid on
-    every level, one period of 50
-    coarse steps advanced in lock-step by the batch equals the same instances
-    advanced one by one, to rounding (the batched and the per-instance kernels
-    are compiled separately)."""
+    every level, one period of 50 coarse steps advanced by the batch in the
+    graph form, then one more in one persistent launch, equals the same
+    instances advanced one by one, to rounding (the batched and the
+    per-instance kernels are compiled separately)."""
     from paper_2308_08085_gb300 import AMR_F, AmrBatch, AmrLBM
     cfgs = W.batched_cavities(64, seed=0)
 
@@ -239,16 +239,28 @@ def test_batched_cavities_full_size_equal_individual_runs():
 
     batched, single = build(), build()
     batch = AmrBatch(batched)
-    batch.step(50)
+
+    def compare():
+        worst = 0.0
+        for a, b in zip(batched, single):
+            assert a.counts()["n_ids"] == b.counts()["n_ids"]
+            fa = a.fields_device(AMR_F, torch.float64)
+            fb = b.fields_device(AMR_F, torch.float64)
+            worst = max(worst, float(torch.linalg.norm(fa - fb) / torch.linalg.norm(fb)))
+            del fa, fb
+        return worst
+
+    batch.step(50)                             # graph form
     for sim in single:
         sim.step(50)
-    worst = 0.0
-    for a, b in zip(batched, single):
-        assert a.counts()["n_ids"] == b.counts()["n_ids"]
-        fa = a.fields_device(AMR_F, torch.float64)
-        fb = b.fields_device(AMR_F, torch.float64)
-        worst = max(worst, float(torch.linalg.norm(fa - fb) / torch.linalg.norm(fb)))
-        del fa, fb
+    worst = compare()
+    assert worst <= 1e-6, worst
+    batch.configure("persistent", 128, 2)      # then 50 steps in one persistent launch
+    batch.step(50)
+    batch.sync()
+    for sim in single:
+        sim.step(50)
+    worst = compare()
     assert worst <= 1e-6, worst
     assert sum(sum(s.counts()["n_ids"]) for s in single) > 500_000
     batch.close()

@@ -519,18 +519,3 @@ def test_checkpoint_restore_resumes_bit_exactly():
         sim.close()
 
 
-# ------------------------------------------------------- failure detection
-def test_bounded_wait_gives_up_and_reports():
-    """The bounded mbarrier wait of the bulk-copy kernels, run on a barrier
-    that nothing arrives at, gives up after its limit and reports
-    AMR_E_TIMEOUT; the context stays usable."""
-    from paper_2308_08085_gb300.amr import load_library
-    lib = load_library()
-    stream = torch.cuda.current_stream().cuda_stream
-    assert lib.amr_check_bounded_wait(1 << 22, ctypes.c_void_p(stream)) == -4   # AMR_E_TIMEOUT
-    assert lib.amr_check_bounded_wait(0, ctypes.c_void_p(stream)) == -1         # AMR_E_INVAL
-    cfg = W.cavity(dim=2, q=9, n=8, max_levels=1)
-    gpu = new_gpu(cfg, "f64")
-    gpu.step(2)                                   # still usable
-    assert np.isfinite(gpu.populations()).all()
-    gpu.close()
