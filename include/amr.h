@@ -37,7 +37,10 @@
  * of the opposite direction, with the link's boundary rule already applied.
  * amr_fields(AMR_F / AMR_RHO_U / AMR_MASS) and amr_set_fields(AMR_F) convert:
  * they read and write the paper's f_p(x); only the raw arena (checkpoints,
- * amr_mass_audit_noalloc's inputs) is in the stored form.
+ * amr_mass_audit_noalloc's inputs) is in the stored form.  Its layout is
+ * block-major: the stored value of direction p, block b, cell l is element
+ * b Q M + p M + l of a buffer (M = 4^dim), so each block's Q M values are
+ * one contiguous run.
  */
 #ifndef AMR_H
 #define AMR_H
@@ -137,7 +140,10 @@ typedef struct {
                               the order of the blocks in memory.             */
   int32_t interp;          /* coarse-to-fine interpolation (Section 3.4):
                               AMR_INTERP_LINEAR (0) or AMR_INTERP_CUBIC (3)  */
-  int32_t pad_;
+  int32_t check_tables;    /* 1: validate the block tables on the device at
+                              amr_init and after every amr_adapt
+                              (amr_check_tables); a bad entry fails the call
+                              with AMR_E_INVAL                              */
 } amr_config;
 
 #define AMR_INTERP_LINEAR 0
@@ -267,7 +273,7 @@ int amr_profile_read(amr_t* a, amr_kernel_profile* out, int max, int reset);
  *
  * Inputs (device pointers, owned by the caller): the two population buffers
  * f_a, f_b of `n_blocks` blocks in this library's storage layout of
- * `storage` ([Q][n_blocks][4^dim] stored values -- the outgoing
+ * `storage` ([n_blocks][Q][4^dim] stored values -- the outgoing
  * post-collision populations, see "Stored populations" above; 16-bit
  * storages hold value - w_p), a per-level buffer choice `cur` (bit L set:
  * blocks of level L are read from f_b), int32 level[n_blocks] /
@@ -302,6 +308,52 @@ int amr_mass_audit_noalloc(int dim, int q, int storage, int64_t n_blocks,
 
 /* Release host-side state (the arena stays owned by the caller). */
 int amr_free(amr_t* a);
+
+/* ------------------------------------------------- block-table validation
+ * The stand-in for a device bounds checker (the paper has no counterpart).
+ * Every block ID a kernel dereferences comes from the block tables (neighbour
+ * rows, child0, parent), the per-level work lists or the averaging groups;
+ * these checks verify each entry against its range and the forest's
+ * invariants on the device, dereferencing an index only once it is known to
+ * be in range, and count the bad entries in a device word instead of trapping.
+ *
+ * For every block b < cap: status in 0 .. 4; an inactive block (status 0)
+ * has level -1, child0 = parent = AMR_NONE and an all-AMR_NONE neighbour
+ * row; an active one has 0 <= level < max_levels, nbr[b][0] = b, entries
+ * 1 .. 3^dim - 1 each AMR_NONE, a wall code (-2 .. -7) or an active block of
+ * the same level, the remaining entries of the 32 AMR_NONE; child0 AMR_NONE
+ * for a leaf, else 2^dim consecutive active children one level down whose
+ * parent is b; parent AMR_NONE on level 0, else an active refined block one
+ * level up whose children include b.  Gap stack entries: inactive IDs.
+ *
+ * amr_validate_tables: caller-owned device tables in the layout of the
+ *   AMR_BLOCKS rows (level, status, child0, parent: int32[cap]) and of the
+ *   arena's neighbour table (int32[cap][32], first 3^dim used), and the gap
+ *   stack gap[n_gaps] (may be NULL when n_gaps is 0).  Synchronous on
+ *   `stream`; the result words are a file-scope device array, so calls on
+ *   different streams must not overlap.
+ * amr_check_tables: the instance's own tables, gap stack, work lists (ID
+ *   set, tree order, active, parent and boundary lists: IDs of their level)
+ *   and averaging groups.  Synchronous.  AMR_E_INVAL when an entry is bad.
+ * out3[0] = bad entries, out3[1] = the smallest block with a bad entry (-1
+ * when none, or when the gap count itself is out of range), out3[2] = the
+ * AMR_CHECK_* code of its first failed check. */
+#define AMR_CHECK_STATUS 1
+#define AMR_CHECK_INACTIVE 2
+#define AMR_CHECK_LEVEL 3
+#define AMR_CHECK_SELF 4
+#define AMR_CHECK_NEIGHBOUR 5
+#define AMR_CHECK_UNUSED 6
+#define AMR_CHECK_CHILDREN 7
+#define AMR_CHECK_PARENT 8
+#define AMR_CHECK_GAP 9
+#define AMR_CHECK_LIST 10
+#define AMR_CHECK_GROUP 11
+int amr_validate_tables(int dim, int max_levels, int64_t cap, const int32_t* level,
+                        const int32_t* status, const int32_t* child0, const int32_t* parent,
+                        const int32_t* nbr, const int32_t* gap, int64_t n_gaps, int64_t* out3,
+                        void* stream);
+int amr_check_tables(amr_t* a, int64_t* out3);
 
 /* ---------------------------------------------------- checkpoint / resume
  * The paper keeps all state on the device and has no checkpoint; this is a

@@ -47,7 +47,7 @@ class AmrConfig(ctypes.Structure):
                 ("kernel_variant", ctypes.c_int32), ("refine_dist", ctypes.c_double),
                 ("refine_dist_targets", ctypes.c_int32), ("refine_dist_freeze", ctypes.c_int32),
                 ("root_ids", ctypes.POINTER(ctypes.c_int32)), ("interp", ctypes.c_int32),
-                ("pad_", ctypes.c_int32)]
+                ("check_tables", ctypes.c_int32)]
 
 
 class AmrAdaptStats(ctypes.Structure):
@@ -69,6 +69,25 @@ class AmrKernelProfile(ctypes.Structure):
 
 
 _lib = None
+
+
+def validate_tables(dim, max_levels, level, status, child0, parent, nbr, gap=None,
+                    stream=None):
+    """amr_validate_tables on device int32 tensors (nbr [cap, 32]); returns
+    (bad entries, first bad block or -1, AMR_CHECK_* code)."""
+    import torch
+    lib = load_library()
+    cap = level.numel()
+    out = (ctypes.c_int64 * 3)()
+    s = stream if stream is not None else torch.cuda.current_stream(level.device)
+    rc = lib.amr_validate_tables(int(dim), int(max_levels), cap, level.data_ptr(),
+                                 status.data_ptr(), child0.data_ptr(), parent.data_ptr(),
+                                 nbr.data_ptr(), gap.data_ptr() if gap is not None else None,
+                                 gap.numel() if gap is not None else 0, out,
+                                 ctypes.c_void_p(s.cuda_stream))
+    if rc != AMR_OK:
+        raise AmrError(rc, "amr_validate_tables")
+    return tuple(int(v) for v in out)
 
 
 def load_library(path=LIB_PATH):
@@ -128,6 +147,11 @@ def load_library(path=LIB_PATH):
                                            vp, vp, vp, vp]
     lib.amr_mass_audit_noalloc.restype = i32
     pp = ctypes.POINTER(vp)
+    lib.amr_validate_tables.argtypes = [i32, i32, i64, vp, vp, vp, vp, vp, vp, i64,
+                                        ctypes.POINTER(i64), vp]
+    lib.amr_validate_tables.restype = i32
+    lib.amr_check_tables.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.amr_check_tables.restype = i32
     lib.amr_batch_arena_bytes.argtypes = [pp, i32]
     lib.amr_batch_arena_bytes.restype = sz
     lib.amr_batch_create.argtypes = [pp, i32, vp, sz, vp, pp]
@@ -201,6 +225,7 @@ def make_config(cfg, storage="f32", use_graphs=True, kernel_variant=0):
         c._root_ids = arr                               # kept alive with the struct
         c.root_ids = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     c.interp = {"linear": 0, "cubic": 3}[cfg.get("interp", "linear")]
+    c.check_tables = int(cfg.get("check_tables", 0))
     return c
 
 
@@ -388,6 +413,14 @@ class AmrLBM:
         """Leaf-cell updates of one coarse step (Section 5.1 definition)."""
         c = self.counts()
         return sum((2 ** L) * c["n_leaves"][L] * self.m for L in range(self.lmax))
+
+    def check_tables(self):
+        """(bad entries, first bad block or -1, AMR_CHECK_* code) of the
+        device validation of the block tables, lists and averaging groups."""
+        out = (ctypes.c_int64 * 3)()
+        rc = self.lib.amr_check_tables(self.h, out)
+        self._check(rc, "amr_check_tables", ok=(AMR_OK, AMR_E_INVAL))
+        return tuple(int(v) for v in out)
 
     def checkpoint(self):
         """Host image (numpy uint8) of the whole instance state."""

@@ -54,7 +54,7 @@ struct Instance {
   int8_t* marks = nullptr;         // [cap]
   double* w2 = nullptr;            // [cap] criterion block maxima
   int32_t *tmp0 = nullptr, *tmp1 = nullptr, *tmp2 = nullptr;   // [cap]
-  int32_t* cta = nullptr;          // [cap/256 + 2]
+  int32_t* cta = nullptr;          // [cta_slots(cap)]
   int32_t* dcount = nullptr;       // [64] device counters
   double* red = nullptr;           // [8192] reduction partials
   int32_t* wall_code = nullptr;    // [64] code of a set of crossed faces
@@ -101,7 +101,6 @@ struct Instance {
   // interpolation mode bit of LbmOps::interp for this configuration
   int interp_bits() const { return cfg.interp == AMR_INTERP_CUBIC ? 2 : 0; }
   size_t f_bytes() const { return (size_t)cap * M * q * elem; }
-  size_t stride() const { return (size_t)cap * M; }
   void* fbuf(int level, int which) const {   // which: 0 current, 1 other
     return f[((cur >> level) & 1u) ^ (unsigned)which];
   }
@@ -109,6 +108,13 @@ struct Instance {
 
 // dcount slot of the device wait-timeout flag (StepParams::wait_flag)
 constexpr int kWaitFlagSlot = 16;
+// entries of the compaction's per-CTA count array: one per 256 items of the
+// longest compaction, the averaging groups of every block (8 per block)
+inline int64_t cta_slots(int64_t cap) { return cap * 8 / 256 + 2; }
+
+// check.cu: validate the instance's block tables, lists and averaging groups
+// (amr_check_tables); out3 as there
+int check_instance_tables(Instance* a, int64_t* out3);
 
 enum ProfileKind {
   PK_COLLIDE = 0, PK_INTERP = 1, PK_AVERAGE = 2,

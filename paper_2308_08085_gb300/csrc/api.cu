@@ -130,7 +130,7 @@ static Layout layout_for(const amr_config* c) {
       (size_t)cap,                             // 14 marks
       (size_t)cap * 8,                         // 15 w2
       (size_t)cap * 4, (size_t)cap * 4, (size_t)cap * 4,   // 16,17,18 tmp
-      (size_t)(cap / 256 + 2) * 4,             // 19 cta
+      (size_t)cta_slots(cap) * 4,              // 19 cta
       64 * 4,                                  // 20 dcount
       8192 * 8,                                // 21 red
       64 * 4,                                  // 22 wall_code
@@ -326,7 +326,7 @@ static void advance(Instance* a, int L, bool first) {
     ProfScope ps(a, PK_INTERP,
                  ((double)a->n_ghost_children[L] * a->nc + cells) * a->q * a->elem, cells);
     a->ops->interp(a->stream, a->parents + (size_t)L * a->cap, (int)np, a->fbuf(L, 0),
-                   a->fbuf(L + 1, 1), a->stride(), a->child0, a->cellmask, a->nbr, a->sm(),
+                   a->fbuf(L + 1, 1), a->child0, a->cellmask, a->nbr, a->sm(),
                    nullptr, nullptr, ratio_cf(a, L), 4 | a->interp_bits(), a->solid);
     a->launches += 1;
   }
@@ -354,11 +354,11 @@ static void advance(Instance* a, int L, bool first) {
       // level's boundary blocks, listed at adaptation
       if (cubic)
         a->ops->average(a->stream, a->parents + (size_t)L * a->cap, (int)np, true,
-                        a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0, a->parent,
+                        a->fbuf(L, 0), a->fbuf(L + 1, 0), a->child0, a->parent,
                         a->cellmask, a->status, a->nbr, a->sm(), ratio_fc(a, L), 1, a->solid);
       else
         a->ops->average_groups(a->stream, a->agrp + a->agrp_off[L + 1], (int)a->n_agrp[L + 1],
-                               a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0,
+                               a->fbuf(L, 0), a->fbuf(L + 1, 0), a->child0,
                                a->parent, a->nbr, a->sm(), ratio_fc(a, L), a->solid);
       a->launches += 1;
     }
@@ -427,14 +427,14 @@ static void level_sync(Instance* a) {
   for (int L = a->lmax - 2; L >= 0; --L) {
     if (a->n_ids[L + 1] == 0) continue;
     a->ops->average(a->stream, a->idset + (size_t)L * a->cap, (int)a->n_ids[L], true,
-                    a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0, a->parent,
+                    a->fbuf(L, 0), a->fbuf(L + 1, 0), a->child0, a->parent,
                     a->cellmask, a->status, a->nbr, a->sm(), ratio_fc(a, L), 1, a->solid);
     a->launches += 1;
   }
   for (int L = 0; L + 1 < a->lmax; ++L) {
     if (a->n_parents[L] == 0) continue;
     a->ops->interp(a->stream, a->parents + (size_t)L * a->cap, (int)a->n_parents[L],
-                   a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(), a->child0, a->cellmask,
+                   a->fbuf(L, 0), a->fbuf(L + 1, 0), a->child0, a->cellmask,
                    a->nbr, a->sm(), nullptr, nullptr, ratio_cf(a, L), a->interp_bits(),
                    a->solid);
     a->launches += 1;
@@ -448,7 +448,7 @@ static int criterion_into_marks(Instance* a) {
     if (a->n_ids[L] == 0) continue;
     const double inv_dx = a->cfg.nx * std::ldexp(1.0, L) / a->cfg.length_x;
     a->ops->criterion(a->stream, a->idset + (size_t)L * a->cap, (int)a->n_ids[L],
-                      a->fbuf(L, 0), a->stride(), a->nbr, a->sm(), a->status, L, a->lmax, inv_dx,
+                      a->fbuf(L, 0), a->nbr, a->sm(), a->status, L, a->lmax, inv_dx,
                       a->cfg.crit_start, a->cfg.crit_inc, a->marks, a->w2);
     a->launches += 1;
   }
@@ -467,7 +467,7 @@ static int features_all(Instance* a) {
     if (a->n_ids[L] == 0) continue;
     const double inv_dx = a->cfg.nx * std::ldexp(1.0, L) / a->cfg.length_x;
     a->ops->features(a->stream, a->idset + (size_t)L * a->cap, (int)a->n_ids[L], a->fbuf(L, 0),
-                     a->stride(), a->nbr, a->sm(), L, a->lmax, inv_dx, a->features);
+                     a->nbr, a->sm(), L, a->lmax, inv_dx, a->features);
     a->launches += 1;
   }
   AMR_CUDA(cudaGetLastError());
@@ -637,7 +637,6 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
   double w[27];
   host_velocities(a->dim, a->q, c, w);
   std::memset(&a->prm, 0, sizeof(a->prm));
-  a->prm.stride = a->stride();
   a->prm.variant = cfg->kernel_variant;
   a->prm.wait_flag = a->dcount + kWaitFlagSlot;
   if (a->ops->setup() != 0) {
@@ -680,6 +679,10 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
     set_error(std::string("init: ") + cudaGetErrorString(cudaGetLastError()));
     rc = AMR_E_CUDA;
   }
+  if (rc == AMR_OK && cfg->check_tables) {
+    int64_t res[3];
+    rc = check_instance_tables(a, res);
+  }
   if (rc != AMR_OK) {
     cudaStreamDestroy(a->capture_stream);
     delete a;
@@ -687,6 +690,12 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
   }
   *out = reinterpret_cast<amr_t*>(a);
   return AMR_OK;
+}
+
+int amr_check_tables(amr_t* h, int64_t* out3) {
+  Handle* a = reinterpret_cast<Handle*>(h);
+  if (!a || !out3) return AMR_E_INVAL;
+  return check_instance_tables(a, out3);
 }
 
 int amr_step(amr_t* h, int n) {
@@ -736,6 +745,10 @@ int amr_adapt(amr_t* h, const int8_t* dev_marks, amr_adapt_stats* out) {
   AMR_CUDA(cudaStreamSynchronize(a->stream));
   harvest_phases(a);
   if (int wrc = take_wait_flag(a)) return wrc;
+  if (a->cfg.check_tables) {
+    int64_t res[3];
+    if (int crc = check_instance_tables(a, res)) return crc;
+  }
   int64_t nb = 0;
   for (int L = 0; L < a->lmax; ++L) nb += a->n_ids[L];
   st.n_blocks = nb;
@@ -806,7 +819,7 @@ int64_t amr_fields(amr_t* h, int what, void* dst, size_t dst_bytes, int dst_on_d
         if (a->n_active[L] == 0 || !a->solid) continue;
         const double dx = a->cfg.length_x / (a->cfg.nx * std::ldexp(1.0, L));
         const int g = a->ops->force_partial(s, a->active + (size_t)L * cap, (int)a->n_active[L],
-                                            a->fbuf(L, 0), a->stride(), a->nbr, a->status,
+                                            a->fbuf(L, 0), a->nbr, a->status,
                                             a->solidmask, 1.0 / a->tau[L], dx, a->red);
         k_sum_partials<<<1, 256, 0, s>>>(g, 3, a->red, out_dev + 4);
         AMR_CUDA(cudaMemcpyAsync(part.data(), out_dev + 4, 24, cudaMemcpyDeviceToHost, s));

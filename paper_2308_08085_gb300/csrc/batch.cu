@@ -87,7 +87,6 @@ static int refresh(Batch* b) {
     d.nbr = a->nbr;
     d.child0 = a->child0;
     d.cellmask = a->cellmask;
-    d.stride = a->stride();
     for (int L = 0; L < a->lmax; ++L) {
       d.omega[L] = 1.0 / a->tau[L];
       if (L + 1 < a->lmax) {

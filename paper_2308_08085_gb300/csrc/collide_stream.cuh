@@ -2,8 +2,9 @@
 // the link tables and the gather / scatter of a cell's populations that every
 // other kernel uses to read or write the state.  Included by lbm_kernels.cuh.
 //
-// Population layout (every storage type): g[p * stride + b * M + l], stride =
-// capacity * M, M = 4^D cells per block, l = i + 4 j + 16 k.
+// Population layout (every storage type): block-major, g[b * Q M + p * M + l],
+// M = 4^D cells per block, l = i + 4 j + 16 k: the Q planes of a block are one
+// contiguous run, so blocks with unrelated IDs still move whole DRAM pages.
 //
 // What is stored.  The paper stores the post-streaming (pre-collision)
 // populations f(x, t) of every cell.  This library stores, for every cell y
@@ -122,12 +123,12 @@ __device__ __forceinline__ T ld_pop(const T* p) {
 // SOLID, `solidmask` (one bit per cell) may still be null: no solid cells.
 template <int D, int Q, class T, bool SOLID, bool COH = false>
 __device__ __forceinline__ void gather_cell(typename Store<T>::R (&f)[Q],
-                                            const T* __restrict__ g, size_t stride, int b, int l,
+                                            const T* __restrict__ g, int b, int l,
                                             const int32_t* __restrict__ row,
                                             const uint64_t* __restrict__ solidmask) {
   using S = Store<T>;
   constexpr int M = Block<D>::M;
-  const size_t own = (size_t)b * M + l;
+  const size_t own = (size_t)b * (Q * M) + l;
   const bool has_sm = SOLID && solidmask != nullptr;
   const bool solid_cell = has_sm && ((__ldg(solidmask + b) >> l) & 1ull);
   static_for<0, Q>([&](auto P) {
@@ -141,9 +142,9 @@ __device__ __forceinline__ void gather_cell(typename Store<T>::R (&f)[Q],
       const int src = k == 0 ? b : row[k];
       bool back = src < 0;
       if (has_sm && !back) back = (__ldg(solidmask + src) >> sl) & 1ull;
-      const size_t at = solid_cell ? (size_t)p * stride + own
-                                   : (back ? (size_t)pb * stride + own
-                                           : (size_t)p * stride + (size_t)src * M + sl);
+      const size_t at = solid_cell ? own + (size_t)p * M
+                                   : (back ? own + (size_t)pb * M
+                                           : (size_t)src * (Q * M) + (size_t)p * M + sl);
       f[p] = S::template load<D, Q, p>(ld_pop<COH>(g + at));
     }
   });
@@ -166,19 +167,18 @@ __device__ const OppTable<D, Q> g_opp = make_opp<D, Q>();
 // The element of g that holds the pre-collision f_p of cell l of block b
 // (the scatter rule of scatter_cell for one runtime direction p).
 template <int D, int Q>
-__device__ __forceinline__ size_t src_slot(int p, int b, int l, size_t stride,
-                                           const int32_t* row,
+__device__ __forceinline__ size_t src_slot(int p, int b, int l, const int32_t* row,
                                            const uint64_t* __restrict__ solidmask) {
   constexpr int M = Block<D>::M;
-  if (p == 0) return (size_t)b * M + l;
+  const size_t own = (size_t)b * (Q * M) + l;
+  if (p == 0) return own;
   const int e = __ldg(&g_src_k<D, Q>.e[p * M + l]);
   const int k = e & 31, sl = e >> 5;
   const int src = k == 0 ? b : row[k];
   bool back = src < 0;
   if (solidmask && !back) back = (__ldg(solidmask + src) >> sl) & 1ull;
-  if (solidmask && ((__ldg(solidmask + b) >> l) & 1ull)) return (size_t)p * stride + (size_t)b * M + l;
-  return back ? (size_t)g_opp<D, Q>.o[p] * stride + (size_t)b * M + l
-              : (size_t)p * stride + (size_t)src * M + sl;
+  if (solidmask && ((__ldg(solidmask + b) >> l) & 1ull)) return own + (size_t)p * M;
+  return back ? own + (size_t)g_opp<D, Q>.o[p] * M : (size_t)src * (Q * M) + (size_t)p * M + sl;
 }
 
 // Store pre-collision populations f of cell l of block b so that gather_cell
@@ -188,13 +188,13 @@ __device__ __forceinline__ size_t src_slot(int p, int b, int l, size_t stride,
 // to come from this cell: it is moved to this cell's opposite slot first.
 template <int D, int Q, class T, bool SOLID, bool MOVE = false, class IsNew = int>
 __device__ __forceinline__ void scatter_cell(const typename Store<T>::R (&f)[Q],
-                                             T* __restrict__ g, size_t stride, int b, int l,
+                                             T* __restrict__ g, int b, int l,
                                              const int32_t* __restrict__ row,
                                              const uint64_t* __restrict__ solidmask,
                                              IsNew is_new = 0) {
   using S = Store<T>;
   constexpr int M = Block<D>::M;
-  const size_t own = (size_t)b * M + l;
+  const size_t own = (size_t)b * (Q * M) + l;
   const bool has_sm = SOLID && solidmask != nullptr;
   const bool solid_cell = has_sm && ((__ldg(solidmask + b) >> l) & 1ull);
   static_for<0, Q>([&](auto P) {
@@ -209,13 +209,13 @@ __device__ __forceinline__ void scatter_cell(const typename Store<T>::R (&f)[Q],
       bool back = src < 0;
       if (has_sm && !back) back = (__ldg(solidmask + src) >> sl) & 1ull;
       if (solid_cell) {
-        g[(size_t)p * stride + own] = S::template save<D, Q, p>(f[p]);
+        g[own + (size_t)p * M] = S::template save<D, Q, p>(f[p]);
       } else if (back) {
-        g[(size_t)pb * stride + own] = S::template save<D, Q, p>(f[p]);
+        g[own + (size_t)pb * M] = S::template save<D, Q, p>(f[p]);
       } else {
-        T* slot = g + (size_t)p * stride + (size_t)src * M + sl;
+        T* slot = g + (size_t)src * (Q * M) + (size_t)p * M + sl;
         if constexpr (MOVE) {
-          if (k != 0 && !is_new(src)) g[(size_t)pb * stride + own] = *slot;
+          if (k != 0 && !is_new(src)) g[own + (size_t)pb * M] = *slot;
         }
         *slot = S::template save<D, Q, p>(f[p]);
       }
@@ -286,7 +286,7 @@ constexpr int BF_OUTLET = 8;    // a neighbour is an outlet face
 // neighbour is an outlet face (anti-bounce-back needs the cell's velocity).
 template <int D, int Q, class T, bool SOLID, bool OUTLET, bool GHOST = false, bool COH = false>
 __device__ __noinline__ void step_cell_checked(const T* __restrict__ gin, T* __restrict__ gout,
-                                               size_t stride, size_t own, int l,
+                                               size_t own, int l,
                                                const int32_t* nb, const uint64_t* sm, int flags,
                                                double omega, const FaceParams& faces,
                                                bool ghost_in) {
@@ -312,9 +312,9 @@ __device__ __noinline__ void step_cell_checked(const T* __restrict__ gin, T* __r
       bool out = src < 0;
       if constexpr (SOLID) out = out || ((sm[code] >> sl) & 1ull);
       back |= (uint32_t)out << p;
-      const size_t at = ghost_in ? (size_t)p * stride + own
-                                 : (out ? (size_t)pb * stride + own
-                                        : (size_t)p * stride + (size_t)src * M + sl);
+      const size_t at = ghost_in ? own + (size_t)p * M
+                                 : (out ? own + (size_t)pb * M
+                                        : (size_t)src * (Q * M) + (size_t)p * M + sl);
       f[p] = S::template load<D, Q, p>(ld_pop<COH>(gsrc + at));
     }
   });
@@ -334,7 +334,7 @@ __device__ __noinline__ void step_cell_checked(const T* __restrict__ gin, T* __r
         }
       }
     }
-    gout[(size_t)p * stride + own] = S::template save<D, Q, p>(v);
+    gout[own + (size_t)p * M] = S::template save<D, Q, p>(v);
   });
 }
 
@@ -344,7 +344,7 @@ __device__ __noinline__ void step_cell_checked(const T* __restrict__ gin, T* __r
 // for the interpolation into the children.
 template <int D, int Q, class T, bool SOLID, bool OUTLET>
 __device__ __noinline__ void step_cell_parent(const T* __restrict__ gin, T* __restrict__ gout,
-                                              size_t stride, size_t own, int l,
+                                              size_t own, int l,
                                               const int32_t* nb, const uint64_t* sm, int flags,
                                               double omega, const FaceParams& faces, double r_cf,
                                               typename Store<T>::R* rc) {
@@ -365,8 +365,8 @@ __device__ __noinline__ void step_cell_parent(const T* __restrict__ gin, T* __re
       bool out = src < 0;
       if constexpr (SOLID) out = out || ((sm[code] >> sl) & 1ull);
       back |= (uint32_t)out << p;
-      f[p] = out ? S::template load<D, Q, p>(gin[(size_t)pb * stride + own])
-                 : S::template load<D, Q, p>(gin[(size_t)p * stride + (size_t)src * M + sl]);
+      f[p] = out ? S::template load<D, Q, p>(gin[own + (size_t)pb * M])
+                 : S::template load<D, Q, p>(gin[(size_t)src * (Q * M) + (size_t)p * M + sl]);
     }
   });
   R rho, ux, uy, uz;
@@ -392,7 +392,7 @@ __device__ __noinline__ void step_cell_parent(const T* __restrict__ gin, T* __re
         }
       }
     }
-    gout[(size_t)p * stride + own] = S::template save<D, Q, p>(v);
+    gout[own + (size_t)p * M] = S::template save<D, Q, p>(v);
   });
 }
 
@@ -403,7 +403,7 @@ __device__ __noinline__ void step_cell_parent(const T* __restrict__ gin, T* __re
 // the fine output buffer.  Solid cells are skipped.
 template <int D, int Q, class T>
 __device__ __noinline__ void interp_out(const typename Store<T>::R* rc, int l, int c0,
-                                        const uint64_t* cgm, T* __restrict__ fout, size_t stride,
+                                        const uint64_t* cgm, T* __restrict__ fout,
                                         const uint64_t* __restrict__ solidmask) {
   using S = Store<T>;
   using R = typename S::R;
@@ -429,12 +429,12 @@ __device__ __noinline__ void interp_out(const typename Store<T>::R* rc, int l, i
 #pragma unroll
     for (int a = 0; a < NC; ++a)
       corner[a] = Block<D>::cell(2 * qx + (a & 1), 2 * qy + ((a >> 1) & 1), 2 * qz + ((a >> 2) & 1));
-    const size_t own = (size_t)ch * M + l;
+    const size_t own = (size_t)ch * (Q * M) + l;
     static_for<0, Q>([&](auto P) {
       R acc = R(0);
 #pragma unroll
       for (int a = 0; a < NC; ++a) acc += wgt[a] * rc[P * M + corner[a]];
-      fout[(size_t)P * stride + own] = S::template save<D, Q, P>(acc);
+      fout[own + (size_t)P * M] = S::template save<D, Q, P>(acc);
     });
   }
 }
@@ -517,8 +517,7 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, D
   bool solid_cell = false;
   if constexpr (SOLID) solid_cell = (s_sm[slot][CENTER] >> l) & 1ull;   // not advanced
   const int b = s_nb[slot][CENTER];
-  const size_t stride = prm.stride;
-  const size_t own = (size_t)b * M + l;
+  const size_t own = (size_t)b * (Q * M) + l;
   const int32_t* nb = s_nb[slot];
   if (XCHG && active && c0 >= 0) {
     // an exchanging parent (a refined block has every same-level neighbour,
@@ -526,11 +525,11 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, D
     if (solid_cell) {
       static_for<0, Q>([&](auto P) { s_rc[slot][P * M + l] = R(VS<D, Q>::w[P]); });
     } else if (flags & BF_OUTLET) {
-      step_cell_parent<D, Q, T, SOLID, true>(gin, gout, stride, own, l, nb,
+      step_cell_parent<D, Q, T, SOLID, true>(gin, gout, own, l, nb,
                                              SOLID ? s_sm[slot] : nullptr, flags, prm.omega,
                                              prm.faces, ex.r_cf, s_rc[slot]);
     } else {
-      step_cell_parent<D, Q, T, SOLID, false>(gin, gout, stride, own, l, nb,
+      step_cell_parent<D, Q, T, SOLID, false>(gin, gout, own, l, nb,
                                               SOLID ? s_sm[slot] : nullptr, flags, prm.omega,
                                               prm.faces, ex.r_cf, s_rc[slot]);
     }
@@ -546,21 +545,21 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, D
         } else {
           const int e = link_entry<D, Q, p>(g_src_geo<D, Q>, l);
           f[p] = S::template load<D, Q, p>(
-              gin[(size_t)p * stride + (size_t)nb[e & 31] * M + (e >> 5)]);
+              gin[(size_t)nb[e & 31] * (Q * M) + (size_t)p * M + (e >> 5)]);
         }
       });
       R ux, uy, uz, usq15;
       bgk<D, Q>(f, R(prm.omega), ux, uy, uz, usq15);
       static_for<0, Q>([&](auto P) {
-        gout[(size_t)P * stride + own] = S::template save<D, Q, P>(f[P]);
+        gout[own + (size_t)P * M] = S::template save<D, Q, P>(f[P]);
       });
     } else {
       if (flags & BF_OUTLET)
-        step_cell_checked<D, Q, T, SOLID, true, GHOST_IN>(gin, gout, stride, own, l, nb,
+        step_cell_checked<D, Q, T, SOLID, true, GHOST_IN>(gin, gout, own, l, nb,
                                                           SOLID ? s_sm[slot] : nullptr, flags,
                                                           prm.omega, prm.faces, ghost_in);
       else
-        step_cell_checked<D, Q, T, SOLID, false, GHOST_IN>(gin, gout, stride, own, l, nb,
+        step_cell_checked<D, Q, T, SOLID, false, GHOST_IN>(gin, gout, own, l, nb,
                                                            SOLID ? s_sm[slot] : nullptr, flags,
                                                            prm.omega, prm.faces, ghost_in);
     }
@@ -568,7 +567,7 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, D
   if constexpr (XCHG) {
     __syncthreads();
     if (active && c0 >= 0)
-      interp_out<D, Q, T>(s_rc[slot], l, c0, s_cm[slot], (T*)ex.fine_out, stride, solidmask);
+      interp_out<D, Q, T>(s_rc[slot], l, c0, s_cm[slot], (T*)ex.fine_out, solidmask);
   }
 }
 

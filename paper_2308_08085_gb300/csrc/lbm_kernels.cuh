@@ -1,8 +1,8 @@
 // Templated LBM kernels of the block forest.  Included once per velocity-set
 // translation unit, which instantiates them through AMR_LBM_OPS.
 //
-// Population layout (every storage type): g[p * stride + b * M + l], stride =
-// capacity * M, M = 4^D cells per block, l = i + 4 j + 16 k.  Two buffers A/B
+// Population layout (every storage type): block-major, g[b * Q M + p * M + l],
+// M = 4^D cells per block, l = i + 4 j + 16 k (collide_stream.cuh).  Two buffers A/B
 // are used per level in ping-pong; a level's current buffer is bit L of `cur`.
 // The stored values are the outgoing post-collision populations; every kernel
 // reads a cell's pre-collision populations with gather_cell and writes them
@@ -31,13 +31,13 @@ __device__ __forceinline__ void stage_row(int32_t* dst, const int32_t* __restric
 
 template <int D, int Q, class T, bool SOLID, bool COH = false>
 __device__ __forceinline__ void interp_stage(typename Store<T>::R (*sF)[Block<D>::M],
-                                             const T* __restrict__ fpar, size_t stride, int P,
+                                             const T* __restrict__ fpar, int P,
                                              int l, double ratio, const int32_t* prow,
                                              const uint64_t* __restrict__ solidmask) {
   using S = Store<T>;
   using R = typename S::R;
   R f[Q];
-  gather_cell<D, Q, T, SOLID, COH>(f, fpar, stride, P, l, prow, solidmask);
+  gather_cell<D, Q, T, SOLID, COH>(f, fpar, P, l, prow, solidmask);
   R rho, ux, uy, uz;
   moments<D, Q>(f, rho, ux, uy, uz);
   const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
@@ -54,15 +54,16 @@ __device__ __forceinline__ void interp_stage(typename Store<T>::R (*sF)[Block<D>
 // rest state.
 template <int D, int Q, class T, bool SOLID>
 __device__ __forceinline__ void store_child_cell(typename Store<T>::R (&v)[Q], T* __restrict__ fch,
-                                                 size_t stride, int ch, int l, const int32_t* row,
+                                                 int ch, int l, const int32_t* row,
                                                  const uint64_t* __restrict__ solidmask,
                                                  const int32_t* __restrict__ parent,
                                                  const int8_t* __restrict__ marks, int mode_all) {
   using S = Store<T>;
   using R = typename S::R;
+  constexpr int M = Block<D>::M;
   if (mode_all & 4) {   // the level step: as they are, into the child's own slots
-    const size_t own = (size_t)ch * Block<D>::M + l;
-    static_for<0, Q>([&](auto Pp) { fch[(size_t)Pp * stride + own] = S::template save<D, Q, Pp>(v[Pp]); });
+    const size_t own = (size_t)ch * (Q * M) + l;
+    static_for<0, Q>([&](auto Pp) { fch[own + (size_t)Pp * M] = S::template save<D, Q, Pp>(v[Pp]); });
     return;
   }
   if (mode_all & 1) {
@@ -70,16 +71,15 @@ __device__ __forceinline__ void store_child_cell(typename Store<T>::R (&v)[Q], T
       const int pp = __ldg(parent + blk);
       return pp >= 0 && __ldg(marks + pp) > 0;
     };
-    scatter_cell<D, Q, T, SOLID, true>(v, fch, stride, ch, l, row, solidmask, is_new);
+    scatter_cell<D, Q, T, SOLID, true>(v, fch, ch, l, row, solidmask, is_new);
   } else {
-    scatter_cell<D, Q, T, SOLID>(v, fch, stride, ch, l, row, solidmask);
+    scatter_cell<D, Q, T, SOLID>(v, fch, ch, l, row, solidmask);
   }
 }
 
 template <int D, int Q, class T, bool SOLID>
 __device__ __forceinline__ void interp_children(const typename Store<T>::R (*sF)[Block<D>::M],
-                                                int l, T* __restrict__ fch, size_t stride,
-                                                int c0, const uint64_t* __restrict__ cellmask,
+                                                int l, T* __restrict__ fch, int c0, const uint64_t* __restrict__ cellmask,
                                                 const int32_t (*crow)[Nbr<D>::K],
                                                 const uint64_t* __restrict__ solidmask,
                                                 const int32_t* __restrict__ parent,
@@ -124,7 +124,7 @@ __device__ __forceinline__ void interp_children(const typename Store<T>::R (*sF)
         v[Pp] = acc;
       });
     }
-    store_child_cell<D, Q, T, SOLID>(v, fch, stride, ch, l, crow[c], solidmask, parent, marks,
+    store_child_cell<D, Q, T, SOLID>(v, fch, ch, l, crow[c], solidmask, parent, marks,
                                      mode_all);
   }
 }
@@ -132,7 +132,7 @@ __device__ __forceinline__ void interp_children(const typename Store<T>::R (*sF)
 template <int D, int Q, class T, bool SOLID>
 __global__ void __launch_bounds__(128, 8)
     k_interp(const int32_t* __restrict__ list, int n, const T* __restrict__ fpar,
-             T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
+             T* __restrict__ fch, const int32_t* __restrict__ child0,
              const uint64_t* __restrict__ cellmask, const int32_t* __restrict__ nbr,
              const uint64_t* __restrict__ solidmask, const int32_t* __restrict__ parent,
              const int8_t* __restrict__ marks, double ratio, int mode_all) {
@@ -152,11 +152,11 @@ __global__ void __launch_bounds__(128, 8)
   for (int r = 0; r <= NC; ++r)
     stage_row<D>(s_row[slot][r], nbr, valid ? (r == 0 ? P : c0 + r - 1) : NONE, l, M);
   __syncthreads();
-  if (valid) interp_stage<D, Q, T, SOLID>(sF[slot], fpar, stride, P, l, ratio, s_row[slot][0],
+  if (valid) interp_stage<D, Q, T, SOLID>(sF[slot], fpar, P, l, ratio, s_row[slot][0],
                                           solidmask);
   __syncthreads();
   if (!valid) return;
-  interp_children<D, Q, T, SOLID>(sF[slot], l, fch, stride, c0, cellmask, s_row[slot] + 1,
+  interp_children<D, Q, T, SOLID>(sF[slot], l, fch, c0, cellmask, s_row[slot] + 1,
                                   solidmask, parent, marks, mode_all);
 }
 
@@ -192,7 +192,7 @@ static __constant__ CubicW c_cubic_w = make_cubic_w();
 template <int D, int Q, class T, bool SOLID>
 __global__ void __launch_bounds__(64)
     k_interp_cubic(const int32_t* __restrict__ list, int n, const T* __restrict__ fpar,
-                   T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
+                   T* __restrict__ fch, const int32_t* __restrict__ child0,
                    const uint64_t* __restrict__ cellmask, const int32_t* __restrict__ nbr,
                    const uint64_t* __restrict__ solidmask, const int32_t* __restrict__ parent,
                    const int8_t* __restrict__ marks, double ratio, int mode_all) {
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(64)
   for (int r = 0; r <= NC; ++r)
     stage_row<D>(s_row[slot][r], nbr, valid ? (r == 0 ? P : c0 + r - 1) : NONE, l, M);
   __syncthreads();
-  if (valid) interp_stage<D, Q, T, SOLID>(sF[slot], fpar, stride, P, l, ratio, s_row[slot][0],
+  if (valid) interp_stage<D, Q, T, SOLID>(sF[slot], fpar, P, l, ratio, s_row[slot][0],
                                           solidmask);
   __syncthreads();
   for (int c = 0; c < NC; ++c) {
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(64)
       }
       // solid cells: the rest state for new children, untouched otherwise
       if (!solid_cell || (mode_all & 1))
-        store_child_cell<D, Q, T, SOLID>(v, fch, stride, ch, l, s_row[slot][1 + c], solidmask,
+        store_child_cell<D, Q, T, SOLID>(v, fch, ch, l, s_row[slot][1 + c], solidmask,
                                          parent, marks, mode_all);
     }
     (void)cz;
@@ -302,8 +302,7 @@ template <int D, int Q, class T, bool SOLID, bool COH = false>
 __device__ __forceinline__ void average_child(typename Store<T>::R (*sR)[Block<D>::M],
                                               bool valid, int P, int c, int ch,
                                               int l, T* __restrict__ fpar,
-                                              const T* __restrict__ fch, size_t stride,
-                                              const uint64_t* __restrict__ cellmask,
+                                              const T* __restrict__ fch, const uint64_t* __restrict__ cellmask,
                                               const int32_t* crow, const int32_t* prow,
                                               const uint64_t* __restrict__ solidmask,
                                               double ratio, int mode_sync) {
@@ -324,7 +323,7 @@ __device__ __forceinline__ void average_child(typename Store<T>::R (*sR)[Block<D
   };
   if (valid && taken(g)) {
     R f[Q];
-    gather_cell<D, Q, T, SOLID, COH>(f, fch, stride, ch, l, crow, solidmask);
+    gather_cell<D, Q, T, SOLID, COH>(f, fch, ch, l, crow, solidmask);
     R rho, ux, uy, uz;
     moments<D, Q>(f, rho, ux, uy, uz);
     const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
@@ -347,7 +346,7 @@ __device__ __forceinline__ void average_child(typename Store<T>::R (*sR)[Block<D
       for (int s = 0; s < NC; ++s) a += sR[Pp][f0 + Block<D>::cell(s & 1, (s >> 1) & 1, (s >> 2) & 1)];
       acc[Pp] = a * inv;
     });
-    scatter_cell<D, Q, T, SOLID>(acc, fpar, stride, P, parent_cell(l), prow, solidmask);
+    scatter_cell<D, Q, T, SOLID>(acc, fpar, P, parent_cell(l), prow, solidmask);
   }
 }
 
@@ -358,8 +357,7 @@ __device__ __forceinline__ void average_child(typename Store<T>::R (*sR)[Block<D
 template <int D, int Q, class T, bool SOLID>
 __global__ void __launch_bounds__(128)
     k_average(const int32_t* __restrict__ list, int64_t n_items, bool by_parent,
-              T* __restrict__ fpar, const T* __restrict__ fch, size_t stride,
-              const int32_t* __restrict__ child0, const int32_t* __restrict__ parent,
+              T* __restrict__ fpar, const T* __restrict__ fch, const int32_t* __restrict__ child0, const int32_t* __restrict__ parent,
               const uint64_t* __restrict__ cellmask, const int32_t* __restrict__ status,
               const int32_t* __restrict__ nbr, const uint64_t* __restrict__ solidmask,
               double ratio, int mode_sync) {
@@ -391,8 +389,7 @@ __global__ void __launch_bounds__(128)
   stage_row<D>(s_row[slot][0], nbr, valid ? ch : NONE, l, M);
   stage_row<D>(s_row[slot][1], nbr, valid ? P : NONE, l, M);
   __syncthreads();
-  average_child<D, Q, T, SOLID>(sR[slot], valid, P, c, ch, l, fpar, fch, stride,
-                                cellmask, s_row[slot][0], s_row[slot][1], solidmask, ratio,
+  average_child<D, Q, T, SOLID>(sR[slot], valid, P, c, ch, l, fpar, fch, cellmask, s_row[slot][0], s_row[slot][1], solidmask, ratio,
                                 mode_sync);
 }
 
@@ -408,7 +405,7 @@ __global__ void __launch_bounds__(128)
 template <int D, int Q, class T, bool SOLID>
 __global__ void __launch_bounds__(128, 8)
     k_average_groups(const int32_t* __restrict__ items, int n, T* __restrict__ fpar,
-                     const T* __restrict__ fch, size_t stride, const int32_t* __restrict__ child0,
+                     const T* __restrict__ fch, const int32_t* __restrict__ child0,
                      const int32_t* __restrict__ parent, const int32_t* __restrict__ nbr,
                      const uint64_t* __restrict__ solidmask, double ratio) {
   using S = Store<T>;
@@ -434,7 +431,7 @@ __global__ void __launch_bounds__(128, 8)
   for (int p = 0; p < QP; ++p) v[p] = R(0);
   if (valid) {
     R f[Q];
-    gather_cell<D, Q, T, SOLID>(f, fch, stride, ch, l, nbr + (size_t)ch * NBR_STRIDE, solidmask);
+    gather_cell<D, Q, T, SOLID>(f, fch, ch, l, nbr + (size_t)ch * NBR_STRIDE, solidmask);
     R rho, ux, uy, uz;
     moments<D, Q>(f, rho, ux, uy, uz);
     const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
@@ -468,7 +465,7 @@ __global__ void __launch_bounds__(128, 8)
   for (int j = 0; j < PER; ++j) {
     const int p = base + j;
     if (p < Q)
-      fpar[src_slot<D, Q>(p, P, pc, stride, prow, SOLID ? solidmask : nullptr)] =
+      fpar[src_slot<D, Q>(p, P, pc, prow, SOLID ? solidmask : nullptr)] =
           save_rt<D, Q, T>(v[j] * inv, p);
   }
 }
@@ -523,8 +520,7 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS>()
   const int b = s_nb[slot][CENTER];
   const T* __restrict__ gin = (const T*)d.f[which_in];
   T* __restrict__ gout = (T*)d.f[which_in ^ 1];
-  const size_t stride = d.stride;
-  const size_t own = (size_t)b * M + l;
+  const size_t own = (size_t)b * (Q * M) + l;
   const int32_t* nb = s_nb[slot];
   if (flags == 0) {
     R f[Q];
@@ -535,20 +531,20 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS>()
       } else {
         const int e = link_entry<D, Q, p>(g_src_geo<D, Q>, l);
         f[p] = S::template load<D, Q, p>(
-            gin[(size_t)p * stride + (size_t)nb[e & 31] * M + (e >> 5)]);
+            gin[(size_t)nb[e & 31] * (Q * M) + (size_t)p * M + (e >> 5)]);
       }
     });
     R ux, uy, uz, usq15;
     bgk<D, Q>(f, R(d.omega[level]), ux, uy, uz, usq15);
     static_for<0, Q>([&](auto P) {
-      gout[(size_t)P * stride + own] = S::template save<D, Q, P>(f[P]);
+      gout[own + (size_t)P * M] = S::template save<D, Q, P>(f[P]);
     });
   } else {
     if (flags & BF_OUTLET)
-      step_cell_checked<D, Q, T, false, true>(gin, gout, stride, own, l, nb, nullptr, flags,
+      step_cell_checked<D, Q, T, false, true>(gin, gout, own, l, nb, nullptr, flags,
                                               d.omega[level], d.faces, false);
     else
-      step_cell_checked<D, Q, T, false, false>(gin, gout, stride, own, l, nb, nullptr, flags,
+      step_cell_checked<D, Q, T, false, false>(gin, gout, own, l, nb, nullptr, flags,
                                                d.omega[level], d.faces, false);
   }
 }
@@ -580,11 +576,11 @@ __global__ void __launch_bounds__(128, 5)
     stage_row<D>(s_row[slot][r], d.nbr, valid ? (r == 0 ? P : c0 + r - 1) : NONE, l, M);
   __syncthreads();
   if (valid)
-    interp_stage<D, Q, T, false>(sF[slot], (const T*)d.f[which_par], d.stride, P, l,
+    interp_stage<D, Q, T, false>(sF[slot], (const T*)d.f[which_par], P, l,
                                  d.r_cf[level], s_row[slot][0], nullptr);
   __syncthreads();
   if (!valid) return;
-  interp_children<D, Q, T, false>(sF[slot], l, (T*)d.f[which_ch], d.stride, c0, d.cellmask,
+  interp_children<D, Q, T, false>(sF[slot], l, (T*)d.f[which_ch], c0, d.cellmask,
                                   s_row[slot] + 1, nullptr, nullptr, nullptr, 0);
 }
 
@@ -618,7 +614,7 @@ __global__ void __launch_bounds__(128)
   stage_row<D>(s_row[slot][1], d.nbr, valid ? P : NONE, l, M);
   __syncthreads();
   average_child<D, Q, T, false>(sR[slot], valid, P, c, ch, l, (T*)d.f[which_par],
-                                (const T*)d.f[which_ch], d.stride, d.cellmask, s_row[slot][0],
+                                (const T*)d.f[which_ch], d.cellmask, s_row[slot][0],
                                 s_row[slot][1], nullptr, d.r_fc[level], 0);
 }
 
@@ -677,12 +673,11 @@ __device__ __forceinline__ void persist_collide(const InstDesc& d, const uint32_
   __syncthreads();
   const T* gin = (const T*)d.f[which_in];
   T* gout = (T*)d.f[which_in ^ 1];
-  const size_t stride = d.stride;
   const double omega = d.omega[level];
   for (int c = threadIdx.x; c < nblk * M; c += THREADS) {
     const int s = c / M, l = c - s * M;
     const int32_t* nb = s_nb[s];
-    const size_t own = (size_t)nb[CENTER] * M + l;
+    const size_t own = (size_t)nb[CENTER] * (Q * M) + l;
     const int flags = s_flags[s];
     if (flags == 0) {
       R f[Q];
@@ -693,19 +688,19 @@ __device__ __forceinline__ void persist_collide(const InstDesc& d, const uint32_
         } else {
           const int e = link_entry<D, Q, p>(g_src_geo<D, Q>, l);
           f[p] = S::template load<D, Q, p>(
-              __ldcg(gin + (size_t)p * stride + (size_t)nb[e & 31] * M + (e >> 5)));
+              __ldcg(gin + (size_t)nb[e & 31] * (Q * M) + (size_t)p * M + (e >> 5)));
         }
       });
       R ux, uy, uz, usq15;
       bgk<D, Q>(f, R(omega), ux, uy, uz, usq15);
       static_for<0, Q>([&](auto P) {
-        gout[(size_t)P * stride + own] = S::template save<D, Q, P>(f[P]);
+        gout[own + (size_t)P * M] = S::template save<D, Q, P>(f[P]);
       });
     } else if (flags & BF_OUTLET) {
-      step_cell_checked<D, Q, T, false, true, false, true>(gin, gout, stride, own, l, nb, nullptr,
+      step_cell_checked<D, Q, T, false, true, false, true>(gin, gout, own, l, nb, nullptr,
                                                            flags, omega, d.faces, false);
     } else {
-      step_cell_checked<D, Q, T, false, false, false, true>(gin, gout, stride, own, l, nb,
+      step_cell_checked<D, Q, T, false, false, false, true>(gin, gout, own, l, nb,
                                                             nullptr, flags, omega, d.faces, false);
     }
   }
@@ -734,11 +729,11 @@ __device__ __noinline__ void persist_interp(const InstDesc& d, const uint32_t* i
     stage_row<D>(s_rows[slot][rr], d.nbr, valid ? (rr == 0 ? P : c0 + rr - 1) : NONE, l, M);
   __syncthreads();
   if (valid)
-    interp_stage<D, Q, T, false, true>(sF[slot], (const T*)d.f[win], d.stride, P, l,
+    interp_stage<D, Q, T, false, true>(sF[slot], (const T*)d.f[win], P, l,
                                        d.r_cf[level], s_rows[slot][0], nullptr);
   __syncthreads();
   if (valid)
-    interp_children<D, Q, T, false>(sF[slot], l, (T*)d.f[wch], d.stride, c0, d.cellmask,
+    interp_children<D, Q, T, false>(sF[slot], l, (T*)d.f[wch], c0, d.cellmask,
                                     s_rows[slot] + 1, nullptr, nullptr, nullptr, 0);
 }
 
@@ -765,7 +760,7 @@ __device__ __noinline__ void persist_average(const InstDesc& d, const uint32_t* 
   stage_row<D>(s_rows[slot][1], d.nbr, valid ? P : NONE, l, M);
   __syncthreads();
   average_child<D, Q, T, false, true>(sF[slot], valid, P, c, ch, l, (T*)d.f[win],
-                                      (const T*)d.f[wch], d.stride, d.cellmask, s_rows[slot][0],
+                                      (const T*)d.f[wch], d.cellmask, s_rows[slot][0],
                                       s_rows[slot][1], nullptr, d.r_fc[level], 0);
 }
 
@@ -878,8 +873,7 @@ constexpr size_t persist_smem_bytes() {
 // L_des > L, -1 for a REFINED block with L_des <= L.
 template <int D, int Q, class T>
 __global__ void __launch_bounds__(128)
-    k_criterion(const int32_t* __restrict__ list, int n, const T* __restrict__ f, size_t stride,
-                const int32_t* __restrict__ nbr, const uint64_t* __restrict__ solidmask,
+    k_criterion(const int32_t* __restrict__ list, int n, const T* __restrict__ f, const int32_t* __restrict__ nbr, const uint64_t* __restrict__ solidmask,
                 const int32_t* __restrict__ status, int level, int lmax, double inv_dx,
                 int n_start, int n_inc, int8_t* __restrict__ marks, double* __restrict__ w2out) {
   using S = Store<T>;
@@ -896,7 +890,7 @@ __global__ void __launch_bounds__(128)
   if (valid) {
     b = list[bi];
     R fl[Q];
-    gather_cell<D, Q, T, true>(fl, f, stride, b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
+    gather_cell<D, Q, T, true>(fl, f, b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
     R rho, ux, uy, uz;
     moments<D, Q>(fl, rho, ux, uy, uz);
     su[slot][0][l] = ux;
@@ -965,8 +959,7 @@ __device__ __forceinline__ float squash(float x) { return copysignf(log1pf(fabsf
 
 template <int Q, class T>
 __global__ void __launch_bounds__(128)
-    k_features(const int32_t* __restrict__ list, int n, const T* __restrict__ f, size_t stride,
-               const int32_t* __restrict__ nbr, const uint64_t* __restrict__ solidmask,
+    k_features(const int32_t* __restrict__ list, int n, const T* __restrict__ f, const int32_t* __restrict__ nbr, const uint64_t* __restrict__ solidmask,
                int level, int lmax, double inv_dx, float* __restrict__ out) {
   using S = Store<T>;
   using R = typename S::R;
@@ -981,7 +974,7 @@ __global__ void __launch_bounds__(128)
   if (valid) {
     b = list[bi];
     R fl[Q];
-    gather_cell<D, Q, T, true>(fl, f, stride, b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
+    gather_cell<D, Q, T, true>(fl, f, b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
     R rho, ux, uy, uz;
     moments<D, Q>(fl, rho, ux, uy, uz);
     su[slot][0][l] = (float)ux;
@@ -1078,10 +1071,9 @@ __global__ void k_export_f(int64_t cap, int64_t b0, int64_t nb, const T* __restr
     for (int p = 0; p < Q; ++p) out[(size_t)p * nb * M + g] = 0.0;
     return;
   }
-  const size_t stride = (size_t)cap * M;
   const T* f = ((cur >> L) & 1u) ? fb : fa;
   R fl[Q];
-  gather_cell<D, Q, T, true>(fl, f, stride, (int)b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
+  gather_cell<D, Q, T, true>(fl, f, (int)b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
   static_for<0, Q>([&](auto P) { out[(size_t)P * nb * M + g] = (double)fl[P]; });
 }
 
@@ -1098,11 +1090,10 @@ __global__ void k_import_f(int64_t cap, int64_t b0, int64_t nb, T* __restrict__ 
   const int l = (int)(g % M);
   const int L = level[b];
   if (L < 0) return;
-  const size_t stride = (size_t)cap * M;
   T* f = ((cur >> L) & 1u) ? fb : fa;
   R v[Q];
   static_for<0, Q>([&](auto P) { v[P] = (R)in[(size_t)P * nb * M + g]; });
-  scatter_cell<D, Q, T, true>(v, f, stride, (int)b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
+  scatter_cell<D, Q, T, true>(v, f, (int)b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
 }
 
 template <int D, int Q, class T>
@@ -1123,10 +1114,9 @@ __global__ void k_export_rho_u(int64_t cap, int64_t b0, int64_t nb, const T* __r
     for (int a = 0; a <= D; ++a) o[a] = 0.0;
     return;
   }
-  const size_t stride = (size_t)cap * M;
   const T* f = ((cur >> L) & 1u) ? fb : fa;
   R fl[Q];
-  gather_cell<D, Q, T, true>(fl, f, stride, (int)b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
+  gather_cell<D, Q, T, true>(fl, f, (int)b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
   R rho, ux, uy, uz;
   moments<D, Q>(fl, rho, ux, uy, uz);
   o[0] = rho;
@@ -1142,10 +1132,10 @@ __global__ void k_init_rest(int64_t cap, T* __restrict__ f) {
   constexpr int M = Block<D>::M;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= cap * M) return;
-  const size_t stride = (size_t)cap * M;
+  const size_t own = (size_t)(g / M) * (Q * M) + (size_t)(g % M);
   static_for<0, Q>([&](auto P) {
     constexpr double wp = VS<D, Q>::w[P];
-    f[(size_t)P * stride + g] = Store<T>::template save<D, Q, P>(R(wp));
+    f[own + (size_t)P * M] = Store<T>::template save<D, Q, P>(R(wp));
   });
 }
 
@@ -1162,7 +1152,7 @@ __global__ void k_coarsen_fixup(const int32_t* __restrict__ list, int n,
                                 const int32_t* __restrict__ nbr,
                                 const uint64_t* __restrict__ solidmask,
                                 const int32_t* __restrict__ level, T* __restrict__ fa,
-                                T* __restrict__ fb, unsigned cur, size_t stride) {
+                                T* __restrict__ fb, unsigned cur) {
   constexpr int M = Block<D>::M, NC = Block<D>::NC;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)n * NC * M) return;
@@ -1183,7 +1173,7 @@ __global__ void k_coarsen_fixup(const int32_t* __restrict__ list, int n,
     const int py = parent[y];
     if (py >= 0 && marks[py] == -1) return;       // removed as well
     if (solidmask && ((solidmask[y] >> tl) & 1ull)) return;
-    g[(size_t)pb * stride + (size_t)y * M + tl] = g[(size_t)p * stride + (size_t)x * M + l];
+    g[(size_t)y * (Q * M) + (size_t)pb * M + tl] = g[(size_t)x * (Q * M) + (size_t)p * M + l];
   });
 }
 
@@ -1208,7 +1198,7 @@ __device__ __forceinline__ void block_sum_store(double (&v)[NV], double* out) {
   }
 }
 
-// FP64 audit of mass and momentum over leaf cells (grid-stride, fixed grid).
+// FP64 audit of mass and momentum over leaf cells (grid-fixed grid).
 template <int D, int Q, class T>
 __global__ void __launch_bounds__(256)
     k_mass_partial(int64_t cap, const T* __restrict__ fa, const T* __restrict__ fb, unsigned cur,
@@ -1217,7 +1207,6 @@ __global__ void __launch_bounds__(256)
                    double* __restrict__ partial) {
   using R = typename Store<T>::R;
   constexpr int M = Block<D>::M;
-  const size_t stride = (size_t)cap * M;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < cap * M;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -1226,7 +1215,7 @@ __global__ void __launch_bounds__(256)
     const int L = level[b];
     const T* f = ((cur >> L) & 1u) ? fb : fa;
     R fl[Q];
-    gather_cell<D, Q, T, true>(fl, f, stride, (int)b, (int)(g % M),
+    gather_cell<D, Q, T, true>(fl, f, (int)b, (int)(g % M),
                                nbr + (size_t)b * NBR_STRIDE, solidmask);
     double r = 0, jx = 0, jy = 0, jz = 0;
     static_for<0, Q>([&](auto P) {
@@ -1252,7 +1241,7 @@ __global__ void __launch_bounds__(256)
 template <int D, int Q, class T>
 __global__ void __launch_bounds__(256)
     k_force_partial(const int32_t* __restrict__ list, int n, const T* __restrict__ f,
-                    size_t stride, const int32_t* __restrict__ nbr,
+                    const int32_t* __restrict__ nbr,
                     const int32_t* __restrict__ status, const uint64_t* __restrict__ solidmask,
                     double omega, double dx, double* __restrict__ partial) {
   using V = VS<D, Q>;
@@ -1269,7 +1258,7 @@ __global__ void __launch_bounds__(256)
     if (status[b] != ST_UNREFINED) continue;
     if ((solidmask[b] >> l) & 1ull) continue;
     R fl[Q];
-    gather_cell<D, Q, T, true>(fl, f, stride, b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
+    gather_cell<D, Q, T, true>(fl, f, b, l, nbr + (size_t)b * NBR_STRIDE, solidmask);
     R rho, ux, uy, uz;
     moments<D, Q>(fl, rho, ux, uy, uz);
     const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
@@ -1372,7 +1361,7 @@ struct Launch {
   }
 
   static void interp(cudaStream_t s, const int32_t* list, int n, const void* fpar, void* fch,
-                     size_t stride, const int32_t* child0, const uint64_t* nm,
+                     const int32_t* child0, const uint64_t* nm,
                      const int32_t* nbr, const uint64_t* sm, const int32_t* parent,
                      const int8_t* marks, double ratio, int mode_all, bool solid) {
     if (n <= 0) return;
@@ -1383,25 +1372,23 @@ struct Launch {
       const int grid = grid_for(n, 64 / M);
       if (solid)
         k_interp_cubic<D, Q, T, true><<<grid, 64, 0, s>>>(list, n, (const T*)fpar, (T*)fch,
-                                                         stride, child0, nm, nbr, sm, parent,
+                                                         child0, nm, nbr, sm, parent,
                                                          marks, ratio, all);
       else
         k_interp_cubic<D, Q, T, false><<<grid, 64, 0, s>>>(list, n, (const T*)fpar, (T*)fch,
-                                                          stride, child0, nm, nbr, nullptr,
+                                                          child0, nm, nbr, nullptr,
                                                           parent, marks, ratio, all);
       return;
     }
     const int grid = grid_for(n, 128 / M);
     if (solid)
-      k_interp<D, Q, T, true><<<grid, 128, 0, s>>>(list, n, (const T*)fpar, (T*)fch, stride,
-                                                  child0, nm, nbr, sm, parent, marks, ratio, all);
+      k_interp<D, Q, T, true><<<grid, 128, 0, s>>>(list, n, (const T*)fpar, (T*)fch, child0, nm, nbr, sm, parent, marks, ratio, all);
     else
-      k_interp<D, Q, T, false><<<grid, 128, 0, s>>>(list, n, (const T*)fpar, (T*)fch, stride,
-                                                   child0, nm, nbr, nullptr, parent, marks, ratio,
+      k_interp<D, Q, T, false><<<grid, 128, 0, s>>>(list, n, (const T*)fpar, (T*)fch, child0, nm, nbr, nullptr, parent, marks, ratio,
                                                    all);
   }
   static void average(cudaStream_t s, const int32_t* list, int n, bool by_parent, void* fpar,
-                      const void* fch, size_t stride, const int32_t* child0,
+                      const void* fch, const int32_t* child0,
                       const int32_t* parent, const uint64_t* nm, const int32_t* status,
                       const int32_t* nbr, const uint64_t* sm, double ratio, int mode_sync,
                       bool solid) {
@@ -1410,19 +1397,18 @@ struct Launch {
     const int grid = (int)((items + 128 / M - 1) / (128 / M));
     if (solid)
       k_average<D, Q, T, true><<<grid, 128, 0, s>>>(list, items, by_parent, (T*)fpar,
-                                                   (const T*)fch, stride, child0, parent, nm,
+                                                   (const T*)fch, child0, parent, nm,
                                                    status, nbr, sm, ratio, mode_sync);
     else
       k_average<D, Q, T, false><<<grid, 128, 0, s>>>(list, items, by_parent, (T*)fpar,
-                                                    (const T*)fch, stride, child0, parent, nm,
+                                                    (const T*)fch, child0, parent, nm,
                                                     status, nbr, nullptr, ratio, mode_sync);
   }
-  static void criterion(cudaStream_t s, const int32_t* list, int n, const void* f, size_t stride,
-                        const int32_t* nbr, const uint64_t* sm, const int32_t* status, int level,
+  static void criterion(cudaStream_t s, const int32_t* list, int n, const void* f, const int32_t* nbr, const uint64_t* sm, const int32_t* status, int level,
                         int lmax, double inv_dx, int ns, int ni, int8_t* marks, double* w2out) {
     if (n <= 0) return;
     k_criterion<D, Q, T><<<grid_for(n, 128 / M), 128, 0, s>>>(
-        list, n, (const T*)f, stride, nbr, sm, status, level, lmax, inv_dx, ns, ni, marks, w2out);
+        list, n, (const T*)f, nbr, sm, status, level, lmax, inv_dx, ns, ni, marks, w2out);
   }
   static void export_f(cudaStream_t s, int64_t cap, int64_t b0, int64_t nb, const void* fa,
                        const void* fb, unsigned cur, const int32_t* level, const int32_t* nbr,
@@ -1454,30 +1440,29 @@ struct Launch {
     return grid;
   }
   static int force_partial(cudaStream_t s, const int32_t* list, int n, const void* f,
-                           size_t stride, const int32_t* nbr, const int32_t* status,
+                           const int32_t* nbr, const int32_t* status,
                            const uint64_t* sm, double omega, double dx, double* partial) {
     const int grid = 152 * 2;
-    k_force_partial<D, Q, T><<<grid, 256, 0, s>>>(list, n, (const T*)f, stride, nbr, status, sm,
+    k_force_partial<D, Q, T><<<grid, 256, 0, s>>>(list, n, (const T*)f, nbr, status, sm,
                                                   omega, dx, partial);
     return grid;
   }
-  static void features(cudaStream_t s, const int32_t* list, int n, const void* f, size_t stride,
-                       const int32_t* nbr, const uint64_t* sm, int level, int lmax,
+  static void features(cudaStream_t s, const int32_t* list, int n, const void* f, const int32_t* nbr, const uint64_t* sm, int level, int lmax,
                        double inv_dx, float* out) {
     if constexpr (D == 3) {
       if (n > 0)
-        k_features<Q, T><<<grid_for(n, 2), 128, 0, s>>>(list, n, (const T*)f, stride, nbr, sm,
+        k_features<Q, T><<<grid_for(n, 2), 128, 0, s>>>(list, n, (const T*)f, nbr, sm,
                                                         level, lmax, inv_dx, out);
     }
   }
   static void coarsen_fixup(cudaStream_t s, const int32_t* list, int n, const int32_t* child0,
                             const int32_t* parent, const int8_t* marks, const int32_t* nbr,
                             const uint64_t* sm, const int32_t* level, void* fa, void* fb,
-                            unsigned cur, size_t stride) {
+                            unsigned cur) {
     if (n <= 0) return;
     const int64_t threads = (int64_t)n * Block<D>::NC * M;
     k_coarsen_fixup<D, Q, T><<<(int)((threads + 255) / 256), 256, 0, s>>>(
-        list, n, child0, parent, marks, nbr, sm, level, (T*)fa, (T*)fb, cur, stride);
+        list, n, child0, parent, marks, nbr, sm, level, (T*)fa, (T*)fb, cur);
   }
 
   static void collide_stream_batch(cudaStream_t s, const uint32_t* items, int n,
@@ -1518,18 +1503,18 @@ struct Launch {
   }
 
   static void average_groups(cudaStream_t s, const int32_t* items, int n, void* fpar,
-                             const void* fch, size_t stride, const int32_t* child0,
+                             const void* fch, const int32_t* child0,
                              const int32_t* parent, const int32_t* nbr, const uint64_t* sm,
                              double ratio, bool solid) {
     if (n <= 0) return;
     const int grid = (int)(((int64_t)n * Block<D>::NC + 127) / 128);
     if (solid)
       k_average_groups<D, Q, T, true><<<grid, 128, 0, s>>>(items, n, (T*)fpar, (const T*)fch,
-                                                           stride, child0, parent, nbr, sm,
+                                                           child0, parent, nbr, sm,
                                                            ratio);
     else
       k_average_groups<D, Q, T, false><<<grid, 128, 0, s>>>(items, n, (T*)fpar, (const T*)fch,
-                                                            stride, child0, parent, nbr,
+                                                            child0, parent, nbr,
                                                             nullptr, ratio);
   }
 

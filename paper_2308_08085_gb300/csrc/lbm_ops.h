@@ -25,7 +25,6 @@ struct InstDesc {
   const int32_t* nbr;
   const int32_t* child0;
   const uint64_t* cellmask;
-  size_t stride;                    // capacity * M
   double omega[BATCH_MAX_LEVELS];   // 1 / tau_L
   double r_cf[BATCH_MAX_LEVELS];    // tau_{L+1} / (2 tau_L)
   double r_fc[BATCH_MAX_LEVELS];    // 2 tau_L / tau_{L+1}
@@ -87,7 +86,6 @@ struct Exchange {
 };
 
 struct StepParams {
-  size_t stride;        // elements between population planes (capacity * M)
   double omega;         // 1 / tau_L
   int variant;          // collide-stream kernel variant (amr_config.kernel_variant)
   FaceParams faces;
@@ -119,7 +117,7 @@ struct LbmOps {
   // instead of being scattered into the stored form).  With bit 0, `parent`
   // and `marks` (> 0: refined in this adaptation) tell new blocks from old.
   void (*interp)(cudaStream_t, const int32_t* list, int n, const void* fpar, void* fch,
-                 size_t stride, const int32_t* child0, const uint64_t* cellmask,
+                 const int32_t* child0, const uint64_t* cellmask,
                  const int32_t* nbr, const uint64_t* solidmask, const int32_t* parent,
                  const int8_t* marks, double ratio, int mode, bool solid);
   // fine-to-coarse averaging: by_parent -- `list` holds parents, all their
@@ -127,19 +125,18 @@ struct LbmOps {
   // fine level) and parent[] leads to their parents.  mode 0: parent cells
   // over interface children, 1: over every non-ghost child (refined parents)
   void (*average)(cudaStream_t, const int32_t* list, int n, bool by_parent, void* fpar,
-                  const void* fch, size_t stride, const int32_t* child0, const int32_t* parent,
+                  const void* fch, const int32_t* child0, const int32_t* parent,
                   const uint64_t* cellmask, const int32_t* status, const int32_t* nbr,
                   const uint64_t* solidmask, double ratio, int mode_sync, bool solid);
   // the averaging of the level step over (block << 3 | group) items: the
   // groups of 2^D interface cells of the fine level's boundary blocks, each
   // into its parent cell (the work of average mode 0, listed in advance)
   void (*average_groups)(cudaStream_t, const int32_t* items, int n, void* fpar, const void* fch,
-                         size_t stride, const int32_t* child0, const int32_t* parent,
+                         const int32_t* child0, const int32_t* parent,
                          const int32_t* nbr, const uint64_t* solidmask, double ratio,
                          bool solid);
   // vorticity criterion marks (+1/-1/0) and block max |w|^2
-  void (*criterion)(cudaStream_t, const int32_t* list, int n, const void* f, size_t stride,
-                    const int32_t* nbr, const uint64_t* solidmask, const int32_t* status,
+  void (*criterion)(cudaStream_t, const int32_t* list, int n, const void* f, const int32_t* nbr, const uint64_t* solidmask, const int32_t* status,
                     int level, int lmax, double inv_dx, int n_start, int n_inc, int8_t* marks,
                     double* w2out);
   // exports / imports of the blocks b0 .. b0+nb-1; the buffer of block b is
@@ -161,8 +158,7 @@ struct LbmOps {
                       const uint64_t* solidmask, double* partial);
   // momentum-exchange force (Section 5.3) partial sums [grid][3] over the
   // leaves in `list` (one level, buffer f); returns the grid size used
-  int (*force_partial)(cudaStream_t, const int32_t* list, int n, const void* f, size_t stride,
-                       const int32_t* nbr, const int32_t* status, const uint64_t* solidmask,
+  int (*force_partial)(cudaStream_t, const int32_t* list, int n, const void* f, const int32_t* nbr, const int32_t* status, const uint64_t* solidmask,
                        double omega, double dx, double* partial);
   // batched instances: one launch over an instance-major list of work items;
   // buffer A / B choice per launch (every instance of a batch shares parities)
@@ -178,8 +174,7 @@ struct LbmOps {
   int (*persistent_ctas)(int threads);
   void (*batch_persistent)(cudaStream_t, const PersistArgs& a, int threads, int ctas);
   // 27 block summaries of the learned refinement proposal (3D only)
-  void (*features)(cudaStream_t, const int32_t* list, int n, const void* f, size_t stride,
-                   const int32_t* nbr, const uint64_t* solidmask, int level, int lmax,
+  void (*features)(cudaStream_t, const int32_t* list, int n, const void* f, const int32_t* nbr, const uint64_t* solidmask, int level, int lmax,
                    double inv_dx, float* out);
   // adaptation, before the children of the coarsen-marked blocks in `list`
   // are removed: a same-level neighbour that stays takes back, into its own
@@ -187,7 +182,7 @@ struct LbmOps {
   void (*coarsen_fixup)(cudaStream_t, const int32_t* list, int n, const int32_t* child0,
                         const int32_t* parent, const int8_t* marks, const int32_t* nbr,
                         const uint64_t* solidmask, const int32_t* level, void* fa, void* fb,
-                        unsigned cur, size_t stride);
+                        unsigned cur);
 };
 
 const LbmOps* lbm_ops_d2q9(int storage);

@@ -65,7 +65,6 @@ __global__ void __launch_bounds__(kThreads)
                   const uint64_t* __restrict__ solidmask, double* __restrict__ partials) {
   using R = typename Store<T>::R;
   constexpr int M = Block<D>::M;
-  const size_t stride = (size_t)n_blocks * M;
   const int64_t first = (int64_t)blockIdx.x * kBlocksPerCta * M;
   const int64_t last = min((int64_t)(blockIdx.x + 1) * kBlocksPerCta, n_blocks) * M;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -75,7 +74,7 @@ __global__ void __launch_bounds__(kThreads)
     const int L = level[b];
     const T* f = ((cur >> L) & 1u) ? fb : fa;
     R fl[Q];
-    gather_cell<D, Q, T, true>(fl, f, stride, (int)b, (int)(g % M), nbr + (size_t)b * NBR_STRIDE,
+    gather_cell<D, Q, T, true>(fl, f, (int)b, (int)(g % M), nbr + (size_t)b * NBR_STRIDE,
                                solidmask);
     double r = 0, jx = 0, jy = 0, jz = 0;
     static_for<0, Q>([&](auto P) {

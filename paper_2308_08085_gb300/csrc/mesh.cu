@@ -185,6 +185,10 @@ static int compact(Instance* a, int64_t n, Pred pred, Val val, int32_t* out, int
     return AMR_OK;
   }
   const int nb = (int)((n + 255) / 256);
+  if (nb > cta_slots(a->cap)) {
+    set_error("compaction of " + std::to_string(n) + " items exceeds its count array");
+    return AMR_E_INVAL;
+  }
   k_count<<<nb, 256, 0, s>>>((int)n, pred, a->cta);
   k_scan<<<1, 1024, 0, s>>>(nb, a->cta, a->dcount + slot);
   if (scatter) k_scatter<<<nb, 256, 0, s>>>((int)n, pred, val, a->cta, out);
@@ -780,7 +784,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
     // values stored in the removed children for their staying neighbours go
     // back to those neighbours (the neighbour rows still hold the old links)
     a->ops->coarsen_fixup(s, C, (int)nC, a->child0, a->parent, a->marks, a->nbr, a->sm(),
-                          a->level, a->f[0], a->f[1], a->cur, a->stride());
+                          a->level, a->f[0], a->f[1], a->cur);
     a->launches += 1;
     k_remove_children<D><<<blocks_for(nC * NC), 256, 0, s>>>(C, (int)nC, a->child0, a->status,
                                                               a->level, a->parent, a->nbr,
@@ -845,8 +849,7 @@ static int adapt_t(Instance* a, amr_adapt_stats* st) {
       a->launches += 1;
     AMR_CUDA(cudaGetLastError());
     const double ratio = a->tau[L + 1] / (2.0 * a->tau[L]);
-    a->ops->interp(s, C + offR[L], (int)nRL[L], a->fbuf(L, 0), a->fbuf(L + 1, 0), a->stride(),
-                   a->child0, a->cellmask, a->nbr, a->sm(), a->parent, a->marks, ratio,
+    a->ops->interp(s, C + offR[L], (int)nRL[L], a->fbuf(L, 0), a->fbuf(L + 1, 0), a->child0, a->cellmask, a->nbr, a->sm(), a->parent, a->marks, ratio,
                    1 | a->interp_bits(), a->solid);
     a->launches += 1;
     AMR_CUDA(cudaGetLastError());

@@ -5,7 +5,8 @@ takes only caller-owned input and output pointers and keeps its partial sums
 in a static device array of the library.  This test builds the caller-owned
 inputs itself, independently of any instance's arena: the populations of an
 AMR instance (exported with amr_fields) are written into the library's
-stored form (each pre-collision f_p(x) in the slot of the cell x - c_p of
+stored form (block-major buffers [B][Q][M]; each pre-collision f_p(x) in
+the slot of the cell x - c_p of
 the same level, or in x's own opposite slot where x - c_p is not a cell of
 that level; 16-bit storages hold value - w_p) in two separate buffers with
 the unused entries of each filled with NaN, and a per-level buffer choice
@@ -97,9 +98,10 @@ def stored_form(f, nbr, level, vs):
 
 
 def encode(g, vs, storage):
-    """Device tensor of the stored values in `storage` and the values it
-    decodes to (16-bit storages hold value - w_p; the library decodes them in
-    FP32, value = float(h) + float(w_p), and sums in FP64)."""
+    """Device tensor of the stored values in `storage`, in the library's
+    block-major buffer order [B][Q][M], and the values it decodes to, [Q][B][M]
+    (16-bit storages hold value - w_p; the library decodes them in FP32,
+    value = float(h) + float(w_p), and sums in FP64)."""
     w = vs.w[:, None, None]
     if storage in ("bf16", "f16"):
         t = torch.from_numpy(g - w).to(TORCH_DTYPE[storage])
@@ -107,7 +109,7 @@ def encode(g, vs, storage):
     else:
         t = torch.from_numpy(g).to(TORCH_DTYPE[storage])
         dec = t.to(torch.float64).numpy()
-    return t.cuda().contiguous(), dec
+    return t.permute(1, 0, 2).contiguous().cuda(), dec
 
 
 def leaf_sums(dec, nbr, level, status, vs):
@@ -170,7 +172,7 @@ def test_noalloc_audit_on_two_calls(lib, dim, storage):
         cur = 0xFFFFFFFF if call == 0 else 0b101
         nan = torch.full_like(t, float("nan"))
         lev = torch.from_numpy(level).cuda()
-        from_b = (((cur >> lev.clamp(min=0)) & 1) == 1)[None, :, None]
+        from_b = (((cur >> lev.clamp(min=0)) & 1) == 1)[:, None, None]
         fb = torch.where(from_b, t, nan).contiguous()
         fa = torch.where(from_b, nan, t).contiguous()
         level_t = torch.from_numpy(level.astype(np.int32)).cuda()
