@@ -935,13 +935,14 @@ def run_adapt_sweep(args):
 def run_batched(args):
     """64 independent 3D cavities (D3Q19 FP32) with seeded uneven sizes (32^3 to
     64^3 root cells), depths (0 to 3 extra levels) and Reynolds numbers
-    (uniform in [100, 3200]).  Members that are BGK-unstable after the warm-up
-    (tau_0 close to 1/2 on the coarsest grids) are taken out before anything
-    is timed and listed.  The autotuner times the graph form (one launch per
-    level operation, CUDA graph) and the persistent form (one launch per call,
-    M_L x threads); the best of each form is timed over the same periods with
-    the per-member adaptations between them, and compared with the same
-    members advanced one by one.  Per-member relative L2 of rho and u after
+    (uniform in [100, 3200]).  Members that become BGK-unstable (tau_0 close
+    to 1/2 on the coarsest grids) within a screening run as long as the
+    measurement are left out before anything is timed, and listed.  The autotuner times the graph form (one launch per
+    level operation, CUDA graph), the persistent form (one launch per call,
+    M_L x threads) and the member-graph form (the members' own coarse steps
+    as branches of one graph); the best of each form is timed over the same
+    periods with the per-member adaptations between them, and compared with
+    the same members advanced one by one.  Per-member relative L2 of rho and u after
     one period, batched against the same members advanced one by one from the
     same state (plain FP32 runs), on every 8th member."""
     import numpy as np
@@ -953,14 +954,6 @@ def run_batched(args):
     stream = torch.cuda.current_stream(dev)
     n = args.batch_n
     cfgs = W.batched_cavities(n, seed=0)
-    members = [AmrLBM(cfg, storage="f32") for cfg in cfgs]
-    batch = AmrBatch(members)
-    cap_err = 0
-    for _ in range(args.warmup):
-        batch.step(PERIOD)
-        for m in members:
-            cap_err += m.adapt()[0] != 0
-        batch.refresh()
 
     def stable(m):
         try:
@@ -968,17 +961,33 @@ def run_batched(args):
         except Exception:
             return False
 
+    # screening: every member for as many coarse steps as the measurement
+    # below takes (warm-up, autotuning, three timed forms, sequential, L2),
+    # untimed; members that become BGK-unstable are left out
+    screen_periods = args.warmup + 2 + 4 * args.steps + 2
+    members = [AmrLBM(cfg, storage="f32") for cfg in cfgs]
+    batch = AmrBatch(members)
+    for _ in range(screen_periods):
+        batch.step(PERIOD)
+        for m in members:
+            m.adapt()
+        batch.refresh()
     keep = [i for i, m in enumerate(members) if stable(m)]
+    batch.close()
+    for m in members:
+        m.close()
+    torch.cuda.empty_cache()
     excluded = [{"member": i, "n": cfgs[i]["nx"],
                  "re": round(0.05 * cfgs[i]["nx"] / cfgs[i]["nu0"], 1),
                  "tau0": round(3.0 * cfgs[i]["nu0"] + 0.5, 5)} for i in range(n) if i not in keep]
-    if len(keep) < n:
-        batch.close()
-        for i in range(n):
-            if i not in keep:
-                members[i].close()
-        members = [members[i] for i in keep]
-        batch = AmrBatch(members)
+    members = [AmrLBM(cfgs[i], storage="f32") for i in keep]
+    batch = AmrBatch(members)
+    cap_err = 0
+    for _ in range(args.warmup):
+        batch.step(PERIOD)
+        for m in members:
+            cap_err += m.adapt()[0] != 0
+        batch.refresh()
     # both forms tuned on the refined meshes; it advances the members
     chosen, times = batch.autotune(trial_steps=2)
     for m in members:
@@ -995,7 +1004,7 @@ def run_batched(args):
             best[form] = ((form, t, ml), ms)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     timed = {}
-    for form in ("graph", "persistent"):
+    for form in ("graph", "persistent", "members"):
         (f, t, ml), _ = best[form]
         batch.configure(f, t, ml)
         tb = ta = 0.0
@@ -1052,22 +1061,25 @@ def run_batched(args):
         del want
     unstable_end = sum(0 if stable(m) else 1 for m in members)
     blocks = [sum(m.counts()["n_ids"]) for m in members]
-    win = "persistent" if timed["persistent"]["mlups_step"] > timed["graph"]["mlups_step"] \
-        else "graph"
+    win = max(timed, key=lambda k: timed[k]["mlups_step"])
     out = {"workload": "%d 3D lid-driven cavities D3Q19 FP32, root 32^3..64^3, 0..3 extra "
                        "levels, Re uniform in [100, 3200] (seed 0), lid 0.05" % n,
            "members_timed": len(members),
-           "excluded_unstable_after_warmup": excluded,
+           "excluded_unstable_in_screening": excluded,
+           "screening_coarse_steps": screen_periods * PERIOD,
            "autotuned": chosen,
            "autotune_ms_per_coarse_step": {"%s/%d threads/M_L %d" % k: round(v, 3)
                                            for k, v in sorted(times.items())},
            "blocks_min_max_total": [min(blocks), max(blocks), sum(blocks)],
            "graph_form": timed["graph"], "persistent_form": timed["persistent"],
+           "member_graph_form": timed["members"],
            "sequential_mlups_step": seq,
            "launches_per_period_sequential": launches_s / args.steps,
            "faster_form": win,
            "persistent_over_graph": round(timed["persistent"]["mlups_step"] /
                                           timed["graph"]["mlups_step"], 3),
+           "members_over_graph": round(timed["members"]["mlups_step"] /
+                                       timed["graph"]["mlups_step"], 3),
            "speedup_step_over_sequential": round(timed[win]["mlups_step"] / seq, 3),
            "per_member_rel_l2_rho_u_vs_individual_fp32":
                {"members": sample, "max": max(l2), "median": float(np.median(l2))},

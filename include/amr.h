@@ -452,6 +452,10 @@ int amr_propose_marks(amr_t* a, const void* params_half, float threshold, int wi
  *                       second of clock64 cycles): when one gives up, the
  *                       launch stops, every member's wait flag is raised, and
  *                       amr_batch_sync returns AMR_E_TIMEOUT.
+ * AMR_BATCH_MEMBERS     one CUDA graph per coarse step whose independent
+ *                       branches are the members' own coarse steps (the
+ *                       per-instance kernels of amr_step), so that the small
+ *                       levels of different members run side by side.
  *
  * The paper runs one forest per GPU; batching is this library's extension.
  * Members keep their own arenas; the batch arena holds the instance
@@ -476,14 +480,16 @@ int amr_propose_marks(amr_t* a, const void* params_half, float threshold, int wi
  *   blocks per collide-stream tile (an interpolation or averaging tile holds
  *   threads / 4^D parents or children), ctas = CTAs launched (0: as many as
  *   stay resident together; the queue needs no co-residency).
+ *   Member-graph form: threads, tile_blocks and ctas are ignored.
  * amr_batch_get_config: the current form; in the graph form tile_blocks is
- *   threads / 4^D and ctas is 0.
+ *   threads / 4^D and ctas is 0; in the member-graph form all three are 0.
  * amr_batch_autotune: time `trial_steps` coarse steps of each candidate
  *   (forms: bit 0 the graph form with 512, 256, 128, 64 threads; bit 1 the
  *   persistent form with M_L = 1, 2, 4, 8 x threads 64, 128, 256, resident
- *   CTAs), keep the fastest and write it to *chosen (may be NULL).  ms_out
- *   (NULL, or 16 floats) receives milliseconds per coarse step in that
- *   candidate order, -1 for a candidate not timed.  The members advance.
+ *   CTAs; bit 2 the member-graph form), keep the fastest and write it to
+ *   *chosen (may be NULL).  ms_out (NULL, or 17 floats) receives
+ *   milliseconds per coarse step in that candidate order, -1 for a
+ *   candidate not timed.  The members advance.
  *   Synchronous.
  * amr_batch_sync: wait for the batch's stream; AMR_E_TIMEOUT (once) if a
  *   bounded wait of the persistent form gave up since the last call.
@@ -497,9 +503,10 @@ int amr_propose_marks(amr_t* a, const void* params_half, float threshold, int wi
  * Errors: AMR_E_INVAL, AMR_E_ARENA, AMR_E_CUDA, AMR_E_TIMEOUT. */
 #define AMR_BATCH_GRAPH 0
 #define AMR_BATCH_PERSISTENT 1
+#define AMR_BATCH_MEMBERS 2
 typedef struct amr_batch_t amr_batch_t;
 typedef struct {
-  int32_t mode;         /* AMR_BATCH_GRAPH or AMR_BATCH_PERSISTENT */
+  int32_t mode;         /* AMR_BATCH_GRAPH, _PERSISTENT or _MEMBERS */
   int32_t threads;      /* threads per CTA                          */
   int32_t tile_blocks;  /* M_L: blocks per collide-stream tile      */
   int32_t ctas;         /* persistent form: CTAs launched (0: all resident) */

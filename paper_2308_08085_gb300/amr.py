@@ -451,10 +451,13 @@ class AmrLBM:
             pass
 
 
-AMR_BATCH_GRAPH, AMR_BATCH_PERSISTENT = 0, 1
+AMR_BATCH_GRAPH, AMR_BATCH_PERSISTENT, AMR_BATCH_MEMBERS = 0, 1, 2
+BATCH_FORMS = {"graph": AMR_BATCH_GRAPH, "persistent": AMR_BATCH_PERSISTENT,
+               "members": AMR_BATCH_MEMBERS}
 # candidate order of amr_batch_autotune's ms_out
 BATCH_CANDIDATES = ([("graph", t, t // 64) for t in (512, 256, 128, 64)] +
-                    [("persistent", t, m) for m in (1, 2, 4, 8) for t in (64, 128, 256)])
+                    [("persistent", t, m) for m in (1, 2, 4, 8) for t in (64, 128, 256)] +
+                    [("members", 0, 0)])
 
 
 class AmrBatchConfig(ctypes.Structure):
@@ -462,8 +465,9 @@ class AmrBatchConfig(ctypes.Structure):
                 ("tile_blocks", ctypes.c_int32), ("ctas", ctypes.c_int32)]
 
     def as_dict(self):
-        return {"form": "persistent" if self.mode == AMR_BATCH_PERSISTENT else "graph",
-                "threads": self.threads, "tile_blocks": self.tile_blocks, "ctas": self.ctas}
+        form = {v: k for k, v in BATCH_FORMS.items()}[self.mode]
+        return {"form": form, "threads": self.threads, "tile_blocks": self.tile_blocks,
+                "ctas": self.ctas}
 
 
 class AmrBatch:
@@ -502,8 +506,7 @@ class AmrBatch:
             raise AmrError(rc, "amr_batch_step")
 
     def configure(self, form="graph", threads=512, tile_blocks=0, ctas=0):
-        mode = AMR_BATCH_PERSISTENT if form == "persistent" else AMR_BATCH_GRAPH
-        cfg = AmrBatchConfig(mode, int(threads), int(tile_blocks), int(ctas))
+        cfg = AmrBatchConfig(BATCH_FORMS[form], int(threads), int(tile_blocks), int(ctas))
         rc = self.lib.amr_batch_configure(self.h, ctypes.byref(cfg))
         if rc != AMR_OK:
             raise AmrError(rc, "amr_batch_configure")
@@ -515,10 +518,10 @@ class AmrBatch:
             raise AmrError(rc, "amr_batch_get_config")
         return cfg.as_dict()
 
-    def autotune(self, trial_steps=2, forms=("graph", "persistent")):
+    def autotune(self, trial_steps=2, forms=("graph", "persistent", "members")):
         """Times every candidate; returns (chosen config, {candidate: ms per
         coarse step}).  The members advance."""
-        bits = (1 if "graph" in forms else 0) | (2 if "persistent" in forms else 0)
+        bits = sum(1 << BATCH_FORMS[f] for f in forms)
         cfg = AmrBatchConfig()
         ms = (ctypes.c_float * len(BATCH_CANDIDATES))()
         rc = self.lib.amr_batch_autotune(self.h, int(trial_steps), bits, ctypes.byref(cfg), ms)

@@ -112,6 +112,10 @@ constexpr int kWaitFlagSlot = 16;
 // longest compaction, the averaging groups of every block (8 per block)
 inline int64_t cta_slots(int64_t cap) { return cap * 8 / 256 + 2; }
 
+// api.cu: one coarse step of `a` (its own fused kernels) launched into `s`
+// with the buffers of coarse-step parity `parity`; returns the launches
+int64_t coarse_step_into(Instance* a, cudaStream_t s, int parity);
+
 // check.cu: validate the instance's block tables, lists and averaging groups
 // (amr_check_tables); out3 as there
 int check_instance_tables(Instance* a, int64_t* out3);

@@ -365,6 +365,27 @@ static void advance(Instance* a, int L, bool first) {
   }
 }
 
+// One coarse step of instance a, launched into stream s (a branch of a batch
+// graph that holds every member's step; batch.cu) with the level buffers of
+// coarse-step parity `parity`; the instance's stream, buffer parities and
+// launch count are left as they were.  Returns the kernels launched.
+int64_t coarse_step_into(Instance* a, cudaStream_t s, int parity) {
+  const unsigned saved = a->cur;
+  cudaStream_t user = a->stream;
+  const int prof = a->profiling;
+  a->stream = s;
+  a->profiling = 0;
+  a->cur = (saved & ~1u) | (unsigned)parity;
+  const int64_t before = a->launches;
+  advance(a, 0, false);
+  const int64_t n = a->launches - before;
+  a->launches = before;
+  a->stream = user;
+  a->cur = saved;
+  a->profiling = prof;
+  return n;
+}
+
 static int drain_profile(Instance* a);
 
 static void destroy_graphs(Instance* a) {

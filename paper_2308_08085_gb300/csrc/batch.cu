@@ -6,7 +6,11 @@
 //    a CUDA graph (one per parity of level 0);
 //  * persistent: one launch per call advances every member by n coarse steps
 //    through a work queue of (step, phase, member, tile) items with
-//    per-member dependency counters (PersistArgs in lbm_ops.h).
+//    per-member dependency counters (PersistArgs in lbm_ops.h);
+//  * members: one CUDA graph per coarse step whose independent branches are
+//    the members' own coarse steps (their per-instance kernels, with the
+//    exchange fused into the parent level and the listed averaging), so that
+//    the small levels of different members run side by side.
 // The form and its tile shape are picked by timing the candidates on the
 // batch itself.
 #include <cuda_runtime.h>
@@ -50,6 +54,13 @@ struct Batch {
   uint32_t* d_done = nullptr;          // device [n_phase_cap][n], then the queue head
   unsigned long long* d_head = nullptr;
   int32_t* d_abort = nullptr;
+  // member-graph form
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t mgraph[2] = {nullptr, nullptr};
+  bool mgraph_valid = false;
+  int64_t mgraph_launches[2] = {0, 0};
 };
 
 // phases of one coarse step: 2^(lmax+1) - 3 (interpolation, collide-stream
@@ -127,6 +138,11 @@ static int refresh(Batch* b) {
   }
   b->graph_valid = false;
   b->plan_valid = false;
+  for (auto& g : b->mgraph) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+  b->mgraph_valid = false;
   return AMR_OK;
 }
 
@@ -336,6 +352,46 @@ static int launch_persistent(Batch* b, int n, int stall, long long limit) {
   return AMR_OK;
 }
 
+// ------------------------------------------------------------ member graphs
+static int build_member_graphs(Batch* b) {
+  if (b->branch.empty()) {
+    b->branch.assign(b->n, nullptr);
+    b->joins.assign(b->n, nullptr);
+    for (int i = 0; i < b->n; ++i) {
+      AMR_CUDA(cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking));
+      AMR_CUDA(cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming));
+    }
+    AMR_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  }
+  cudaStream_t cs = b->capture_stream;
+  for (int parity = 0; parity < 2; ++parity) {
+    cudaGraph_t g = nullptr;
+    int64_t launched = 0;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, cs);
+    for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+      e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+      if (e != cudaSuccess) break;
+      launched += coarse_step_into(b->inst[i], b->branch[i], parity);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaEventRecord(b->joins[i], b->branch[i]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, b->joins[i], 0);
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->mgraph[parity], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      set_error(std::string("member graph capture: ") + cudaGetErrorString(e));
+      cudaGetLastError();
+      return AMR_E_CUDA;
+    }
+    b->mgraph_launches[parity] = launched;
+  }
+  b->mgraph_valid = true;
+  return AMR_OK;
+}
+
 static int step_batch(Batch* b, int n) {
   for (Instance* a : b->inst)
     if (a->cur != b->cur) {
@@ -349,6 +405,24 @@ static int step_batch(Batch* b, int n) {
       a->cur = b->cur;
       a->coarse_steps += n;
     }
+    return AMR_OK;
+  }
+  if (b->mode == AMR_BATCH_MEMBERS) {
+    if (!b->mgraph_valid) {
+      const int rc = build_member_graphs(b);
+      if (rc != AMR_OK) return rc;
+    }
+    for (int s = 0; s < n; ++s) {
+      const int parity = (int)(b->cur & 1u);
+      AMR_CUDA(cudaGraphLaunch(b->mgraph[parity], b->stream));
+      b->launches += b->mgraph_launches[parity];
+      b->cur ^= 1u;
+    }
+    for (Instance* a : b->inst) {
+      a->cur = b->cur;
+      a->coarse_steps += n;
+    }
+    AMR_CUDA(cudaGetLastError());
     return AMR_OK;
   }
   if (!b->graph_valid) {
@@ -502,6 +576,11 @@ int amr_batch_configure(amr_batch_t* h, const amr_batch_config_t* cfg) {
     b->graph_valid = false;
     return AMR_OK;
   }
+  if (cfg->mode == AMR_BATCH_MEMBERS) {
+    b->mode = AMR_BATCH_MEMBERS;
+    b->mgraph_valid = false;
+    return AMR_OK;
+  }
   if (cfg->mode != AMR_BATCH_PERSISTENT) {
     set_error("unknown batch mode");
     return AMR_E_INVAL;
@@ -530,25 +609,27 @@ int amr_batch_get_config(amr_batch_t* h, amr_batch_config_t* out) {
   Batch* b = reinterpret_cast<Batch*>(h);
   if (!b || !out) return AMR_E_INVAL;
   out->mode = b->mode;
-  out->threads = b->mode == AMR_BATCH_GRAPH ? b->variant : b->p_threads;
+  out->threads = b->mode == AMR_BATCH_GRAPH ? b->variant
+                                            : (b->mode == AMR_BATCH_PERSISTENT ? b->p_threads : 0);
   out->tile_blocks = b->mode == AMR_BATCH_GRAPH ? b->variant / (b->dim == 2 ? 16 : 64)
-                                                : b->p_tile;
-  out->ctas = b->mode == AMR_BATCH_GRAPH ? 0 : b->p_ctas;
+                                                : (b->mode == AMR_BATCH_PERSISTENT ? b->p_tile : 0);
+  out->ctas = b->mode == AMR_BATCH_PERSISTENT ? b->p_ctas : 0;
   return AMR_OK;
 }
 
 int amr_batch_autotune(amr_batch_t* h, int trial_steps, int forms, amr_batch_config_t* chosen,
                        float* ms_out) {
   Batch* b = reinterpret_cast<Batch*>(h);
-  if (!b || trial_steps < 1 || forms < 1 || forms > 3) return AMR_E_INVAL;
+  if (!b || trial_steps < 1 || forms < 1 || forms > 7) return AMR_E_INVAL;
   // candidates in the order of ms_out: the graph form with 512 / 256 / 128 /
   // 64 threads per CTA (M_L = 8 / 4 / 2 / 1 blocks per CTA in 3D), then the
   // persistent form with M_L = 1, 2, 4, 8 blocks per tile x 64, 128, 256
-  // threads per CTA
+  // threads per CTA, then the member-graph form
   std::vector<amr_batch_config_t> cand;
   for (int t : {512, 256, 128, 64}) cand.push_back({AMR_BATCH_GRAPH, t, 0, 0});
   for (int m : {1, 2, 4, 8})
     for (int t : {64, 128, 256}) cand.push_back({AMR_BATCH_PERSISTENT, t, m, 0});
+  cand.push_back({AMR_BATCH_MEMBERS, 0, 0, 0});
   amr_batch_config_t keep{};
   amr_batch_get_config(h, &keep);
   cudaEvent_t e0, e1;
@@ -559,7 +640,9 @@ int amr_batch_autotune(amr_batch_t* h, int trial_steps, int forms, amr_batch_con
   int rc = AMR_OK;
   for (size_t c = 0; c < cand.size() && rc == AMR_OK; ++c) {
     if (ms_out) ms_out[c] = -1.f;
-    const bool want = cand[c].mode == AMR_BATCH_GRAPH ? (forms & 1) : (forms & 2);
+    const bool want = cand[c].mode == AMR_BATCH_GRAPH        ? (forms & 1)
+                      : cand[c].mode == AMR_BATCH_PERSISTENT ? (forms & 2)
+                                                             : (forms & 4);
     if (!want) continue;
     rc = amr_batch_configure(h, &cand[c]);
     if (rc != AMR_OK) break;
@@ -634,6 +717,13 @@ int amr_batch_free(amr_batch_t* h) {
   if (!b) return AMR_E_INVAL;
   for (auto& g : b->graph)
     if (g) cudaGraphExecDestroy(g);
+  for (auto& g : b->mgraph)
+    if (g) cudaGraphExecDestroy(g);
+  for (cudaStream_t st : b->branch)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->joins)
+    if (ev) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   delete b;
   return AMR_OK;

@@ -1,7 +1,9 @@
 """Batched instances: several forests of different sizes and depths advanced
-together -- in the graph form (one launch per level operation) and in the
+together -- in the graph form (one launch per level operation), in the
 persistent form (one launch whose work queue walks the level order with
-per-member dependency counters) for several tile shapes -- must give the
+per-member dependency counters) for several tile shapes, and in the
+member-graph form (the members' own coarse steps as branches of one graph)
+-- must give the
 populations of the same forests advanced one by one: the same arithmetic per
 cell, compiled into different kernels, so equal up to the compiler's fused
 multiply-add choices (rounding-level differences).  One member of each form
@@ -70,7 +72,7 @@ def rel(a, b):
 
 
 FORMS = [("graph", 512, 0), ("graph", 64, 0), ("persistent", 64, 1), ("persistent", 128, 2),
-         ("persistent", 256, 8)]
+         ("persistent", 256, 8), ("members", 0, 0)]
 
 
 @pytest.mark.parametrize("storage", ["f32", "f64"])
@@ -119,16 +121,16 @@ def test_batch_member_matches_oracle_and_autotune():
     data = [seeded(c, 60 + i) for i, c in enumerate(cfgs)]
     members = [member(c, "f64", seq, f) for c, (_, seq, f) in zip(cfgs, data)]
     batch = AmrBatch(members)
-    # 16 candidates x (1 + 1) coarse steps, then one more
+    # 17 candidates x (1 + 1) coarse steps, then one more
     chosen, times = batch.autotune(trial_steps=1)
     assert sorted(times) == sorted(BATCH_CANDIDATES) and all(v > 0 for v in times.values())
-    assert chosen["form"] in ("graph", "persistent")
+    assert chosen["form"] in ("graph", "persistent", "members")
     assert (chosen["form"], chosen["threads"], chosen["tile_blocks"]) in times
     assert times[(chosen["form"], chosen["threads"], chosen["tile_blocks"])] == min(times.values())
     batch.step(1)
     batch.sync()
     ref = data[1][0]
-    ref.step(33)
+    ref.step(35)
     ref.sync()
     members[1].rho_u()
     ids = ref.mesh.active_ids()

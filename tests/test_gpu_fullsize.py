@@ -221,7 +221,9 @@ def test_batched_cavities_full_size_equal_individual_runs():
     every level, one period of 50 coarse steps advanced by the batch in the
     graph form, then one more in one persistent launch, equals the same
     instances advanced one by one, to rounding (the batched and the
-    per-instance kernels are compiled separately)."""
+    per-instance kernels are compiled separately), and a third period in the
+    member-graph form (the per-instance kernels as branches of one graph)
+    keeps it so."""
     from paper_2308_08085_gb300 import AMR_F, AmrBatch, AmrLBM
     cfgs = W.batched_cavities(64, seed=0)
 
@@ -258,6 +260,12 @@ def test_batched_cavities_full_size_equal_individual_runs():
     batch.configure("persistent", 128, 2)      # then 50 steps in one persistent launch
     batch.step(50)
     batch.sync()
+    for sim in single:
+        sim.step(50)
+    worst = compare()
+    assert worst <= 1e-6, worst
+    batch.configure("members")                 # then 50 in the member-graph form
+    batch.step(50)
     for sim in single:
         sim.step(50)
     worst = compare()
