@@ -1301,11 +1301,14 @@ def run_learned(args):
         torch.cuda.empty_cache()
 
     shadow_on = not args.learn_no_shadow
-    ev = {"plain_every_50": evaluate("plain", 50, shadow_on),
-          "plain_every_100": evaluate("plain", 100, shadow_on),
-          "plain_every_200": evaluate("plain", 200, shadow_on),
-          "learned_every_200": evaluate("learned", 200, shadow_on)}
-    fr = [ev["plain_every_%d" % p]["under_refined_leaf_fraction"] for p in (50, 100, 200)]
+    ev = {}
+    for mode in args.learn_modes.split(","):
+        if mode == "learned":
+            ev["learned_every_200"] = evaluate("learned", 200, shadow_on)
+        else:
+            ev["plain_every_%d" % int(mode)] = evaluate("plain", int(mode), shadow_on)
+    fr = [ev["plain_every_%d" % p]["under_refined_leaf_fraction"] for p in (50, 100, 200)
+          if "plain_every_%d" % p in ev]
     return {"workload": "learned refinement proposal, channel past a square prism D3Q27 FP32, "
                         "%dx%dx%d root, L_max %d, criterion N_start %d" % (
                             nx, int(64 * sc), int(64 * sc), args.cyl_levels,
@@ -1316,11 +1319,12 @@ def run_learned(args):
             "train_seconds": round(t_train, 3), "threshold": args.learn_threshold,
             "test": test, "capacity": args.cyl_cap,
             "capacity_errors_spin_up": int(cap_errors["spin"]),
-            "under_refinement_monotone_in_period": bool(fr[0] <= fr[1] <= fr[2]),
+            "under_refinement_monotone_in_period": bool(all(a <= b for a, b in zip(fr, fr[1:]))),
             "sample_every": every, "fp64_reference": fp64_ref, "evaluation": ev,
             "learned_speedup_over_plain_every_50": round(
                 ev["learned_every_200"]["mlups_incl_adapt"] /
-                ev["plain_every_50"]["mlups_incl_adapt"], 3)}
+                ev["plain_every_50"]["mlups_incl_adapt"], 3)
+            if "learned_every_200" in ev and "plain_every_50" in ev else None}
 
 
 # ----------------------------------------------------------- reference arm
@@ -1442,6 +1446,8 @@ def main():
     ap.add_argument("--learn-crit-start", type=int, default=-3)
     ap.add_argument("--learn-no-shadow", action="store_true")
     ap.add_argument("--learn-fp64-ref", action="store_true")
+    ap.add_argument("--learn-modes", default="50,100,200,learned",
+                    help="adaptation periods of the plain criterion, and 'learned'")
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--cyl-nx", type=int, default=256)
     ap.add_argument("--cyl-levels", type=int, default=5)

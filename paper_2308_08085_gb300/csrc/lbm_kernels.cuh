@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(128)
 // directions into the parent cell's slots.  No shared memory, no barrier,
 // every lane busy.
 template <int D, int Q, class T, bool SOLID>
-__global__ void __launch_bounds__(128, sizeof(typename Store<T>::R) == 4 ? 12 : 8)
+__global__ void __launch_bounds__(128, 8)
     k_average_groups(const int32_t* __restrict__ items, int n, T* __restrict__ fpar,
                      const T* __restrict__ fch, const int32_t* __restrict__ child0,
                      const int32_t* __restrict__ parent, const int32_t* __restrict__ nbr,
