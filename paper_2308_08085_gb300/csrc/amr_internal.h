@@ -48,7 +48,6 @@ struct Instance {
   // in space are advanced close together in time whatever their IDs
   int32_t* order = nullptr;
   int32_t* bnd = nullptr;          // [lmax][cap]: blocks with a NONE neighbour, tree order
-  int32_t* leaf = nullptr;         // [lmax][cap]: leaves, tree order
   int32_t* agrp = nullptr;         // [cap * N_c]: averaging groups (block << 3 | group) of
                                    // the boundary blocks, level L at agrp_off[L]
   int32_t* gap = nullptr;          // [cap]
@@ -77,14 +76,6 @@ struct Instance {
   unsigned cur = 0;                // bit L: current population buffer of level L
   double tau[AMR_MAX_LEVELS] = {};
   StepParams prm{};
-
-  // The averaging of level L+1 into level L runs on a side stream: only the
-  // exchanging parents of level L read what it writes (the pre-collision
-  // values of their cells over interface children), so the next
-  // collide-stream of level L's leaves overlaps it, and its parents wait.
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fine[AMR_MAX_LEVELS] = {}, ev_avg[AMR_MAX_LEVELS] = {};
-  bool avg_pending[AMR_MAX_LEVELS] = {};
 
   // CUDA graphs of one coarse step, one per parity of level 0
   cudaGraphExec_t graph[2] = {nullptr, nullptr};

@@ -141,7 +141,6 @@ static Layout layout_for(const amr_config* c) {
       (size_t)lmax * cap * 4,                  // 27 tree order of each level
       (size_t)lmax * cap * 4,                  // 28 blocks with a NONE neighbour, per level
       (size_t)cap * (c->dim == 2 ? 4 : 8) * 4, // 29 averaging groups, packed by level
-      (size_t)lmax * cap * 4,                  // 30 leaves, per level
   };
   size_t off = 0;
   int i = 0;
@@ -174,7 +173,7 @@ struct CheckpointHeader {
   int64_t n_gaps, coarse_steps;
   uint32_t cur, pad2_;
 };
-static const char kCheckpointTag[8] = {'A', 'M', 'R', 'C', 'K', 'P', 'T', '4'};
+static const char kCheckpointTag[8] = {'A', 'M', 'R', 'C', 'K', 'P', 'T', '3'};
 
 // ------------------------------------------------------------ profiling
 static const char* kPkNames[PK_COUNT] = {
@@ -287,47 +286,26 @@ static double ratio_fc(const Instance* a, int L) { return 2.0 * a->tau[L] / a->t
 // values the level step's interpolation left in their own output slots.
 // xchg: level L's exchanging parents interpolate into their children's ghost
 // cells (linear interpolation).
-static void collide_launch(Instance* a, int L, const int32_t* list, int64_t n, bool ghost_in,
-                           const Exchange* xchg) {
-  if (n == 0) return;
+static void collide_stream_level(Instance* a, int L, bool ghost_in, const Exchange* xchg) {
+  const int64_t n = a->n_active[L];
+  // the parity flips even without active blocks: graph replay and batches
+  // rely on level 0 flipping once and deeper levels an even number of times
+  if (n == 0) {
+    a->cur ^= 1u << L;
+    return;
+  }
   StepParams prm = a->prm;
   prm.omega = 1.0 / a->tau[L];
   double bytes = (double)n * a->M * 2.0 * a->q * a->elem;
   if (xchg) bytes += (double)a->n_ghost_cells[L] * a->q * a->elem;   // ghost cells written
-  ProfScope ps(a, PK_COLLIDE, bytes, (double)n * a->M);
-  a->ops->collide_stream(a->stream, list, (int)n, a->fbuf(L, 0), a->fbuf(L, 1), a->nbr, a->sm(),
-                         prm, a->solid,
-                         ghost_in ? a->cellmask : nullptr, xchg);
-  a->launches += 1;
-}
-
-// The collide-stream of level L.  When the averaging of level L+1 into L is
-// still running on the side stream, the leaves go first (they read nothing
-// it writes), then the exchanging parents, after it.
-static void collide_stream_level(Instance* a, int L, bool ghost_in, const Exchange* xchg) {
-  // the parity flips even without active blocks: graph replay and batches
-  // rely on level 0 flipping once and deeper levels an even number of times
-  if (a->n_active[L] > 0) {
-    if (a->avg_pending[L]) {
-      collide_launch(a, L, a->leaf + (size_t)L * a->cap, a->n_leaves[L], ghost_in, nullptr);
-      cudaStreamWaitEvent(a->stream, a->ev_avg[L], 0);
-      a->avg_pending[L] = false;
-      collide_launch(a, L, a->parents + (size_t)L * a->cap, a->n_parents[L], ghost_in, xchg);
-    } else {
-      collide_launch(a, L, a->active + (size_t)L * a->cap, a->n_active[L], ghost_in, xchg);
-    }
+  {
+    ProfScope ps(a, PK_COLLIDE, bytes, (double)n * a->M);
+    a->ops->collide_stream(a->stream, a->active + (size_t)L * a->cap, (int)n, a->fbuf(L, 0),
+                           a->fbuf(L, 1), a->nbr, a->sm(), prm, a->solid,
+                           ghost_in ? a->cellmask : nullptr, xchg);
+    a->launches += 1;
   }
   a->cur ^= 1u << L;
-}
-
-// Averagings still running on the side stream join the main stream (before
-// a graph capture ends, and at the end of every coarse step).
-static void join_averages(Instance* a) {
-  for (int L = 0; L < a->lmax; ++L)
-    if (a->avg_pending[L]) {
-      cudaStreamWaitEvent(a->stream, a->ev_avg[L], 0);
-      a->avg_pending[L] = false;
-    }
 }
 
 // Recursive level step (Section 4.1): interpolate into level L+1, collide and
@@ -368,34 +346,20 @@ static void advance(Instance* a, int L, bool first) {
       // algorithmic bytes: interface fine cells (read) and their parent
       // cells, one per 2^D children (written)
       const double cells = (double)a->n_iface_cells[L];
-      const double bytes = cells * (1.0 + 1.0 / a->nc) * a->q * a->elem;
+      ProfScope ps(a, PK_AVERAGE, cells * (1.0 + 1.0 / a->nc) * a->q * a->elem, cells);
       // cubic interpolation samples every cell of the parent, so with it the
       // parent cells over interior children are averaged as well (mode 1:
-      // every cell whose children are not ghosts), and the next level step's
-      // interpolation reads them; else only those over interface children
-      // are averaged (the groups of interface cells of the fine level's
-      // boundary blocks, listed at adaptation), on the side stream, and only
-      // the next collide-stream of level L's exchanging parents waits for it
-      if (cubic) {
-        ProfScope ps(a, PK_AVERAGE, bytes, cells);
+      // every cell whose children are not ghosts), else only those over
+      // interface children: the groups of interface cells of the fine
+      // level's boundary blocks, listed at adaptation
+      if (cubic)
         a->ops->average(a->stream, a->parents + (size_t)L * a->cap, (int)np, true,
                         a->fbuf(L, 0), a->fbuf(L + 1, 0), a->child0, a->parent,
                         a->cellmask, a->status, a->nbr, a->sm(), ratio_fc(a, L), 1, a->solid);
-      } else {
-        cudaEventRecord(a->ev_fine[L], a->stream);
-        cudaStreamWaitEvent(a->side, a->ev_fine[L], 0);
-        cudaStream_t main = a->stream;
-        a->stream = a->side;
-        {
-          ProfScope ps(a, PK_AVERAGE, bytes, cells);
-          a->ops->average_groups(a->stream, a->agrp + a->agrp_off[L + 1], (int)a->n_agrp[L + 1],
-                                 a->fbuf(L, 0), a->fbuf(L + 1, 0), a->child0,
-                                 a->parent, a->nbr, a->sm(), ratio_fc(a, L), a->solid);
-        }
-        a->stream = main;
-        cudaEventRecord(a->ev_avg[L], a->side);
-        a->avg_pending[L] = true;
-      }
+      else
+        a->ops->average_groups(a->stream, a->agrp + a->agrp_off[L + 1], (int)a->n_agrp[L + 1],
+                               a->fbuf(L, 0), a->fbuf(L + 1, 0), a->child0,
+                               a->parent, a->nbr, a->sm(), ratio_fc(a, L), a->solid);
       a->launches += 1;
     }
   }
@@ -414,7 +378,6 @@ int64_t coarse_step_into(Instance* a, cudaStream_t s, int parity) {
   a->cur = (saved & ~1u) | (unsigned)parity;
   const int64_t before = a->launches;
   advance(a, 0, false);
-  join_averages(a);
   const int64_t n = a->launches - before;
   a->launches = before;
   a->stream = user;
@@ -424,17 +387,6 @@ int64_t coarse_step_into(Instance* a, cudaStream_t s, int parity) {
 }
 
 static int drain_profile(Instance* a);
-
-static void release_streams(Handle* a) {
-  for (int L = 0; L < AMR_MAX_LEVELS; ++L) {
-    if (a->ev_fine[L]) cudaEventDestroy(a->ev_fine[L]);
-    if (a->ev_avg[L]) cudaEventDestroy(a->ev_avg[L]);
-    a->ev_fine[L] = a->ev_avg[L] = nullptr;
-  }
-  if (a->side) cudaStreamDestroy(a->side);
-  if (a->capture_stream) cudaStreamDestroy(a->capture_stream);
-  a->side = a->capture_stream = nullptr;
-}
 
 static void destroy_graphs(Instance* a) {
   // keep the sample of the last replayed coarse step before its events go
@@ -468,7 +420,6 @@ static int build_graphs(Handle* h) {
       h->capture_parity = parity;
       const int64_t before = h->launches;
       advance(h, 0, false);
-      join_averages(h);
       h->graph_launches[parity] = h->launches - before;
       h->launches = before;
       h->capturing = false;
@@ -687,7 +638,6 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
   a->order = (int32_t*)(base + L.off[i++]);
   a->bnd = (int32_t*)(base + L.off[i++]);
   a->agrp = (int32_t*)(base + L.off[i++]);
-  a->leaf = (int32_t*)(base + L.off[i++]);
 
   const double tau0 = 3.0 * cfg->nu0 + 0.5;
   for (int l = 0; l < a->lmax; ++l) a->tau[l] = 0.5 + std::ldexp(tau0 - 0.5, l);
@@ -726,21 +676,11 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
     }
   }
   int rc = AMR_OK;
-  if (cudaStreamCreateWithFlags(&a->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&a->side, cudaStreamNonBlocking) != cudaSuccess) {
-    set_error("cannot create the capture and side streams");
-    release_streams(a);
+  if (cudaStreamCreateWithFlags(&a->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    set_error("cannot create capture stream");
     delete a;
     return AMR_E_CUDA;
   }
-  for (int L = 0; L < AMR_MAX_LEVELS; ++L)
-    if (cudaEventCreateWithFlags(&a->ev_fine[L], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&a->ev_avg[L], cudaEventDisableTiming) != cudaSuccess) {
-      set_error("cannot create the averaging events");
-      release_streams(a);
-      delete a;
-      return AMR_E_CUDA;
-    }
   if (cudaMemcpyAsync(a->wall_code, codes, sizeof(codes), cudaMemcpyHostToDevice, a->stream) !=
       cudaSuccess) {
     set_error("wall code upload failed");
@@ -765,7 +705,7 @@ int amr_init(const amr_config* cfg, void* arena, size_t arena_bytes, void* strea
     rc = check_instance_tables(a, res);
   }
   if (rc != AMR_OK) {
-    release_streams(a);
+    cudaStreamDestroy(a->capture_stream);
     delete a;
     return rc;
   }
@@ -796,7 +736,6 @@ int amr_step(amr_t* h, int n) {
       a->cur ^= 1u;   // levels >= 1 flip an even number of times per coarse step
     } else {
       advance(a, 0, false);
-      join_averages(a);
     }
     a->coarse_steps += 1;
   }
@@ -1197,7 +1136,7 @@ int amr_free(amr_t* h) {
   drain_profile(a);
   destroy_graphs(a);
   for (auto e : a->event_pool) cudaEventDestroy(e);
-  release_streams(a);
+  if (a->capture_stream) cudaStreamDestroy(a->capture_stream);
   delete a;
   return AMR_OK;
 }

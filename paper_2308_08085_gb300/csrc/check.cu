@@ -156,11 +156,11 @@ int check_instance_tables(Instance* a, int64_t* out3) {
                     a->nbr, a->gap, a->n_gaps, dev);
     for (int L = 0; L < a->lmax; ++L) {
       const size_t off = (size_t)L * a->cap;
-      const int64_t lists[6] = {a->n_ids[L], a->n_active[L], a->n_parents[L], a->n_bnd[L],
-                                a->n_ids[L], a->n_leaves[L]};
-      const int32_t* ptr[6] = {a->idset + off, a->active + off, a->parents + off, a->bnd + off,
-                               a->order + off, a->leaf + off};
-      for (int j = 0; j < 6; ++j)
+      const int64_t lists[5] = {a->n_ids[L], a->n_active[L], a->n_parents[L], a->n_bnd[L],
+                                a->n_ids[L]};
+      const int32_t* ptr[5] = {a->idset + off, a->active + off, a->parents + off, a->bnd + off,
+                               a->order + off};
+      for (int j = 0; j < 5; ++j)
         if (lists[j] > 0)
           k_validate_list<<<blocks_of(lists[j]), 256, 0, s>>>(ptr[j], lists[j], L, a->nc, false,
                                                               a->cap, a->level, dev);

@@ -677,8 +677,7 @@ int mesh_refresh_lists(Instance* a) {
     PActive par{ord, a->status, a->child0, a->nonemask, a->nc, true};
     AMR_TRY(compact(a, n, act, VList{ord}, a->active + (size_t)L * a->cap, &a->n_active[L]));
     AMR_TRY(compact(a, n, par, VList{ord}, a->parents + (size_t)L * a->cap, &a->n_parents[L]));
-    AMR_TRY(compact(a, n, PLeaf{ord, a->status}, VList{ord}, a->leaf + (size_t)L * a->cap,
-                    &a->n_leaves[L]));
+    AMR_TRY(compact(a, n, PLeaf{ord, a->status}, VIdent{}, nullptr, &a->n_leaves[L], 0, false));
     AMR_TRY(compact(a, n, PNoneNbr{ord, a->nonemask}, VList{ord}, a->bnd + (size_t)L * a->cap,
                     &a->n_bnd[L]));
   }
