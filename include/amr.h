@@ -235,9 +235,15 @@ int amr_adapt(amr_t* a, const int8_t* dev_marks, amr_adapt_stats* out);
                            refinement proposal (3D only; after a sync; 0 for
                            blocks outside the mesh), see amr_propose_marks     */
 
-/* Copy field `what` into `dst` (device pointer if dst_on_device, else host).
+/* Copy field `what` into `dst` (device pointer if dst_on_device, else host):
+ * the populations and moments the recursive level step (Section 4.1) leaves,
+ * after the level synchronisation of Section 4.4 for AMR_RHO_U; the block
+ * tables, ID sets and gap stack of the forest (Sections 3.2-3.3); the cell
+ * classes (Section 3.4); the momentum-exchange force (Section 5.3).
  * dst == NULL returns the required bytes.  Returns bytes written or a
- * negative code (AMR_E_INVAL if dst_bytes is too small). */
+ * negative code (AMR_E_INVAL if dst_bytes is too small; AMR_E_TIMEOUT, for
+ * a host destination, when a bounded device wait gave up since the last
+ * synchronising call). */
 int64_t amr_fields(amr_t* a, int what, void* dst, size_t dst_bytes,
                    int dst_on_device);
 
