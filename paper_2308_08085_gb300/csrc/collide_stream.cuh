@@ -234,6 +234,40 @@ __device__ __forceinline__ void bgk(R (&f)[Q], R om, R& ux, R& uy, R& uz, R& usq
   });
 }
 
+// The BGK step on shifted populations g_p = f_p - w_p, as the 16-bit
+// storages hold them: rho = 1 + sum_p g_p and j = sum_p c_p g_p (the weights
+// have no first moment), and f_eq,p - w_p = w_p (rho - 1) + w_p rho (3 c.u +
+// 4.5 (c.u)^2 - 1.5 u^2), so the shift is neither added on load nor removed
+// on store.
+template <int D, int Q, class R>
+__device__ __forceinline__ void bgk_shifted(R (&g)[Q], R om) {
+  using V = VS<D, Q>;
+  R dr = 0, jx = 0, jy = 0, jz = 0;
+  static_for<0, Q>([&](auto P) {
+    constexpr int p = P;
+    constexpr int cx = V::cx[p], cy = V::cy[p], cz = V::cz[p];
+    dr += g[p];
+    if constexpr (cx != 0) jx += cx > 0 ? g[p] : -g[p];
+    if constexpr (cy != 0) jy += cy > 0 ? g[p] : -g[p];
+    if constexpr (cz != 0) jz += cz > 0 ? g[p] : -g[p];
+  });
+  const R rho = R(1) + dr;
+  const R inv = R(1) / rho;
+  const R ux = jx * inv, uy = jy * inv, uz = D == 3 ? jz * inv : R(0);
+  const R usq15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+  static_for<0, Q>([&](auto P) {
+    constexpr int p = P;
+    constexpr int cx = V::cx[p], cy = V::cy[p], cz = V::cz[p];
+    R cu = R(0);
+    if constexpr (cx != 0) cu += cx > 0 ? ux : -ux;
+    if constexpr (cy != 0) cu += cy > 0 ? uy : -uy;
+    if constexpr (cz != 0) cu += cz > 0 ? uz : -uz;
+    constexpr double wp = V::w[p];
+    const R geq = R(wp) * (dr + rho * (R(3) * cu + R(4.5) * cu * cu - usq15));
+    g[p] = g[p] + om * (geq - g[p]);
+  });
+}
+
 // Value stored in the own slot p of a cell whose link p leaves through wall
 // face `face` (Section 2 boundary equations): the moving-wall bounce-back
 // f* + bb, or the anti-bounce-back outlet value with the cell's velocity.
@@ -540,19 +574,24 @@ __global__ void __launch_bounds__(THREADS, (one_pass_min_blocks<T, Q, THREADS, D
       R f[Q];
       static_for<0, Q>([&](auto P) {
         constexpr int p = P;
-        if constexpr (p == 0) {
-          f[0] = S::template load<D, Q, 0>(gin[own]);
-        } else {
+        size_t at = own;
+        if constexpr (p != 0) {
           const int e = link_entry<D, Q, p>(g_src_geo<D, Q>, l);
-          f[p] = S::template load<D, Q, p>(
-              gin[(size_t)nb[e & 31] * (Q * M) + (size_t)p * M + (e >> 5)]);
+          at = (size_t)nb[e & 31] * (Q * M) + (size_t)p * M + (e >> 5);
         }
+        if constexpr (S::kShifted) f[p] = S::raw(gin[at]);
+        else f[p] = S::template load<D, Q, p>(gin[at]);
       });
-      R ux, uy, uz, usq15;
-      bgk<D, Q>(f, R(prm.omega), ux, uy, uz, usq15);
-      static_for<0, Q>([&](auto P) {
-        gout[own + (size_t)P * M] = S::template save<D, Q, P>(f[P]);
-      });
+      if constexpr (S::kShifted) {
+        bgk_shifted<D, Q>(f, R(prm.omega));
+        static_for<0, Q>([&](auto P) { gout[own + (size_t)P * M] = S::from_raw(f[P]); });
+      } else {
+        R ux, uy, uz, usq15;
+        bgk<D, Q>(f, R(prm.omega), ux, uy, uz, usq15);
+        static_for<0, Q>([&](auto P) {
+          gout[own + (size_t)P * M] = S::template save<D, Q, P>(f[P]);
+        });
+      }
     } else {
       if (flags & BF_OUTLET)
         step_cell_checked<D, Q, T, SOLID, true, GHOST_IN>(gin, gout, own, l, nb,

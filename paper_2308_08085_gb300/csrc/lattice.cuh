@@ -118,16 +118,21 @@ __device__ __forceinline__ int cell_class(uint32_t none_mask, int i, int j, int 
 template <class T> struct Store;
 template <> struct Store<double> {
   using R = double;
+  static constexpr bool kShifted = false;
   template <int D, int Q, int P> __device__ static R load(double v) { return v; }
   template <int D, int Q, int P> __device__ static double save(R v) { return v; }
 };
 template <> struct Store<float> {
   using R = float;
+  static constexpr bool kShifted = false;
   template <int D, int Q, int P> __device__ static R load(float v) { return v; }
   template <int D, int Q, int P> __device__ static float save(R v) { return v; }
 };
 template <> struct Store<__nv_bfloat16> {
   using R = float;
+  static constexpr bool kShifted = true;   // holds f - w_p
+  __device__ static R raw(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __device__ static __nv_bfloat16 from_raw(R v) { return __float2bfloat16_rn(v); }
   template <int D, int Q, int P> __device__ static R load(__nv_bfloat16 v) {
     constexpr float wp = float(VS<D, Q>::w[P]);
     return __bfloat162float(v) + wp;
@@ -139,6 +144,9 @@ template <> struct Store<__nv_bfloat16> {
 };
 template <> struct Store<__half> {
   using R = float;
+  static constexpr bool kShifted = true;   // holds f - w_p
+  __device__ static R raw(__half v) { return __half2float(v); }
+  __device__ static __half from_raw(R v) { return __float2half_rn(v); }
   template <int D, int Q, int P> __device__ static R load(__half v) {
     constexpr float wp = float(VS<D, Q>::w[P]);
     return __half2float(v) + wp;
