@@ -151,3 +151,24 @@ def test_root_ids_and_interp_validated_on_host(lib):
     for interp, ok in ((0, True), (3, True), (1, False), (2, False), (-1, False)):
         c.interp = interp
         assert (lib.amr_arena_bytes(ctypes.byref(c)) > 0) == ok, interp
+
+
+def test_batch_and_table_calls_reject_bad_arguments_on_the_host(lib):
+    """Argument checks that return before any device call."""
+    from paper_2308_08085_gb300.amr import AmrBatchConfig
+    assert ctypes.sizeof(AmrBatchConfig) == 16
+    out = (ctypes.c_int64 * 3)()
+    ptr = ctypes.c_void_p(16)                     # never dereferenced: rejected first
+    # dimension 5, a zero capacity, missing tables
+    assert lib.amr_validate_tables(5, 3, 64, ptr, ptr, ptr, ptr, ptr, None, 0, out, None) == -1
+    assert lib.amr_validate_tables(3, 3, 0, ptr, ptr, ptr, ptr, ptr, None, 0, out, None) == -1
+    assert lib.amr_validate_tables(3, 3, 64, None, ptr, ptr, ptr, ptr, None, 0, out, None) == -1
+    assert lib.amr_validate_tables(3, 3, 64, ptr, ptr, ptr, ptr, ptr, None, 4, out, None) == -1
+    assert lib.amr_check_tables(None, out) == -1
+    cfg = AmrBatchConfig(1, 128, 2, 0)
+    assert lib.amr_batch_configure(None, ctypes.byref(cfg)) == -1
+    assert lib.amr_batch_get_config(None, ctypes.byref(cfg)) == -1
+    assert lib.amr_batch_step(None, 1) == -1
+    assert lib.amr_batch_sync(None) == -1
+    assert lib.amr_batch_check_timeout(None, 1 << 20) == -1
+    assert lib.amr_batch_autotune(None, 1, 7, None, None) == -1
