@@ -43,7 +43,7 @@ PAPER_A100_MLUPS = 1753.0     # paper, 3D LDC D3Q19 FP32 64^3 L_max 4 on A100 (c
 # single-level 256^3 D3Q19 FP32 forest, and the hash of the kernel source it
 # was measured on.  A changed source reports null.
 NCU_TRAFFIC_PER_UPDATE = 152.2     # bytes (dram read + write) per cell update
-NCU_SOURCE_SHA = "d594ac91af7bde93"
+NCU_SOURCE_SHA = "408d1e3a376e2bc2"
 
 
 def kernel_source_sha():

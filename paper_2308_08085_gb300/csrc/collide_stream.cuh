@@ -234,11 +234,11 @@ __device__ __forceinline__ void bgk(R (&f)[Q], R om, R& ux, R& uy, R& uz, R& usq
   });
 }
 
-// The BGK step on shifted populations g_p = f_p - w_p, as the 16-bit
-// storages hold them: rho = 1 + sum_p g_p and j = sum_p c_p g_p (the weights
-// have no first moment), and f_eq,p - w_p = w_p (rho - 1) + w_p rho (3 c.u +
-// 4.5 (c.u)^2 - 1.5 u^2), so the shift is neither added on load nor removed
-// on store.
+// The BGK step (Section 2) on shifted populations g_p = f_p - w_p, as the
+// 16-bit storages hold them: rho = 1 + sum_p g_p and j = sum_p c_p g_p (the
+// weights have no first moment), and f_eq,p - w_p = w_p (rho - 1) + w_p rho
+// (3 c.u + 4.5 (c.u)^2 - 1.5 u^2), so the shift is neither added on load nor
+// removed on store.
 template <int D, int Q, class R>
 __device__ __forceinline__ void bgk_shifted(R (&g)[Q], R om) {
   using V = VS<D, Q>;
