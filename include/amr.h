@@ -528,6 +528,27 @@ int amr_batch_autotune(amr_batch_t* b, int trial_steps, int forms, amr_batch_con
                        float* ms_out);
 int amr_batch_sync(amr_batch_t* b);
 int amr_batch_check_timeout(amr_batch_t* b, long long limit_cycles);
+
+/* The persistent form's plan for members with the given counts, computed on
+ * the host (no device work; what amr_batch_step builds for the persistent
+ * form, for inspection and tests).  n members; lmax = the batch's level
+ * count (the largest member L_max); member_lmax[n]; n_ids, n_active,
+ * n_parents [n][lmax] (AMR_COUNTS per level: ID-set size, active blocks,
+ * exchanging parents; 0 beyond a member's levels); threads and tile_blocks
+ * as in amr_batch_configure; cur: the level buffer parities at the start of
+ * the coarse step.  Outputs, sized for max_phases phases: *n_phase;
+ * phases[4 k .. 4 k + 3] = kind (0 interpolation into level + 1,
+ * 1 collide-stream, 2 averaging of level + 1 into level), level, buffer of
+ * the level read (interpolation, collide-stream) or written (averaging),
+ * buffer of level + 1; tile_off[k (n + 1) + i] = first tile of member i in
+ * phase k, tile_off[k (n + 1) + n] = the phase's tiles; dep[k n + i] = 2 k'
+ * + wrap: the member's previous phase with tiles, wrap 1 when it lies in the
+ * previous coarse step.  AMR_E_INVAL on bad arguments or when the phases do
+ * not fit. */
+int amr_batch_plan(int dim, int n, int lmax, const int32_t* member_lmax, const int64_t* n_ids,
+                   const int64_t* n_active, const int64_t* n_parents, int threads,
+                   int tile_blocks, uint32_t cur, int max_phases, int32_t* n_phase,
+                   int32_t* phases, int32_t* tile_off, int32_t* dep);
 int64_t amr_batch_launches(amr_batch_t* b);
 int amr_batch_free(amr_batch_t* b);
 

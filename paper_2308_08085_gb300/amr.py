@@ -171,6 +171,9 @@ def load_library(path=LIB_PATH):
     lib.amr_batch_sync.restype = i32
     lib.amr_batch_check_timeout.argtypes = [vp, ctypes.c_longlong]
     lib.amr_batch_check_timeout.restype = i32
+    lib.amr_batch_plan.argtypes = [i32, i32, i32, vp, vp, vp, vp, i32, i32, ctypes.c_uint32, i32,
+                                   vp, vp, vp, vp]
+    lib.amr_batch_plan.restype = i32
     lib.amr_batch_launches.argtypes = [vp]
     lib.amr_batch_launches.restype = i64
     lib.amr_batch_free.argtypes = [vp]

@@ -208,75 +208,90 @@ struct PhaseRec {
   int op, level, which_in, which_ch;
 };
 
+// What the plan of the persistent form depends on: per member, its level
+// count and per-level counts ([n][lmax], 0 beyond the member's levels), the
+// batch's level count, the CTA and tile shape, the buffer parities.
+struct PlanCounts {
+  int dim = 3, n = 0, lmax = 0, threads = 128, tile = 2;
+  unsigned cur = 0;
+  std::vector<int> member_lmax;
+  std::vector<int64_t> n_ids, n_active, n_parents;
+  int64_t ids(int i, int L) const { return n_ids[(size_t)i * lmax + L]; }
+  int64_t act(int i, int L) const { return n_active[(size_t)i * lmax + L]; }
+  int64_t par(int i, int L) const { return n_parents[(size_t)i * lmax + L]; }
+  int64_t sum(int64_t (PlanCounts::*f)(int, int) const, int L) const {
+    int64_t t = 0;
+    for (int i = 0; i < n; ++i) t += (this->*f)(i, L);
+    return t;
+  }
+};
+
+struct HostPlan {
+  std::vector<PhaseRec> rec[2];           // steps starting with cur bit 0 clear / set
+  std::vector<int32_t> toff, ioff, dep;   // [phase][n + 1], [phase][n + 1], [phase][n]
+  int64_t tiles_per_step = 0, max_member_tiles = 0;
+};
+
 // The phases of one coarse step in the order of advance_batch.
-static void plan_rec(const Batch* b, int L, unsigned& cur, std::vector<PhaseRec>& out) {
-  const bool fine = L + 1 < b->lmax && b->n_ids[L + 1] > 0;
-  const int64_t np = b->n_par[L];
+static void plan_rec(const PlanCounts& c, int L, unsigned& cur, std::vector<PhaseRec>& out) {
+  const bool fine = L + 1 < c.lmax && c.sum(&PlanCounts::ids, L + 1) > 0;
+  const int64_t np = c.sum(&PlanCounts::par, L);
   const int wl = (int)((cur >> L) & 1u);
   if (fine && np > 0) out.push_back({PH_INTERP, L, wl, (int)((cur >> (L + 1)) & 1u)});
-  if (b->n_act[L] > 0) out.push_back({PH_COLLIDE, L, wl, 0});
+  if (c.sum(&PlanCounts::act, L) > 0) out.push_back({PH_COLLIDE, L, wl, 0});
   cur ^= 1u << L;
   if (fine) {
-    plan_rec(b, L + 1, cur, out);
-    plan_rec(b, L + 1, cur, out);
+    plan_rec(c, L + 1, cur, out);
+    plan_rec(c, L + 1, cur, out);
     if (np > 0)
       out.push_back({PH_AVERAGE, L, (int)((cur >> L) & 1u), (int)((cur >> (L + 1)) & 1u)});
   }
 }
 
-// Items of member a in a phase, and the tiles they make.
-static int64_t member_items(const Instance* a, const PhaseRec& r) {
-  if (r.level >= a->lmax) return 0;
-  return r.op == PH_COLLIDE ? a->n_active[r.level] : a->n_parents[r.level];
+// Items of member i in a phase, and the tiles they make: M_L blocks per
+// collide-stream tile, threads / 4^D parents per interpolation tile and
+// threads / 4^D children per averaging tile.
+static int64_t member_items(const PlanCounts& c, int i, const PhaseRec& r) {
+  if (r.level >= c.member_lmax[i]) return 0;
+  return r.op == PH_COLLIDE ? c.act(i, r.level) : c.par(i, r.level);
 }
 
-static int64_t member_tiles(const Batch* b, const Instance* a, const PhaseRec& r) {
-  const int64_t ni = member_items(a, r);
-  const int M = b->dim == 2 ? 16 : 64, NC = b->dim == 2 ? 4 : 8;
-  const int U = b->p_threads / M;
-  if (r.op == PH_COLLIDE) return (ni + b->p_tile - 1) / b->p_tile;
+static int64_t member_tiles(const PlanCounts& c, int i, const PhaseRec& r) {
+  const int64_t ni = member_items(c, i, r);
+  const int M = c.dim == 2 ? 16 : 64, NC = c.dim == 2 ? 4 : 8;
+  const int U = c.threads / M;
+  if (r.op == PH_COLLIDE) return (ni + c.tile - 1) / c.tile;
   if (r.op == PH_INTERP) return (ni + U - 1) / U;
   return (ni * NC + U - 1) / U;
 }
 
-static int build_plan(Batch* b) {
-  std::vector<PhaseRec> rec[2];
+static int make_plan(const PlanCounts& c, int max_phases, HostPlan* hp) {
   for (int parity = 0; parity < 2; ++parity) {
-    unsigned cur = (b->cur & ~1u) | (unsigned)parity;
-    plan_rec(b, 0, cur, rec[parity]);
+    unsigned cur = (c.cur & ~1u) | (unsigned)parity;
+    plan_rec(c, 0, cur, hp->rec[parity]);
   }
-  const int n = b->n;
-  const int np = (int)rec[0].size();
-  if (np == 0 || np > b->n_phase_cap || rec[1].size() != rec[0].size()) {
+  const int n = c.n;
+  const int np = (int)hp->rec[0].size();
+  if (np == 0 || np > max_phases || hp->rec[1].size() != hp->rec[0].size()) {
     set_error("persistent batch: unexpected phase list");
     return AMR_E_INVAL;
   }
-  std::vector<int32_t> toff((size_t)np * (n + 1)), ioff((size_t)np * (n + 1)), dep((size_t)np * n);
-  std::vector<PersistPhase> ph(2 * (size_t)np);
-  int64_t tile0 = 0, max_tiles = 0;
+  hp->toff.assign((size_t)np * (n + 1), 0);
+  hp->ioff.assign((size_t)np * (n + 1), 0);
+  hp->dep.assign((size_t)np * n, 0);
+  int64_t tile0 = 0;
   for (int k = 0; k < np; ++k) {
     int64_t t = 0, it = 0;
     for (int i = 0; i < n; ++i) {
-      toff[(size_t)k * (n + 1) + i] = (int32_t)t;
-      ioff[(size_t)k * (n + 1) + i] = (int32_t)it;
-      const int64_t ti = member_tiles(b, b->inst[i], rec[0][k]);
+      hp->toff[(size_t)k * (n + 1) + i] = (int32_t)t;
+      hp->ioff[(size_t)k * (n + 1) + i] = (int32_t)it;
+      const int64_t ti = member_tiles(c, i, hp->rec[0][k]);
       t += ti;
-      it += member_items(b->inst[i], rec[0][k]);
-      max_tiles = std::max(max_tiles, ti);
+      it += member_items(c, i, hp->rec[0][k]);
+      hp->max_member_tiles = std::max(hp->max_member_tiles, ti);
     }
-    toff[(size_t)k * (n + 1) + n] = (int32_t)t;
-    ioff[(size_t)k * (n + 1) + n] = (int32_t)it;
-    for (int parity = 0; parity < 2; ++parity) {
-      const PhaseRec& r = rec[parity][k];
-      PersistPhase& p = ph[(size_t)parity * np + k];
-      p.op = r.op;
-      p.level = r.level;
-      p.which_in = r.which_in;
-      p.which_ch = r.which_ch;
-      p.tile0 = (int32_t)tile0;
-      p.n_tiles = (int32_t)t;
-      p.items = r.op == PH_COLLIDE ? b->act[r.level] : b->par[r.level];
-    }
+    hp->toff[(size_t)k * (n + 1) + n] = (int32_t)t;
+    hp->ioff[(size_t)k * (n + 1) + n] = (int32_t)it;
     tile0 += t;
     if (tile0 >= (1ll << 30)) {
       set_error("persistent batch: more than 2^30 tiles per coarse step");
@@ -290,24 +305,69 @@ static int build_plan(Batch* b) {
       for (int back = 1; back <= np; ++back) {
         const int kk = k - back;
         const int kc = kk < 0 ? kk + np : kk;
-        if (toff[(size_t)kc * (n + 1) + i + 1] > toff[(size_t)kc * (n + 1) + i]) {
+        if (hp->toff[(size_t)kc * (n + 1) + i + 1] > hp->toff[(size_t)kc * (n + 1) + i]) {
           d = kc;
           wrap = kk < 0 ? 1 : 0;
           break;
         }
       }
-      dep[(size_t)k * n + i] = d < 0 ? 1 : 2 * d + wrap;   // no tiles at all: never waits
+      hp->dep[(size_t)k * n + i] = d < 0 ? 1 : 2 * d + wrap;   // no tiles at all: never waits
+    }
+  hp->tiles_per_step = tile0;
+  return AMR_OK;
+}
+
+static int build_plan(Batch* b) {
+  PlanCounts c;
+  c.dim = b->dim;
+  c.n = b->n;
+  c.lmax = b->lmax;
+  c.threads = b->p_threads;
+  c.tile = b->p_tile;
+  c.cur = b->cur;
+  c.member_lmax.resize(b->n);
+  c.n_ids.assign((size_t)b->n * b->lmax, 0);
+  c.n_active.assign((size_t)b->n * b->lmax, 0);
+  c.n_parents.assign((size_t)b->n * b->lmax, 0);
+  for (int i = 0; i < b->n; ++i) {
+    const Instance* a = b->inst[i];
+    c.member_lmax[i] = a->lmax;
+    for (int L = 0; L < a->lmax; ++L) {
+      c.n_ids[(size_t)i * b->lmax + L] = a->n_ids[L];
+      c.n_active[(size_t)i * b->lmax + L] = a->n_active[L];
+      c.n_parents[(size_t)i * b->lmax + L] = a->n_parents[L];
+    }
+  }
+  HostPlan hp;
+  const int rc = make_plan(c, b->n_phase_cap, &hp);
+  if (rc != AMR_OK) return rc;
+  const int np = (int)hp.rec[0].size();
+  std::vector<PersistPhase> ph(2 * (size_t)np);
+  for (int k = 0; k < np; ++k)
+    for (int parity = 0; parity < 2; ++parity) {
+      const PhaseRec& r = hp.rec[parity][k];
+      PersistPhase& p = ph[(size_t)parity * np + k];
+      p.op = r.op;
+      p.level = r.level;
+      p.which_in = r.which_in;
+      p.which_ch = r.which_ch;
+      p.tile0 = k == 0 ? 0 : ph[(size_t)parity * np + k - 1].tile0 +
+                                 ph[(size_t)parity * np + k - 1].n_tiles;
+      p.n_tiles = hp.toff[(size_t)k * (b->n + 1) + b->n];
+      p.items = r.op == PH_COLLIDE ? b->act[r.level] : b->par[r.level];
     }
   cudaStream_t s = b->stream;
   AMR_CUDA(cudaMemcpyAsync(b->d_phases, ph.data(), sizeof(PersistPhase) * ph.size(),
                            cudaMemcpyHostToDevice, s));
-  AMR_CUDA(cudaMemcpyAsync(b->d_tile_off, toff.data(), 4 * toff.size(), cudaMemcpyHostToDevice, s));
-  AMR_CUDA(cudaMemcpyAsync(b->d_item_off, ioff.data(), 4 * ioff.size(), cudaMemcpyHostToDevice, s));
-  AMR_CUDA(cudaMemcpyAsync(b->d_dep, dep.data(), 4 * dep.size(), cudaMemcpyHostToDevice, s));
+  AMR_CUDA(cudaMemcpyAsync(b->d_tile_off, hp.toff.data(), 4 * hp.toff.size(),
+                           cudaMemcpyHostToDevice, s));
+  AMR_CUDA(cudaMemcpyAsync(b->d_item_off, hp.ioff.data(), 4 * hp.ioff.size(),
+                           cudaMemcpyHostToDevice, s));
+  AMR_CUDA(cudaMemcpyAsync(b->d_dep, hp.dep.data(), 4 * hp.dep.size(), cudaMemcpyHostToDevice, s));
   AMR_CUDA(cudaStreamSynchronize(s));   // the host vectors go out of scope
   b->n_phase = np;
-  b->tiles_per_step = (int)tile0;
-  b->max_member_tiles = (int)max_tiles;
+  b->tiles_per_step = (int)hp.tiles_per_step;
+  b->max_member_tiles = (int)hp.max_member_tiles;
   b->plan_valid = true;
   return AMR_OK;
 }
@@ -705,6 +765,50 @@ int amr_batch_check_timeout(amr_batch_t* h, long long limit_cycles) {
   rc = launch_persistent(b, 1, 1, limit_cycles);
   if (rc != AMR_OK) return rc;
   return amr_batch_sync(h);
+}
+
+int amr_batch_plan(int dim, int n, int lmax, const int32_t* member_lmax, const int64_t* n_ids,
+                   const int64_t* n_active, const int64_t* n_parents, int threads,
+                   int tile_blocks, uint32_t cur, int max_phases, int32_t* n_phase,
+                   int32_t* phases, int32_t* tile_off, int32_t* dep) {
+  if ((dim != 2 && dim != 3) || n <= 0 || lmax < 1 || lmax > BATCH_MAX_LEVELS ||
+      (threads != 64 && threads != 128 && threads != 256) || tile_blocks < 1 ||
+      tile_blocks > PERSIST_MAX_TILE || max_phases < 1 || !member_lmax || !n_ids ||
+      !n_active || !n_parents || !n_phase || !phases || !tile_off || !dep) {
+    set_error("amr_batch_plan: bad arguments");
+    return AMR_E_INVAL;
+  }
+  PlanCounts c;
+  c.dim = dim;
+  c.n = n;
+  c.lmax = lmax;
+  c.threads = threads;
+  c.tile = tile_blocks;
+  c.cur = cur;
+  c.member_lmax.assign(member_lmax, member_lmax + n);
+  for (int i = 0; i < n; ++i)
+    if (c.member_lmax[i] < 1 || c.member_lmax[i] > lmax) {
+      set_error("amr_batch_plan: a member's level count is out of range");
+      return AMR_E_INVAL;
+    }
+  c.n_ids.assign(n_ids, n_ids + (size_t)n * lmax);
+  c.n_active.assign(n_active, n_active + (size_t)n * lmax);
+  c.n_parents.assign(n_parents, n_parents + (size_t)n * lmax);
+  HostPlan hp;
+  const int rc = make_plan(c, max_phases, &hp);
+  if (rc != AMR_OK) return rc;
+  const int np = (int)hp.rec[0].size();
+  *n_phase = np;
+  for (int k = 0; k < np; ++k) {
+    const PhaseRec& r = hp.rec[c.cur & 1u][k];
+    phases[4 * k] = r.op;
+    phases[4 * k + 1] = r.level;
+    phases[4 * k + 2] = r.which_in;
+    phases[4 * k + 3] = r.which_ch;
+  }
+  std::copy(hp.toff.begin(), hp.toff.end(), tile_off);
+  std::copy(hp.dep.begin(), hp.dep.end(), dep);
+  return AMR_OK;
 }
 
 int64_t amr_batch_launches(amr_batch_t* h) {
