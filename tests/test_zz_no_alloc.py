@@ -5,12 +5,11 @@ takes only caller-owned input and output pointers and keeps its partial sums
 in a static device array of the library.  This test builds the caller-owned
 inputs itself, independently of any instance's arena: the populations of an
 AMR instance (exported with amr_fields) are written into the library's
-stored form (block-major buffers [B][Q][M]; each pre-collision f_p(x) in
-the slot of the cell x - c_p of
-the same level, or in x's own opposite slot where x - c_p is not a cell of
-that level; 16-bit storages hold value - w_p) in two separate buffers with
-the unused entries of each filled with NaN, and a per-level buffer choice
-selects them.  The audit must equal an FP64 numpy sum of the same values
+stored form (block-major buffers [B][Q][M]; each pre-collision f_p(x) in the
+slot of the cell x - c_p of the same level, or in x's own opposite slot
+where x - c_p is not a cell of that level; 16-bit storages hold value - w_p)
+in two separate buffers with the unused entries of each filled with NaN, and
+a per-level buffer choice selects them.  The audit must equal an FP64 numpy sum of the same values
 over the leaf cells, and the instance's own audit (AMR_MASS), on two calls
 in a row with different states and buffer choices, within the FP64
 tolerance of the parity tests.  D3Q19 in FP64, FP32, BF16 and FP16 storage,
