@@ -1,6 +1,6 @@
 // Batched instances: many independent block forests advanced together.  The
 // recursive level step of Section 4.1 has the same shape for every instance
-// (an instance without level L+1 contributes no work there).  Two forms:
+// (an instance without level L+1 contributes no work there).  Three forms:
 //  * graph: each level operation is one launch over an instance-major list
 //    of (instance, block) items, and the batched coarse step is captured as
 //    a CUDA graph (one per parity of level 0);
@@ -43,9 +43,9 @@ struct Batch {
   int64_t launches = 0, graph_launches[2] = {0, 0};
   // persistent form
   int mode = AMR_BATCH_GRAPH;
-  int p_threads = 128, p_tile = 2, p_ctas_req = 0, p_ctas = 0;
+  int p_threads = 128, p_tile = 2, p_ctas = 0;
   long long wait_limit = 1ll << 31;
-  int n_phase_cap = 0, n_phase = 0, tiles_per_step = 0, max_member_tiles = 0;
+  int n_phase_cap = 0, n_phase = 0, tiles_per_step = 0;
   bool plan_valid = false;
   PersistPhase* d_phases = nullptr;    // device [2][n_phase_cap]
   int32_t* d_tile_off = nullptr;       // device [n_phase_cap][n + 1]
@@ -229,7 +229,7 @@ struct PlanCounts {
 struct HostPlan {
   std::vector<PhaseRec> rec[2];           // steps starting with cur bit 0 clear / set
   std::vector<int32_t> toff, ioff, dep;   // [phase][n + 1], [phase][n + 1], [phase][n]
-  int64_t tiles_per_step = 0, max_member_tiles = 0;
+  int64_t tiles_per_step = 0;
 };
 
 // The phases of one coarse step in the order of advance_batch.
@@ -285,10 +285,8 @@ static int make_plan(const PlanCounts& c, int max_phases, HostPlan* hp) {
     for (int i = 0; i < n; ++i) {
       hp->toff[(size_t)k * (n + 1) + i] = (int32_t)t;
       hp->ioff[(size_t)k * (n + 1) + i] = (int32_t)it;
-      const int64_t ti = member_tiles(c, i, hp->rec[0][k]);
-      t += ti;
+      t += member_tiles(c, i, hp->rec[0][k]);
       it += member_items(c, i, hp->rec[0][k]);
-      hp->max_member_tiles = std::max(hp->max_member_tiles, ti);
     }
     hp->toff[(size_t)k * (n + 1) + n] = (int32_t)t;
     hp->ioff[(size_t)k * (n + 1) + n] = (int32_t)it;
@@ -367,7 +365,6 @@ static int build_plan(Batch* b) {
   AMR_CUDA(cudaStreamSynchronize(s));   // the host vectors go out of scope
   b->n_phase = np;
   b->tiles_per_step = (int)hp.tiles_per_step;
-  b->max_member_tiles = (int)hp.max_member_tiles;
   b->plan_valid = true;
   return AMR_OK;
 }
@@ -659,7 +656,6 @@ int amr_batch_configure(amr_batch_t* h, const amr_batch_config_t* cfg) {
   b->mode = AMR_BATCH_PERSISTENT;
   b->p_threads = cfg->threads;
   b->p_tile = cfg->tile_blocks;
-  b->p_ctas_req = cfg->ctas;
   b->p_ctas = cfg->ctas > 0 ? cfg->ctas : resident;
   b->plan_valid = false;
   return AMR_OK;
